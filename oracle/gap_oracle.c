@@ -1,0 +1,716 @@
+/*
+ * gap_oracle.c -- plain FP64 CPU oracle for one time step of the 1D radiative
+ * particle-in-cell model of a pulsar polar-cap pair discharge
+ * (paper: "Pair Discharges and Radio Emission from Pulsar Magnetospheres").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file: only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two agree only because both follow
+ * the paper and the readings written down beside each function.
+ *
+ * Style: slow and literal.  One lepton at a time, in storage order; every
+ * formula is written as the paper states it in the code units below.
+ *
+ * Code units (Sect. 2.2, eq. ngj): length c/omega_p,co, time 1/omega_p,co,
+ * momentum u = gamma*beta (m_e c), density n_co, charge e n_co, current
+ * e n_co c, field m_e c omega_p / e.  Then the 1D Gauss and Ampere laws of
+ * Sect. 2.2 read  dE/dx = eta - eta_co  and  dE/dt = j_m - J,  with
+ * eta_co = -1 (aligned rotator: electrons fill the gap) and j_m = alpha j_co
+ * = -alpha.  Charges q/m = -1 (e-), +1 (e+).
+ *
+ * QED scales in code units: lambda_hat = (reduced Compton wavelength)/d_e,
+ * rho_hat = R_curv/d_e, r_g = lambda_C/b (from B_Q = m^2 c^3/(hbar e)).
+ *   lepton (Sect. 3.1, eq. chipm with sin(psi) -> gamma r_g/R_curv):
+ *     chi = gamma^2 lambda_hat/rho_hat,
+ *     d tau/dt = alpha_em gamma T_syn(chi)/rho_hat   (eq. tau_syn),
+ *     spectrum scale x_c = (3/2) gamma chi            (eq. xcurv).
+ *   photon (Sect. 3.2, eq. tau_bw; Sect. 6.1 for the accumulated angle):
+ *     sin(psi) = |sin(l/rho_hat)|, chi_x = x b sin(psi),
+ *     d tau/dt = (alpha_em/lambda_hat) b sin(psi) T_BW(chi_x).
+ *
+ * Parity status: every function below is pinned by tests/test_oracle_pins.py
+ * (closed forms, published test vectors, brute force or library routines),
+ * except the full discharge run as a whole, whose plotted curves are absent
+ * from the paper: "parity unpinned" for the discharge statistics; only the
+ * order-of-magnitude statements of Sect. 6.3 are checked there.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_ALPHA_EM 7.2973525693e-3 /* fine-structure constant (CODATA 2018) */
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11,  */
+/* "Parallel random numbers: as easy as 1, 2, 3"), written from its           */
+/* published definition: 10 rounds of a two-multiplier S-box with a Weyl key  */
+/* schedule.                                                                  */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform deviate in (0,1] for the draw keyed by (seed; id, step, channel, k).
+ * Counter = (id low word, id high word, step, channel<<16 | k); key = seed.
+ * 53 bits are taken from the first two output words (27 + 26 bits), so the
+ * value m in [0, 2^53) maps to (m + 1) 2^-53 and -ln(U) is always finite. */
+double orc_uniform(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
+                   uint32_t k) {
+  uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step,
+                     (channel << 16) | (k & 0xFFFFu)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  uint64_t m = ((uint64_t)(o[0] >> 5) << 26) | (uint64_t)(o[1] >> 6);
+  return ((double)m + 1.0) * 0x1.0p-53;
+}
+
+/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): golden-ratio
+ * increment followed by the two xor-shift-multiply rounds. */
+uint64_t orc_mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+#define ORC_PHOTON_BIT 0x8000000000000000ull
+/* Identity of a particle created by `parent` at `step` through `channel`,
+ * draw k: a pure function of its inputs, so it does not depend on the order
+ * in which new particles are appended.  Photons carry the top bit. */
+uint64_t orc_child_id(uint64_t parent, uint32_t step, uint32_t channel,
+                      uint32_t k) {
+  uint64_t salt = ((uint64_t)step << 32) | ((uint64_t)channel << 16) | (k & 0xFFFFu);
+  return orc_mix64(parent ^ orc_mix64(salt));
+}
+
+/* Draw channels (shared interface with the library; values only). */
+enum {
+  CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9
+};
+
+/* ------------------------------------------------------------------------- */
+/* QED rate functions                                                         */
+/* ------------------------------------------------------------------------- */
+/* Sect. 3.1: fit of the synchrotron emission function,
+ * T_syn(chi) = 5/(2 sqrt3) (1 + (16 sqrt3/5) chi + 1.1 chi^2)^(-1/6). */
+double orc_tsyn(double chi) {
+  const double a0 = 5.0 / (2.0 * sqrt(3.0));
+  const double a1 = 16.0 * sqrt(3.0) / 5.0;
+  return a0 * pow(1.0 + a1 * chi + 1.1 * chi * chi, -1.0 / 6.0);
+}
+
+/* Sect. 3.2: fit of the one-photon pair-creation function,
+ * T_BW(chi) = 0.23 exp(-8/(3 chi)) (1 + 0.22 chi)^(-1/3). */
+double orc_tbw(double chi) {
+  if (!(chi > 0.0)) return 0.0;
+  return 0.23 * exp(-8.0 / (3.0 * chi)) * pow(1.0 + 0.22 * chi, -1.0 / 3.0);
+}
+
+/* Classical curvature (synchrotron-shape) photon spectrum, the reading of
+ * the unspecified S(gamma,x) of Sect. 3.1: dN/dxi proportional to F(xi)/xi with
+ * F(xi) = xi int_xi^inf K_{5/3}(t) dt and xi = x/x_c.  Its survival function
+ *   S(xi) = P(xi' > xi) = int_xi^inf int_s^inf K_{5/3} dt ds / (5 pi/3)
+ * follows from K_nu(z) = int_0^inf exp(-z cosh t) cosh(nu t) dt by doing the
+ * two outer integrals in closed form:
+ *   S(xi) = 3/(5 pi) int_0^inf cosh(5t/3) exp(-xi cosh t) / cosh(t)^2 dt.
+ * The integrand is analytic in the strip |Im t| < pi/2, so the trapezoid rule
+ * with step h converges like exp(-pi^2/h); h = 1/8 gives exp(-79). */
+double orc_spec_survival(double xi) {
+  if (!(xi > 0.0)) return 1.0;
+  const double h = 0.125;
+  double sum = 0.0;
+  for (int k = 0;; ++k) {
+    double t = k * h;
+    double ch = cosh(t);
+    double arg = xi * ch;
+    if (arg > 745.0 || t > 700.0) break;
+    double f = cosh(5.0 * t / 3.0) * exp(-arg) / (ch * ch);
+    sum += (k == 0 ? 0.5 : 1.0) * f;
+  }
+  return 3.0 / (5.0 * M_PI) * h * sum;
+}
+
+/* S(xi) and dS/dxi = -3/(5 pi) int_0^inf cosh(5t/3) exp(-xi cosh t)/cosh t dt
+ * by the same trapezoid rule. */
+static void spec_survival_deriv(double xi, double *S, double *dS) {
+  const double h = 0.125;
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0;; ++k) {
+    double t = k * h;
+    double ch = cosh(t);
+    double arg = xi * ch;
+    if (arg > 745.0 || t > 700.0) break;
+    double f = cosh(5.0 * t / 3.0) * exp(-arg) / ch;
+    double wk = k == 0 ? 0.5 : 1.0;
+    s0 += wk * f / ch;
+    s1 += wk * f;
+  }
+  *S = 3.0 / (5.0 * M_PI) * h * s0;
+  *dS = -3.0 / (5.0 * M_PI) * h * s1;
+}
+
+/* Inverse of the survival function: the xi with S(xi) = U, U in (0,1].
+ * Newton iteration in y = ln(xi), safeguarded by the bracket [ln 1e-60,
+ * ln 800] on which S is strictly decreasing: a step that leaves the current
+ * bracket is replaced by bisection. */
+double orc_spec_inverse(double U) {
+  double lo = log(1e-60), hi = log(800.0);
+  if (orc_spec_survival(1e-60) <= U) return 1e-60;
+  double y = -log(U);
+  y = y > 1e-30 ? log(y) : lo;
+  if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    double xi = exp(y), S, dS;
+    spec_survival_deriv(xi, &S, &dS);
+    if (S > U) lo = y; else hi = y;
+    double step = (S - U) / (xi * dS);
+    double yn = y - step;
+    if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+    double d = fabs(yn - y);
+    y = yn;
+    if (d < 1e-14 || hi - lo < 1e-15) break;
+  }
+  return exp(y);
+}
+
+/* 1D Maxwell-Juttner deviate, f(u) proportional to exp(-(gamma-1)/theta), by
+ * the ratio-of-uniforms method (Kinderman & Monahan 1977): (a, v) uniform on
+ * (0,1] x [-bmax, bmax], u = v/a accepted when a^2 <= f(u).  bmax =
+ * sup |u| sqrt(f(u)), attained at u^2 = 2 theta gamma, gamma = theta +
+ * sqrt(theta^2+1).  Draws: channel CH_INIT_U, k = 2r, 2r+1 for round r. */
+double orc_mj_sample(uint64_t seed, uint64_t id, double theta, int *ok) {
+  double gs = theta + sqrt(theta * theta + 1.0);
+  double us = sqrt(2.0 * theta * gs);
+  double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
+  for (uint32_t r = 0; r < 64; ++r) {
+    double a = orc_uniform(seed, id, 0, CH_INIT_U, 2 * r);
+    double v = bmax * (2.0 * orc_uniform(seed, id, 0, CH_INIT_U, 2 * r + 1) - 1.0);
+    double u = v / a;
+    double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
+    if (2.0 * log(a) <= -gm1 / theta) { *ok = 1; return u; }
+  }
+  *ok = 0;
+  return 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* PIC model                                                                  */
+/* ------------------------------------------------------------------------- */
+enum { ORC_BC_SURFACE = 0, ORC_BC_PERIODIC = 1 };
+enum { ORC_INIT_EMPTY = 0, ORC_INIT_COLD = 1, ORC_INIT_PAIR_THERMAL = 2 };
+
+typedef struct {
+  double alpha;      /* j_m / j_co (Sect. 2.2) */
+  double b;          /* B / B_Q (Sect. 2.1) */
+  double lambda_hat; /* lambda_C / d_e */
+  double rho_hat;    /* R_curv / d_e */
+  double rate_mult;  /* multiplies both QED rates (macro-particle rescale, Sect. 6.1) */
+  double gap_length; /* H_gap in d_e; QED inhibited above it (Sect. 6.1) */
+  double density;    /* initial lepton density in n_co = |eta_co|/e */
+  double dx, dt;     /* grid spacing (d_e) and time step (1/omega_p) */
+  double theta;      /* temperature of the thermal loader (m_e c^2) */
+  double seed_amp;   /* Langmuir seed: relative density perturbation */
+  int64_t nx;        /* cells */
+  int64_t ppc;       /* macro-particles per cell per species at load */
+  uint64_t seed;     /* Philox key */
+  int32_t gap_index; /* enters the initial ids */
+  int32_t qed;       /* 0/1 */
+  int32_t boundary;  /* ORC_BC_* */
+  int32_t init;      /* ORC_INIT_* */
+  int32_t kmax_emit; /* emission events per lepton per step (sub-cycling cap) */
+  int32_t kmax_inject; /* injected electrons per step cap */
+} orc_params;
+
+typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
+typedef struct { uint64_t id; double X, x, w, tau_star, tau_acc; int32_t dir, n0, alive, pad; } orc_photon;
+
+/* Event counters and the energy ledger.  Energies are total energies (rest
+ * mass included: w gamma for leptons, w x for photons) per unit area in
+ * n_co m_e c^2 d_e, so that emission (gamma -> gamma - x + x), pair creation
+ * (x -> 2 (x/2)) and injection (rest energy w) are exact ledger moves. */
+typedef struct {
+  int64_t emit_events, photons, pairs, injected, absorbed, escaped,
+      photons_escaped, emit_overflow, inject_overflow, load_overflow;
+  double e_radiated, e_absorbed, e_escaped, e_photon_escaped, e_injected, work_jm;
+} orc_counters;
+
+typedef struct {
+  orc_params p;
+  int64_t nnode;       /* nodes holding E: nx+1 (surface) or nx (periodic) */
+  double *E, *D;       /* E on nodes; D = sum q w dF, the charge through each node */
+  double eta_bg;       /* Gauss background: eta_co = -1 (surface), mean load charge (periodic) */
+  double w0;           /* weight of a loaded / injected macro-particle */
+  orc_lepton *lep; int64_t nlep, caplep;
+  orc_photon *ph;  int64_t nph, capph;
+  int64_t step;
+  orc_counters cnt;
+} orc_sim;
+
+static double Fshape(double s) { /* fraction of the unit cloud right of a node */
+  double v = s + 0.5;
+  return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+}
+static int64_t imod(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
+
+static void push_lepton(orc_sim *s, orc_lepton L) {
+  if (s->nlep == s->caplep) {
+    s->caplep = s->caplep ? 2 * s->caplep : 1024;
+    s->lep = (orc_lepton *)realloc(s->lep, (size_t)s->caplep * sizeof(orc_lepton));
+  }
+  s->lep[s->nlep++] = L;
+}
+static void push_photon(orc_sim *s, orc_photon P) {
+  if (s->nph == s->capph) {
+    s->capph = s->capph ? 2 * s->capph : 1024;
+    s->ph = (orc_photon *)realloc(s->ph, (size_t)s->capph * sizeof(orc_photon));
+  }
+  s->ph[s->nph++] = P;
+}
+
+/* Initial identity of loaded particle j of cell c of species sp. */
+static uint64_t load_id(int32_t gap, int32_t sp, int64_t cell, int64_t ppc, int64_t j) {
+  return ((uint64_t)gap << 40) | ((uint64_t)sp << 39) | (uint64_t)(cell * ppc + j);
+}
+static uint64_t inject_root(int32_t gap) { return ((uint64_t)gap << 40) | (1ull << 38); }
+
+double orc_cell_charge(const orc_sim *s, int64_t c);
+
+/* Gauss's law (Sect. 2.2) on the grid: E_{c+1} - E_c = Q_c - eta_bg dx, with
+ * Q_c the cloud-in-cell charge of cell c (between nodes c and c+1).  Surface:
+ * E_0 = 0 (conductor).  Periodic: zero-mean E. */
+void orc_solve_gauss(orc_sim *s) {
+  const orc_params *p = &s->p;
+  double *Q = (double *)calloc((size_t)p->nx, sizeof(double));
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    int64_t c0 = (int64_t)floor(L->X - 0.5);
+    for (int64_t c = c0; c <= c0 + 1; ++c) {
+      double fr = Fshape(L->X - c) - Fshape(L->X - c - 1);
+      if (fr == 0.0) continue;
+      int64_t cc = c;
+      if (p->boundary == ORC_BC_PERIODIC) cc = imod(c, p->nx);
+      else if (c < 0 || c >= p->nx) continue;
+      Q[cc] += L->q * L->w * fr;
+    }
+  }
+  s->E[0] = 0.0;
+  int64_t last = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx;
+  for (int64_t c = 0; c < last; ++c) s->E[c + 1] = s->E[c] + Q[c] - s->eta_bg * p->dx;
+  if (p->boundary == ORC_BC_PERIODIC) {
+    double m = 0.0;
+    for (int64_t i = 0; i < s->nnode; ++i) m += s->E[i];
+    m /= (double)s->nnode;
+    for (int64_t i = 0; i < s->nnode; ++i) s->E[i] -= m;
+  }
+  free(Q);
+}
+
+orc_sim *orc_create(const orc_params *pin) {
+  orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+  s->p = *pin;
+  const orc_params *p = &s->p;
+  s->nnode = p->boundary == ORC_BC_PERIODIC ? p->nx : p->nx + 1;
+  s->E = (double *)calloc((size_t)s->nnode, sizeof(double));
+  s->D = (double *)calloc((size_t)s->nnode, sizeof(double));
+  s->w0 = p->ppc > 0 ? p->density * p->dx / (double)p->ppc : 0.0;
+  s->eta_bg = -1.0;
+  if (p->init == ORC_INIT_COLD) {
+    /* Cold electrons at rest, quiet start: X = c + (j + 1/2)/ppc. */
+    for (int64_t c = 0; c < p->nx; ++c)
+      for (int64_t j = 0; j < p->ppc; ++j) {
+        orc_lepton L = {0};
+        L.id = load_id(p->gap_index, 0, c, p->ppc, j);
+        L.X = (double)c + ((double)j + 0.5) / (double)p->ppc;
+        L.u = 0.0; L.w = s->w0; L.q = -1; L.alive = 1;
+        L.tau = -log(orc_uniform(p->seed, L.id, 0, CH_TAU0, 0));
+        push_lepton(s, L);
+      }
+  } else if (p->init == ORC_INIT_PAIR_THERMAL) {
+    /* e- and e+ at density/2 each, 1D Maxwell-Juttner momenta; the electrons
+     * are displaced by (A/k) sin(k X) with k = 2 pi / nx (cells): a Langmuir
+     * seed of relative density amplitude A. */
+    double w = 0.5 * p->density * p->dx / (double)p->ppc;
+    double k1 = 2.0 * M_PI / (double)p->nx;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int64_t c = 0; c < p->nx; ++c)
+        for (int64_t j = 0; j < p->ppc; ++j) {
+          orc_lepton L = {0};
+          L.id = load_id(p->gap_index, sp, c, p->ppc, j);
+          double X = (double)c + ((double)j + 0.5) / (double)p->ppc;
+          if (sp == 0 && p->seed_amp != 0.0) {
+            X += p->seed_amp / k1 * sin(k1 * X);
+            X = fmod(X, (double)p->nx);
+            if (X < 0.0) X += (double)p->nx;
+          }
+          int ok = 1;
+          L.X = X;
+          L.u = p->theta > 0.0 ? orc_mj_sample(p->seed, L.id, p->theta, &ok) : 0.0;
+          if (!ok) s->cnt.load_overflow++;
+          L.w = w; L.q = sp == 0 ? -1 : +1; L.alive = 1;
+          L.tau = -log(orc_uniform(p->seed, L.id, 0, CH_TAU0, 0));
+          push_lepton(s, L);
+        }
+    s->w0 = w;
+  }
+  if (p->boundary == ORC_BC_PERIODIC) {
+    double qt = 0.0;
+    for (int64_t i = 0; i < s->nlep; ++i) qt += s->lep[i].q * s->lep[i].w;
+    s->eta_bg = qt / ((double)p->nx * p->dx);
+  }
+  orc_solve_gauss(s);
+  return s;
+}
+
+void orc_destroy(orc_sim *s) {
+  if (!s) return;
+  free(s->E); free(s->D); free(s->lep); free(s->ph); free(s);
+}
+
+/* Append a test particle (tests build tiny hand-checkable states). */
+void orc_add_lepton(orc_sim *s, uint64_t id, int32_t q, double X, double u,
+                    double w, double tau) {
+  orc_lepton L = {0};
+  L.id = id; L.q = q; L.X = X; L.u = u; L.w = w; L.tau = tau; L.alive = 1;
+  push_lepton(s, L);
+}
+void orc_add_photon(orc_sim *s, uint64_t id, double X, double x, double w,
+                    int32_t dir, int32_t n0, double tau_star) {
+  orc_photon P = {0};
+  P.id = id | ORC_PHOTON_BIT; P.X = X; P.x = x; P.w = w; P.dir = dir; P.n0 = n0;
+  P.tau_star = tau_star; P.tau_acc = 0.0; P.alive = 1;
+  push_photon(s, P);
+}
+void orc_set_eta_bg(orc_sim *s, double eta) { s->eta_bg = eta; }
+void orc_set_E(orc_sim *s, const double *E) { memcpy(s->E, E, (size_t)s->nnode * sizeof(double)); }
+
+/* Deposit of one move X0 -> X1 (unwrapped): the charge through node i is
+ * q w [F(X1 - i) - F(X0 - i)], the change of the cloud fraction right of i
+ * (first-order shape; the ZigZag-type flux of Sect. 6.1 in 1D). */
+static void deposit(orc_sim *s, double q, double w, double X0, double X1) {
+  const orc_params *p = &s->p;
+  if (!isfinite(X0) || !isfinite(X1) || fabs(X1 - X0) > 1.0) abort(); /* never reached */
+  double lo = X0 < X1 ? X0 : X1, hi = X0 < X1 ? X1 : X0;
+  int64_t i0 = (int64_t)floor(lo - 0.5), i1 = (int64_t)floor(hi + 0.5);
+  for (int64_t i = i0; i <= i1; ++i) {
+    double dF = Fshape(X1 - (double)i) - Fshape(X0 - (double)i);
+    if (dF == 0.0) continue;
+    int64_t node = i;
+    if (p->boundary == ORC_BC_PERIODIC) node = imod(i, p->nx);
+    else if (i < 0 || i > p->nx) continue;
+    s->D[node] += q * w * dF;
+  }
+}
+
+/* Linear ("first-order", Sect. 6.1) gather of node E at X. */
+static double gather(const orc_sim *s, double X) {
+  const orc_params *p = &s->p;
+  double cf = floor(X);
+  double o = X - cf;
+  int64_t c = (int64_t)cf, c1 = c + 1;
+  if (p->boundary == ORC_BC_PERIODIC) { c = imod(c, p->nx); c1 = imod(c1, p->nx); }
+  return (1.0 - o) * s->E[c] + o * s->E[c1];
+}
+
+static int in_domain(const orc_params *p, double X) {
+  return X >= 0.0 && X < (double)p->nx;
+}
+static double wrap(const orc_params *p, double X) {
+  double L = (double)p->nx;
+  X = fmod(X, L);
+  if (X < 0.0) X += L;
+  if (X >= L) X -= L;
+  return X;
+}
+
+/* One time step n -> n+1.  Order (Sect. 6.1 PIC cycle, reduced to 1D along B):
+ *  1. every lepton: gather E^n, kick (Sect. 4: du/dt = (q/m) E), curvature
+ *     emission by optical-depth sub-cycling (eq. tau_syn, Sect. 6.1 MC
+ *     sub-cycling), drift, charge-conserving deposit, boundaries;
+ *  2. every photon alive at step start: propagate at c, accumulate the
+ *     Breit-Wheeler optical depth (eq. tau_bw) at the accumulated angle of
+ *     Sect. 6.1, convert into an e-e+ pair when it reaches its threshold;
+ *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface;
+ *  4. surface injection of cold electrons (Sect. 2.3 / 6.1 atmosphere). */
+void orc_step(orc_sim *s) {
+  const orc_params *p = &s->p;
+  const double dt = p->dt, dx = p->dx, cdx = dt / dx;
+  const double Hc = p->gap_length / dx;   /* gap height in cells */
+  const double jm = -p->alpha;            /* j_m = alpha j_co, j_co = -1 */
+  const uint32_t n = (uint32_t)s->step;
+  memset(s->D, 0, (size_t)s->nnode * sizeof(double));
+  int64_t nph_old = s->nph;
+
+  for (int64_t ip = 0; ip < s->nlep; ++ip) {
+    orc_lepton *L = &s->lep[ip];
+    double X0 = L->X, u = L->u;
+    /* a1-a2: gather and kick */
+    u += (double)L->q * gather(s, X0) * dt;
+    /* a3: emission sub-cycling within this step */
+    orc_photon born[64];
+    int nborn = 0;
+    if (p->qed && X0 < Hc) {
+      double trem = dt, tau = L->tau;
+      int k = 0;
+      for (;;) {
+        double g = sqrt(1.0 + u * u);
+        double chi = g * g * p->lambda_hat / p->rho_hat;
+        double r = p->rate_mult * ORC_ALPHA_EM * g * orc_tsyn(chi) / p->rho_hat;
+        if (!(r > 0.0)) break;
+        if (tau > r * trem) { tau -= r * trem; break; }
+        trem -= tau / r;
+        double U = orc_uniform(p->seed, L->id, n, CH_EMIT_X, (uint32_t)k);
+        double xi = orc_spec_inverse(U);
+        double x = xi * 1.5 * g * chi;
+        double gm1 = u * u / (g + 1.0);
+        if (x > gm1) x = gm1;
+        double g2 = g - x;
+        double dir = u >= 0.0 ? 1.0 : -1.0;
+        /* a photon clipped to gamma - 1 leaves the lepton at rest; rounding of
+         * gamma - x may land just below 1, which means exactly at rest */
+        double pp = (g2 - 1.0) * (g2 + 1.0);
+        u = pp > 0.0 ? dir * sqrt(pp) : 0.0;
+        s->cnt.emit_events++;
+        if (x >= 2.0) {
+          orc_photon P = {0};
+          P.id = orc_child_id(L->id, n, CH_PHOTON, (uint32_t)k) | ORC_PHOTON_BIT;
+          P.x = x; P.w = L->w; P.dir = (int32_t)dir; P.n0 = (int32_t)n + 1;
+          P.tau_star = -log(orc_uniform(p->seed, P.id, n + 1, CH_BW_TAU, 0));
+          P.tau_acc = 0.0; P.alive = 1;
+          born[nborn++] = P;
+        } else {
+          s->cnt.e_radiated += L->w * x;
+        }
+        tau = -log(orc_uniform(p->seed, L->id, n, CH_EMIT_TAU, (uint32_t)k));
+        if (++k >= p->kmax_emit) { s->cnt.emit_overflow++; break; }
+      }
+      L->tau = tau;
+    }
+    /* a4: drift; a8: deposit of the move */
+    double g = sqrt(1.0 + u * u);
+    double X1 = X0 + u / g * cdx;
+    deposit(s, (double)L->q, L->w, X0, X1);
+    L->u = u;
+    /* a7: boundaries */
+    if (p->boundary == ORC_BC_PERIODIC) {
+      X1 = wrap(p, X1);
+    } else if (X1 < 0.0) {
+      L->alive = 0; s->cnt.absorbed++; s->cnt.e_absorbed += L->w * g;
+    } else if (X1 >= (double)p->nx) {
+      L->alive = 0; s->cnt.escaped++; s->cnt.e_escaped += L->w * g;
+    }
+    L->X = X1;
+    for (int b = 0; b < nborn; ++b) {
+      born[b].X = X1;
+      if (p->boundary != ORC_BC_PERIODIC && !in_domain(p, X1)) {
+        s->cnt.photons_escaped++; s->cnt.e_photon_escaped += born[b].w * born[b].x;
+        continue;
+      }
+      s->cnt.photons++;
+      push_photon(s, born[b]);
+    }
+  }
+
+  /* a5: photons alive at the start of the step */
+  for (int64_t ip = 0; ip < nph_old; ++ip) {
+    orc_photon *P = &s->ph[ip];
+    if (!P->alive) continue;
+    if (P->X < Hc) {
+      double lmid = ((double)n - (double)P->n0 + 0.5) * dt;
+      double sp = fabs(sin(lmid / p->rho_hat));
+      double chi = P->x * p->b * sp;
+      P->tau_acc += dt * p->rate_mult * ORC_ALPHA_EM / p->lambda_hat * p->b * sp * orc_tbw(chi);
+    }
+    double X1 = P->X + (double)P->dir * cdx;
+    if (p->boundary == ORC_BC_PERIODIC) X1 = wrap(p, X1);
+    P->X = X1;
+    if (p->boundary != ORC_BC_PERIODIC && !in_domain(p, X1)) {
+      P->alive = 0; s->cnt.photons_escaped++; s->cnt.e_photon_escaped += P->w * P->x;
+      continue;
+    }
+    if (P->tau_acc >= P->tau_star) {
+      P->alive = 0;
+      double gp = 0.5 * P->x;
+      double up = (double)P->dir * sqrt((gp - 1.0) * (gp + 1.0));
+      for (int k = 0; k < 2; ++k) {
+        orc_lepton L = {0};
+        L.id = orc_child_id(P->id, n, CH_PAIR, (uint32_t)k) & ~ORC_PHOTON_BIT;
+        L.q = k == 0 ? -1 : +1;
+        L.X = X1; L.u = up; L.w = P->w; L.alive = 1;
+        L.tau = -log(orc_uniform(p->seed, L.id, n + 1, CH_TAU0, 0));
+        push_lepton(s, L);
+      }
+      s->cnt.pairs++;
+    }
+  }
+
+  /* compaction (storage order of the survivors is kept) */
+  int64_t m = 0;
+  for (int64_t i = 0; i < s->nlep; ++i) if (s->lep[i].alive) s->lep[m++] = s->lep[i];
+  s->nlep = m;
+  m = 0;
+  for (int64_t i = 0; i < s->nph; ++i) if (s->ph[i].alive) s->ph[m++] = s->ph[i];
+  s->nph = m;
+
+  /* a9: Ampere, with the work of the imposed current on the field */
+  int64_t i0 = p->boundary == ORC_BC_PERIODIC ? 0 : 1;
+  double work = 0.0;
+  for (int64_t i = i0; i < s->nnode; ++i) {
+    double En = s->E[i];
+    s->E[i] = En + (dt * jm - s->D[i]);
+    work += 0.5 * (En + s->E[i]);
+  }
+  if (p->boundary != ORC_BC_PERIODIC) s->E[0] = 0.0;
+  s->cnt.work_jm += dt * dx * jm * work;
+
+  /* a7: surface injection.  Cell 0 must hold the co-rotation charge
+   * eta_co dx = -dx; while its deficit exceeds half a macro-particle charge,
+   * add a cold electron at X = U/2 in (0, 1/2] (cloud inside cell 0 and the
+   * conductor only, so no other cell's Gauss balance changes). */
+  if (p->boundary == ORC_BC_SURFACE && s->w0 > 0.0) {
+    double Q0 = orc_cell_charge(s, 0);
+    double deficit = Q0 - (-1.0) * dx;
+    int j = 0;
+    while (deficit > 0.5 * s->w0) {
+      if (j >= p->kmax_inject) { s->cnt.inject_overflow++; break; }
+      orc_lepton L = {0};
+      L.id = orc_child_id(inject_root(p->gap_index), n, CH_INJECT, (uint32_t)j) & ~ORC_PHOTON_BIT;
+      double o = 0.5 * orc_uniform(p->seed, L.id, n + 1, CH_INJECT, 0);
+      L.q = -1; L.X = o; L.u = 0.0; L.w = s->w0; L.alive = 1;
+      L.tau = -log(orc_uniform(p->seed, L.id, n + 1, CH_TAU0, 0));
+      push_lepton(s, L);
+      deficit -= s->w0 * (o + 0.5);
+      s->cnt.injected++;
+      s->cnt.e_injected += s->w0; /* rest energy of a cold electron */
+      ++j;
+    }
+  }
+  s->step++;
+}
+
+void orc_run(orc_sim *s, int64_t nsteps) { for (int64_t i = 0; i < nsteps; ++i) orc_step(s); }
+
+/* Cloud-in-cell charge of cell c (between nodes c and c+1). */
+double orc_cell_charge(const orc_sim *s, int64_t c) {
+  double Q = 0.0;
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    double X = L->X;
+    if (s->p.boundary == ORC_BC_PERIODIC) {
+      /* nearest periodic image of the cell */
+      double L0 = (double)s->p.nx;
+      double d = X - (double)c;
+      d -= L0 * floor(d / L0 + 0.5);
+      X = (double)c + d;
+    }
+    double fr = Fshape(X - (double)c) - Fshape(X - (double)c - 1.0);
+    Q += L->q * L->w * fr;
+  }
+  return Q;
+}
+
+/* Largest |Gauss residual| (E_{c+1} - E_c) - (Q_c - eta_bg dx) over the cells
+ * that touch no boundary (surface: 1..nx-2; periodic: all). */
+double orc_gauss_residual(const orc_sim *s, double *max_abs_E) {
+  const orc_params *p = &s->p;
+  double *Q = (double *)calloc((size_t)p->nx, sizeof(double));
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    int64_t c0 = (int64_t)floor(L->X - 0.5);
+    for (int64_t c = c0; c <= c0 + 1; ++c) {
+      double fr = Fshape(L->X - c) - Fshape(L->X - c - 1);
+      if (fr == 0.0) continue;
+      int64_t cc = c;
+      if (p->boundary == ORC_BC_PERIODIC) cc = imod(c, p->nx);
+      else if (c < 0 || c >= p->nx) continue;
+      Q[cc] += L->q * L->w * fr;
+    }
+  }
+  double r = 0.0, em = 0.0;
+  int64_t c_lo = p->boundary == ORC_BC_PERIODIC ? 0 : 1;
+  int64_t c_hi = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx - 2;
+  for (int64_t c = c_lo; c <= c_hi; ++c) {
+    int64_t c1 = p->boundary == ORC_BC_PERIODIC ? imod(c + 1, p->nx) : c + 1;
+    double res = (s->E[c1] - s->E[c]) - (Q[c] - s->eta_bg * p->dx);
+    if (fabs(res) > r) r = fabs(res);
+  }
+  for (int64_t i = 0; i < s->nnode; ++i) if (fabs(s->E[i]) > em) em = fabs(s->E[i]);
+  if (max_abs_E) *max_abs_E = em;
+  free(Q);
+  return r;
+}
+
+/* Per-cell moments for the diagnostics of Sect. 6.2 (Fig. 5): cloud-in-cell
+ * density of each species split by direction (u >= 0 up, u < 0 down), the
+ * weighted sums of gamma^-3 and of the weight (for <gamma^-3>), and the
+ * charge.  Arrays have nx entries; dens is [2 species][2 dirs][nx]. */
+void orc_moments(const orc_sim *s, double *dens, double *g3w, double *wsum, double *charge) {
+  const orc_params *p = &s->p;
+  int64_t nx = p->nx;
+  memset(dens, 0, (size_t)(4 * nx) * sizeof(double));
+  memset(g3w, 0, (size_t)nx * sizeof(double));
+  memset(wsum, 0, (size_t)nx * sizeof(double));
+  memset(charge, 0, (size_t)nx * sizeof(double));
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    double g = sqrt(1.0 + L->u * L->u);
+    int sp = L->q < 0 ? 0 : 1, dr = L->u >= 0.0 ? 0 : 1;
+    int64_t c0 = (int64_t)floor(L->X - 0.5);
+    for (int64_t c = c0; c <= c0 + 1; ++c) {
+      double fr = Fshape(L->X - c) - Fshape(L->X - c - 1);
+      if (fr == 0.0) continue;
+      int64_t cc = c;
+      if (p->boundary == ORC_BC_PERIODIC) cc = imod(c, nx);
+      else if (c < 0 || c >= nx) continue;
+      dens[(sp * 2 + dr) * nx + cc] += L->w * fr / p->dx;
+      g3w[cc] += L->w * fr / (g * g * g);
+      wsum[cc] += L->w * fr;
+      charge[cc] += L->q * L->w * fr;
+    }
+  }
+}
+
+/* Accessors used by the Python wrapper. */
+int64_t orc_nlep(const orc_sim *s) { return s->nlep; }
+int64_t orc_nph(const orc_sim *s) { return s->nph; }
+int64_t orc_nnode(const orc_sim *s) { return s->nnode; }
+int64_t orc_stepno(const orc_sim *s) { return s->step; }
+double orc_w0(const orc_sim *s) { return s->w0; }
+double orc_eta_bg(const orc_sim *s) { return s->eta_bg; }
+void orc_get_E(const orc_sim *s, double *E) { memcpy(E, s->E, (size_t)s->nnode * sizeof(double)); }
+void orc_get_counters(const orc_sim *s, orc_counters *c) { *c = s->cnt; }
+void orc_get_leptons(const orc_sim *s, uint64_t *id, int32_t *q, double *X, double *u,
+                     double *w, double *tau) {
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    id[i] = s->lep[i].id; q[i] = s->lep[i].q; X[i] = s->lep[i].X; u[i] = s->lep[i].u;
+    w[i] = s->lep[i].w; tau[i] = s->lep[i].tau;
+  }
+}
+void orc_get_photons(const orc_sim *s, uint64_t *id, double *X, double *x, double *w,
+                     double *tau_star, double *tau_acc, int32_t *dir, int32_t *n0) {
+  for (int64_t i = 0; i < s->nph; ++i) {
+    id[i] = s->ph[i].id; X[i] = s->ph[i].X; x[i] = s->ph[i].x; w[i] = s->ph[i].w;
+    tau_star[i] = s->ph[i].tau_star; tau_acc[i] = s->ph[i].tau_acc;
+    dir[i] = s->ph[i].dir; n0[i] = s->ph[i].n0;
+  }
+}
