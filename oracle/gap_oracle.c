@@ -483,13 +483,17 @@ void orc_step(orc_sim *s) {
         double xi = orc_spec_inverse(U);
         double x = xi * 1.5 * g * chi;
         double gm1 = u * u / (g + 1.0);
-        if (x > gm1) x = gm1;
-        double g2 = g - x;
         double dir = u >= 0.0 ? 1.0 : -1.0;
-        /* a photon clipped to gamma - 1 leaves the lepton at rest; rounding of
-         * gamma - x may land just below 1, which means exactly at rest */
-        double pp = (g2 - 1.0) * (g2 + 1.0);
-        u = pp > 0.0 ? dir * sqrt(pp) : 0.0;
+        if (x >= gm1) {
+          /* the photon takes the whole kinetic energy: the lepton is at rest
+           * (gamma - x would otherwise carry only rounding noise) */
+          x = gm1;
+          u = 0.0;
+        } else {
+          double g2 = g - x;
+          double pp = (g2 - 1.0) * (g2 + 1.0);
+          u = pp > 0.0 ? dir * sqrt(pp) : 0.0;
+        }
         s->cnt.emit_events++;
         if (x >= 2.0) {
           orc_photon P = {0};
