@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of the 1D radiative PIC time step (push + QED + deposit +
+Ampere, with the amortised store compaction) in macroparticle-steps/s.
+
+Workload (one GPU): Nx = 2^20 periodic cells, 200 e- + 200 e+ per cell
+(4.19e8 macroparticles), 1D Maxwell-Juttner theta = 0.1, 1e-3 Langmuir seed,
+QED off: the roofline microbenchmark of the method.  The headline is the FP32
+particle state with the FP64 field; the FP64 plain state is reported beside
+it.  Inputs are resident in HBM and larger than L2 (no flush needed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own independent replica (weak scaling,
+no collective on the data path); the timed region is bracketed by barriers
+and the maximum over ranks is reported.  `--impl reference` times the FP64
+CPU oracle of the same method on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "macroparticle-steps/s (push+QED+deposit)"
+UNIT = "macroparticle-steps/s"
+NX, PPC = 1 << 20, 200
+WORKLOAD = dict(nx=NX, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
+                init=2, boundary=1, qed=0)
+N_PARTICLES = 2 * NX * PPC
+
+
+def set_size(nx):
+    """Smaller copies of the workload (same density and temperature) serve
+    profiling captures; the bench line is always the full size."""
+    global NX, N_PARTICLES
+    NX = nx
+    WORKLOAD["nx"] = nx
+    N_PARTICLES = 2 * NX * PPC
+WORKLOAD_NAME = ("cfg2 push+deposit roofline: Nx=2^20 periodic, 4.19e8 e+- (200+200 per cell, "
+                 "0.5 n_co each), Maxwell-Juttner theta=0.1, 1e-3 Langmuir seed, QED off")
+# algorithmic bytes of the push kernel per particle-step (no QED, uniform
+# weights): read cell int32 + offset + momentum, write them back
+BYTES_PER_PARTICLE = {"fp32": 24, "fp64": 40}
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def traffic_record(kernel, precision):
+    """DRAM traffic per launch of the push kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[f"{kernel}:{precision}"]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2608_21920_b300", "csrc", "step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("step_cu_sha") != sha:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2608_21920_b300 import Gap
+    from paper_2608_21920_b300 import _abi as A
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    peaks, peak_kind = measured_peaks()
+    cfg = dict(WORKLOAD, seed=rank, gap_index=rank)
+    results = {}
+    tuned = None
+    if args.autotune:
+        from paper_2608_21920_b300 import autotune
+        (args.tile, args.threads), times = autotune.tune(cfg, "fp32", verbose=(rank == 0))
+        tuned = {f"{t}x{th}": round(ms, 4) for (t, th), ms in times.items()}
+    for precision in (["fp32", "fp64"] if not args.fp32_only else ["fp32"]):
+        K = args.steps if precision == "fp32" else max(3, min(args.steps, args.fp64_steps))
+        g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads)
+        g.step(args.warmup)
+        barrier()
+        clocks = ClockSampler(local)
+        if precision == "fp32":
+            clocks.start()
+        g.profile(True)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(s)
+        g.step(K)
+        e1.record(s)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        push_ms, push_n, lps = g.profile(False)
+        clk = clocks.stop() if precision == "fp32" else None
+        ms = max_over_ranks(ms)
+        d = g.diag(spectrum=False)
+        r = dict(ms=ms, K=K, push_ms=push_ms / max(push_n, 1), push_n=push_n, launches=lps * K,
+                 gauss=d["gauss_residual"], E_abs_max=d["E_abs_max"],
+                 n=d["n_electrons"] + d["n_positrons"], clocks=clk)
+        results[precision] = r
+        if precision == "fp32" and not args.no_e2e:
+            # end to end through the public API: init from host parameters,
+            # then every step the result (E and counters) read back to pinned
+            # host memory
+            del g
+            torch.cuda.empty_cache()
+            Ehost = torch.empty(NX, dtype=torch.float64, pin_memory=True)
+            Ke = args.e2e_steps
+            barrier()
+            t0 = time.perf_counter()
+            g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads)
+            import ctypes as C
+            for _ in range(Ke):
+                g.step(1)
+                A.check(A.lib().gap_get_field(g.handle, 0, C.c_void_p(Ehost.data_ptr()), NX, g.stream()),
+                        g.handle, "get_field")
+            barrier()
+            t_e2e = max_over_ranks(time.perf_counter() - t0)
+            # host->device bytes of gap_init: gap and tile tables, tile-edge
+            # counts, segment layout, spectrum tables (the plasma is loaded on
+            # the device from the parameters); device->host per step: E and
+            # the control block that locates it
+            tile = args.tile or 256
+            nt = (NX + tile - 1) // tile
+            h2d_init = 256 + 16 * nt + NX + 2 * 12 * nt + 1024 * 8 + 2 * 577 * 8
+            r["e2e"] = dict(value=world * N_PARTICLES * Ke / t_e2e, steps=Ke,
+                            h2d_bytes_per_step=int(math.ceil(h2d_init / Ke)),
+                            d2h_bytes_per_step=int(NX * 8 + 64))
+        del g
+        torch.cuda.empty_cache()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    r32 = results["fp32"]
+    value = world * N_PARTICLES * r32["K"] / (r32["ms"] / 1e3)
+    bpp = BYTES_PER_PARTICLE["fp32"]
+    achieved = bpp * N_PARTICLES / (r32["push_ms"] / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r32["K"],
+        "warmup": args.warmup, "ms_per_step": r32["ms"] / r32["K"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": "FP32 particle state, FP64 field",
+                   "macroparticles_per_gpu": N_PARTICLES, "tile": args.tile or 256,
+                   "l2": "inputs larger than L2 (11.7 GB particle state per GPU), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "kernel": "k_push<float,false,false>", "bytes_per_particle": bpp,
+                     "push_ms_per_launch": r32["push_ms"],
+                     "traffic": traffic_record("k_push", "fp32")},
+        "gpu_launches": int(r32["launches"]),
+        "clocks": r32["clocks"],
+        "gauss_residual": r32["gauss"], "E_abs_max": r32["E_abs_max"],
+        "particles_alive": r32["n"],
+    }
+    if tuned:
+        line["config"]["autotune_ms_per_push"] = tuned
+        line["config"]["threads"] = args.threads
+    if "e2e" in r32:
+        e = r32["e2e"]
+        line["e2e"] = {"value": e["value"], "unit": UNIT, "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e["d2h_bytes_per_step"], "steps": e["steps"],
+                       "includes": "gap_init from host parameters + per-step E readback to pinned host"}
+    if "fp64" in results:
+        r64 = results["fp64"]
+        v64 = world * N_PARTICLES * r64["K"] / (r64["ms"] / 1e3)
+        a64 = BYTES_PER_PARTICLE["fp64"] * N_PARTICLES / (r64["push_ms"] / 1e3) / 1e9
+        line["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": r64["K"], "ms_per_step": r64["ms"] / r64["K"],
+                              "achieved_gbs": a64, "frac": a64 / peak, "gauss_residual": r64["gauss"],
+                              "fp32_over_fp64": value / v64}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(nx, steps, warmup):
+    import oracle as O
+    s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
+              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0)
+    if warmup:
+        s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return 2 * nx * PPC * steps / dt, dt
+
+
+def cpu_baseline(seconds):
+    """The FP64 oracle as it stands, single-threaded on the host, on a bounded
+    sample of the workload (same density, temperature and seed; fewer cells)."""
+    nx = 1 << 14
+    rate, dt = _oracle_sample(nx, 2, 0)
+    steps = max(2, int(seconds * rate / (2 * nx * PPC)))
+    rate, dt = _oracle_sample(nx, steps, 1)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Nx=2^14 periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), {steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    total = (args.steps + args.warmup)
+    nx = 1 << max(8, int(math.log2(max(256, 1.5e9 / (2 * PPC * max(total, 1))))))
+    import oracle as O
+    s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
+              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = 2 * nx * PPC * args.steps / dt
+    sample = f"Nx={nx} periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), theta=0.1, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "precision": "FP64 oracle (plain C, 1 thread)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="pick tile and threads by timing the push kernel")
+    ap.add_argument("--nx", type=int, default=0, help="smaller workload for profiling captures only")
+    args = ap.parse_args()
+    if args.nx:
+        set_size(args.nx)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * gap.h -- C ABI of the B300 library for the time step of the 1D radiative
+ * particle-in-cell model of a pulsar polar-cap pair discharge, and of the
+ * batched integrator of the discharge concurrency model with its adjoint.
+ *
+ * Paper: "Pair Discharges and Radio Emission from Pulsar Magnetospheres".
+ *
+ * Conventions for every entry point
+ *  - Status: 0 (GAP_OK) or a negative GAP_E* code.  The first error is sticky
+ *    on a handle; gap_last_error() returns a one-line description.
+ *  - Device memory is owned by the caller.  gap_workspace_bytes() says how
+ *    much one handle needs; the caller allocates it (for example a torch
+ *    uint8 CUDA tensor) and passes the pointer to gap_init().  The library
+ *    never calls cudaMalloc/cudaFree.  Host memory of the handle itself is
+ *    owned by the library and released by gap_free().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that return host data synchronise that stream; the
+ *    others only enqueue work.
+ *  - Pointers named host_* are host memory; pointers named dev_* are device
+ *    memory on the current device.
+ *
+ * Code units (Sect. 2.2): length c/omega_p,co, time 1/omega_p,co, momentum
+ * u = gamma beta, density n_co = |eta_co|/e, field m_e c omega_p/e.  In them
+ * Gauss reads dE/dx = eta - eta_co and Ampere dE/dt = j_m - J, with
+ * eta_co = -1 and j_m = alpha j_co = -alpha (aligned rotator).
+ */
+#ifndef GAP_H
+#define GAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GAP_OK 0
+#define GAP_EINVAL (-1)   /* bad argument or parameter */
+#define GAP_ENOSPACE (-2) /* workspace smaller than gap_workspace_bytes() */
+#define GAP_ECAP (-3)     /* particle storage exhausted (cap / capacity) */
+#define GAP_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define GAP_ECUDA (-5)    /* a CUDA runtime call failed */
+#define GAP_ECHECK (-6)   /* a device-side consistency check failed */
+
+/* precision of the particle state (Sect. 6.1 pushes; BASELINE precision pattern) */
+#define GAP_FP64_PLAIN 0 /* FP64 offsets, momenta, weights; FP64 charge deposit */
+#define GAP_FP32_STATE 1 /* FP32 offsets and momenta; exact integer charge deposit; FP64 field */
+
+/* boundaries (Sect. 6.1: star + atmosphere at h = 0, free outflow at the top) */
+#define GAP_BC_SURFACE 0
+#define GAP_BC_PERIODIC 1
+
+/* initial loads */
+#define GAP_INIT_EMPTY 0        /* no particles (use gap_add_particles) */
+#define GAP_INIT_COLD 1         /* cold electrons at rest, `density`, ppc per cell */
+#define GAP_INIT_PAIR_THERMAL 2 /* e- and e+ at density/2 each, 1D Maxwell-Juttner(theta),
+                                   electrons displaced by a Langmuir seed of amplitude seed_amp */
+
+/* particle kinds for gap_get_particles / gap_add_particles */
+#define GAP_ELECTRON 0
+#define GAP_POSITRON 1
+#define GAP_PHOTON 2
+
+/* Parameters of one gap.  The problem statement of the paper (Sect. 2.2 and
+ * 6.1): twist alpha = j_m/j_co, field b = B/B_Q, field-line curvature radius
+ * R_curv (as rho_hat = R_curv/d_e), gap height H_gap and density in units of
+ * |eta_co|/e.  QED rates follow Sect. 3 (eq. tau_syn, eq. tau_bw) with the
+ * Compton wavelength lambda_hat = lambda_C/d_e; rate_mult multiplies both
+ * rates (the macro-particle rescaling of Sect. 6.1). */
+typedef struct gap_params {
+  double alpha;      /* j_m / j_co */
+  double b;          /* B / B_Q */
+  double lambda_hat; /* reduced Compton wavelength / skin depth */
+  double rho_hat;    /* field-line curvature radius / skin depth */
+  double rate_mult;  /* multiplier of both QED rates (>= 0) */
+  double gap_length; /* H_gap in skin depths; QED inhibited above it.  0 -> 0.8 nx dx */
+  double density;    /* initial lepton density, units of n_co */
+  double dx;         /* cell size (skin depths) */
+  double dt;         /* time step (1/omega_p); c dt/dx must be < 0.5 */
+  double theta;      /* temperature of GAP_INIT_PAIR_THERMAL (m_e c^2) */
+  double seed_amp;   /* Langmuir seed relative density amplitude */
+  int64_t nx;        /* cells (>= 8) */
+  int64_t ppc;       /* macro-particles per cell per species at load */
+  int64_t cap;       /* macro-particle cap (leptons + photons) of this gap; 0 -> none */
+  uint64_t seed;     /* Philox4x32-10 key of this gap */
+  int32_t qed;       /* 0/1: curvature emission and one-photon pair creation */
+  int32_t boundary;  /* GAP_BC_* */
+  int32_t init;      /* GAP_INIT_* */
+  int32_t kmax_emit; /* emission events per lepton per step (0 -> 16) */
+  int32_t kmax_inject; /* injected electrons per step (0 -> 64) */
+  int32_t gap_index; /* enters the ids of loaded and injected particles */
+} gap_params;
+
+/* Options shared by all gaps of one handle. */
+typedef struct gap_config {
+  int32_t precision;       /* GAP_FP64_PLAIN or GAP_FP32_STATE */
+  int32_t tile;            /* dual cells per tile (>= 8; 0 -> 256) */
+  int32_t threads;         /* threads per block of the push kernel (0 -> 256) */
+  int32_t rebin_every;     /* steps between store compactions (0 -> 64) */
+  double slack;            /* headroom of each tile segment (0 -> 0.125) */
+  int64_t lepton_capacity; /* slots per species over all gaps (0 -> derived) */
+  int64_t photon_capacity; /* photon slots (0 -> derived) */
+} gap_config;
+
+typedef struct gap_handle gap_handle;
+
+/* Event counters and energy ledger of one gap (cumulative since init).
+ * Energies are total energies (rest mass included) per unit area in units of
+ * n_co m_e c^2 d_e. */
+typedef struct gap_counters {
+  int64_t emit_events, photons, pairs, injected, absorbed, escaped, photons_escaped,
+      emit_overflow, inject_overflow, load_overflow, spilled, photon_overflow, merged,
+      reserved0, reserved1, reserved2;
+  double e_radiated, e_absorbed, e_escaped, e_photon_escaped, e_injected, work_jm,
+      reserved3, reserved4;
+} gap_counters;
+
+/* Diagnostics of one gap (Sect. 6.2, Fig. 5; Sect. 6.6, Fig. 8). */
+typedef struct gap_diag_out {
+  int64_t step;
+  int64_t n_electrons, n_positrons, n_photons;
+  double M_peak;      /* max over gap cells of (n_e- + n_e+)/n_co */
+  double M_avg;       /* mean over gap cells */
+  int64_t peak_cell;
+  double g3_peak;     /* <gamma^-3> at the peak cell */
+  double M_split[4];  /* at the peak cell: e- up, e- down, e+ up, e+ down */
+  double E_min, E_max;/* over gap nodes */
+  double gauss_residual; /* max |(E_{c+1}-E_c) - (Q_c - eta_bg dx)| over interior cells */
+  double E_abs_max;
+  double field_energy, lepton_energy, photon_energy;
+  int64_t spectrum_len; /* P/2 + 1 entries written to host_spectrum when given */
+  gap_counters counters;
+} gap_diag_out;
+
+/* Workspace size for n_gaps gaps (params[0..n_gaps-1]) and options cfg
+ * (NULL -> defaults).  Returns GAP_EINVAL for inconsistent parameters. */
+int gap_workspace_bytes(const gap_params *params, int32_t n_gaps, const gap_config *cfg,
+                        size_t *bytes);
+
+/* Lay out the handle in dev_workspace (>= gap_workspace_bytes, 256-byte
+ * aligned), load the initial particles, solve Gauss's law for the initial E
+ * and build the emission-spectrum tables.  Synchronises `stream`. */
+int gap_init(const gap_params *params, int32_t n_gaps, const gap_config *cfg,
+             void *dev_workspace, size_t bytes, void *stream, gap_handle **out);
+
+/* Advance every gap by nsteps time steps (Sect. 6.1 cycle: gather, kick,
+ * emission, drift, deposit, photon propagation and pair creation, Ampere,
+ * surface injection; compaction of the particle store when due).  Enqueues
+ * work only; no host synchronisation. */
+int gap_step(gap_handle *h, int64_t nsteps, void *stream);
+
+/* Same as gap_step, but replays a CUDA graph of `chunk` steps (captured on
+ * first use) for the whole multiples of chunk and launches the remainder
+ * directly. */
+int gap_step_graph(gap_handle *h, int64_t nsteps, int32_t chunk, void *stream);
+
+/* Diagnostics of gap `gap`.  host_spectrum (may be NULL) receives |E_k|^2/P
+ * of E over the gap nodes zero-padded to P = next power of two, P/2+1
+ * values; host_moments (may be NULL) receives 8 arrays of nx doubles:
+ * density e-up, e-down, e+up, e+down, sum w gamma^-3, sum w, charge, photon
+ * density.  Synchronises `stream`. */
+int gap_diag(gap_handle *h, int32_t gap, gap_diag_out *out, double *host_spectrum,
+             int64_t spectrum_cap, double *host_moments, void *stream);
+
+/* Copy E of gap `gap` (nnode = nx+1 surface, nx periodic values). */
+int gap_get_field(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream);
+int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, void *stream);
+
+/* Export the particles of one kind of one gap, in arbitrary order, as FP64:
+ * X is the absolute position in cells, u = gamma beta (photons: x, the
+ * energy in m_e c^2, in host_u), w the weight, tau the remaining optical
+ * depth (photons: tau_acc in host_tau and tau_star in host_aux).  host_aux
+ * may be NULL for leptons; for photons host_aux2 receives dir and birth
+ * step packed as (n0 << 1) | (dir > 0).  *n_out = count; GAP_ECAP if cap is
+ * too small.  Synchronises `stream`. */
+int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uint64_t *host_id,
+                      double *host_X, double *host_u, double *host_w, double *host_tau,
+                      double *host_aux, int64_t *host_aux2, int64_t *n_out, void *stream);
+
+/* Append n particles of one kind to gap `gap` (tests build hand-checkable
+ * states).  Photons: host_u is x, host_tau is tau_star, host_aux2 packs
+ * (n0 << 1) | (dir > 0).  Synchronises `stream`. */
+int gap_add_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t n, const uint64_t *host_id,
+                      const double *host_X, const double *host_u, const double *host_w,
+                      const double *host_tau, const int64_t *host_aux2, void *stream);
+
+/* Recompute E of every gap from Gauss's law (Sect. 2.2): E_0 = 0 at the
+ * surface, zero mean for periodic gaps; the periodic background eta_bg is
+ * set to the mean charge density when set_background is nonzero. */
+int gap_solve_gauss(gap_handle *h, int32_t set_background, void *stream);
+
+/* Override the Gauss background eta_bg of a gap (default: -1 at a surface). */
+int gap_set_background(gap_handle *h, int32_t gap, double eta_bg);
+
+/* The inverse CDF of the classical curvature-photon spectrum used by the
+ * emission sampler (reading of the unspecified S(gamma, x) of Sect. 3.1:
+ * dN/dxi proportional to F(xi)/xi, F(xi) = xi int_xi^inf K_5/3): for each
+ * uniform U in (0,1] of dev_U, dev_xi receives the xi with P(xi' > xi) = U,
+ * as the FP64 path (precision GAP_FP64_PLAIN: table and Newton steps on the
+ * quadrature) or the FP32 path (GAP_FP32_STATE: table only) evaluates it.
+ * n doubles each, device memory; enqueues work only. */
+int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int64_t n, int32_t precision,
+                         void *stream);
+
+/* Steps taken so far (host mirror). */
+int64_t gap_steps_done(const gap_handle *h);
+
+/* Live timing of the push kernel (the dominant kernel of a step).  With
+ * on != 0, later gap_step calls bracket each push launch with CUDA events on
+ * the launching stream.  Every call first returns, through the non-NULL
+ * outputs, the summed push duration (ms) and the number of push launches
+ * timed since the previous call (synchronising on the last event), and the
+ * number of kernel launches one step makes; then it resets the sums and sets
+ * the mode.  Graph replays are not timed. */
+int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_launches,
+                int64_t *launches_per_step);
+
+/* Release host state.  The caller frees the workspace afterwards. */
+void gap_free(gap_handle *h);
+
+const char *gap_last_error(const gap_handle *h);
+const char *gap_status_string(int status);
+
+/* ------------------------------------------------------------------------
+ * Concurrency model (Sect. 5.2, eq. dis1-dis4) -- batched RK4 integrator
+ * with a hand-written discrete adjoint.
+ *
+ * State y = (m_pm, m_x, eps, j), parameters p = (alpha, t_x, t_pm, t_acc, g3)
+ * in units of t_esc = 1.  The gate H(|eps| - 1) is the Heaviside step when
+ * delta == 0 and the smoothed (1 + tanh(z/delta))/2 otherwise.
+ * Layouts (row-major, device memory):
+ *   dev_p   [B][5], dev_y0 [B][4], dev_dt [B] (per-set step size),
+ *   dev_out [T][B][4] states at steps 0, every, 2*every, ... (T = nsteps/every + 1),
+ *   dev_ckpt [nsteps/ckpt_every + 1][B][4] checkpoints kept for the adjoint.
+ * Precision: dtype 0 = FP64, 1 = FP32 (all arrays of that type).
+ * ------------------------------------------------------------------------ */
+int ode_forward(const void *dev_p, const void *dev_y0, const void *dev_dt, int32_t B, int32_t nsteps,
+                int32_t every, int32_t ckpt_every, double delta, int32_t dtype, void *dev_out,
+                void *dev_ckpt, void *stream);
+
+/* Given dL/d(out) in dev_gout [T][B][4], accumulate dL/dp into dev_gp [B][5]
+ * and dL/dy0 into dev_gy0 [B][4] (both overwritten) by the discrete adjoint
+ * of the same RK4 steps, recomputing each checkpoint segment forward.
+ * dev_scratch holds ckpt_every+1 states per set: (ckpt_every+1)*B*4 values. */
+int ode_adjoint(const void *dev_p, const void *dev_dt, const void *dev_ckpt, const void *dev_gout,
+                int32_t B, int32_t nsteps, int32_t every, int32_t ckpt_every, double delta,
+                int32_t dtype, void *dev_gp, void *dev_gy0, void *dev_scratch, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAP_H */

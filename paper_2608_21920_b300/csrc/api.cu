@@ -1,0 +1,793 @@
+// api.cu -- the C ABI (include/gap.h): workspace layout, initialisation,
+// stepping, diagnostics and particle export/import.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gap_internal.cuh"
+#include "kernels.h"
+
+using namespace gapk;
+
+struct gap_handle {
+  View v{};
+  int32_t n_gaps = 0, precision = 0, threads = 256;
+  double slack = 0.125;
+  std::vector<gap_params> params;
+  std::vector<GapDev> gaps_h;
+  std::vector<TileDev> tiles_h;
+  std::vector<LoadSpec> loads;
+  int64_t total_nodes = 0, steps_done = 0;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  char *buf_base[2] = {nullptr, nullptr};
+  size_t buf_bytes = 0;
+  unsigned long long *export_count = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int32_t graph_chunk = 0;
+  cudaStream_t graph_stream = nullptr;
+  int status = GAP_OK;
+  std::string err;
+  // live timing of the push kernel (gap_profile_*)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // pairs around each push launch
+  size_t ev_used = 0;
+};
+
+namespace {
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(char *b) : base(b) {}
+  template <class T>
+  T *take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+int fail(gap_handle *h, int code, const std::string &msg) {
+  if (h && h->status == GAP_OK) {
+    h->status = code;
+    h->err = msg;
+  }
+  return code;
+}
+
+int cuda_check(gap_handle *h, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return GAP_OK;
+  return fail(h, GAP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+gap_config default_config(const gap_config *c) {
+  gap_config d{};
+  if (c) d = *c;
+  if (d.tile <= 0) d.tile = 256;
+  if (d.threads <= 0) d.threads = 256;
+  if (d.rebin_every <= 0) d.rebin_every = 64;
+  if (!(d.slack > 0.0)) d.slack = 0.125;
+  return d;
+}
+
+int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string &msg) {
+  if (!p || n <= 0) { msg = "no gaps"; return GAP_EINVAL; }
+  if (cfg.precision != GAP_FP64_PLAIN && cfg.precision != GAP_FP32_STATE) { msg = "precision"; return GAP_EINVAL; }
+  if (cfg.tile < 8 || cfg.tile > 4096) { msg = "tile must be in [8, 4096]"; return GAP_EINVAL; }
+  if (cfg.threads < 32 || cfg.threads > 256 || cfg.threads % 32) { msg = "threads must be a multiple of 32 in [32, 256]"; return GAP_EINVAL; }
+  for (int i = 0; i < n; ++i) {
+    const gap_params &q = p[i];
+    if (q.nx < 8 || q.nx > (1ll << 28)) { msg = "nx out of range"; return GAP_EINVAL; }
+    if (!(q.dx > 0) || !(q.dt > 0) || q.dt / q.dx >= 0.5) { msg = "need dx, dt > 0 and c dt/dx < 1/2"; return GAP_EINVAL; }
+    if (q.boundary != GAP_BC_SURFACE && q.boundary != GAP_BC_PERIODIC) { msg = "boundary"; return GAP_EINVAL; }
+    if (q.init < GAP_INIT_EMPTY || q.init > GAP_INIT_PAIR_THERMAL) { msg = "init"; return GAP_EINVAL; }
+    if (q.init != GAP_INIT_EMPTY && q.ppc <= 0) { msg = "ppc must be > 0 for a load"; return GAP_EINVAL; }
+    if (q.kmax_emit < 0 || q.kmax_emit > kMaxEmit) { msg = "kmax_emit must be <= 16"; return GAP_EINVAL; }
+    if (q.qed && (!(q.lambda_hat > 0) || !(q.rho_hat > 0) || q.rate_mult < 0)) { msg = "QED scales"; return GAP_EINVAL; }
+    if (q.init == GAP_INIT_PAIR_THERMAL && q.boundary != GAP_BC_PERIODIC) { msg = "thermal pair load needs a periodic gap"; return GAP_EINVAL; }
+  }
+  return GAP_OK;
+}
+
+// Host quadrature of the survival function S(xi) of the classical curvature
+// spectrum and of dS/dxi (trapezoid in t with the integral representation
+// S = 3/(5 pi) int cosh(5t/3) e^{-xi cosh t} / cosh^2 t dt), used to build the
+// tables that the kernels read.
+struct SpecQuad {
+  double h;
+  std::vector<double> c, a;
+  explicit SpecQuad(double hh, double tmax) : h(hh) {
+    for (int k = 0; k * h <= tmax; ++k) {
+      double t = k * h;
+      c.push_back(std::cosh(t));
+      a.push_back(std::cosh(5.0 * t / 3.0) / std::cosh(t));
+    }
+  }
+  void eval(double xi, double &S, double &dS) const {
+    double s0 = 0, s1 = 0;
+    for (size_t k = 0; k < c.size(); ++k) {
+      if (xi * (c[k] - 1.0) - (double)k * h > 40.0) break;
+      double f = a[k] * std::exp(-xi * c[k]);
+      double wk = k == 0 ? 0.5 : 1.0;
+      s0 += wk * f / c[k];
+      s1 += wk * f;
+    }
+    const double norm = 3.0 / (5.0 * M_PI) * h;
+    S = norm * s0;
+    dS = -norm * s1;
+  }
+  // xi with S(xi) = exp(-v): bracketed Newton on ln xi.
+  double inverse_of_v(double v) const {
+    const double U = std::exp(-v);
+    double lo = std::log(1e-45), hi = std::log(80.0);
+    double y = v > 1.0 ? std::log(v) : 3.0 * std::log(v) + 0.5;
+    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+    for (int it = 0; it < 300; ++it) {
+      double xi = std::exp(y), S, dS;
+      eval(xi, S, dS);
+      // compare in terms of -ln S to keep relative accuracy at both ends
+      double g = -std::log(S) - v;  // increasing in y
+      if (g < 0) lo = y; else hi = y;
+      double dg = -xi * dS / S;
+      double yn = y - g / dg;
+      if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+      if (std::fabs(yn - y) < 1e-13) { y = yn; break; }
+      y = yn;
+    }
+    (void)U;
+    return std::exp(y);
+  }
+};
+
+}  // namespace
+
+static int64_t next_pow2(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// Lay out (or, with base == nullptr, only measure) one handle.
+static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, char *base,
+                        gap_handle *h, size_t *bytes_out) {
+  const bool fp32 = cfg.precision == GAP_FP32_STATE;
+  const size_t rs = fp32 ? 4 : 8, wsz = fp32 ? 4 : 8;
+  const int T = cfg.tile;
+  std::vector<GapDev> gaps(n);
+  std::vector<TileDev> tiles;
+  std::vector<LoadSpec> loads;
+  std::vector<int64_t> cap0[2];
+  int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
+  bool qed_any = false, surface_any = false;
+  for (int i = 0; i < n; ++i) {
+    const gap_params &q = p[i];
+    GapDev &g = gaps[i];
+    std::memset(&g, 0, sizeof(g));
+    g.nx = q.nx;
+    g.periodic = q.boundary == GAP_BC_PERIODIC;
+    g.nnode = g.periodic ? q.nx : q.nx + 1;
+    g.node_off = total_nodes;
+    total_nodes += g.nnode;
+    max_nx = std::max<int64_t>(max_nx, g.nnode);
+    g.qed = q.qed ? 1 : 0;
+    g.kmax_emit = q.kmax_emit > 0 ? q.kmax_emit : 16;
+    g.kmax_inject = q.kmax_inject > 0 ? q.kmax_inject : 64;
+    g.gap_index = q.gap_index;
+    g.dx = q.dx;
+    g.dt = q.dt;
+    g.cdx = q.dt / q.dx;
+    g.jm = -q.alpha;
+    const double H = q.gap_length > 0 ? q.gap_length : 0.8 * (double)q.nx * q.dx;
+    g.Hc = H / q.dx;
+    g.lambda_hat = q.qed ? q.lambda_hat : 1.0;
+    g.rho_hat = q.qed ? q.rho_hat : 1.0;
+    g.rate_mult = q.rate_mult;
+    g.b = q.b;
+    g.eta_bg = -1.0;
+    const double frac = q.init == GAP_INIT_PAIR_THERMAL ? 0.5 : 1.0;
+    g.w0 = q.ppc > 0 ? frac * q.density * q.dx / (double)q.ppc : 0.0;
+    g.w_unit = (g.w0 > 0 ? g.w0 : q.dx) / (double)(1 << kWeightShift);
+    g.f_dt = (float)g.dt;
+    g.f_cdx = (float)g.cdx;
+    g.f_Hc = (float)g.Hc;
+    g.f_lam = (float)g.lambda_hat;
+    g.f_rho = (float)g.rho_hat;
+    g.f_rate = (float)g.rate_mult;
+    g.seed = q.seed;
+    g.inj_root = ((uint64_t)(uint32_t)q.gap_index << 40) | (1ull << 38);
+    qed_any |= g.qed != 0;
+    surface_any |= !g.periodic;
+    max_P = std::max<int64_t>(max_P, next_pow2(std::min<int64_t>((int64_t)std::floor(g.Hc) + 1, g.nnode)));
+    // tiles of T dual cells; a remainder below 4 joins the previous tile
+    int64_t nt = (g.nnode + T - 1) / T;
+    int64_t rem = g.nnode - (nt - 1) * T;
+    if (rem < 4 && nt > 1) nt -= 1;
+    g.tile_begin = (int32_t)tiles.size();
+    g.n_tiles = (int32_t)nt;
+    const int64_t species = q.init == GAP_INIT_PAIR_THERMAL ? 2 : (q.init == GAP_INIT_COLD ? 1 : 0);
+    for (int64_t t = 0; t < nt; ++t) {
+      TileDev td{};
+      td.gap = i;
+      td.k0 = (int32_t)(t * T);
+      td.nk = (int32_t)(t == nt - 1 ? g.nnode - t * T : T);
+      tiles.push_back(td);
+      for (int s = 0; s < 2; ++s) {
+        int64_t cnt = (s < species) ? (int64_t)td.nk * q.ppc : 0;
+        int64_t c = (int64_t)(cnt * (1.0 + cfg.slack)) + 64;
+        c = (c + 31) & ~31ll;
+        cap0[s].push_back(c);
+      }
+    }
+    const int64_t load = q.nx * (q.init != GAP_INIT_EMPTY ? q.ppc : 0);
+    for (int s = 0; s < 2; ++s) {
+      const int64_t ls = s < species ? load : 0;
+      int64_t need = (int64_t)(1.3 * (double)ls) + 160 * nt;
+      if (q.qed) {
+        int64_t grow = q.cap > 0 ? q.cap : 16 * std::max<int64_t>(load, 1024);
+        need = std::max<int64_t>(need, grow + 160 * nt);
+      }
+      lep_need[s] += need;
+    }
+    if (q.qed) ph_need += q.cap > 0 ? q.cap : 16 * std::max<int64_t>(load, 1024);
+    if (q.init != GAP_INIT_EMPTY) {
+      LoadSpec ls{};
+      ls.gap = i;
+      ls.init = q.init;
+      ls.species_count = (int32_t)species;
+      ls.ppc = q.ppc;
+      ls.n_per_species = load;
+      ls.density = q.density;
+      ls.theta = q.theta;
+      ls.seed_amp = q.seed_amp;
+      loads.push_back(ls);
+    }
+  }
+  const int NT = (int)tiles.size();
+  int64_t lep_cap = cfg.lepton_capacity > 0 ? cfg.lepton_capacity : std::max(lep_need[0], lep_need[1]);
+  int64_t cap_sum0 = 0, cap_sum1 = 0;
+  for (int t = 0; t < NT; ++t) { cap_sum0 += cap0[0][t]; cap_sum1 += cap0[1][t]; }
+  lep_cap = std::max<int64_t>(lep_cap, std::max(cap_sum0, cap_sum1));
+  const int64_t ph_cap = cfg.photon_capacity > 0 ? cfg.photon_capacity : std::max<int64_t>(ph_need, 1024);
+  const int64_t spill_cap = std::max<int64_t>(65536, lep_cap / 32);
+  const int64_t dchg = std::max(total_nodes, max_nx);
+
+  Carver C(base);
+  View v{};
+  v.n_gaps = n;
+  v.n_tiles = NT;
+  v.tile = T;
+  v.precision = cfg.precision;
+  v.qed_any = qed_any;
+  v.surface_any = surface_any;
+  v.has_w = qed_any ? 1 : 0;
+  v.rebin_every = cfg.rebin_every;
+  v.gaps = C.take<GapDev>(n);
+  v.tiles = C.take<TileDev>(NT);
+  v.ctl = C.take<Ctl>(1);
+  v.E[0] = C.take<double>(total_nodes);
+  v.E[1] = C.take<double>(total_nodes);
+  v.Dg = C.take<unsigned long long>(total_nodes);
+  v.arrive = C.take<int32_t>(total_nodes);
+  v.expect = C.take<int8_t>(total_nodes);
+  for (int s = 0; s < 2; ++s) {
+    v.seg_start[s] = C.take<int64_t>(NT);
+    v.seg_cap[s] = C.take<int32_t>(NT);
+    v.seg_used[s] = C.take<int32_t>(NT);
+    v.seg_append[s] = C.take<int32_t>(NT);
+    v.seg_alive[s] = C.take<int32_t>(NT);
+    v.spill_cnt[s] = C.take<int32_t>(NT);
+    v.new_start[s] = C.take<int64_t>(NT);
+    v.new_cap[s] = C.take<int32_t>(NT);
+    v.new_fill[s] = C.take<int32_t>(NT);
+  }
+  v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);
+  v.ledger = C.take<double>((size_t)n * L_NLED);
+  v.q0 = C.take<unsigned long long>(n);
+  const int spec_n = 1024;
+  v.spec_n = spec_n;
+  v.spec_tab = C.take<float2>(spec_n);
+  const double quad_h = 0.1, quad_tmax = 96.0;  // trapezoid error ~ exp(xi - pi^2/h) < 1e-27 for xi < 35
+  v.quad_h = quad_h;
+  v.quad_n = (int32_t)(quad_tmax / quad_h) + 1;
+  v.quad_c = C.take<double>(v.quad_n);
+  v.quad_a = C.take<double>(v.quad_n);
+  v.max_nx = max_nx;
+  v.max_P = max_P;
+  v.dmom = C.take<double>(8 * (size_t)max_nx);
+  v.dcharge = C.take<unsigned long long>(dchg);
+  v.dcharge_len = dchg;
+  v.fft[0] = C.take<double>(2 * (size_t)max_P);
+  v.fft[1] = C.take<double>(2 * (size_t)max_P);
+  v.dred = C.take<double>(32);
+  unsigned long long *export_count = C.take<unsigned long long>(4);
+  size_t meta_end = C.off;
+  for (int s = 0; s < 2; ++s) {
+    v.sk[s] = C.take<int32_t>(spill_cap);
+    v.stile[s] = C.take<int32_t>(spill_cap);
+    v.sphi[s] = C.take<double>(spill_cap);
+    v.su[s] = C.take<double>(spill_cap);
+    v.sw[s] = C.take<double>(spill_cap);
+    v.stau[s] = C.take<double>(spill_cap);
+    v.sid[s] = C.take<uint64_t>(spill_cap);
+  }
+  v.spill_capacity = spill_cap;
+  for (int b = 0; b < 2; ++b) {
+    v.pX[b] = C.take<double>(ph_cap);
+    v.px[b] = C.take<double>(ph_cap);
+    v.pw[b] = C.take<double>(ph_cap);
+    v.pts[b] = C.take<double>(ph_cap);
+    v.pta[b] = C.take<double>(ph_cap);
+    v.pid[b] = C.take<uint64_t>(ph_cap);
+    v.pn0[b] = C.take<int32_t>(ph_cap);
+    v.pdir[b] = C.take<int32_t>(ph_cap);
+    v.pgap[b] = C.take<int32_t>(ph_cap);
+  }
+  v.ph_capacity = ph_cap;
+  char *bb[2];
+  size_t bbytes = 0;
+  for (int b = 0; b < 2; ++b) {
+    C.off = (C.off + 255) & ~(size_t)255;
+    size_t b0 = C.off;
+    bb[b] = base ? base + b0 : nullptr;
+    for (int s = 0; s < 2; ++s) {
+      v.lk[b][s] = C.take<int32_t>(lep_cap);
+      v.lphi[b][s] = C.take<char>(rs * lep_cap);
+      v.lu[b][s] = C.take<char>(rs * lep_cap);
+      v.lw[b][s] = C.take<char>(wsz * lep_cap);
+      v.ltau[b][s] = C.take<char>(rs * lep_cap);
+      v.lid[b][s] = C.take<uint64_t>(lep_cap);
+    }
+    bbytes = C.off - b0;
+  }
+  v.lep_capacity = lep_cap;
+  *bytes_out = C.off + 256;
+  if (!base) return GAP_OK;
+
+  h->v = v;
+  h->n_gaps = n;
+  h->precision = cfg.precision;
+  h->threads = cfg.threads;
+  h->slack = cfg.slack;
+  h->params.assign(p, p + n);
+  h->gaps_h = gaps;
+  h->tiles_h = tiles;
+  h->loads = loads;
+  h->total_nodes = total_nodes;
+  h->buf_base[0] = bb[0];
+  h->buf_base[1] = bb[1];
+  h->buf_bytes = bbytes;
+  h->export_count = export_count;
+  // expected contributors of every tile-edge node
+  std::vector<int8_t> expect(total_nodes, 0);
+  for (const TileDev &td : tiles) {
+    const GapDev &g = gaps[td.gap];
+    const int locals[4] = {0, 1, td.nk, td.nk + 1};
+    for (int L : locals) {
+      int64_t node = (int64_t)td.k0 - 1 + L;
+      if (g.periodic) node = (node + g.nx) % g.nx;
+      else if (node < 0 || node > g.nx) continue;
+      expect[g.node_off + node] += 1;
+    }
+  }
+  // initial segment layout
+  std::vector<int64_t> start[2];
+  std::vector<int32_t> capv[2];
+  for (int s = 0; s < 2; ++s) {
+    int64_t acc = 0;
+    for (int t = 0; t < NT; ++t) {
+      start[s].push_back(acc);
+      capv[s].push_back((int32_t)cap0[s][t]);
+      acc += cap0[s][t];
+    }
+  }
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaMemsetAsync(base, 0, meta_end, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.gaps, gaps.data(), sizeof(GapDev) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.tiles, tiles.data(), sizeof(TileDev) * NT, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.expect, expect.data(), total_nodes, cudaMemcpyHostToDevice, st);
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+    e = cudaMemcpyAsync(v.seg_start[s], start[s].data(), sizeof(int64_t) * NT, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v.seg_cap[s], capv[s].data(), sizeof(int32_t) * NT, cudaMemcpyHostToDevice, st);
+  }
+  // spectrum tables
+  SpecQuad sq(quad_h, quad_tmax);
+  std::vector<double> qc(v.quad_n), qa(v.quad_n);
+  for (int k = 0; k < v.quad_n; ++k) {
+    const double t = k * quad_h;
+    qc[k] = std::cosh(t);
+    qa[k] = std::cosh(5.0 * t / 3.0) / std::cosh(t);
+  }
+  const double z0 = std::log(1e-7), z1 = std::log(40.0);
+  const double dz = (z1 - z0) / (spec_n - 1);
+  std::vector<float2> tab(spec_n);
+  for (int i = 0; i < spec_n; ++i) {
+    const double z = z0 + i * dz, vv = std::exp(z);
+    const double xi = sq.inverse_of_v(vv);
+    double S, dS;
+    sq.eval(xi, S, dS);
+    tab[i].x = (float)std::log(xi);
+    tab[i].y = (float)(-vv * S / (xi * dS));
+  }
+  h->v.spec_z0 = (float)z0;
+  h->v.spec_dz = (float)dz;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.spec_tab, tab.data(), sizeof(float2) * spec_n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_c, qc.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_a, qa.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "layout upload");
+}
+
+static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(c, h->v.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(h, e, "control block");
+  if (c->error & 8) return fail(h, GAP_ECHECK, "store compaction overflowed a segment");
+  if (c->error & 7)
+    return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
+                             : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));
+  return GAP_OK;
+}
+
+extern "C" {
+
+int gap_workspace_bytes(const gap_params *params, int32_t n_gaps, const gap_config *cfg, size_t *bytes) {
+  if (!bytes) return GAP_EINVAL;
+  gap_config c = default_config(cfg);
+  std::string msg;
+  int r = validate(params, n_gaps, c, msg);
+  if (r) return r;
+  return build_layout(params, n_gaps, c, nullptr, nullptr, bytes);
+}
+
+int gap_init(const gap_params *params, int32_t n_gaps, const gap_config *cfg, void *dev_workspace,
+             size_t bytes, void *stream, gap_handle **out) {
+  if (!out) return GAP_EINVAL;
+  *out = nullptr;
+  gap_config c = default_config(cfg);
+  std::string msg;
+  int r = validate(params, n_gaps, c, msg);
+  if (r) return r;
+  size_t need = 0;
+  build_layout(params, n_gaps, c, nullptr, nullptr, &need);
+  if (!dev_workspace || bytes < need) return GAP_ENOSPACE;
+  if (((uintptr_t)dev_workspace) & 255) return GAP_EINVAL;
+  gap_handle *h = new gap_handle();
+  h->ws = (char *)dev_workspace;
+  h->ws_bytes = bytes;
+  r = build_layout(params, n_gaps, c, (char *)dev_workspace, h, &need);
+  if (r) { *out = h; return r; }
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_load(h->v, h->loads.data(), (int)h->loads.size(), 0, st);
+  launch_sync_used(h->v, st);
+  launch_force_rebin(h->v, st);
+  launch_rebin(h->v, h->slack, st);
+  launch_gauss(h->v, 1, st);
+  r = cuda_check(h, cudaGetLastError(), "init kernels");
+  Ctl cc;
+  if (!r) r = read_ctl(h, &cc, st);
+  *out = h;
+  return r;
+}
+
+int gap_step(gap_handle *h, int64_t nsteps, void *stream) {
+  if (!h || nsteps < 0) return GAP_EINVAL;
+  if (h->status) return h->status;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    if (h->profiling) {
+      if (h->ev_used + 2 > h->ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) return fail(h, GAP_ECUDA, "event create");
+          h->ev.push_back(e);
+        }
+      }
+      cudaEventRecord(h->ev[h->ev_used], st);
+      launch_push(h->v, h->threads, st);
+      cudaEventRecord(h->ev[h->ev_used + 1], st);
+      h->ev_used += 2;
+      launch_after_push(h->v, st);
+    } else {
+      launch_step(h->v, h->threads, st);
+    }
+    launch_rebin(h->v, h->slack, st);
+  }
+  h->steps_done += nsteps;
+  return cuda_check(h, cudaGetLastError(), "step launch");
+}
+
+int gap_step_graph(gap_handle *h, int64_t nsteps, int32_t chunk, void *stream) {
+  if (!h || nsteps < 0 || chunk <= 0) return GAP_EINVAL;
+  if (h->status) return h->status;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return gap_step(h, nsteps, stream);
+  if (!h->graph || h->graph_chunk != chunk) {
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(h, e, "begin capture");
+    for (int i = 0; i < chunk; ++i) {
+      launch_step(h->v, h->threads, st);
+      launch_rebin(h->v, h->slack, st);
+    }
+    e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess) return cuda_check(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_check(h, e, "instantiate");
+    h->graph_chunk = chunk;
+  }
+  int64_t full = nsteps / chunk, rest = nsteps % chunk;
+  for (int64_t i = 0; i < full; ++i) {
+    cudaError_t e = cudaGraphLaunch(h->graph, st);
+    if (e != cudaSuccess) return cuda_check(h, e, "graph launch");
+  }
+  h->steps_done += full * chunk;
+  return gap_step(h, rest, stream);
+}
+
+int gap_get_field(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || !host_E) return GAP_EINVAL;
+  const GapDev &g = h->gaps_h[gap];
+  if (n < g.nnode) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctl c;
+  int r = read_ctl(h, &c, st);
+  if (r) return r;
+  cudaError_t e = cudaMemcpyAsync(host_E, h->v.E[c.e_cur] + g.node_off, sizeof(double) * g.nnode,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "get field");
+}
+
+int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || !host_E) return GAP_EINVAL;
+  const GapDev &g = h->gaps_h[gap];
+  if (n < g.nnode) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    e = cudaMemcpyAsync(h->v.E[b] + g.node_off, host_E, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "set field");
+}
+
+int gap_solve_gauss(gap_handle *h, int32_t set_background, void *stream) {
+  if (!h) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_gauss(h->v, set_background, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && set_background) {
+    std::vector<GapDev> gd(h->n_gaps);
+    e = cudaMemcpy(gd.data(), h->v.gaps, sizeof(GapDev) * h->n_gaps, cudaMemcpyDeviceToHost);
+    for (int i = 0; i < h->n_gaps && e == cudaSuccess; ++i) h->gaps_h[i].eta_bg = gd[i].eta_bg;
+  }
+  return cuda_check(h, e, "gauss");
+}
+
+int gap_set_background(gap_handle *h, int32_t gap, double eta_bg) {
+  if (!h || gap < 0 || gap >= h->n_gaps) return GAP_EINVAL;
+  h->gaps_h[gap].eta_bg = eta_bg;
+  cudaError_t e = cudaMemcpy(&h->v.gaps[gap].eta_bg, &eta_bg, sizeof(double), cudaMemcpyHostToDevice);
+  return cuda_check(h, e, "set background");
+}
+
+int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uint64_t *host_id,
+                      double *host_X, double *host_u, double *host_w, double *host_tau, double *host_aux,
+                      int64_t *host_aux2, int64_t *n_out, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > 2 || !n_out) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctl c;
+  int r = read_ctl(h, &c, st);
+  if (r) return r;
+  const int64_t scap = (int64_t)(h->buf_bytes / (8 * 7));
+  double *stage = reinterpret_cast<double *>(h->buf_base[c.lep_cur ^ 1]);
+  cudaError_t e = cudaMemsetAsync(h->export_count, 0, sizeof(unsigned long long), st);
+  launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  unsigned long long cnt = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, h->export_count, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(h, e, "export");
+  *n_out = (int64_t)cnt;
+  if ((int64_t)cnt > cap || (int64_t)cnt > scap) return GAP_ECAP;
+  const size_t nb = sizeof(double) * cnt;
+  struct { void *dst; int idx; } cp[7] = {{host_id, 0}, {host_X, 1}, {host_u, 2}, {host_w, 3},
+                                          {nullptr, 4}, {nullptr, 5}, {nullptr, 6}};
+  if (kind == GAP_PHOTON) {
+    cp[4].dst = host_tau;   // tau_acc
+    cp[5].dst = host_aux;   // tau_star
+    cp[6].dst = host_aux2;  // (n0 << 1) | dir
+  } else {
+    cp[4].dst = host_tau;
+  }
+  for (auto &x : cp) {
+    if (!x.dst || cnt == 0) continue;
+    e = cudaMemcpyAsync(x.dst, stage + (size_t)x.idx * scap, nb, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "export copy");
+}
+
+int gap_add_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t n, const uint64_t *host_id,
+                      const double *host_X, const double *host_u, const double *host_w,
+                      const double *host_tau, const int64_t *host_aux2, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > 2 || n < 0) return GAP_EINVAL;
+  if (n == 0) return GAP_OK;
+  if (!host_id || !host_X || !host_u || !host_w || !host_tau) return GAP_EINVAL;
+  if (kind == GAP_PHOTON && !host_aux2) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctl c;
+  int r = read_ctl(h, &c, st);
+  if (r) return r;
+  const int64_t per = kind == GAP_PHOTON ? 7 : 5;
+  if ((size_t)(n * per * 8) > h->buf_bytes) return GAP_ECAP;
+  double *stage = reinterpret_cast<double *>(h->buf_base[c.lep_cur ^ 1]);
+  const size_t nb = sizeof(double) * n;
+  cudaError_t e = cudaMemcpyAsync(stage, host_id, nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + n, host_X, nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 2 * n, host_u, nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 3 * n, host_w, nb, cudaMemcpyHostToDevice, st);
+  if (kind == GAP_PHOTON) {
+    // photons: x in host_u, tau_star in host_tau (stage slot 5), tau_acc = 0
+    if (e == cudaSuccess) e = cudaMemsetAsync(stage + 4 * n, 0, nb, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 5 * n, host_tau, nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 6 * n, host_aux2, nb, cudaMemcpyHostToDevice, st);
+  } else {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 4 * n, host_tau, nb, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return cuda_check(h, e, "import copy");
+  launch_import(h->v, gap, kind, n, stage, st);
+  if (kind != GAP_PHOTON) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(h, e, "import");
+    // fold the appended particles into the layout (the stage is the inactive
+    // buffer, so the compaction runs after the import has finished)
+    launch_sync_used(h->v, st);
+    launch_force_rebin(h->v, st);
+    launch_rebin(h->v, h->slack, st);
+  }
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(h, e, "import");
+  return read_ctl(h, &c, st);
+}
+
+int gap_diag(gap_handle *h, int32_t gap, gap_diag_out *out, double *host_spectrum, int64_t spectrum_cap,
+             double *host_moments, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || !out) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctl c;
+  int r = read_ctl(h, &c, st);
+  if (r) return r;
+  const GapDev &g = h->gaps_h[gap];
+  const int64_t ng = std::min<int64_t>((int64_t)std::floor(g.Hc) + 1, g.nnode);
+  const int64_t P = next_pow2(ng);
+  launch_diag(h->v, gap, g.nx, P, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(h, e, "diag launch");
+  double red[32];
+  e = cudaMemcpyAsync(red, h->v.dred, sizeof(red), cudaMemcpyDeviceToHost, st);
+  std::vector<int32_t> alive[2];
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+    alive[s].resize(g.n_tiles);
+    e = cudaMemcpyAsync(alive[s].data(), h->v.seg_alive[s] + g.tile_begin, sizeof(int32_t) * g.n_tiles,
+                        cudaMemcpyDeviceToHost, st);
+  }
+  unsigned long long cnt[C_NCNT];
+  double led[L_NLED];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, h->v.counters + (size_t)gap * C_NCNT, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(led, h->v.ledger + (size_t)gap * L_NLED, sizeof(led), cudaMemcpyDeviceToHost, st);
+  if (host_spectrum && e == cudaSuccess) {
+    const int64_t ns = std::min<int64_t>(spectrum_cap, P / 2 + 1);
+    e = cudaMemcpyAsync(host_spectrum, h->v.fft[1], sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
+  }
+  std::vector<unsigned long long> qbits;
+  if (host_moments && e == cudaSuccess) {
+    e = cudaMemcpyAsync(host_moments, h->v.dmom, sizeof(double) * 8 * g.nx, cudaMemcpyDeviceToHost, st);
+    qbits.resize(g.nx);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(qbits.data(), h->v.dcharge, sizeof(unsigned long long) * g.nx, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(h, e, "diag");
+  if (host_moments) {
+    for (int64_t i = 0; i < g.nx; ++i) {
+      double q;
+      if (h->precision == GAP_FP32_STATE) q = (double)(long long)qbits[i] * g.w_unit * kPhiUnit;
+      else std::memcpy(&q, &qbits[i], sizeof(double));
+      host_moments[6 * g.nx + i] = q;
+    }
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->step = c.step;
+  int64_t ne = 0, np = 0;
+  for (int t = 0; t < g.n_tiles; ++t) { ne += alive[0][t]; np += alive[1][t]; }
+  out->n_electrons = ne;
+  out->n_positrons = np;
+  unsigned long long phc;
+  std::memcpy(&phc, &red[20], sizeof(phc));
+  out->n_photons = (int64_t)phc;
+  out->M_peak = red[0];
+  out->M_avg = red[1];
+  out->peak_cell = (int64_t)red[2];
+  out->g3_peak = red[3];
+  for (int q = 0; q < 4; ++q) out->M_split[q] = red[4 + q];
+  out->E_min = red[8];
+  out->E_max = red[9];
+  out->gauss_residual = red[10];
+  out->E_abs_max = red[11];
+  out->field_energy = red[12];
+  out->lepton_energy = red[16];
+  out->photon_energy = red[17];
+  out->spectrum_len = P / 2 + 1;
+  int64_t *ci = &out->counters.emit_events;
+  for (int q = 0; q < 16; ++q) ci[q] = (int64_t)cnt[q];
+  double *cd = &out->counters.e_radiated;
+  for (int q = 0; q < 8; ++q) cd[q] = led[q];
+  return GAP_OK;
+}
+
+int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int64_t n, int32_t precision,
+                         void *stream) {
+  if (!h || n < 0 || (n > 0 && (!dev_U || !dev_xi))) return GAP_EINVAL;
+  if (precision != GAP_FP64_PLAIN && precision != GAP_FP32_STATE) return GAP_EINVAL;
+  launch_spec_inverse(h->v, dev_U, dev_xi, n, precision == GAP_FP32_STATE, (cudaStream_t)stream);
+  return cuda_check(h, cudaGetLastError(), "spectrum inverse");
+}
+
+int64_t gap_steps_done(const gap_handle *h) { return h ? h->steps_done : 0; }
+
+int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_launches,
+                int64_t *launches_per_step) {
+  if (!h) return GAP_EINVAL;
+  if (launches_per_step) *launches_per_step = ::gapk::launches_per_step(h->v);
+  double tot = 0.0;
+  int64_t n = 0;
+  if (h->ev_used) {
+    cudaError_t e = cudaEventSynchronize(h->ev[h->ev_used - 1]);
+    if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]);
+      if (e != cudaSuccess) return cuda_check(h, e, "profile read");
+      tot += ms;
+      ++n;
+    }
+  }
+  if (push_ms_total) *push_ms_total = tot;
+  if (push_launches) *push_launches = n;
+  h->ev_used = 0;
+  h->profiling = on != 0;
+  return GAP_OK;
+}
+
+void gap_free(gap_handle *h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  delete h;
+}
+
+const char *gap_last_error(const gap_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+const char *gap_status_string(int s) {
+  switch (s) {
+    case GAP_OK: return "ok";
+    case GAP_EINVAL: return "invalid argument";
+    case GAP_ENOSPACE: return "workspace too small";
+    case GAP_ECAP: return "particle storage exhausted";
+    case GAP_ETIMEOUT: return "device wait timed out";
+    case GAP_ECUDA: return "CUDA error";
+    case GAP_ECHECK: return "device consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

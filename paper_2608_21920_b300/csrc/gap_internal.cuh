@@ -1,0 +1,369 @@
+// gap_internal.cuh -- device-side data layout and helpers of the B300 PIC library.
+//
+// Particle positions are node-centred: a lepton is a dual-cell index k (the
+// grid node nearest to it) plus an offset phi' in [1, 2), so that its
+// first-order cloud [X - 1/2, X + 1/2] (X = k + phi' - 3/2 in cell units)
+// covers node k and the fraction right of node k is phi = phi' - 1.  Storing
+// the offset biased into [1, 2) puts every representable value on a uniform
+// grid (2^-23 in FP32, 2^-52 in FP64), so the charge flux through a node,
+// a difference of two such offsets, is exact; in FP32 it is accumulated as an
+// integer number of 2^-23 units and the deposit conserves charge exactly.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gap.h"
+
+namespace gapk {
+
+constexpr double kAlphaEm = 7.2973525693e-3;  // fine-structure constant
+constexpr uint64_t kPhotonBit = 0x8000000000000000ull;
+constexpr int kPhiBits = 23;                   // FP32 offset grid 2^-23
+constexpr double kPhiUnit = 1.0 / 8388608.0;   // 2^-23
+constexpr int kWeightShift = 8;                // FP32 weight unit = w0 / 2^8
+constexpr int kMaxEmit = 16;                   // emission events per lepton-step (upper bound)
+
+// Draw channels of the counter-based generator (interface values).
+enum Channel : uint32_t {
+  CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9
+};
+
+enum Counter {
+  C_EMIT = 0, C_PHOTONS, C_PAIRS, C_INJECTED, C_ABSORBED, C_ESCAPED, C_PH_ESCAPED,
+  C_EMIT_OVF, C_INJ_OVF, C_LOAD_OVF, C_SPILL, C_PH_OVF, C_MERGED, C_R0, C_R1, C_R2, C_NCNT
+};
+enum Ledger { L_RAD = 0, L_ABS, L_ESC, L_PH_ESC, L_INJ, L_WORK, L_R3, L_R4, L_NLED };
+
+struct GapDev {
+  int64_t nx, nnode, node_off;
+  int32_t periodic, qed, kmax_emit, kmax_inject;
+  int32_t tile_begin, n_tiles, gap_index, pad;
+  double dx, dt, cdx, jm, Hc, lambda_hat, rho_hat, rate_mult, b, eta_bg, w0, w_unit;
+  float f_dt, f_cdx, f_Hc, f_lam, f_rho, f_rate;
+  uint64_t seed, inj_root;
+};
+
+struct TileDev {
+  int32_t gap, k0, nk, pad;
+};
+
+// Device control block (all mutable scalars of a handle live here so that a
+// captured CUDA graph replays correctly).
+struct Ctl {
+  int64_t step;
+  int32_t lep_cur, ph_cur, e_cur, need_rebin;
+  int32_t error, flags;
+  int64_t ph_count[2];
+  int64_t spill_n[2];
+  int64_t new_total[2];
+};
+
+// Everything a kernel needs, passed by value.
+struct View {
+  GapDev *gaps;
+  TileDev *tiles;
+  int32_t n_gaps, n_tiles, tile, precision;
+  int32_t qed_any, surface_any, has_w, rebin_every;
+  Ctl *ctl;
+  double *E[2];
+  unsigned long long *Dg;  // int64 (FP32) or double (FP64) bit patterns
+  int32_t *arrive;
+  int8_t *expect;
+  // segments [species][tile]
+  int64_t *seg_start[2];
+  int32_t *seg_cap[2], *seg_used[2], *seg_append[2], *seg_alive[2], *spill_cnt[2];
+  int64_t *new_start[2];
+  int32_t *new_cap[2], *new_fill[2];
+  // lepton stores [buffer][species]
+  int32_t *lk[2][2];
+  void *lphi[2][2], *lu[2][2], *lw[2][2], *ltau[2][2];
+  uint64_t *lid[2][2];
+  int64_t lep_capacity;
+  // spill buffers [species]
+  int32_t *sk[2], *stile[2];
+  double *sphi[2], *su[2], *sw[2], *stau[2];
+  uint64_t *sid[2];
+  int64_t spill_capacity;
+  // photon stores [buffer]
+  double *pX[2], *px[2], *pw[2], *pts[2], *pta[2];
+  uint64_t *pid[2];
+  int32_t *pn0[2], *pdir[2], *pgap[2];
+  int64_t ph_capacity;
+  // per-gap accumulators
+  unsigned long long *counters;  // [gap][C_NCNT]
+  double *ledger;                // [gap][L_NLED]
+  unsigned long long *q0;        // [gap] cell-0 charge (int64 or double bits)
+  // emission-spectrum tables (built by the library at init)
+  float2 *spec_tab;  // (ln xi, d ln xi / d ln v) on a uniform grid of z = ln v, v = -ln U
+  int32_t spec_n;
+  float spec_z0, spec_dz;
+  double *quad_c, *quad_a;  // cosh t_k and cosh(5 t_k/3)/cosh t_k (trapezoid nodes)
+  int32_t quad_n;
+  double quad_h;
+  // diagnostics scratch
+  double *dmom;                 // [8][max_nx]
+  unsigned long long *dcharge;  // [max_nx] exact charge (int64 or double bits)
+  double *fft[2];               // complex scratch [2][2*max_P]
+  int64_t max_nx, max_P, dcharge_len;
+  double *dred;                 // reduction outputs
+  // export / import staging (the inactive buffers are used as scratch)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), device implementation.
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c[0];
+    uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2];
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+// Uniform in (0, 1] keyed by (seed; id, step, channel, k): 53 bits from the
+// first two output words.
+__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t id, uint32_t step,
+                                            uint32_t channel, uint32_t k) {
+  uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, (channel << 16) | (k & 0xFFFFu)};
+  philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  uint64_t m = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);
+  return ((double)m + 1.0) * 1.1102230246251565e-16;  // 2^-53
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).
+__device__ __host__ __forceinline__ uint64_t mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __host__ __forceinline__ uint64_t child_id(uint64_t parent, uint32_t step,
+                                                      uint32_t channel, uint32_t k) {
+  uint64_t salt = ((uint64_t)step << 32) | ((uint64_t)channel << 16) | (k & 0xFFFFu);
+  return mix64(parent ^ mix64(salt));
+}
+
+// ---------------------------------------------------------------------------
+// QED rate functions: Sect. 3.1 fit of T_syn and Sect. 3.2 fit of T_BW.
+__device__ __forceinline__ double tsyn_d(double chi) {
+  const double a0 = 1.4433756729740644;  // 5/(2 sqrt 3)
+  const double a1 = 5.542562584220407;   // 16 sqrt3 / 5
+  return a0 * pow(1.0 + a1 * chi + 1.1 * chi * chi, -1.0 / 6.0);
+}
+__device__ __forceinline__ float tsyn_f(float chi) {
+  const float a0 = 1.4433757f, a1 = 5.5425626f;
+  return a0 * exp2f(-log2f(1.0f + a1 * chi + 1.1f * chi * chi) * (1.0f / 6.0f));
+}
+__device__ __forceinline__ double tbw_d(double chi) {
+  if (!(chi > 0.0)) return 0.0;
+  return 0.23 * exp(-8.0 / (3.0 * chi)) * pow(1.0 + 0.22 * chi, -1.0 / 3.0);
+}
+
+// ---------------------------------------------------------------------------
+// Classical curvature spectrum: xi with S(xi) = U, S the survival function
+//   S(xi) = 3/(5 pi) int_0^inf cosh(5t/3) exp(-xi cosh t)/cosh^2 t dt.
+// Table: Hermite interpolation of y = ln xi in z = ln v, v = -ln U, on a
+// uniform grid; linear extrapolation with the end slopes (the small-v end is
+// the xi^(1/3) asymptote of the spectrum, slope 3).
+template <class R>
+__device__ __forceinline__ R spec_y_table(const View &v, R z) {
+  R s = (z - (R)v.spec_z0) / (R)v.spec_dz;
+  int n = v.spec_n;
+  if (s <= (R)0) {
+    float2 a = v.spec_tab[0];
+    return (R)a.x + (R)a.y * (z - (R)v.spec_z0);
+  }
+  if (s >= (R)(n - 1)) {
+    float2 a = v.spec_tab[n - 1];
+    return (R)a.x + (R)a.y * (z - ((R)v.spec_z0 + (R)(n - 1) * (R)v.spec_dz));
+  }
+  int i = (int)s;
+  R t = s - (R)i;
+  float2 a = v.spec_tab[i], b = v.spec_tab[i + 1];
+  R h = (R)v.spec_dz;
+  R t2 = t * t, t3 = t2 * t;
+  return ((R)2 * t3 - (R)3 * t2 + (R)1) * (R)a.x + (t3 - (R)2 * t2 + t) * h * (R)a.y +
+         ((R)-2 * t3 + (R)3 * t2) * (R)b.x + (t3 - t2) * h * (R)b.y;
+}
+
+// FP32 path: table only.
+__device__ __forceinline__ float spec_inverse_f(const View &v, float U) {
+  if (!(U < 1.0f)) return 0.0f;
+  float lv = -logf(U);
+  return expf(spec_y_table<float>(v, logf(lv)));
+}
+
+// FP64 path: the table value refined by Newton steps in ln xi on the
+// trapezoid quadrature of S and dS/dxi (nodes t_k = k h).  The sum stops once
+// a term is below e^-40 of the first: xi (cosh t - 1) - t > 40, since the
+// node weight cosh(5t/3)/cosh t is at most e^(2t/3).
+__device__ __forceinline__ void spec_S_dS(const View &v, double xi, double &S, double &dS) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0; k < v.quad_n; ++k) {
+    double c = v.quad_c[k];
+    if (xi * (c - 1.0) - k * v.quad_h > 40.0) break;
+    double f = v.quad_a[k] * exp(-xi * c);
+    double wk = k == 0 ? 0.5 : 1.0;
+    s0 += wk * f / c;
+    s1 += wk * f;
+  }
+  const double norm = 3.0 / (5.0 * 3.141592653589793) * v.quad_h;
+  S = norm * s0;
+  dS = -norm * s1;
+}
+__device__ __forceinline__ double spec_inverse_d(const View &v, double U) {
+  if (U >= 1.0 - 1e-13) return 0.0;  // xi < 1e-36: no energy at double precision
+  double lv = -log1p(U - 1.0);
+  double y = spec_y_table<double>(v, log(lv));
+  for (int it = 0; it < 12; ++it) {
+    double xi = exp(y), S, dS;
+    spec_S_dS(v, xi, S, dS);
+    double step = (S - U) / (xi * dS);
+    if (step > 1.0) step = 1.0;
+    if (step < -1.0) step = -1.0;
+    y -= step;
+    if (fabs(step) < 1e-14) break;
+  }
+  return exp(y);
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T *as(void *p) { return reinterpret_cast<T *>(p); }
+
+// N values of T moved by one vector load or store.
+template <class T, int N>
+struct alignas(sizeof(T) * N) Vec {
+  T a[N];
+};
+
+__device__ __forceinline__ int tile_of(const View &v, const GapDev &g, int64_t k) {
+  int64_t lt = k / v.tile;
+  if (lt >= g.n_tiles) lt = g.n_tiles - 1;
+  if (lt < 0) lt = 0;
+  return g.tile_begin + (int)lt;
+}
+
+// Warp-aggregated atomic increment of a 64-bit counter; returns this lane's slot.
+__device__ __forceinline__ long long warp_reserve(unsigned long long *ctr) {
+  unsigned mask = __activemask();
+  int leader = __ffs(mask) - 1;
+  int lane = threadIdx.x & 31;
+  int rank = __popc(mask & ((1u << lane) - 1u));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return (long long)(base + rank);
+}
+
+// ---------------------------------------------------------------------------
+template <class R> struct Prec;
+template <> struct Prec<float> {
+  using W = uint32_t;   // weight in units of w_unit = w0 / 2^8
+  using Acc = long long;  // charge in units of w_unit * 2^-23
+};
+template <> struct Prec<double> {
+  using W = double;
+  using Acc = double;
+};
+
+__device__ __forceinline__ void acc_add(long long *p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ void acc_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void acc_add_global(unsigned long long *p, long long v) {
+  atomicAdd(p, (unsigned long long)v);
+}
+__device__ __forceinline__ void acc_add_global(unsigned long long *p, double v) {
+  atomicAdd(reinterpret_cast<double *>(p), v);
+}
+__device__ __forceinline__ double acc_take(unsigned long long *p, long long *) {
+  return (double)(long long)atomicExch(p, 0ull);
+}
+__device__ __forceinline__ double acc_take(unsigned long long *p, double *) {
+  return __longlong_as_double((long long)atomicExch(p, 0ull));
+}
+
+// Append one lepton to tile t of species s (current buffer); spills to the
+// overflow list when the segment is full.
+template <class R>
+__device__ void append_lepton(const View &v, int s, int t, int32_t k, R phi, R u,
+                              typename Prec<R>::W w, R tau, uint64_t id) {
+  const int cur = v.ctl->lep_cur;
+  int pos = atomicAdd(&v.seg_append[s][t], 1);
+  if (pos < v.seg_cap[s][t]) {
+    int64_t slot = v.seg_start[s][t] + pos;
+    as<R>(v.lphi[cur][s])[slot] = phi;
+    as<R>(v.lu[cur][s])[slot] = u;
+    as<typename Prec<R>::W>(v.lw[cur][s])[slot] = w;
+    as<R>(v.ltau[cur][s])[slot] = tau;
+    v.lid[cur][s][slot] = id;
+    __threadfence_block();
+    v.lk[cur][s][slot] = k;
+    atomicAdd(&v.seg_alive[s][t], 1);
+  } else {
+    long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->spill_n[s]), 1ull);
+    if (i < v.spill_capacity) {
+      v.sk[s][i] = k;
+      v.stile[s][i] = t;
+      v.sphi[s][i] = (double)phi;
+      v.su[s][i] = (double)u;
+      v.sw[s][i] = (double)w;
+      v.stau[s][i] = (double)tau;
+      v.sid[s][i] = id;
+      atomicAdd(&v.spill_cnt[s][t], 1);
+    } else {
+      atomicOr(&v.ctl->error, 1);  // storage exhausted
+    }
+    v.ctl->need_rebin = 1;
+    atomicAdd(&v.counters[v.tiles[t].gap * C_NCNT + C_SPILL], 1ull);
+  }
+}
+
+// Lepton position from an absolute X (cells): node-centred (k, phi').
+template <class R>
+__device__ __forceinline__ void split_position(double X, int64_t nx, bool periodic, int32_t &k,
+                                               R &phi) {
+  double a = X + 0.5;
+  double kf = floor(a);
+  double f = a - kf;  // [0, 1)
+  int64_t kk = (int64_t)kf;
+  R p = (R)(1.0 + f);
+  if (p >= (R)2) {
+    p -= (R)1;
+    kk += 1;
+  }
+  if (periodic) {
+    kk %= nx;
+    if (kk < 0) kk += nx;
+  }
+  k = (int32_t)kk;
+  phi = p;
+}
+
+__device__ __forceinline__ void photon_append(const View &v, int buf, int gap, double X, double x,
+                                              double w, double tau_star, double tau_acc, uint64_t id,
+                                              int32_t n0, int32_t dir) {
+  long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[buf]));
+  if (slot < v.ph_capacity) {
+    v.pX[buf][slot] = X;
+    v.px[buf][slot] = x;
+    v.pw[buf][slot] = w;
+    v.pts[buf][slot] = tau_star;
+    v.pta[buf][slot] = tau_acc;
+    v.pid[buf][slot] = id;
+    v.pn0[buf][slot] = n0;
+    v.pdir[buf][slot] = dir;
+    v.pgap[buf][slot] = gap;
+  } else {
+    atomicAdd(&v.counters[gap * C_NCNT + C_PH_OVF], 1ull);
+    atomicOr(&v.ctl->error, 2);
+  }
+}
+
+}  // namespace gapk

@@ -1,0 +1,607 @@
+// init.cu -- initial loads, Gauss solve, diagnostics (moments, reductions,
+// FFT of E) and particle export/import.
+#include "gap_internal.cuh"
+#include "kernels.h"
+
+namespace gapk {
+
+// ---------------------------------------------------------------------------
+// Loader: quiet start X = cell + (j + 1/2)/ppc; for the thermal pair load the
+// electrons are displaced by (A/k1) sin(k1 X), k1 = 2 pi/nx (a Langmuir seed
+// of relative density amplitude A) and momenta are 1D Maxwell-Juttner by the
+// ratio-of-uniforms method (Kinderman & Monahan 1977).
+__device__ double mj_sample(uint64_t seed, uint64_t id, double theta, bool &ok) {
+  const double gs = theta + sqrt(theta * theta + 1.0);
+  const double us = sqrt(2.0 * theta * gs);
+  const double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
+  for (uint32_t r = 0; r < 64; ++r) {
+    const double a = uniform53(seed, id, 0, CH_INIT_U, 2 * r);
+    const double vv = bmax * (2.0 * uniform53(seed, id, 0, CH_INIT_U, 2 * r + 1) - 1.0);
+    const double u = vv / a;
+    const double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
+    if (2.0 * log(a) <= -gm1 / theta) {
+      ok = true;
+      return u;
+    }
+  }
+  ok = false;
+  return 0.0;
+}
+
+template <class R>
+__global__ void k_load(View v, LoadSpec sp) {
+  using W = typename Prec<R>::W;
+  const GapDev &g = v.gaps[sp.gap];
+  const int64_t total = sp.n_per_species * sp.species_count;
+  const double w = (sp.init == GAP_INIT_PAIR_THERMAL ? 0.5 : 1.0) * sp.density * g.dx / (double)sp.ppc;
+  const double k1 = 2.0 * 3.141592653589793 / (double)g.nx;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(p / sp.n_per_species);
+    const int64_t idx = p % sp.n_per_species;
+    const int64_t cell = idx / sp.ppc, j = idx % sp.ppc;
+    const uint64_t id = ((uint64_t)g.gap_index << 40) | ((uint64_t)s << 39) | (uint64_t)(cell * sp.ppc + j);
+    double X = (double)cell + ((double)j + 0.5) / (double)sp.ppc;
+    double u = 0.0;
+    if (sp.init == GAP_INIT_PAIR_THERMAL) {
+      if (s == 0 && sp.seed_amp != 0.0) {
+        X += sp.seed_amp / k1 * sin(k1 * X);
+        X = fmod(X, (double)g.nx);
+        if (X < 0.0) X += (double)g.nx;
+      }
+      if (sp.theta > 0.0) {
+        bool ok = true;
+        u = mj_sample(g.seed, id, sp.theta, ok);
+        if (!ok) atomicAdd(&v.counters[sp.gap * C_NCNT + C_LOAD_OVF], 1ull);
+      }
+    }
+    const double tau = -log(uniform53(g.seed, id, 0, CH_TAU0, 0));
+    int32_t k;
+    R phi;
+    split_position<R>(X, g.nx, g.periodic != 0, k, phi);
+    W wq;
+    if (sizeof(R) == 4) wq = (W)(1u << kWeightShift);
+    else wq = (W)w;
+    append_lepton<R>(v, s, tile_of(v, g, k), k, phi, (R)u, wq, (R)tau, id);
+  }
+}
+
+void launch_load(const View &v, const LoadSpec *spec, int n_specs, int64_t max_n, cudaStream_t st) {
+  (void)max_n;
+  for (int i = 0; i < n_specs; ++i) {
+    const LoadSpec &sp = spec[i];
+    const int64_t total = sp.n_per_species * sp.species_count;
+    if (total <= 0) continue;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    if (v.precision == GAP_FP32_STATE) k_load<float><<<blocks, 256, 0, st>>>(v, sp);
+    else k_load<double><<<blocks, 256, 0, st>>>(v, sp);
+  }
+}
+
+__global__ void k_set_rebin(View v) { v.ctl->need_rebin = 1; }
+void launch_force_rebin(const View &v, cudaStream_t st) { k_set_rebin<<<1, 1, 0, st>>>(v); }
+
+// ---------------------------------------------------------------------------
+// Cell charges of every gap (cloud in cell: a lepton at dual cell k with
+// offset phi' puts 2 - phi' of its charge in cell k-1 and phi' - 1 in cell
+// k), exact in the FP32 state (integer units w_unit 2^-23).
+template <class R>
+__device__ __forceinline__ void cell_fracs(R phi, long long &fl, long long &fr, double &dl, double &dr) {
+  if (sizeof(R) == 4) {
+    const int F = __float2int_rn(((float)phi - 1.0f) * 8388608.0f);
+    fr = F;
+    fl = (1 << kPhiBits) - F;
+  } else {
+    dr = (double)phi - 1.0;
+    dl = 2.0 - (double)phi;
+  }
+}
+
+template <class R>
+__global__ void k_cell_charge(View v, int only_gap, unsigned long long *Q) {
+  using W = typename Prec<R>::W;
+  const int t = blockIdx.x;
+  const TileDev ti = v.tiles[t];
+  if (only_gap >= 0 && ti.gap != only_gap) return;
+  const GapDev &g = v.gaps[ti.gap];
+  const int cur = v.ctl->lep_cur;
+  const int64_t off = only_gap >= 0 ? 0 : g.node_off;
+  for (int s = 0; s < 2; ++s) {
+    const int q = s == 0 ? -1 : 1;
+    const int64_t start = v.seg_start[s][t];
+    const int used = v.seg_used[s][t];
+    for (int i = threadIdx.x; i < used; i += blockDim.x) {
+      const int64_t slot = start + i;
+      const int32_t k = v.lk[cur][s][slot];
+      if (k < 0) continue;
+      const R phi = as<R>(v.lphi[cur][s])[slot];
+      const W w = as<W>(v.lw[cur][s])[slot];
+      long long fl = 0, fr = 0;
+      double dl = 0, dr = 0;
+      cell_fracs<R>(phi, fl, fr, dl, dr);
+      for (int side = 0; side < 2; ++side) {
+        int64_t c = side == 0 ? (int64_t)k - 1 : (int64_t)k;
+        if (g.periodic) c = (c + g.nx) % g.nx;
+        else if (c < 0 || c >= g.nx) continue;
+        if (sizeof(R) == 4) {
+          const long long val = (long long)q * (long long)w * (side == 0 ? fl : fr);
+          atomicAdd(&Q[off + c], (unsigned long long)val);
+        } else {
+          const double val = (double)q * (double)w * (side == 0 ? dl : dr);
+          atomicAdd(reinterpret_cast<double *>(&Q[off + c]), val);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double charge_value(const View &v, const GapDev &g, unsigned long long bits) {
+  if (v.precision == GAP_FP32_STATE) return (double)(long long)bits * g.w_unit * kPhiUnit;
+  return __longlong_as_double((long long)bits);
+}
+
+// Block-wide exclusive scan of one double per thread; returns the prefix.
+__device__ double block_exclusive_scan(double x, double *total) {
+  __shared__ double ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double y = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    double z = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= o) y += z;
+  }
+  if (lane == 31) ws[wid] = y;
+  __syncthreads();
+  if (wid == 0) {
+    double a = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    for (int o = 1; o < 32; o <<= 1) {
+      double z = __shfl_up_sync(0xffffffffu, a, o);
+      if (lane >= o) a += z;
+    }
+    ws[lane] = a;
+  }
+  __syncthreads();
+  const double before = (wid > 0 ? ws[wid - 1] : 0.0) + y - x;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+// Gauss's law (Sect. 2.2) per gap, one block each: E_0 = 0 and
+// E_{c+1} = E_c + Q_c - eta_bg dx; periodic gaps take zero-mean E.
+__global__ void __launch_bounds__(1024) k_gauss_scan(View v, int set_background) {
+  const int gi = blockIdx.x;
+  GapDev &g = v.gaps[gi];
+  const int64_t nx = g.nx;
+  double *E = v.E[v.ctl->e_cur] + g.node_off;
+  const unsigned long long *Q = v.dcharge + g.node_off;
+  const int T = blockDim.x;
+  const int64_t chunk = (nx + T - 1) / T;
+  const int64_t c0 = threadIdx.x * chunk;
+  const int64_t c1 = c0 + chunk < nx ? c0 + chunk : nx;
+  double local = 0.0;
+  for (int64_t c = c0; c < c1; ++c) local += charge_value(v, g, Q[c]);
+  double total = 0.0;
+  (void)block_exclusive_scan(local, &total);
+  __shared__ double eta;
+  if (threadIdx.x == 0) {
+    if (set_background && g.periodic) g.eta_bg = total / ((double)nx * g.dx);
+    eta = g.eta_bg;
+  }
+  __syncthreads();
+  const double bg = eta * g.dx;
+  // prefix of (Q_c - bg) over the cells of the preceding threads
+  double mine = 0.0;
+  for (int64_t c = c0; c < c1; ++c) mine += charge_value(v, g, Q[c]) - bg;
+  double run = block_exclusive_scan(mine, nullptr);
+  const int64_t last = g.periodic ? nx - 1 : nx;  // E has nodes 0..last
+  if (threadIdx.x == 0) E[0] = 0.0;
+  for (int64_t c = c0; c < c1; ++c) {
+    run += charge_value(v, g, Q[c]) - bg;
+    if (c + 1 <= last) E[c + 1] = run;
+  }
+  if (g.periodic) {
+    __syncthreads();
+    double part = 0.0;
+    for (int64_t i = threadIdx.x; i < nx; i += T) part += E[i];
+    double tot = 0.0;
+    (void)block_exclusive_scan(part, &tot);
+    const double mean = tot / (double)nx;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nx; i += T) E[i] -= mean;
+  }
+  // both E buffers start equal
+  __syncthreads();
+  double *E2 = v.E[v.ctl->e_cur ^ 1] + g.node_off;
+  for (int64_t i = threadIdx.x; i < g.nnode; i += T) E2[i] = E[i];
+}
+
+void launch_gauss(const View &v, int set_background, cudaStream_t st) {
+  // dcharge covers every node of every gap (>= every cell)
+  cudaMemsetAsync(v.dcharge, 0, sizeof(unsigned long long) * (size_t)v.dcharge_len, st);
+  if (v.precision == GAP_FP32_STATE) k_cell_charge<float><<<v.n_tiles, 256, 0, st>>>(v, -1, v.dcharge);
+  else k_cell_charge<double><<<v.n_tiles, 256, 0, st>>>(v, -1, v.dcharge);
+  k_gauss_scan<<<v.n_gaps, 1024, 0, st>>>(v, set_background);
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics of one gap (Sect. 6.2 Fig. 5, Sect. 6.6 Fig. 8).
+// dmom layout: [0..3] density of (species, direction) per cell, [4] sum w
+// gamma^-3, [5] sum w, [6] charge (double copy), [7] photon density.
+template <class R>
+__global__ void k_moments(View v, int gap) {
+  using W = typename Prec<R>::W;
+  const GapDev &g = v.gaps[gap];
+  const int t = g.tile_begin + blockIdx.x;
+  const int cur = v.ctl->lep_cur;
+  const int64_t nx = g.nx;
+  double *M = v.dmom;
+  double en = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    const int q = s == 0 ? -1 : 1;
+    const int64_t start = v.seg_start[s][t];
+    const int used = v.seg_used[s][t];
+    for (int i = threadIdx.x; i < used; i += blockDim.x) {
+      const int64_t slot = start + i;
+      const int32_t k = v.lk[cur][s][slot];
+      if (k < 0) continue;
+      const R phi = as<R>(v.lphi[cur][s])[slot];
+      const double u = (double)as<R>(v.lu[cur][s])[slot];
+      const W wq = as<W>(v.lw[cur][s])[slot];
+      const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+      const double gm = sqrt(1.0 + u * u);
+      en += w * gm;
+      const int dir = u >= 0.0 ? 0 : 1;
+      long long fl = 0, fr = 0;
+      double dl = 0, dr = 0;
+      cell_fracs<R>(phi, fl, fr, dl, dr);
+      if (sizeof(R) == 4) {
+        dl = (double)fl * kPhiUnit;
+        dr = (double)fr * kPhiUnit;
+      }
+      for (int side = 0; side < 2; ++side) {
+        int64_t c = side == 0 ? (int64_t)k - 1 : (int64_t)k;
+        if (g.periodic) c = (c + nx) % nx;
+        else if (c < 0 || c >= nx) continue;
+        const double fr_ = side == 0 ? dl : dr;
+        if (fr_ == 0.0) continue;
+        atomicAdd(&M[(s * 2 + dir) * nx + c], w * fr_ / g.dx);
+        atomicAdd(&M[4 * nx + c], w * fr_ / (gm * gm * gm));
+        atomicAdd(&M[5 * nx + c], w * fr_);
+        if (sizeof(R) == 4) {
+          const long long val = (long long)q * (long long)wq * (side == 0 ? fl : fr);
+          atomicAdd(&v.dcharge[c], (unsigned long long)val);
+        } else {
+          atomicAdd(reinterpret_cast<double *>(&v.dcharge[c]), (double)q * w * fr_);
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_down_sync(0xffffffffu, en, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[16], en);
+}
+
+__global__ void k_photon_moments(View v, int gap) {
+  const int cur = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_count[cur];
+  const GapDev &g = v.gaps[gap];
+  double en = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pgap[cur][i] != gap) continue;
+    const double X = v.pX[cur][i];
+    int64_t c = (int64_t)floor(X);
+    if (c < 0) c = 0;
+    if (c >= g.nx) c = g.nx - 1;
+    atomicAdd(&v.dmom[7 * g.nx + c], v.pw[cur][i] / g.dx);
+    en += v.pw[cur][i] * v.px[cur][i];
+    atomicAdd(reinterpret_cast<unsigned long long *>(&v.dred[20]), 1ull);
+  }
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_down_sync(0xffffffffu, en, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[17], en);
+}
+
+// One block: peak and mean multiplicity over the gap cells, <gamma^-3> at
+// the peak, E extrema, Gauss residual, field energy.  dred layout:
+// 0 M_peak, 1 M_avg, 2 peak cell, 3 g3_peak, 4-7 split, 8 E_min, 9 E_max,
+// 10 gauss residual, 11 |E| max, 12 field energy, 16 lepton energy,
+// 17 photon energy, 20 photon count (integer bits).
+__global__ void __launch_bounds__(1024) k_reduce(View v, int gap) {
+  const GapDev &g = v.gaps[gap];
+  const int64_t nx = g.nx;
+  const double *M = v.dmom;
+  const double *E = v.E[v.ctl->e_cur] + g.node_off;
+  __shared__ double sv[1024];
+  __shared__ long long si[1024];
+  double best = -1.0, sum = 0.0;
+  long long bi = 0;
+  long long ncell = 0;
+  for (int64_t c = threadIdx.x; c < nx; c += blockDim.x) {
+    if (!((double)c + 0.5 < g.Hc)) continue;
+    const double m = M[c] + M[nx + c] + M[2 * nx + c] + M[3 * nx + c];
+    sum += m;
+    ++ncell;
+    if (m > best) {
+      best = m;
+      bi = c;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const double b2 = sv[threadIdx.x + o];
+      const long long i2 = si[threadIdx.x + o];
+      if (b2 > sv[threadIdx.x] || (b2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = b2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  const double Mpk = sv[0];
+  const long long ipk = si[0];
+  __syncthreads();
+  // sums
+  double tot = 0.0;
+  (void)block_exclusive_scan(sum, &tot);
+  double tcell = 0.0;
+  (void)block_exclusive_scan((double)ncell, &tcell);
+  // E extrema over gap nodes, |E| max and field energy over all nodes
+  double emin = 1e300, emax = -1e300, eabs = 0.0, fe = 0.0;
+  for (int64_t i = threadIdx.x; i < g.nnode; i += blockDim.x) {
+    const double e = E[i];
+    if ((double)i <= g.Hc) {
+      emin = fmin(emin, e);
+      emax = fmax(emax, e);
+    }
+    eabs = fmax(eabs, fabs(e));
+    fe += 0.5 * g.dx * e * e;
+  }
+  // Gauss residual over cells touching no boundary
+  double gr = 0.0;
+  const int64_t clo = g.periodic ? 0 : 1, chi = g.periodic ? nx - 1 : nx - 2;
+  for (int64_t c = clo + threadIdx.x; c <= chi; c += blockDim.x) {
+    const int64_t c1 = g.periodic ? (c + 1) % nx : c + 1;
+    const double Qc = charge_value(v, g, v.dcharge[c]);
+    const double r = (E[c1] - E[c]) - (Qc - g.eta_bg * g.dx);
+    gr = fmax(gr, fabs(r));
+  }
+  sv[threadIdx.x] = emin;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sv[threadIdx.x] = fmin(sv[threadIdx.x], sv[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double Emin = sv[0];
+  __syncthreads();
+  sv[threadIdx.x] = emax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sv[threadIdx.x] = fmax(sv[threadIdx.x], sv[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double Emax = sv[0];
+  __syncthreads();
+  sv[threadIdx.x] = eabs;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sv[threadIdx.x] = fmax(sv[threadIdx.x], sv[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double Eabs = sv[0];
+  __syncthreads();
+  sv[threadIdx.x] = gr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sv[threadIdx.x] = fmax(sv[threadIdx.x], sv[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double Gr = sv[0];
+  __syncthreads();
+  double fet = 0.0;
+  (void)block_exclusive_scan(fe, &fet);
+  if (threadIdx.x == 0) {
+    double *o = v.dred;
+    o[0] = Mpk < 0 ? 0.0 : Mpk;
+    o[1] = tcell > 0 ? tot / tcell : 0.0;
+    o[2] = (double)ipk;
+    const double ws = M[5 * nx + ipk];
+    o[3] = ws > 0 ? M[4 * nx + ipk] / ws : 0.0;
+    for (int q = 0; q < 4; ++q) o[4 + q] = M[q * nx + ipk];
+    o[8] = Emin;
+    o[9] = Emax;
+    o[10] = Gr;
+    o[11] = Eabs;
+    o[12] = fet;
+  }
+}
+
+// Radix-2 Stockham FFT stage (self-sorting, out of place): with n the current
+// sub-transform length and s the stride, for p < n/2, q < s:
+//   a = x[q + s p], b = x[q + s (p + n/2)], w = exp(-2 pi i p / n),
+//   y[q + s 2p] = a + b, y[q + s (2p + 1)] = (a - b) w.
+__global__ void k_fft_stage(const double2 *x, double2 *y, int64_t n, int64_t s, int64_t P) {
+  const int64_t half = P / 2;
+  const int64_t m = n / 2;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < half;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx / s, q = idx % s;
+    const double2 a = x[q + s * p];
+    const double2 b = x[q + s * (p + m)];
+    double sn, cs;
+    sincospi(-2.0 * (double)p / (double)n, &sn, &cs);
+    const double2 d = make_double2(a.x - b.x, a.y - b.y);
+    y[q + s * (2 * p)] = make_double2(a.x + b.x, a.y + b.y);
+    y[q + s * (2 * p + 1)] = make_double2(d.x * cs - d.y * sn, d.x * sn + d.y * cs);
+  }
+}
+
+__global__ void k_fft_fill(View v, int gap, double2 *buf, int64_t P) {
+  const GapDev &g = v.gaps[gap];
+  const double *E = v.E[v.ctl->e_cur] + g.node_off;
+  int64_t ng = (int64_t)floor(g.Hc) + 1;
+  if (ng > g.nnode) ng = g.nnode;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (int64_t)gridDim.x * blockDim.x)
+    buf[i] = make_double2(i < ng ? E[i] : 0.0, 0.0);
+}
+
+__global__ void k_fft_power(const double2 *X, double *out, int64_t P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= P / 2;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (X[i].x * X[i].x + X[i].y * X[i].y) / (double)P;
+}
+
+void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st) {
+  cudaMemsetAsync(v.dmom, 0, sizeof(double) * 8 * (size_t)nx, st);
+  cudaMemsetAsync(v.dcharge, 0, sizeof(unsigned long long) * (size_t)nx, st);
+  cudaMemsetAsync(v.dred, 0, sizeof(double) * 32, st);
+  GapDev gh;
+  cudaMemcpyAsync(&gh, &v.gaps[gap], sizeof(GapDev), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (v.precision == GAP_FP32_STATE) k_moments<float><<<gh.n_tiles, 256, 0, st>>>(v, gap);
+  else k_moments<double><<<gh.n_tiles, 256, 0, st>>>(v, gap);
+  k_photon_moments<<<148, 256, 0, st>>>(v, gap);
+  k_reduce<<<1, 1024, 0, st>>>(v, gap);
+  if (P >= 2) {
+    double2 *a = reinterpret_cast<double2 *>(v.fft[0]);
+    double2 *b = reinterpret_cast<double2 *>(v.fft[1]);
+    const int blocks = (int)((P / 2 + 255) / 256 < 1184 ? (P / 2 + 255) / 256 : 1184);
+    k_fft_fill<<<blocks, 256, 0, st>>>(v, gap, a, P);
+    int64_t s = 1;
+    for (int64_t n = P; n > 1; n /= 2) {
+      k_fft_stage<<<blocks, 256, 0, st>>>(a, b, n, s, P);
+      double2 *tmp = a;
+      a = b;
+      b = tmp;
+      s *= 2;
+    }
+    // result in `a`; power spectrum into the other buffer (real part reused)
+    k_fft_power<<<blocks, 256, 0, st>>>(a, reinterpret_cast<double *>(b), P);
+    if (b != reinterpret_cast<double2 *>(v.fft[1])) {
+      cudaMemcpyAsync(v.fft[1], b, sizeof(double) * (size_t)(P / 2 + 1), cudaMemcpyDeviceToDevice, st);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Export / import through a staging area (the inactive particle buffers).
+// Lepton stage: id | X | u | w | tau, each an array of `cap` doubles.
+// Photon stage: id | X | x | w | tau_acc | tau_star | aux2.
+template <class R>
+__global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t cap,
+                                 unsigned long long *count) {
+  using W = typename Prec<R>::W;
+  const GapDev &g = v.gaps[gap];
+  const int t = g.tile_begin + blockIdx.x;
+  const int cur = v.ctl->lep_cur;
+  const int64_t start = v.seg_start[s][t];
+  const int used = v.seg_used[s][t];
+  for (int i = threadIdx.x; i < used; i += blockDim.x) {
+    const int64_t slot = start + i;
+    const int32_t k = v.lk[cur][s][slot];
+    if (k < 0) continue;
+    const unsigned long long o = atomicAdd(count, 1ull);
+    if ((int64_t)o >= cap) continue;
+    const R phi = as<R>(v.lphi[cur][s])[slot];
+    reinterpret_cast<uint64_t *>(stage)[o] = v.lid[cur][s][slot];
+    stage[cap + o] = (double)k + ((double)phi - 1.5);
+    stage[2 * cap + o] = (double)as<R>(v.lu[cur][s])[slot];
+    const W wq = as<W>(v.lw[cur][s])[slot];
+    stage[3 * cap + o] = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+    stage[4 * cap + o] = (double)as<R>(v.ltau[cur][s])[slot];
+  }
+}
+
+__global__ void k_export_photons(View v, int gap, double *stage, int64_t cap, unsigned long long *count) {
+  const int cur = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_count[cur];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pgap[cur][i] != gap) continue;
+    const unsigned long long o = atomicAdd(count, 1ull);
+    if ((int64_t)o >= cap) continue;
+    reinterpret_cast<uint64_t *>(stage)[o] = v.pid[cur][i];
+    stage[cap + o] = v.pX[cur][i];
+    stage[2 * cap + o] = v.px[cur][i];
+    stage[3 * cap + o] = v.pw[cur][i];
+    stage[4 * cap + o] = v.pta[cur][i];
+    stage[5 * cap + o] = v.pts[cur][i];
+    reinterpret_cast<int64_t *>(stage)[6 * cap + o] =
+        ((int64_t)v.pn0[cur][i] << 1) | (v.pdir[cur][i] > 0 ? 1 : 0);
+  }
+}
+
+template <class R>
+__global__ void k_import_leptons(View v, int gap, int s, int64_t n, const double *stage) {
+  using W = typename Prec<R>::W;
+  const GapDev &g = v.gaps[gap];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t id = reinterpret_cast<const uint64_t *>(stage)[i];
+    const double X = stage[n + i];
+    const double u = stage[2 * n + i];
+    const double w = stage[3 * n + i];
+    const double tau = stage[4 * n + i];
+    int32_t k;
+    R phi;
+    split_position<R>(X, g.nx, g.periodic != 0, k, phi);
+    W wq;
+    if (sizeof(R) == 4) wq = (W)llrint(w / g.w_unit);
+    else wq = (W)w;
+    append_lepton<R>(v, s, tile_of(v, g, k), k, phi, (R)u, wq, (R)tau, id);
+  }
+}
+
+__global__ void k_import_photons(View v, int gap, int64_t n, const double *stage) {
+  const int cur = v.ctl->ph_cur;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t id = reinterpret_cast<const uint64_t *>(stage)[i] | kPhotonBit;
+    const int64_t aux = reinterpret_cast<const int64_t *>(stage)[6 * n + i];
+    photon_append(v, cur, gap, stage[n + i], stage[2 * n + i], stage[3 * n + i], stage[5 * n + i],
+                  stage[4 * n + i], id, (int32_t)(aux >> 1), (aux & 1) ? 1 : -1);
+  }
+}
+
+// Inverse CDF of the classical curvature spectrum as the emission kernels
+// evaluate it (FP64: table + Newton on the quadrature; FP32: table).
+__global__ void k_spec_inverse(View v, const double *U, double *xi, int64_t n, int fp32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    xi[i] = fp32 ? (double)spec_inverse_f(v, (float)U[i]) : spec_inverse_d(v, U[i]);
+}
+
+void launch_spec_inverse(const View &v, const double *U, double *xi, int64_t n, int fp32, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 1184) blocks = 1184;
+  if (n > 0) k_spec_inverse<<<blocks, 256, 0, st>>>(v, U, xi, n, fp32);
+}
+
+void launch_import(const View &v, int gap, int kind, int64_t n, const double *stage, cudaStream_t st) {
+  if (n <= 0) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 1184) blocks = 1184;
+  if (kind == GAP_PHOTON) {
+    k_import_photons<<<blocks, 256, 0, st>>>(v, gap, n, stage);
+  } else if (v.precision == GAP_FP32_STATE) {
+    k_import_leptons<float><<<blocks, 256, 0, st>>>(v, gap, kind, n, stage);
+  } else {
+    k_import_leptons<double><<<blocks, 256, 0, st>>>(v, gap, kind, n, stage);
+  }
+}
+
+void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
+                        unsigned long long *count, int n_tiles_gap, cudaStream_t st) {
+  if (kind == GAP_PHOTON) {
+    k_export_photons<<<148, 256, 0, st>>>(v, gap, stage, cap, count);
+  } else if (v.precision == GAP_FP32_STATE) {
+    k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count);
+  } else {
+    k_export_leptons<double><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count);
+  }
+}
+
+}  // namespace gapk
