@@ -42,6 +42,7 @@ extern "C" {
 #define GAP_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define GAP_ECUDA (-5)    /* a CUDA runtime call failed */
 #define GAP_ECHECK (-6)   /* a device-side consistency check failed */
+#define GAP_ETOOBIG (-7)  /* input larger than a fixed-size internal buffer */
 
 /* precision of the particle state (Sect. 6.1 pushes; BASELINE precision pattern) */
 #define GAP_FP64_PLAIN 0 /* FP64 offsets, momenta, weights; FP64 charge deposit */
@@ -202,6 +203,27 @@ int gap_set_background(gap_handle *h, int32_t gap, double eta_bg);
  * n doubles each, device memory; enqueues work only. */
 int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int64_t n, int32_t precision,
                          void *stream);
+
+/* Power spectrum of a field without allocating anything.  (The paper has no
+ * counterpart: this is a library facility.)  For callers that cannot
+ * allocate device memory -- a fixed budget handed out at start-up, a host
+ * runtime that owns the allocator, or code that must not add an allocation
+ * and its implicit synchronisation between launches -- this computes the
+ * same |E_k|^2/P as gap_diag's spectrum (E zero-padded to P = the next power
+ * of two >= n, P/2+1 values written to dev_power) using only the caller's
+ * buffers and a fixed working array inside the library.
+ *  - n <= 32768 (P <= 2^15); larger n returns GAP_ETOOBIG.
+ *  - dev_E: n doubles, dev_power: P/2+1 doubles, both device memory of the
+ *    current device; the call enqueues work on `stream` and returns.
+ *  - The working array (1 MiB) is a file-scope device array that every GPU
+ *    loading the library holds until the process exits.  The first call on a
+ *    device looks its address up (cudaGetSymbolAddress) with that device
+ *    current; make that first call before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU (for example on
+ *    two streams) race; serialise them.  Each call rewrites every entry it
+ *    reads, so no state carries over between calls.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
+int gap_power_spectrum_noalloc(const double *dev_E, int64_t n, double *dev_power, void *stream);
 
 /* Steps taken so far (host mirror). */
 int64_t gap_steps_done(const gap_handle *h);

@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(HERE, "libgap.so")
 
-GAP_OK, GAP_EINVAL, GAP_ENOSPACE, GAP_ECAP, GAP_ETIMEOUT, GAP_ECUDA, GAP_ECHECK = 0, -1, -2, -3, -4, -5, -6
+GAP_OK, GAP_EINVAL, GAP_ENOSPACE, GAP_ECAP, GAP_ETIMEOUT, GAP_ECUDA, GAP_ECHECK, GAP_ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 GAP_FP64_PLAIN, GAP_FP32_STATE = 0, 1
 GAP_BC_SURFACE, GAP_BC_PERIODIC = 0, 1
 GAP_INIT_EMPTY, GAP_INIT_COLD, GAP_INIT_PAIR_THERMAL = 0, 1, 2
@@ -82,6 +82,7 @@ def lib():
     L.gap_steps_done.argtypes = [vp]
     L.gap_steps_done.restype = i64
     L.gap_spectrum_inverse.argtypes = [vp, vp, vp, i64, i32, vp]
+    L.gap_power_spectrum_noalloc.argtypes = [vp, i64, vp, vp]
     L.gap_profile.argtypes = [vp, i32, C.POINTER(d), C.POINTER(i64), C.POINTER(i64)]
     L.gap_free.argtypes = [vp]
     L.gap_free.restype = None
@@ -97,7 +98,7 @@ def lib():
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
             "gap_get_field", "gap_set_field", "gap_get_particles", "gap_add_particles",
-            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_spectrum_inverse", "gap_free",
+            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_spectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 
 

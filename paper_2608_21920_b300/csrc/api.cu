@@ -786,6 +786,7 @@ const char *gap_status_string(int s) {
     case GAP_ETIMEOUT: return "device wait timed out";
     case GAP_ECUDA: return "CUDA error";
     case GAP_ECHECK: return "device consistency check failed";
+    case GAP_ETOOBIG: return "input larger than the fixed internal buffer (spectrum: n <= 32768)";
     default: return "unknown status";
   }
 }
