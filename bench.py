@@ -160,11 +160,12 @@ def run_ours(args):
     tuned = None
     if args.autotune:
         from paper_2608_21920_b300 import autotune
-        (args.tile, args.threads), times = autotune.tune(cfg, "fp32", verbose=(rank == 0))
-        tuned = {f"{t}x{th}": round(ms, 4) for (t, th), ms in times.items()}
+        (args.tile, args.threads, args.variant), times = autotune.tune(cfg, "fp32", verbose=(rank == 0))
+        tuned = {f"{t}x{th}v{vv}": round(ms, 4) for (t, th, vv), ms in times.items()}
     for precision in (["fp32", "fp64"] if not args.fp32_only else ["fp32"]):
         K = args.steps if precision == "fp32" else max(3, min(args.steps, args.fp64_steps))
-        g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads)
+        g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads,
+                variant=args.variant if precision == "fp32" else 0)
         g.step(args.warmup)
         barrier()
         clocks = ClockSampler(local)
@@ -197,7 +198,7 @@ def run_ours(args):
             Ke = args.e2e_steps
             barrier()
             t0 = time.perf_counter()
-            g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads)
+            g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads, variant=args.variant)
             import ctypes as C
             for _ in range(Ke):
                 g.step(1)
@@ -236,7 +237,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "kernel": "k_push<float,false,false>", "bytes_per_particle": bpp,
+                     "kernel": "k_push_lean (FP32, no QED, uniform weights)", "bytes_per_particle": bpp,
                      "push_ms_per_launch": r32["push_ms"],
                      "traffic": traffic_record("k_push", "fp32")},
         "gpu_launches": int(r32["launches"]),
@@ -247,6 +248,7 @@ def run_ours(args):
     if tuned:
         line["config"]["autotune_ms_per_push"] = tuned
         line["config"]["threads"] = args.threads
+        line["config"]["variant"] = args.variant
     if "e2e" in r32:
         e = r32["e2e"]
         line["e2e"] = {"value": e["value"], "unit": UNIT, "h2d_bytes_per_step": e["h2d_bytes_per_step"],
@@ -323,6 +325,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

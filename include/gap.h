@@ -99,6 +99,10 @@ typedef struct gap_config {
   int32_t tile;            /* dual cells per tile (>= 8; 0 -> 256) */
   int32_t threads;         /* threads per block of the push kernel (0 -> 256) */
   int32_t rebin_every;     /* steps between store compactions (0 -> 64) */
+  int32_t variant;         /* push-kernel variant of the FP32 path without QED:
+                              0: 4 leptons/thread, >= 4 blocks/SM; 1: 4, >= 6;
+                              2: 2, >= 8; 3: 4, >= 8 (the autotuner picks one) */
+  int32_t reserved;
   double slack;            /* headroom of each tile segment (0 -> 0.125) */
   int64_t lepton_capacity; /* slots per species over all gaps (0 -> derived) */
   int64_t photon_capacity; /* photon slots (0 -> derived) */

@@ -29,7 +29,8 @@ class GapParams(C.Structure):
 class GapConfig(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("tile", C.c_int32), ("threads", C.c_int32),
-        ("rebin_every", C.c_int32), ("slack", C.c_double),
+        ("rebin_every", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32),
+        ("slack", C.c_double),
         ("lepton_capacity", C.c_int64), ("photon_capacity", C.c_int64),
     ]
 

@@ -10,19 +10,19 @@ import torch
 from .gap import Gap
 
 
-def tune(params, precision="fp32", tiles=(128, 256, 512, 1024), threads=(128, 256), steps=6,
-         warmup=2, verbose=False):
-    """Returns (best (tile, threads), {(tile, threads): ms per push launch})."""
+def tune(params, precision="fp32", tiles=(128, 256, 512), threads=(128, 256), variants=(0, 1, 2, 3),
+         steps=6, warmup=2, verbose=False):
+    """Returns (best (tile, threads, variant), {(tile, threads, variant): ms per push launch})."""
     times = {}
-    for tile, thr in itertools.product(tiles, threads):
-        g = Gap(params, precision=precision, tile=tile, threads=thr)
+    for tile, thr, var in itertools.product(tiles, threads, variants):
+        g = Gap(params, precision=precision, tile=tile, threads=thr, variant=var)
         g.step(warmup)
         g.profile(True)
         g.step(steps)
         ms, n, _ = g.profile(False)
-        times[(tile, thr)] = ms / max(n, 1)
+        times[(tile, thr, var)] = ms / max(n, 1)
         if verbose:
-            print(f"tile {tile:5d} threads {thr:4d}: {times[(tile, thr)]:.3f} ms/push", flush=True)
+            print(f"tile {tile:5d} threads {thr:4d} variant {var}: {times[(tile, thr, var)]:.3f} ms/push", flush=True)
         g.close()
         del g
         torch.cuda.empty_cache()

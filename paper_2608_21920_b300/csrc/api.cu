@@ -79,6 +79,7 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
   if (cfg.precision != GAP_FP64_PLAIN && cfg.precision != GAP_FP32_STATE) { msg = "precision"; return GAP_EINVAL; }
   if (cfg.tile < 8 || cfg.tile > 4096) { msg = "tile must be in [8, 4096]"; return GAP_EINVAL; }
   if (cfg.threads < 32 || cfg.threads > 256 || cfg.threads % 32) { msg = "threads must be a multiple of 32 in [32, 256]"; return GAP_EINVAL; }
+  if (cfg.variant < 0 || cfg.variant > 3) { msg = "variant must be in [0, 3]"; return GAP_EINVAL; }
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     if (q.nx < 8 || q.nx > (1ll << 28)) { msg = "nx out of range"; return GAP_EINVAL; }
@@ -265,6 +266,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.surface_any = surface_any;
   v.has_w = qed_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
+  v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
   v.tiles = C.take<TileDev>(NT);
   v.ctl = C.take<Ctl>(1);

@@ -65,6 +65,7 @@ struct View {
   TileDev *tiles;
   int32_t n_gaps, n_tiles, tile, precision;
   int32_t qed_any, surface_any, has_w, rebin_every;
+  int32_t variant, pad_v;
   Ctl *ctl;
   double *E[2];
   unsigned long long *Dg;  // int64 (FP32) or double (FP64) bit patterns

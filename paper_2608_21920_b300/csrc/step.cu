@@ -348,6 +348,255 @@ __global__ void __launch_bounds__(256) k_push(View v) {
 }
 
 // ---------------------------------------------------------------------------
+// k_push_lean: the push kernel specialised to FP32 state, uniform weights and
+// no QED (the thermal and cold plasmas without emission).  Same arithmetic as
+// k_push, arranged for memory-level parallelism and few shared-memory
+// wavefronts: each thread loads VEC leptons with 16-byte vector loads, then
+// gathers E for all of them (one 8-byte (E_i, E_{i+1}) pair each), then does
+// the arithmetic, then deposits with 32-bit reductions that return nothing.
+// The deposit accumulates c = q (F_new - F_old) in units of 2^-23 (|c| < 2^22)
+// exactly in two 32-bit counters per node, hi = c >> 12 and lo = c & 4095,
+// neither of which can overflow below 2^20 contributions; the node total is
+// hi 2^12 + lo, and the uniform weight multiplies it once, when it leaves
+// shared memory.
+__device__ __forceinline__ void red_shared_add_u32(unsigned *p, unsigned v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_add_s32(int *p, int v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void deposit_split(unsigned *lo, int *hi, int c) {
+  red_shared_add_u32(lo, (unsigned)(c & 4095));
+  red_shared_add_s32(hi, c >> 12);
+}
+
+template <int VEC, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long sQ0;
+  __shared__ unsigned long long sCnt[4];
+  __shared__ double sLed[4];
+  __shared__ int sDead[2];
+
+  const int t = blockIdx.x;
+  const TileDev ti = v.tiles[t];
+  const GapDev &g = v.gaps[ti.gap];
+  const int nk = ti.nk, k0 = ti.k0;
+  const int64_t nx = g.nx;
+  const bool periodic = g.periodic != 0;
+  unsigned *sLo = reinterpret_cast<unsigned *>(smem);
+  int *sHi = reinterpret_cast<int *>(smem + sizeof(unsigned) * (nk + 2));
+  float2 *sE2 = reinterpret_cast<float2 *>(smem + 2 * sizeof(unsigned) * (nk + 2) + 8);
+
+  const Ctl *ctl = v.ctl;
+  const int ecur = ctl->e_cur;
+  const double *Eo = v.E[ecur] + g.node_off;
+  double *En = v.E[ecur ^ 1] + g.node_off;
+  const int cur = ctl->lep_cur;
+
+  auto e_at = [&](int64_t node) -> float {
+    if (periodic) return (float)Eo[(node + nx) % nx];
+    return (node >= 0 && node <= nx) ? (float)Eo[node] : 0.0f;
+  };
+  for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+    const int64_t node = (int64_t)k0 - 1 + i;
+    sE2[i] = make_float2(e_at(node), e_at(node + 1));
+    sLo[i] = 0u;
+    sHi[i] = 0;
+  }
+  if (threadIdx.x < 4) {
+    sCnt[threadIdx.x] = 0ull;
+    sLed[threadIdx.x] = 0.0;
+  }
+  if (threadIdx.x < 2) sDead[threadIdx.x] = 0;
+  if (threadIdx.x == 0) sQ0 = 0;
+  __syncthreads();
+
+  const float dt = (float)g.dt, cdx = (float)g.cdx;
+  const bool q0_tile = !periodic && k0 == 0;
+  const unsigned m0 = 1u << kWeightShift;
+
+  for (int s = 0; s < 2; ++s) {
+    const int q = s == 0 ? -1 : 1;
+    const float qdt = (float)q * dt;
+    const int64_t start = v.seg_start[s][t];
+    const int used = v.seg_used[s][t];
+    int32_t *Kp = v.lk[cur][s];
+    float *Pp = as<float>(v.lphi[cur][s]);
+    float *Up = as<float>(v.lu[cur][s]);
+    int dead = 0;
+    const int ngroups = (used + VEC - 1) / VEC;
+    for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+      const int base = gi * VEC;
+      const int64_t slot0 = start + base;
+      Vec<int32_t, VEC> kv = *reinterpret_cast<const Vec<int32_t, VEC> *>(Kp + slot0);
+      Vec<float, VEC> pv = *reinterpret_cast<const Vec<float, VEC> *>(Pp + slot0);
+      Vec<float, VEC> uv = *reinterpret_cast<const Vec<float, VEC> *>(Up + slot0);
+      const int nvalid = used - base < VEC ? used - base : VEC;
+      bool live[VEC];
+      int jx[VEC];
+      float tt[VEC];
+      float2 e2[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        live[j] = j < nvalid && kv.a[j] >= 0;
+        const int lk = live[j] ? kv.a[j] - (k0 - 1) : 1;
+        const float sph = pv.a[j] - 1.5f;
+        jx[j] = sph >= 0.0f ? lk : lk - 1;
+        tt[j] = sph >= 0.0f ? sph : sph + 1.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) e2[j] = sE2[jx[j]];
+      int32_t kn[VEC];
+      float pn[VEC];
+      int f0[VEC], f1[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        // a1-a2: gather and kick; a4: drift
+        float u = uv.a[j] + qdt * (e2[j].x + tt[j] * (e2[j].y - e2[j].x));
+        const float dX = u * rsqrtf(1.0f + u * u) * cdx;
+        float p = pv.a[j] + dX;
+        int32_t k = kv.a[j];
+        if (p >= 2.0f) {
+          p -= 1.0f;
+          k += 1;
+        } else if (p < 1.0f) {
+          p += 1.0f;
+          k -= 1;
+          if (p >= 2.0f) {
+            p -= 1.0f;
+            k += 1;
+          }
+        }
+        // a8: exact charge through nodes k_old and k_new, units 2^-23
+        const int Fo = __float2int_rn((pv.a[j] - 1.0f) * 8388608.0f);
+        const int Fn = __float2int_rn((p - 1.0f) * 8388608.0f);
+        const int dk = k - kv.a[j];
+        f0[j] = dk == 0 ? Fn - Fo : (dk > 0 ? (1 << kPhiBits) - Fo : -Fo);
+        f1[j] = dk == 0 ? 0 : (dk > 0 ? Fn : Fn - (1 << kPhiBits));
+        if (live[j]) uv.a[j] = u;
+        kn[j] = k;
+        pn[j] = p;
+      }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        if (!live[j]) continue;
+        const int lk = kv.a[j] - (k0 - 1);
+        deposit_split(&sLo[lk], &sHi[lk], q * f0[j]);
+        if (kn[j] != kv.a[j]) {
+          const int l1 = lk + kn[j] - kv.a[j];
+          deposit_split(&sLo[l1], &sHi[l1], q * f1[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        if (!live[j]) continue;
+        int32_t k = kn[j];
+        const float p = pn[j];
+        // a7: boundaries
+        if (!periodic) {
+          const bool below = k < 0 || (k == 0 && p < 1.5f);
+          const bool above = (int64_t)k > nx || ((int64_t)k == nx && p >= 1.5f);
+          if (below || above) {
+            const float gm = sqrtf(1.0f + uv.a[j] * uv.a[j]);
+            atomicAdd(&sCnt[below ? 0 : 1], 1ull);
+            atomicAdd(&sLed[below ? 0 : 1], g.w0 * (double)gm);
+            kv.a[j] = -1;
+            ++dead;
+            continue;
+          }
+        } else {
+          if (k < 0) k += (int32_t)nx;
+          else if ((int64_t)k >= nx) k -= (int32_t)nx;
+        }
+        if (q0_tile && k <= 1) {
+          const int Fn = __float2int_rn((p - 1.0f) * 8388608.0f);
+          const long long frac = k == 0 ? Fn : (1 << kPhiBits) - Fn;
+          atomicAdd(reinterpret_cast<unsigned long long *>(&sQ0), (unsigned long long)((long long)q * m0 * frac));
+        }
+        if (k >= k0 && k < k0 + nk) {
+          kv.a[j] = k;
+          pv.a[j] = p;
+        } else {
+          const uint64_t id = v.lid[cur][s][slot0 + j];
+          const float tau = as<float>(v.ltau[cur][s])[slot0 + j];
+          append_lepton<float>(v, s, tile_of(v, g, k), k, p, uv.a[j], (uint32_t)m0, tau, id);
+          kv.a[j] = -1;
+          ++dead;
+        }
+      }
+      if (nvalid == VEC) {
+        *reinterpret_cast<Vec<int32_t, VEC> *>(Kp + slot0) = kv;
+        *reinterpret_cast<Vec<float, VEC> *>(Pp + slot0) = pv;
+        *reinterpret_cast<Vec<float, VEC> *>(Up + slot0) = uv;
+      } else {
+        for (int j = 0; j < nvalid; ++j) {
+          Kp[slot0 + j] = kv.a[j];
+          Pp[slot0 + j] = pv.a[j];
+          Up[slot0 + j] = uv.a[j];
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, o);
+    if ((threadIdx.x & 31) == 0 && dead) atomicAdd(&sDead[s], dead);
+  }
+  __syncthreads();
+
+  // a9: Ampere on the tile's nodes (node sums carry the weight m0)
+  const double scale = g.w_unit * (double)m0 * kPhiUnit;
+  const double djm = g.dt * g.jm;
+  double work = 0.0;
+  auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
+  for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
+    const int64_t node = (int64_t)k0 - 1 + i;
+    const double eo = Eo[node];
+    const double en = eo + (djm - (double)node_sum(i) * scale);
+    En[node] = en;
+    work += eo + en;
+  }
+  if (threadIdx.x < 4) {
+    const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
+    int64_t node = (int64_t)k0 - 1 + local;
+    bool valid = true;
+    if (periodic) node = (node + nx) % nx;
+    else valid = node >= 0 && node <= nx;
+    if (valid) {
+      const int64_t gn = g.node_off + node;
+      // global edge sums are in the units of k_push: weight units x 2^-23
+      atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
+      __threadfence();
+      const int old = atomicAdd(&v.arrive[gn], 1);
+      if (old == (int)v.expect[gn] - 1) {
+        __threadfence();
+        const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
+        const double eo = Eo[node];
+        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
+        En[node] = en;
+        v.arrive[gn] = 0;
+        work += eo + en;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+  if ((threadIdx.x & 31) == 0 && work != 0.0)
+    atomicAdd(&v.ledger[ti.gap * L_NLED + L_WORK], 0.5 * work * g.dt * g.dx * g.jm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long *C = v.counters + ti.gap * C_NCNT;
+    double *Lg = v.ledger + ti.gap * L_NLED;
+    if (sCnt[0]) atomicAdd(&C[C_ABSORBED], sCnt[0]);
+    if (sCnt[1]) atomicAdd(&C[C_ESCAPED], sCnt[1]);
+    if (sLed[0] != 0.0) atomicAdd(&Lg[L_ABS], sLed[0]);
+    if (sLed[1] != 0.0) atomicAdd(&Lg[L_ESC], sLed[1]);
+    for (int s = 0; s < 2; ++s)
+      if (sDead[s]) atomicAdd(&v.seg_alive[s][t], -sDead[s]);
+    if (q0_tile) atomicAdd(&v.q0[ti.gap], (unsigned long long)sQ0);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_photons: every photon alive at step start moves by c dt, accumulates the
 // Breit-Wheeler optical depth at the mid-step angle sin(psi) = |sin(l/R_curv)|
 // (eq. tau_bw, Sect. 6.1) inside the gap, and converts into an e-e+ pair with
@@ -655,6 +904,16 @@ __global__ void k_rebin_finish(View v) {
 // ---------------------------------------------------------------------------
 template <class R>
 static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w) {
+    const size_t smem_lean = (size_t)(v.tile + 8) * (2 * sizeof(unsigned) + sizeof(float2)) + 64;
+    switch (v.variant) {
+      case 1: k_push_lean<4, 6><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
+      case 2: k_push_lean<2, 8><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
+      case 3: k_push_lean<4, 8><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
+      default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
+    }
+    return;
+  }
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(typename Prec<R>::Acc) + sizeof(R)) + 64;
   if (v.qed_any) {
     if (v.has_w)

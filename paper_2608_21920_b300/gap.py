@@ -44,7 +44,7 @@ class Gap:
     """A batch of independent gaps advanced together by one launch per step."""
 
     def __init__(self, params: dict | Iterable[dict], precision: str = "fp32", tile: int = 0,
-                 threads: int = 0, rebin_every: int = 0, slack: float = 0.0,
+                 threads: int = 0, rebin_every: int = 0, slack: float = 0.0, variant: int = 0,
                  lepton_capacity: int = 0, photon_capacity: int = 0, device: str = "cuda:0"):
         if isinstance(params, dict):
             params = [params]
@@ -60,7 +60,7 @@ class Gap:
         n = len(plist)
         self._params = (A.GapParams * n)(*[make_params(**p) for p in self.param_dicts])
         self._cfg = A.GapConfig(precision=PRECISION[precision], tile=tile, threads=threads,
-                                rebin_every=rebin_every, slack=slack,
+                                rebin_every=rebin_every, variant=variant, slack=slack,
                                 lepton_capacity=lepton_capacity, photon_capacity=photon_capacity)
         self.precision = precision
         self.n_gaps = n
