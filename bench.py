@@ -165,7 +165,7 @@ def run_ours(args):
     for precision in (["fp32", "fp64"] if not args.fp32_only else ["fp32"]):
         K = args.steps if precision == "fp32" else max(3, min(args.steps, args.fp64_steps))
         g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads,
-                variant=args.variant if precision == "fp32" else 0)
+                variant=args.variant if precision == "fp32" else 0, rebin_every=args.rebin_every)
         g.step(args.warmup)
         barrier()
         clocks = ClockSampler(local)
@@ -198,7 +198,8 @@ def run_ours(args):
             Ke = args.e2e_steps
             barrier()
             t0 = time.perf_counter()
-            g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads, variant=args.variant)
+            g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads, variant=args.variant,
+                    rebin_every=args.rebin_every)
             import ctypes as C
             for _ in range(Ke):
                 g.step(1)
@@ -249,6 +250,7 @@ def run_ours(args):
         line["config"]["autotune_ms_per_push"] = tuned
         line["config"]["threads"] = args.threads
         line["config"]["variant"] = args.variant
+    line["config"]["rebin_every"] = args.rebin_every or 64
     if "e2e" in r32:
         e = r32["e2e"]
         line["e2e"] = {"value": e["value"], "unit": UNIT, "h2d_bytes_per_step": e["h2d_bytes_per_step"],
@@ -323,9 +325,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--rebin-every", type=int, default=0, help="steps between sorted compactions (0: library default)")
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

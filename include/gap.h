@@ -101,7 +101,8 @@ typedef struct gap_config {
   int32_t rebin_every;     /* steps between store compactions (0 -> 64) */
   int32_t variant;         /* push-kernel variant of the FP32 path without QED:
                               0: 4 leptons/thread, >= 4 blocks/SM; 1: 4, >= 6;
-                              2: 2, >= 8; 3: 4, >= 8 (the autotuner picks one) */
+                              2: 2, >= 8; 3: 4, >= 8; 4, 5: TMA bulk-copy
+                              pipeline with 3 or 2 stages (the autotuner picks) */
   int32_t reserved;
   double slack;            /* headroom of each tile segment (0 -> 0.125) */
   int64_t lepton_capacity; /* slots per species over all gaps (0 -> derived) */
@@ -185,7 +186,9 @@ int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uin
 
 /* Append n particles of one kind to gap `gap` (tests build hand-checkable
  * states).  Photons: host_u is x, host_tau is tau_star, host_aux2 packs
- * (n0 << 1) | (dir > 0).  Synchronises `stream`. */
+ * (n0 << 1) | (dir > 0).  In a handle without QED every lepton carries the
+ * uniform weight w0 = density dx / ppc (host_w is not used) and no optical
+ * depth.  Synchronises `stream`. */
 int gap_add_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t n, const uint64_t *host_id,
                       const double *host_X, const double *host_u, const double *host_w,
                       const double *host_tau, const int64_t *host_aux2, void *stream);

@@ -10,7 +10,7 @@ import torch
 from .gap import Gap
 
 
-def tune(params, precision="fp32", tiles=(128, 256, 512), threads=(128, 256), variants=(0, 1, 2, 3),
+def tune(params, precision="fp32", tiles=(128, 256, 512), threads=(128, 256), variants=(0, 1, 4, 5),
          steps=6, warmup=2, verbose=False):
     """Returns (best (tile, threads, variant), {(tile, threads, variant): ms per push launch})."""
     times = {}

@@ -79,7 +79,8 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
   if (cfg.precision != GAP_FP64_PLAIN && cfg.precision != GAP_FP32_STATE) { msg = "precision"; return GAP_EINVAL; }
   if (cfg.tile < 8 || cfg.tile > 4096) { msg = "tile must be in [8, 4096]"; return GAP_EINVAL; }
   if (cfg.threads < 32 || cfg.threads > 256 || cfg.threads % 32) { msg = "threads must be a multiple of 32 in [32, 256]"; return GAP_EINVAL; }
-  if (cfg.variant < 0 || cfg.variant > 3) { msg = "variant must be in [0, 3]"; return GAP_EINVAL; }
+  if (cfg.variant < 0 || cfg.variant > 5) { msg = "variant must be in [0, 5]"; return GAP_EINVAL; }
+  if (cfg.variant >= 4 && cfg.tile > 512) { msg = "TMA variants need tile <= 512 (48 KB shared memory)"; return GAP_EINVAL; }
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     if (q.nx < 8 || q.nx > (1ll << 28)) { msg = "nx out of range"; return GAP_EINVAL; }
@@ -428,6 +429,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_check(h, e, "control block");
   if (c->error & 8) return fail(h, GAP_ECHECK, "store compaction overflowed a segment");
+  if (c->error & 16) return fail(h, GAP_ETIMEOUT, "a bulk-copy stage of the push kernel never completed");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));

@@ -326,6 +326,18 @@ __device__ void append_lepton(const View &v, int s, int t, int32_t k, R phi, R u
   }
 }
 
+// Weight of a stored lepton in the units of its precision: without QED and
+// variable weights the state carries no weights and every lepton has w0
+// (FP32: 2^kWeightShift weight units).
+template <class R>
+__device__ __forceinline__ typename Prec<R>::W lepton_weight(const View &v, const GapDev &g, int buf, int s,
+                                                            int64_t slot) {
+  using W = typename Prec<R>::W;
+  if (v.qed_any || v.has_w) return as<W>(v.lw[buf][s])[slot];
+  if (sizeof(R) == 4) return (W)(1u << kWeightShift);
+  return (W)g.w0;
+}
+
 // Lepton position from an absolute X (cells): node-centred (k, phi').
 template <class R>
 __device__ __forceinline__ void split_position(double X, int64_t nx, bool periodic, int32_t &k,

@@ -116,7 +116,7 @@ __global__ void k_cell_charge(View v, int only_gap, unsigned long long *Q) {
       const int32_t k = v.lk[cur][s][slot];
       if (k < 0) continue;
       const R phi = as<R>(v.lphi[cur][s])[slot];
-      const W w = as<W>(v.lw[cur][s])[slot];
+      const W w = lepton_weight<R>(v, g, cur, s, slot);
       long long fl = 0, fr = 0;
       double dl = 0, dr = 0;
       cell_fracs<R>(phi, fl, fr, dl, dr);
@@ -247,7 +247,7 @@ __global__ void k_moments(View v, int gap) {
       if (k < 0) continue;
       const R phi = as<R>(v.lphi[cur][s])[slot];
       const double u = (double)as<R>(v.lu[cur][s])[slot];
-      const W wq = as<W>(v.lw[cur][s])[slot];
+      const W wq = lepton_weight<R>(v, g, cur, s, slot);
       const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
       const double gm = sqrt(1.0 + u * u);
       en += w * gm;
@@ -509,9 +509,11 @@ __global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t 
     reinterpret_cast<uint64_t *>(stage)[o] = v.lid[cur][s][slot];
     stage[cap + o] = (double)k + ((double)phi - 1.5);
     stage[2 * cap + o] = (double)as<R>(v.lu[cur][s])[slot];
+    // without QED or variable weights every lepton carries w0 and no optical depth
+    const bool full_state = v.qed_any || v.has_w;
     const W wq = as<W>(v.lw[cur][s])[slot];
-    stage[3 * cap + o] = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
-    stage[4 * cap + o] = (double)as<R>(v.ltau[cur][s])[slot];
+    stage[3 * cap + o] = !full_state ? g.w0 : (sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq);
+    stage[4 * cap + o] = full_state ? (double)as<R>(v.ltau[cur][s])[slot] : 0.0;
   }
 }
 

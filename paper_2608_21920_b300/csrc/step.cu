@@ -597,6 +597,335 @@ __global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
 }
 
 // ---------------------------------------------------------------------------
+// TMA (bulk-copy) helpers: 1D cp.async.bulk into shared memory, completion
+// tracked by an mbarrier transaction count.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after 2^24 polls (each try_wait may itself suspend
+// for a while), returning false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+// k_push_tma: k_push_lean with the particle arrays of the tile streamed
+// through a ring of shared-memory stages by the TMA unit.  Thread 0 issues
+// one bulk copy per array and chunk (CH leptons: k, phi', u); every thread
+// waits on the stage's mbarrier, pushes its VEC leptons from shared memory
+// and stores them straight back to global memory; after a block-wide barrier
+// the stage is refilled with the chunk STAGES ahead.  Up to STAGES chunks per
+// block are in flight, decoupling HBM latency from the arithmetic.
+template <int STAGES>
+__global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
+  constexpr int VEC = 4;
+  constexpr int CH = 1024;  // leptons per chunk (4 per thread at 256 threads)
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[STAGES];
+  __shared__ long long sQ0;
+  __shared__ unsigned long long sCnt[4];
+  __shared__ double sLed[4];
+  __shared__ int sDead[2];
+  __shared__ int sAbort;
+
+  const int t = blockIdx.x;
+  const TileDev ti = v.tiles[t];
+  const GapDev &g = v.gaps[ti.gap];
+  const int nk = ti.nk, k0 = ti.k0;
+  const int64_t nx = g.nx;
+  const bool periodic = g.periodic != 0;
+  unsigned char *stage_base = smem;  // STAGES x (3 arrays x CH x 4 bytes)
+  constexpr int STAGE_BYTES = 3 * CH * 4;
+  unsigned *sLo = reinterpret_cast<unsigned *>(smem + STAGES * STAGE_BYTES);
+  int *sHi = reinterpret_cast<int *>(smem + STAGES * STAGE_BYTES + sizeof(unsigned) * (nk + 2));
+  float2 *sE2 = reinterpret_cast<float2 *>(smem + STAGES * STAGE_BYTES + 2 * sizeof(unsigned) * (nk + 2) + 8);
+
+  const Ctl *ctl = v.ctl;
+  const int ecur = ctl->e_cur;
+  const double *Eo = v.E[ecur] + g.node_off;
+  double *En = v.E[ecur ^ 1] + g.node_off;
+  const int cur = ctl->lep_cur;
+
+  // chunk list over both species
+  const int used0 = v.seg_used[0][t], used1 = v.seg_used[1][t];
+  const int n0 = (used0 + CH - 1) / CH, n1 = (used1 + CH - 1) / CH;
+  const int nch = n0 + n1;
+  auto chunk_info = [&](int gidx, int &s, int &c, int &cnt, int64_t &slot) {
+    s = gidx < n0 ? 0 : 1;
+    c = gidx < n0 ? gidx : gidx - n0;
+    const int used = s == 0 ? used0 : used1;
+    cnt = used - c * CH < CH ? used - c * CH : CH;
+    slot = v.seg_start[s][t] + (int64_t)c * CH;
+  };
+  auto issue = [&](int gidx) {
+    int s, c, cnt;
+    int64_t slot;
+    chunk_info(gidx, s, c, cnt, slot);
+    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~3) * 4);  // multiple of 16 inside the segment
+    unsigned char *st = stage_base + (gidx % STAGES) * STAGE_BYTES;
+    uint64_t *mb = &mbar[gidx % STAGES];
+    mbar_expect_tx(mb, 3 * bytes);
+    bulk_copy_g2s(st, v.lk[cur][s] + slot, bytes, mb);
+    bulk_copy_g2s(st + CH * 4, as<float>(v.lphi[cur][s]) + slot, bytes, mb);
+    bulk_copy_g2s(st + 2 * CH * 4, as<float>(v.lu[cur][s]) + slot, bytes, mb);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) mbar_init(&mbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sAbort = 0;
+  }
+  auto e_at = [&](int64_t node) -> float {
+    if (periodic) return (float)Eo[(node + nx) % nx];
+    return (node >= 0 && node <= nx) ? (float)Eo[node] : 0.0f;
+  };
+  for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+    const int64_t node = (int64_t)k0 - 1 + i;
+    sE2[i] = make_float2(e_at(node), e_at(node + 1));
+    sLo[i] = 0u;
+    sHi[i] = 0;
+  }
+  if (threadIdx.x < 4) {
+    sCnt[threadIdx.x] = 0ull;
+    sLed[threadIdx.x] = 0.0;
+  }
+  if (threadIdx.x < 2) sDead[threadIdx.x] = 0;
+  if (threadIdx.x == 0) sQ0 = 0;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < STAGES && i < nch; ++i) issue(i);
+
+  const float dt = (float)g.dt, cdx = (float)g.cdx;
+  const bool q0_tile = !periodic && k0 == 0;
+  const unsigned m0 = 1u << kWeightShift;
+  int dead0 = 0, dead1 = 0;
+  int consumed = 0;
+
+  for (int gidx = 0; gidx < nch; ++gidx) {
+    int s, c, cnt;
+    int64_t slot_c;
+    chunk_info(gidx, s, c, cnt, slot_c);
+    const bool ok = mbar_wait_bounded(&mbar[gidx % STAGES], (uint32_t)((gidx / STAGES) & 1));
+    if (!ok) atomicExch(&sAbort, 1);
+    __syncthreads();
+    if (sAbort) break;
+    consumed = gidx + 1;
+    const int q = s == 0 ? -1 : 1;
+    const float qdt = (float)q * dt;
+    const unsigned char *st = stage_base + (gidx % STAGES) * STAGE_BYTES;
+    const int base = threadIdx.x * VEC;
+    if (base < cnt) {
+      Vec<int32_t, VEC> kv = *reinterpret_cast<const Vec<int32_t, VEC> *>(st + base * 4);
+      Vec<float, VEC> pv = *reinterpret_cast<const Vec<float, VEC> *>(st + CH * 4 + base * 4);
+      Vec<float, VEC> uv = *reinterpret_cast<const Vec<float, VEC> *>(st + 2 * CH * 4 + base * 4);
+      const int nvalid = cnt - base < VEC ? cnt - base : VEC;
+      const int64_t slot0 = slot_c + base;
+      bool live[VEC];
+      int jx[VEC];
+      float tt[VEC];
+      float2 e2[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        live[j] = j < nvalid && kv.a[j] >= 0;
+        const int lk = live[j] ? kv.a[j] - (k0 - 1) : 1;
+        const float sph = pv.a[j] - 1.5f;
+        jx[j] = sph >= 0.0f ? lk : lk - 1;
+        tt[j] = sph >= 0.0f ? sph : sph + 1.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) e2[j] = sE2[jx[j]];
+      int32_t kn[VEC];
+      float pn[VEC];
+      int f0[VEC], f1[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        float u = uv.a[j] + qdt * (e2[j].x + tt[j] * (e2[j].y - e2[j].x));
+        const float dX = u * rsqrtf(1.0f + u * u) * cdx;
+        float p = pv.a[j] + dX;
+        int32_t k = kv.a[j];
+        if (p >= 2.0f) {
+          p -= 1.0f;
+          k += 1;
+        } else if (p < 1.0f) {
+          p += 1.0f;
+          k -= 1;
+          if (p >= 2.0f) {
+            p -= 1.0f;
+            k += 1;
+          }
+        }
+        const int Fo = __float2int_rn((pv.a[j] - 1.0f) * 8388608.0f);
+        const int Fn = __float2int_rn((p - 1.0f) * 8388608.0f);
+        const int dk = k - kv.a[j];
+        f0[j] = dk == 0 ? Fn - Fo : (dk > 0 ? (1 << kPhiBits) - Fo : -Fo);
+        f1[j] = dk == 0 ? 0 : (dk > 0 ? Fn : Fn - (1 << kPhiBits));
+        if (live[j]) uv.a[j] = u;
+        kn[j] = k;
+        pn[j] = p;
+      }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        if (!live[j]) continue;
+        const int lk = kv.a[j] - (k0 - 1);
+        deposit_split(&sLo[lk], &sHi[lk], q * f0[j]);
+        if (kn[j] != kv.a[j]) {
+          const int l1 = lk + kn[j] - kv.a[j];
+          deposit_split(&sLo[l1], &sHi[l1], q * f1[j]);
+        }
+      }
+      int dead = 0;
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        if (!live[j]) continue;
+        int32_t k = kn[j];
+        const float p = pn[j];
+        if (!periodic) {
+          const bool below = k < 0 || (k == 0 && p < 1.5f);
+          const bool above = (int64_t)k > nx || ((int64_t)k == nx && p >= 1.5f);
+          if (below || above) {
+            const float gm = sqrtf(1.0f + uv.a[j] * uv.a[j]);
+            atomicAdd(&sCnt[below ? 0 : 1], 1ull);
+            atomicAdd(&sLed[below ? 0 : 1], g.w0 * (double)gm);
+            kv.a[j] = -1;
+            ++dead;
+            continue;
+          }
+        } else {
+          if (k < 0) k += (int32_t)nx;
+          else if ((int64_t)k >= nx) k -= (int32_t)nx;
+        }
+        if (q0_tile && k <= 1) {
+          const int Fn = __float2int_rn((p - 1.0f) * 8388608.0f);
+          const long long frac = k == 0 ? Fn : (1 << kPhiBits) - Fn;
+          atomicAdd(reinterpret_cast<unsigned long long *>(&sQ0), (unsigned long long)((long long)q * m0 * frac));
+        }
+        if (k >= k0 && k < k0 + nk) {
+          kv.a[j] = k;
+          pv.a[j] = p;
+        } else {
+          const uint64_t id = v.lid[cur][s][slot0 + j];
+          const float tau = as<float>(v.ltau[cur][s])[slot0 + j];
+          append_lepton<float>(v, s, tile_of(v, g, k), k, p, uv.a[j], (uint32_t)m0, tau, id);
+          kv.a[j] = -1;
+          ++dead;
+        }
+      }
+      if (s == 0) dead0 += dead;
+      else dead1 += dead;
+      int32_t *Kp = v.lk[cur][s];
+      float *Pp = as<float>(v.lphi[cur][s]);
+      float *Up = as<float>(v.lu[cur][s]);
+      if (nvalid == VEC) {
+        *reinterpret_cast<Vec<int32_t, VEC> *>(Kp + slot0) = kv;
+        *reinterpret_cast<Vec<float, VEC> *>(Pp + slot0) = pv;
+        *reinterpret_cast<Vec<float, VEC> *>(Up + slot0) = uv;
+      } else {
+        for (int j = 0; j < nvalid; ++j) {
+          Kp[slot0 + j] = kv.a[j];
+          Pp[slot0 + j] = pv.a[j];
+          Up[slot0 + j] = uv.a[j];
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0 && gidx + STAGES < nch) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(gidx + STAGES);
+    }
+  }
+  if (sAbort) {
+    // a stage never completed: record it, then let the copies still in
+    // flight land (bounded) before the block's shared memory is released
+    if (threadIdx.x == 0) {
+      atomicOr(&v.ctl->error, 16);
+      const int issued = nch < consumed + STAGES ? nch : consumed + STAGES;
+      for (int gi = consumed; gi < issued; ++gi)
+        (void)mbar_wait_bounded(&mbar[gi % STAGES], (uint32_t)((gi / STAGES) & 1));
+    }
+    return;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dead0 += __shfl_down_sync(0xffffffffu, dead0, o);
+    dead1 += __shfl_down_sync(0xffffffffu, dead1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (dead0) atomicAdd(&sDead[0], dead0);
+    if (dead1) atomicAdd(&sDead[1], dead1);
+  }
+  __syncthreads();
+
+  const double scale = g.w_unit * (double)m0 * kPhiUnit;
+  const double djm = g.dt * g.jm;
+  double work = 0.0;
+  auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
+  for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
+    const int64_t node = (int64_t)k0 - 1 + i;
+    const double eo = Eo[node];
+    const double en = eo + (djm - (double)node_sum(i) * scale);
+    En[node] = en;
+    work += eo + en;
+  }
+  if (threadIdx.x < 4) {
+    const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
+    int64_t node = (int64_t)k0 - 1 + local;
+    bool valid = true;
+    if (periodic) node = (node + nx) % nx;
+    else valid = node >= 0 && node <= nx;
+    if (valid) {
+      const int64_t gn = g.node_off + node;
+      atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
+      __threadfence();
+      const int old = atomicAdd(&v.arrive[gn], 1);
+      if (old == (int)v.expect[gn] - 1) {
+        __threadfence();
+        const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
+        const double eo = Eo[node];
+        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
+        En[node] = en;
+        v.arrive[gn] = 0;
+        work += eo + en;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+  if ((threadIdx.x & 31) == 0 && work != 0.0)
+    atomicAdd(&v.ledger[ti.gap * L_NLED + L_WORK], 0.5 * work * g.dt * g.dx * g.jm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long *C = v.counters + ti.gap * C_NCNT;
+    double *Lg = v.ledger + ti.gap * L_NLED;
+    if (sCnt[0]) atomicAdd(&C[C_ABSORBED], sCnt[0]);
+    if (sCnt[1]) atomicAdd(&C[C_ESCAPED], sCnt[1]);
+    if (sLed[0] != 0.0) atomicAdd(&Lg[L_ABS], sLed[0]);
+    if (sLed[1] != 0.0) atomicAdd(&Lg[L_ESC], sLed[1]);
+    for (int s = 0; s < 2; ++s)
+      if (sDead[s]) atomicAdd(&v.seg_alive[s][t], -sDead[s]);
+    if (q0_tile) atomicAdd(&v.q0[ti.gap], (unsigned long long)sQ0);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_photons: every photon alive at step start moves by c dt, accumulates the
 // Breit-Wheeler optical depth at the mid-step angle sin(psi) = |sin(l/R_curv)|
 // (eq. tau_bw, Sect. 6.1) inside the gap, and converts into an e-e+ pair with
@@ -793,7 +1122,11 @@ __global__ void __launch_bounds__(1024) k_rebin_layout(View v, double slack) {
 }
 
 // r2: one block per (species, tile): ordered compaction of the alive slots
-// into the other buffer.
+// into the other buffer (the order within the tile is kept: the push kernel
+// measured fastest on the interleaved order of the initial load, slower on
+// random order and slowest on fully node-sorted order).  Without QED and with
+// uniform weights the optical depth and the weight are not part of the state
+// and are not copied.
 template <class R>
 __global__ void k_rebin_compact(View v) {
   using W = typename Prec<R>::W;
@@ -805,6 +1138,7 @@ __global__ void k_rebin_compact(View v) {
   const int64_t src0 = v.seg_start[s][t];
   const int used = v.seg_used[s][t];
   const int64_t dst0 = v.new_start[s][t];
+  const bool full_state = v.qed_any || v.has_w;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int base = 0; base < used; base += blockDim.x) {
@@ -833,9 +1167,11 @@ __global__ void k_rebin_compact(View v) {
       v.lk[nxt][s][d] = k;
       as<R>(v.lphi[nxt][s])[d] = as<R>(v.lphi[cur][s])[sidx];
       as<R>(v.lu[nxt][s])[d] = as<R>(v.lu[cur][s])[sidx];
-      as<W>(v.lw[nxt][s])[d] = as<W>(v.lw[cur][s])[sidx];
-      as<R>(v.ltau[nxt][s])[d] = as<R>(v.ltau[cur][s])[sidx];
       v.lid[nxt][s][d] = v.lid[cur][s][sidx];
+      if (full_state) {
+        as<W>(v.lw[nxt][s])[d] = as<W>(v.lw[cur][s])[sidx];
+        as<R>(v.ltau[nxt][s])[d] = as<R>(v.ltau[cur][s])[sidx];
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) carry += warp_cnt[31];
@@ -910,6 +1246,15 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       case 1: k_push_lean<4, 6><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
       case 2: k_push_lean<2, 8><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
       case 3: k_push_lean<4, 8><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
+      case 4:
+      case 5: {
+        // TMA pipeline: 256 threads, 3 or 2 stages of 12 KB
+        const int stages = v.variant == 4 ? 3 : 2;
+        const size_t smem_tma = (size_t)stages * 3 * 1024 * 4 + (size_t)(v.tile + 8) * 16 + 64;
+        if (stages == 3) k_push_tma<3><<<v.n_tiles, 256, smem_tma, st>>>(v);
+        else k_push_tma<2><<<v.n_tiles, 256, smem_tma, st>>>(v);
+        break;
+      }
       default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
     }
     return;
