@@ -119,14 +119,17 @@ class ClockSampler:
 
 def traffic_record(kernel, precision):
     """DRAM traffic per launch of the push kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged."""
+    valid only while the kernel's source text is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[f"{kernel}:{precision}"]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2608_21920_b300", "csrc", "step.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    src = open(os.path.join(ROOT, "paper_2608_21920_b300", "csrc", "step.cu")).read()
+    i = src.index("k_push_lean(View v)")
+    i = src.rfind("template", 0, i)
+    j = src.index("// -----------", i)
+    sha = hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
     if rec.get("step_cu_sha") != sha:
         return None
     return rec.get("bytes_per_launch")
