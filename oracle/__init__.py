@@ -24,8 +24,8 @@ BC_SURFACE, BC_PERIODIC = 0, 1
 INIT_EMPTY, INIT_COLD, INIT_PAIR_THERMAL = 0, 1, 2
 ALPHA_EM = 7.2973525693e-3
 PHOTON_BIT = 1 << 63
-CH_INIT_U, CH_TAU0, CH_EMIT_X, CH_EMIT_TAU, CH_BW_TAU, CH_INJECT, CH_PAIR, CH_PHOTON = (
-    1, 3, 4, 5, 6, 7, 8, 9)
+CH_INIT_U, CH_TAU0, CH_EMIT_X, CH_EMIT_TAU, CH_BW_TAU, CH_INJECT, CH_PAIR, CH_PHOTON, CH_MERGE = (
+    1, 3, 4, 5, 6, 7, 8, 9, 10)
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("rho_hat", C.c_double), ("rate_mult", C.c_double), ("gap_length", C.c_double),
         ("density", C.c_double), ("dx", C.c_double), ("dt", C.c_double),
         ("theta", C.c_double), ("seed_amp", C.c_double),
-        ("nx", C.c_int64), ("ppc", C.c_int64), ("seed", C.c_uint64),
+        ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("gap_index", C.c_int32), ("qed", C.c_int32), ("boundary", C.c_int32),
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
     ]
@@ -52,7 +52,7 @@ class Params(C.Structure):
 class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "emit_events", "photons", "pairs", "injected", "absorbed", "escaped",
-        "photons_escaped", "emit_overflow", "inject_overflow", "load_overflow")] + [
+        "photons_escaped", "emit_overflow", "inject_overflow", "load_overflow", "merged")] + [
         (n, C.c_double) for n in (
             "e_radiated", "e_absorbed", "e_escaped", "e_photon_escaped", "e_injected",
             "work_jm")]
@@ -156,7 +156,7 @@ def mj_sample(seed, pid, theta):
 # ---------------------------------------------------------------- PIC model
 DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
-                nx=64, ppc=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
+                nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
                 init=INIT_EMPTY, kmax_emit=16, kmax_inject=64)
 
 

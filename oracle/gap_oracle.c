@@ -106,7 +106,7 @@ uint64_t orc_child_id(uint64_t parent, uint32_t step, uint32_t channel,
 /* Draw channels (shared interface with the library; values only). */
 enum {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
-  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_MERGE = 10
 };
 
 /* ------------------------------------------------------------------------- */
@@ -233,6 +233,7 @@ typedef struct {
   double seed_amp;   /* Langmuir seed: relative density perturbation */
   int64_t nx;        /* cells */
   int64_t ppc;       /* macro-particles per cell per species at load */
+  int64_t cap;       /* macro-particle cap (leptons + photons); 0 = none */
   uint64_t seed;     /* Philox key */
   int32_t gap_index; /* enters the initial ids */
   int32_t qed;       /* 0/1 */
@@ -251,7 +252,7 @@ typedef struct { uint64_t id; double X, x, w, tau_star, tau_acc; int32_t dir, n0
  * (x -> 2 (x/2)) and injection (rest energy w) are exact ledger moves. */
 typedef struct {
   int64_t emit_events, photons, pairs, injected, absorbed, escaped,
-      photons_escaped, emit_overflow, inject_overflow, load_overflow;
+      photons_escaped, emit_overflow, inject_overflow, load_overflow, merged;
   double e_radiated, e_absorbed, e_escaped, e_photon_escaped, e_injected, work_jm;
 } orc_counters;
 
@@ -264,6 +265,7 @@ typedef struct {
   orc_lepton *lep; int64_t nlep, caplep;
   orc_photon *ph;  int64_t nph, capph;
   int64_t step;
+  int32_t merge_level; /* consecutive over-cap steps (bin width 0.1 * 2^level) */
   orc_counters cnt;
 } orc_sim;
 
@@ -443,6 +445,96 @@ static double wrap(const orc_params *p, double X) {
   return X;
 }
 
+/* Weight-conserving merge (the macro-particle cap of the workloads; the paper
+ * gives no scheme).  When leptons + photons exceed the cap after a step, the
+ * leptons of each (species, dual cell k = floor(X + 1/2), direction, bin of
+ * ln(gamma) of width 0.1 * 2^level) group with at least three members are
+ * replaced by two leptons of weights W/2 at the weight-averaged offset in the
+ * dual cell, with momenta from two-body kinematics on S+ = sum w (gamma + u)
+ * and S- = sum w (gamma - u): rapidity of the centre 0.5 ln(S+/S-), invariant
+ * mass M = sqrt(S+ S-), CM momentum p* = sqrt(M^2 - W^2)/2; this conserves
+ * weight, energy and momentum.  Moving the charge inside the dual cell
+ * carries charge across node k, which is applied to E_k as a deposit, so
+ * Gauss's law holds.  level grows by one per consecutive over-cap step (up to
+ * 7) and returns to 0 when the gap is under the cap. */
+typedef struct { int32_t q, dir; int64_t k; int64_t bin; uint64_t id; int64_t idx; } mkey;
+static int mkey_cmp(const void *a, const void *b) {
+  const mkey *x = (const mkey *)a, *y = (const mkey *)b;
+  if (x->q != y->q) return x->q < y->q ? -1 : 1;
+  if (x->k != y->k) return x->k < y->k ? -1 : 1;
+  if (x->dir != y->dir) return x->dir < y->dir ? -1 : 1;
+  if (x->bin != y->bin) return x->bin < y->bin ? -1 : 1;
+  if (x->id != y->id) return x->id < y->id ? -1 : 1;
+  return 0;
+}
+static void merge(orc_sim *s, uint32_t n) {
+  const orc_params *p = &s->p;
+  if (p->cap <= 0 || s->nlep + s->nph <= p->cap) { s->merge_level = 0; return; }
+  const double width = 0.1 * (double)(1 << s->merge_level);
+  if (s->merge_level < 7) s->merge_level++;
+  int64_t nl = s->nlep;
+  mkey *key = (mkey *)malloc((size_t)(nl > 0 ? nl : 1) * sizeof(mkey));
+  for (int64_t i = 0; i < nl; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    double g = sqrt(1.0 + L->u * L->u);
+    int64_t b = (int64_t)floor(log(g) / width);
+    if (b < 0) b = 0;
+    if (b > 255) b = 255;
+    int64_t k = (int64_t)floor(L->X + 0.5);
+    if (p->boundary == ORC_BC_PERIODIC) k = imod(k, p->nx);
+    key[i].q = L->q; key[i].dir = L->u >= 0.0 ? 1 : 0; key[i].k = k; key[i].bin = b;
+    key[i].id = L->id; key[i].idx = i;
+  }
+  qsort(key, (size_t)nl, sizeof(mkey), mkey_cmp);
+  int64_t a = 0;
+  while (a < nl) {
+    int64_t e = a + 1;
+    while (e < nl && key[e].q == key[a].q && key[e].k == key[a].k && key[e].dir == key[a].dir &&
+           key[e].bin == key[a].bin)
+      ++e;
+    if (e - a >= 3) {
+      double W = 0.0, Sp = 0.0, Sm = 0.0, Sphi = 0.0;
+      const int64_t k = key[a].k;
+      for (int64_t j = a; j < e; ++j) {
+        orc_lepton *L = &s->lep[key[j].idx];
+        double g = sqrt(1.0 + L->u * L->u);
+        double big = g + fabs(L->u);
+        double gp = L->u >= 0.0 ? big : 1.0 / big, gm = L->u >= 0.0 ? 1.0 / big : big;
+        double X = L->X;
+        if (p->boundary == ORC_BC_PERIODIC && X + 0.5 - (double)k >= (double)p->nx) X -= (double)p->nx;
+        double phi = X + 0.5 - (double)k; /* [0, 1): fraction right of node k */
+        W += L->w; Sp += L->w * gp; Sm += L->w * gm; Sphi += L->w * phi;
+        L->alive = 0;
+      }
+      const double phim = Sphi / W;
+      /* charge moved across node k by re-centring: q (W phim - sum w phi) */
+      const double flux = (double)key[a].q * (W * phim - Sphi);
+      int64_t node = k;
+      if (p->boundary == ORC_BC_PERIODIC || (node > 0 && node <= p->nx)) s->E[node] -= flux;
+      const double eta = 0.5 * log(Sp / Sm), M = sqrt(Sp * Sm);
+      const double wa = 0.5 * W, wb = W - wa;
+      double q2 = (M * M - W * W) * (M * M - (wa - wb) * (wa - wb));
+      const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
+      const double ua = sinh(eta + asinh(ps / wa)), ub = sinh(eta - asinh(ps / wb));
+      double X = (double)k + phim - 0.5;
+      if (p->boundary == ORC_BC_PERIODIC && X < 0.0) X += (double)p->nx;
+      for (int c = 0; c < 2; ++c) {
+        orc_lepton L = {0};
+        L.id = orc_child_id(key[a].id, n, CH_MERGE, (uint32_t)c) & ~ORC_PHOTON_BIT;
+        L.q = key[a].q; L.X = X; L.u = c == 0 ? ua : ub; L.w = c == 0 ? wa : wb; L.alive = 1;
+        L.tau = -log(orc_uniform(p->seed, L.id, n + 1, CH_TAU0, 0));
+        push_lepton(s, L);
+      }
+      s->cnt.merged += (e - a) - 2;
+    }
+    a = e;
+  }
+  free(key);
+  int64_t m = 0;
+  for (int64_t i = 0; i < s->nlep; ++i) if (s->lep[i].alive) s->lep[m++] = s->lep[i];
+  s->nlep = m;
+}
+
 /* One time step n -> n+1.  Order (Sect. 6.1 PIC cycle, reduced to 1D along B):
  *  1. every lepton: gather E^n, kick (Sect. 4: du/dt = (q/m) E), curvature
  *     emission by optical-depth sub-cycling (eq. tau_syn, Sect. 6.1 MC
@@ -451,7 +543,8 @@ static double wrap(const orc_params *p, double X) {
  *     Breit-Wheeler optical depth (eq. tau_bw) at the accumulated angle of
  *     Sect. 6.1, convert into an e-e+ pair when it reaches its threshold;
  *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface;
- *  4. surface injection of cold electrons (Sect. 2.3 / 6.1 atmosphere). */
+ *  4. surface injection of cold electrons (Sect. 2.3 / 6.1 atmosphere);
+ *  5. merge when leptons + photons exceed the cap (see merge()). */
 void orc_step(orc_sim *s) {
   const orc_params *p = &s->p;
   const double dt = p->dt, dx = p->dx, cdx = dt / dx;
@@ -609,6 +702,7 @@ void orc_step(orc_sim *s) {
       ++j;
     }
   }
+  merge(s, n);
   s->step++;
 }
 

@@ -513,3 +513,51 @@ def test_ode_empirical_peak_multiplicity_fit():
         _, mp = _cycles(q, T=25.0)
         pred = c * q["t_acc"] / (q["t_x"] * q["g3"]) * q["alpha"] ** 0.25
         assert abs(mp[1:].mean() - pred) / pred < tol
+
+
+# ------------------------------------------------------------------ merge
+def _sums(L):
+    g = np.sqrt(1 + L["u"] ** 2)
+    out = {}
+    for q in (-1, 1):
+        m = L["q"] == q
+        out[q] = (L["w"][m].sum(), (L["w"] * L["u"])[m].sum(), (L["w"] * g)[m].sum(), int(m.sum()))
+    return out
+
+
+def test_merge_conserves_weight_momentum_energy():
+    """Groups of >= 3 leptons become two with the same weight, momentum and
+    energy (two-body kinematics on sum w (gamma +- u)); compared with a twin
+    run without the cap."""
+    cfg = dict(nx=64, boundary=O.BC_PERIODIC, dx=0.1, dt=0.045)
+    a, b = O.Sim(cap=6, **cfg), O.Sim(**cfg)
+    rng = np.random.default_rng(4)
+    pid = 1
+    for s in (a, b):
+        pid = 1
+        for q in (-1, 1):
+            for X, u0 in ((10.2, 3.0), (20.7, -5.0)):
+                for j in range(5):
+                    s.add_lepton(pid, q, X + 0.01 * j, u0 * (1 + 0.003 * j), 1e-20 * (1 + 0.1 * j))
+                    pid += 1
+    a.step(1)
+    b.step(1)
+    sa, sb = _sums(a.leptons()), _sums(b.leptons())
+    assert a.counters()["merged"] == 4 * 3  # four groups of five -> two each
+    for q in (-1, 1):
+        for i in range(3):
+            assert sa[q][i] == pytest.approx(sb[q][i], rel=1e-13)
+        assert sa[q][3] == 4 and sb[q][3] == 10
+    La = a.leptons()
+    assert np.all(np.isfinite(La["u"])) and np.unique(La["id"]).size == La["id"].size
+
+
+def test_merge_keeps_gauss_and_cap_in_a_discharge():
+    s = _discharge_sim(cap=450)
+    s.step(900)
+    c = s.counters()
+    r, emax = s.gauss_residual()
+    assert c["merged"] > 0 and c["pairs"] > 0
+    assert r < 1e-12 * max(1.0, emax)
+    n = s.leptons()["id"].size + s.photons()["id"].size
+    assert n < 2 * 450
