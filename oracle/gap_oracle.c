@@ -451,12 +451,13 @@ static double wrap(const orc_params *p, double X) {
  * ln(gamma) of width 0.1 * 2^level) group with at least three members are
  * replaced by two leptons of weights W/2 at the weight-averaged offset in the
  * dual cell, with momenta from two-body kinematics on S+ = sum w (gamma + u)
- * and S- = sum w (gamma - u): rapidity of the centre 0.5 ln(S+/S-), invariant
- * mass M = sqrt(S+ S-), CM momentum p* = sqrt(M^2 - W^2)/2; this conserves
- * weight, energy and momentum.  Moving the charge inside the dual cell
- * carries charge across node k, which is applied to E_k as a deposit, so
- * Gauss's law holds.  level grows by one per consecutive over-cap step (up to
- * 7) and returns to 0 when the gap is under the cap. */
+ * and S- = sum w (gamma - u): rapidity of the centre eta = 0.5 ln(S+/S-),
+ * invariant mass M = sqrt(S+ S-) = sum w cosh(asinh(u) - eta), CM momentum
+ * p* = sqrt(M^2 - W^2)/2; this conserves weight, energy and momentum.
+ * Moving the charge inside the dual cell carries charge across node k, which
+ * is applied to E_k as a deposit, so Gauss's law holds.  level grows by one
+ * per consecutive over-cap step (up to 7) and returns to 0 when the gap is
+ * under the cap. */
 typedef struct { int32_t q, dir; int64_t k; int64_t bin; uint64_t id; int64_t idx; } mkey;
 static int mkey_cmp(const void *a, const void *b) {
   const mkey *x = (const mkey *)a, *y = (const mkey *)b;
@@ -511,9 +512,21 @@ static void merge(orc_sim *s, uint32_t n) {
       const double flux = (double)key[a].q * (W * phim - Sphi);
       int64_t node = k;
       if (p->boundary == ORC_BC_PERIODIC || (node > 0 && node <= p->nx)) s->E[node] -= flux;
-      const double eta = 0.5 * log(Sp / Sm), M = sqrt(Sp * Sm);
+      /* centre rapidity; the invariant mass as M = sum w cosh(a - eta) with
+       * a = asinh(u) the rapidity of each member, written as W + D with
+       * D = sum w 2 sinh^2((a - eta)/2) >= 0, so that M^2 - W^2 = D (2W + D)
+       * carries no cancellation for nearly cold groups (sqrt(S+ S-) - W
+       * would lose all digits of a small momentum spread). */
+      const double eta = 0.5 * log(Sp / Sm);
+      double D = 0.0;
+      for (int64_t j = a; j < e; ++j) {
+        const orc_lepton *L = &s->lep[key[j].idx];
+        const double h = sinh(0.5 * (asinh(L->u) - eta));
+        D += L->w * 2.0 * h * h;
+      }
+      const double M = W + D;
       const double wa = 0.5 * W, wb = W - wa;
-      double q2 = (M * M - W * W) * (M * M - (wa - wb) * (wa - wb));
+      double q2 = D * (2.0 * W + D) * (M * M - (wa - wb) * (wa - wb));
       const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
       const double ua = sinh(eta + asinh(ps / wa)), ub = sinh(eta - asinh(ps / wb));
       double X = (double)k + phim - 0.5;

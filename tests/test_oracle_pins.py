@@ -552,6 +552,38 @@ def test_merge_conserves_weight_momentum_energy():
     assert np.all(np.isfinite(La["u"])) and np.unique(La["id"]).size == La["id"].size
 
 
+def test_merge_cold_group_keeps_internal_energy():
+    """A nearly cold group (u ~ 1e-3 with a relative spread ~1e-3): the two
+    merged leptons keep the group's momentum and its internal energy M - W
+    (M the invariant mass, ~2e-13 of W here) to 1e-8, both evaluated in
+    50-digit arithmetic.  Forming M^2 - W^2 as S+ S- - W^2 in FP64 gets M - W
+    wrong by ~1e-4 in this group."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    s = O.Sim(nx=16, boundary=O.BC_PERIODIC, dx=0.1, dt=0.045, cap=3)
+    s.set_E(np.zeros(16))
+    us = [1e-3 * (1 + 1e-4 * j * j) for j in range(5)]
+    ws = [0.1 * (1 + 0.25 * j) for j in range(5)]
+    for j in range(5):
+        s.add_lepton(j + 1, -1, 5.1 + 0.02 * j, us[j], ws[j])
+    s.step(1)  # E = 0 at the kick: the group reaches the merge unchanged
+    L = s.leptons()
+    assert L["id"].size == 2 and s.counters()["merged"] == 3
+
+    def invariants(u, w):
+        mp = [(mpmath.mpf(float(ui)), mpmath.mpf(float(wi))) for ui, wi in zip(u, w)]
+        E = sum(wi * mpmath.sqrt(1 + ui * ui) for ui, wi in mp)
+        P = sum(wi * ui for ui, wi in mp)
+        W = sum(wi for _, wi in mp)
+        return P, mpmath.sqrt(E * E - P * P) - W
+
+    P0, I0 = invariants(us, ws)
+    P1, I1 = invariants(L["u"], L["w"])
+    assert abs(P1 - P0) / P0 < 1e-12  # eta = ln(S+/S-)/2 of a ratio near 1: ~eps/eta
+    assert abs(I1 - I0) / I0 < 1e-8
+    assert sum(L["w"]) == pytest.approx(sum(ws), rel=1e-15)
+
+
 def test_merge_keeps_gauss_and_cap_in_a_discharge():
     s = _discharge_sim(cap=450)
     s.step(900)
