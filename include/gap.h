@@ -83,7 +83,14 @@ typedef struct gap_params {
   double seed_amp;   /* Langmuir seed relative density amplitude */
   int64_t nx;        /* cells (>= 8) */
   int64_t ppc;       /* macro-particles per cell per species at load */
-  int64_t cap;       /* macro-particle cap (leptons + photons) of this gap; 0 -> none */
+  int64_t cap;       /* macro-particle cap (leptons + photons) of this gap; 0 -> none.
+                        Over the cap after a step, leptons of the same species,
+                        dual cell, direction and ln(gamma) bin (width
+                        0.1 * 2^level, level = consecutive over-cap steps, at
+                        most 7) are merged in groups of >= 3 into two, keeping
+                        weight, momentum, energy and Gauss's law.  The paper
+                        describes no merging scheme; this one is the
+                        library's own.  Photons are not merged. */
   uint64_t seed;     /* Philox4x32-10 key of this gap */
   int32_t qed;       /* 0/1: curvature emission and one-photon pair creation */
   int32_t boundary;  /* GAP_BC_* */
@@ -186,9 +193,10 @@ int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uin
 
 /* Append n particles of one kind to gap `gap` (tests build hand-checkable
  * states).  Photons: host_u is x, host_tau is tau_star, host_aux2 packs
- * (n0 << 1) | (dir > 0).  In a handle without QED every lepton carries the
- * uniform weight w0 = density dx / ppc (host_w is not used) and no optical
- * depth.  Synchronises `stream`. */
+ * (n0 << 1) | (dir > 0).  In a handle without QED and without a cap
+ * every lepton carries the uniform weight w0 = density dx / ppc (host_w is
+ * not used) and no optical depth; otherwise weights are stored (FP32 state:
+ * rounded to multiples of w0 / 256).  Synchronises `stream`. */
 int gap_add_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t n, const uint64_t *host_id,
                       const double *host_X, const double *host_u, const double *host_w,
                       const double *host_tau, const int64_t *host_aux2, void *stream);

@@ -164,7 +164,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<LoadSpec> loads;
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
-  bool qed_any = false, surface_any = false;
+  bool qed_any = false, surface_any = false, merge_any = false;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     GapDev &g = gaps[i];
@@ -200,6 +200,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.f_rho = (float)g.rho_hat;
     g.f_rate = (float)g.rate_mult;
     g.seed = q.seed;
+    g.cap = q.cap > 0 ? q.cap : 0;
+    merge_any |= q.cap > 0;
     g.inj_root = ((uint64_t)(uint32_t)q.gap_index << 40) | (1ull << 38);
     qed_any |= g.qed != 0;
     surface_any |= !g.periodic;
@@ -265,7 +267,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.precision = cfg.precision;
   v.qed_any = qed_any;
   v.surface_any = surface_any;
-  v.has_w = qed_any ? 1 : 0;
+  v.has_w = (qed_any || merge_any) ? 1 : 0;  // merging makes weights unequal
+  v.merge_any = merge_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
   v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
@@ -290,6 +293,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);
   v.ledger = C.take<double>((size_t)n * L_NLED);
   v.q0 = C.take<unsigned long long>(n);
+  v.merge_state = C.take<int32_t>(4 * (size_t)n);
+  v.merge_width = C.take<double>(n);
+  v.ph_gap[0] = C.take<int32_t>(n);
+  v.ph_gap[1] = C.take<int32_t>(n);
   const int spec_n = 1024;
   v.spec_n = spec_n;
   v.spec_tab = C.take<float2>(spec_n);
@@ -430,6 +437,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_check(h, e, "control block");
   if (c->error & 8) return fail(h, GAP_ECHECK, "store compaction overflowed a segment");
   if (c->error & 16) return fail(h, GAP_ETIMEOUT, "a bulk-copy stage of the push kernel never completed");
+  if (c->error & 32) return fail(h, GAP_ECHECK, "a lepton outside its tile's nodes reached the merge");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));
@@ -499,6 +507,7 @@ int gap_step(gap_handle *h, int64_t nsteps, void *stream) {
       launch_step(h->v, h->threads, st);
     }
     launch_rebin(h->v, h->slack, st);
+    if (h->v.merge_any) launch_merge(h->v, st);  // after the re-bin: no spilled leptons left
   }
   h->steps_done += nsteps;
   return cuda_check(h, cudaGetLastError(), "step launch");
@@ -517,6 +526,7 @@ int gap_step_graph(gap_handle *h, int64_t nsteps, int32_t chunk, void *stream) {
     for (int i = 0; i < chunk; ++i) {
       launch_step(h->v, h->threads, st);
       launch_rebin(h->v, h->slack, st);
+      if (h->v.merge_any) launch_merge(h->v, st);
     }
     e = cudaStreamEndCapture(st, &g);
     if (e != cudaSuccess) return cuda_check(h, e, "end capture");

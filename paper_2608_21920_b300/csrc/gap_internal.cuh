@@ -42,6 +42,7 @@ struct GapDev {
   double dx, dt, cdx, jm, Hc, lambda_hat, rho_hat, rate_mult, b, eta_bg, w0, w_unit;
   float f_dt, f_cdx, f_Hc, f_lam, f_rho, f_rate;
   uint64_t seed, inj_root;
+  int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
 };
 
 struct TileDev {
@@ -65,7 +66,10 @@ struct View {
   TileDev *tiles;
   int32_t n_gaps, n_tiles, tile, precision;
   int32_t qed_any, surface_any, has_w, rebin_every;
-  int32_t variant, pad_v;
+  int32_t variant, merge_any;
+  int32_t *merge_state;  // [gap][4]: merge flag, level
+  double *merge_width;   // [gap]
+  int32_t *ph_gap[2];    // photons per gap in each photon buffer
   Ctl *ctl;
   double *E[2];
   unsigned long long *Dg;  // int64 (FP32) or double (FP64) bit patterns
@@ -359,7 +363,7 @@ __device__ __forceinline__ void split_position(double X, int64_t nx, bool period
   phi = p;
 }
 
-__device__ __forceinline__ void photon_append(const View &v, int buf, int gap, double X, double x,
+__device__ __forceinline__ bool photon_append(const View &v, int buf, int gap, double X, double x,
                                               double w, double tau_star, double tau_acc, uint64_t id,
                                               int32_t n0, int32_t dir) {
   long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[buf]));
@@ -373,10 +377,11 @@ __device__ __forceinline__ void photon_append(const View &v, int buf, int gap, d
     v.pn0[buf][slot] = n0;
     v.pdir[buf][slot] = dir;
     v.pgap[buf][slot] = gap;
-  } else {
-    atomicAdd(&v.counters[gap * C_NCNT + C_PH_OVF], 1ull);
-    atomicOr(&v.ctl->error, 2);
+    return true;
   }
+  atomicAdd(&v.counters[gap * C_NCNT + C_PH_OVF], 1ull);
+  atomicOr(&v.ctl->error, 2);
+  return false;
 }
 
 }  // namespace gapk

@@ -563,8 +563,9 @@ __global__ void k_import_photons(View v, int gap, int64_t n, const double *stage
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t id = reinterpret_cast<const uint64_t *>(stage)[i] | kPhotonBit;
     const int64_t aux = reinterpret_cast<const int64_t *>(stage)[6 * n + i];
-    photon_append(v, cur, gap, stage[n + i], stage[2 * n + i], stage[3 * n + i], stage[5 * n + i],
-                  stage[4 * n + i], id, (int32_t)(aux >> 1), (aux & 1) ? 1 : -1);
+    if (photon_append(v, cur, gap, stage[n + i], stage[2 * n + i], stage[3 * n + i], stage[5 * n + i],
+                      stage[4 * n + i], id, (int32_t)(aux >> 1), (aux & 1) ? 1 : -1))
+      atomicAdd(&v.ph_gap[cur][gap], 1);
   }
 }
 

@@ -17,6 +17,7 @@ void launch_push(const View &v, int threads, cudaStream_t st);
 void launch_after_push(const View &v, cudaStream_t st);
 int launches_per_step(const View &v);
 void launch_rebin(const View &v, double slack, cudaStream_t st);
+void launch_merge(const View &v, cudaStream_t st);
 void launch_force_rebin(const View &v, cudaStream_t st);
 void launch_sync_used(const View &v, cudaStream_t st);
 

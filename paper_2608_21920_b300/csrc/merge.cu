@@ -1,0 +1,308 @@
+// merge.cu -- weight-conserving merge of leptons under the macro-particle cap.
+//
+// When a gap holds more leptons + photons than its cap after a step, the
+// leptons of every (species, dual cell k, direction, bin of ln gamma of width
+// 0.1 * 2^level) group with at least three members become two leptons at the
+// weight-averaged offset of the dual cell.  Their momenta follow from
+// two-body kinematics on S+ = sum w (gamma + u) and S- = sum w (gamma - u):
+// the centre moves with rapidity eta = 0.5 ln(S+/S-), the invariant mass is
+// M = sqrt(S+ S-) = W + D with D = sum w 2 sinh^2((asinh u - eta)/2) (a
+// second pass, free of the cancellation in S+ S- - W^2), and in the centre
+// frame the two move apart with momentum
+// p* = sqrt((M^2 - W^2)(M^2 - (w_a - w_b)^2)) / (2M); weight, momentum and
+// energy are conserved.  Re-centring moves charge across node k; that charge
+// is applied to E_k like a deposit, so Gauss's law holds (exactly, in the
+// integer charge units of the FP32 state).  level counts the consecutive
+// over-cap steps of the gap (at most 7) and resets when the gap is under cap.
+#include "gap_internal.cuh"
+#include "kernels.h"
+
+namespace gapk {
+
+constexpr int kMergeBins = 256;
+constexpr int kMergeKeys = 2 * kMergeBins;  // direction x bin
+constexpr uint32_t CH_MERGE = 10;
+
+// One thread per gap: decide whether the gap merges this step.
+__global__ void k_merge_check(View v) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= v.n_gaps) return;
+  const GapDev &g = v.gaps[gi];
+  int32_t *st = v.merge_state + 4 * gi;  // [flag, level, -, -]
+  double *width = v.merge_width + gi;
+  if (g.cap <= 0) {
+    st[0] = 0;
+    return;
+  }
+  int64_t total = v.ph_gap[v.ctl->ph_cur][gi];
+  for (int t = g.tile_begin; t < g.tile_begin + g.n_tiles; ++t)
+    total += (int64_t)v.seg_alive[0][t] + (int64_t)v.seg_alive[1][t];
+  if (total > g.cap) {
+    const int level = st[1];
+    *width = 0.1 * (double)(1 << level);
+    st[1] = level < 7 ? level + 1 : 7;
+    st[0] = 1;
+    atomicOr(&v.ctl->flags, 1);
+  } else {
+    st[0] = 0;
+    st[1] = 0;
+  }
+}
+
+template <class R>
+struct MergeAcc;
+template <>
+struct MergeAcc<double> {  // FP64 state: FP64 sums of w and w phi
+  using T = double;
+};
+template <>
+struct MergeAcc<float> {  // FP32 state: exact integer sums of m and m Phi (2^-23 units)
+  using T = unsigned long long;
+};
+
+template <class R>
+__global__ void __launch_bounds__(256) k_merge(View v) {
+  using W = typename Prec<R>::W;
+  using A = typename MergeAcc<R>::T;
+  if (!(v.ctl->flags & 1)) return;
+  const int s = blockIdx.x / v.n_tiles, t = blockIdx.x % v.n_tiles;
+  const TileDev ti = v.tiles[t];
+  const GapDev &g = v.gaps[ti.gap];
+  if (!v.merge_state[4 * ti.gap]) return;
+  const double width = v.merge_width[ti.gap];
+  const int nk = ti.nk, k0 = ti.k0;
+  const int cur = v.ctl->lep_cur, nxt = cur ^ 1;
+  const int64_t step = v.ctl->step;  // the step just completed is step - 1
+  const int q = s == 0 ? -1 : 1;
+
+  extern __shared__ __align__(16) unsigned char msm[];
+  int *cnt = reinterpret_cast<int *>(msm);                                            // [kMergeKeys]
+  unsigned long long *minid = reinterpret_cast<unsigned long long *>(msm + 4 * kMergeKeys);
+  A *sw = reinterpret_cast<A *>(msm + 12 * kMergeKeys);                                // sum w
+  A *sphi = reinterpret_cast<A *>(msm + 20 * kMergeKeys);                              // sum w phi
+  double *sp = reinterpret_cast<double *>(msm + 28 * kMergeKeys);                      // sum w (g+u)
+  double *sm = reinterpret_cast<double *>(msm + 36 * kMergeKeys);                      // sum w (g-u)
+  int *hist = reinterpret_cast<int *>(msm + 44 * kMergeKeys);                          // [nk + 1]
+  __shared__ int wsum[8];
+  __shared__ int carry, out_cursor;
+  __shared__ unsigned long long merged_count;
+
+  const int64_t seg0 = v.seg_start[s][t];
+  const int used = v.seg_used[s][t];
+  // 1. counting sort of the segment by node into the other buffer
+  for (int i = threadIdx.x; i <= nk; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    out_cursor = 0;
+    merged_count = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < used; i += blockDim.x) {
+    const int32_t k = v.lk[cur][s][seg0 + i];
+    if (k < 0) continue;
+    if (k < k0 || k >= k0 + nk) {  // never: a tile holds only its own nodes
+      atomicOr(&v.ctl->error, 32);
+      continue;
+    }
+    atomicAdd(&hist[k - k0], 1);
+  }
+  __syncthreads();
+  for (int base = 0; base < nk; base += blockDim.x) {  // exclusive scan in place
+    const int i = base + threadIdx.x;
+    const int x = i < nk ? hist[i] : 0;
+    int y = x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane == 31) wsum[wid] = y;
+    __syncthreads();
+    int before = carry;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    if (i < nk) hist[i] = before + y - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + y;
+    __syncthreads();
+  }
+  // scatter: hist[i] is the next free slot of node i's run
+  for (int i = threadIdx.x; i < used; i += blockDim.x) {
+    const int64_t src = seg0 + i;
+    const int32_t k = v.lk[cur][s][src];
+    if (k < k0 || k >= k0 + nk) continue;
+    const int pos = atomicAdd(&hist[k - k0], 1);
+    const int64_t d = seg0 + pos;
+    v.lk[nxt][s][d] = k;
+    as<R>(v.lphi[nxt][s])[d] = as<R>(v.lphi[cur][s])[src];
+    as<R>(v.lu[nxt][s])[d] = as<R>(v.lu[cur][s])[src];
+    as<W>(v.lw[nxt][s])[d] = lepton_weight<R>(v, g, cur, s, src);
+    as<R>(v.ltau[nxt][s])[d] = as<R>(v.ltau[cur][s])[src];
+    v.lid[nxt][s][d] = v.lid[cur][s][src];
+  }
+  __syncthreads();
+  // after the scatter hist[i] holds the end of node i's run = start of node i+1
+  // 2. node by node: group, merge, write back into the current buffer
+  for (int node = 0; node < nk; ++node) {
+    const int r0 = node == 0 ? 0 : hist[node - 1], r1 = hist[node];
+    if (r1 - r0 < 3) {  // nothing to merge: copy through
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const int64_t src = seg0 + i;
+        const int o = atomicAdd(&out_cursor, 1);
+        const int64_t d = seg0 + o;
+        v.lk[cur][s][d] = v.lk[nxt][s][src];
+        as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
+        as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
+        as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
+        as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
+        v.lid[cur][s][d] = v.lid[nxt][s][src];
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int i = threadIdx.x; i < kMergeKeys; i += blockDim.x) {
+      cnt[i] = 0;
+      minid[i] = ~0ull;
+      sw[i] = (A)0;
+      sphi[i] = (A)0;
+      sp[i] = 0.0;
+      sm[i] = 0.0;
+    }
+    __syncthreads();
+    auto key_of = [&](int64_t src) -> int {
+      const double u = (double)as<R>(v.lu[nxt][s])[src];
+      const double gm = sqrt(1.0 + u * u);
+      int64_t b = (int64_t)floor(log(gm) / width);
+      if (b < 0) b = 0;
+      if (b > kMergeBins - 1) b = kMergeBins - 1;
+      return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
+    };
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t src = seg0 + i;
+      const int key = key_of(src);
+      const double u = (double)as<R>(v.lu[nxt][s])[src];
+      const W wq = as<W>(v.lw[nxt][s])[src];
+      const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+      const double gm = sqrt(1.0 + u * u);
+      const double big = gm + fabs(u);
+      const double gp = u >= 0.0 ? big : 1.0 / big, gmn = u >= 0.0 ? 1.0 / big : big;
+      const R phi = as<R>(v.lphi[nxt][s])[src];
+      atomicAdd(&cnt[key], 1);
+      atomicMin(&minid[key], (unsigned long long)v.lid[nxt][s][src]);
+      atomicAdd(&sp[key], w * gp);
+      atomicAdd(&sm[key], w * gmn);
+      if (sizeof(R) == 4) {
+        const long long F = __float2int_rn(((float)phi - 1.0f) * 8388608.0f);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sw[key]), (unsigned long long)wq);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sphi[key]), (unsigned long long)((long long)wq * F));
+      } else {
+        atomicAdd(reinterpret_cast<double *>(&sw[key]), w);
+        atomicAdd(reinterpret_cast<double *>(&sphi[key]), w * ((double)phi - 1.0));
+      }
+    }
+    __syncthreads();
+    // centre rapidity eta into sp[]; sm[] then accumulates
+    // D = sum w 2 sinh^2((asinh u - eta)/2), so that M = W + D and
+    // M^2 - W^2 = D (2W + D) carry no cancellation for nearly cold groups
+    for (int key = threadIdx.x; key < kMergeKeys; key += blockDim.x) {
+      if (cnt[key] < 3) continue;
+      sp[key] = 0.5 * log(sp[key] / sm[key]);
+      sm[key] = 0.0;
+    }
+    __syncthreads();
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t src = seg0 + i;
+      const int key = key_of(src);
+      if (cnt[key] < 3) continue;
+      const double u = (double)as<R>(v.lu[nxt][s])[src];
+      const W wq = as<W>(v.lw[nxt][s])[src];
+      const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+      const double h = sinh(0.5 * (asinh(u) - sp[key]));
+      atomicAdd(&sm[key], w * 2.0 * h * h);
+    }
+    __syncthreads();
+    // leptons of small groups are copied through
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t src = seg0 + i;
+      if (cnt[key_of(src)] >= 3) continue;
+      const int o = atomicAdd(&out_cursor, 1);
+      const int64_t d = seg0 + o;
+      v.lk[cur][s][d] = v.lk[nxt][s][src];
+      as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
+      as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
+      as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
+      as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
+      v.lid[cur][s][d] = v.lid[nxt][s][src];
+    }
+    // groups of three or more become two
+    const int32_t kn = k0 + node;
+    for (int key = threadIdx.x; key < kMergeKeys; key += blockDim.x) {
+      const int n = cnt[key];
+      if (n < 3) continue;
+      double Wt, phim, flux;
+      W wa, wb;
+      R phi_store;
+      if (sizeof(R) == 4) {
+        const long long Wi = (long long)sw[key], Si = (long long)sphi[key];
+        const long long Fm = (2 * Si + Wi) / (2 * Wi);  // round(S/W) for S >= 0
+        flux = (double)q * (double)(Wi * Fm - Si) * g.w_unit * kPhiUnit;
+        phim = (double)Fm * kPhiUnit;
+        phi_store = (R)(1.0f + (float)Fm * (float)kPhiUnit);
+        wa = (W)(Wi / 2);
+        wb = (W)(Wi - Wi / 2);
+        Wt = (double)Wi * g.w_unit;
+      } else {
+        const double Wd = (double)sw[key], Sd = (double)sphi[key];
+        phim = Sd / Wd;
+        flux = (double)q * (Wd * phim - Sd);
+        phi_store = (R)(1.0 + phim);
+        if (phi_store >= (R)2) phi_store = (R)2 - (R)2.220446049250313e-16;
+        wa = (W)(0.5 * Wd);
+        wb = (W)(Wd - 0.5 * Wd);
+        Wt = Wd;
+      }
+      (void)phim;
+      const double wad = sizeof(R) == 4 ? (double)wa * g.w_unit : (double)wa;
+      const double wbd = sizeof(R) == 4 ? (double)wb * g.w_unit : (double)wb;
+      const double eta = sp[key], D = sm[key], M = Wt + D;
+      const double q2 = D * (2.0 * Wt + D) * (M * M - (wad - wbd) * (wad - wbd));
+      const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
+      const double ua = sinh(eta + asinh(ps / wad)), ub = sinh(eta - asinh(ps / wbd));
+      // the charge moved across node kn by re-centring
+      int64_t node_g = kn;
+      if (g.periodic) node_g %= g.nx;
+      if (flux != 0.0 && (g.periodic || node_g > 0))
+        atomicAdd(&v.E[v.ctl->e_cur][g.node_off + node_g], -flux);
+      const int o = atomicAdd(&out_cursor, 2);
+      for (int c = 0; c < 2; ++c) {
+        const int64_t d = seg0 + o + c;
+        const uint64_t id = child_id(minid[key], (uint32_t)(step - 1), CH_MERGE, (uint32_t)c) & ~kPhotonBit;
+        v.lk[cur][s][d] = kn;
+        as<R>(v.lphi[cur][s])[d] = phi_store;
+        as<R>(v.lu[cur][s])[d] = (R)(c == 0 ? ua : ub);
+        as<W>(v.lw[cur][s])[d] = c == 0 ? wa : wb;
+        as<R>(v.ltau[cur][s])[d] = (R)(-log(uniform53(g.seed, id, (uint32_t)step, CH_TAU0, 0)));
+        v.lid[cur][s][d] = id;
+      }
+      atomicAdd(&merged_count, (unsigned long long)(n - 2));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v.seg_used[s][t] = out_cursor;
+    v.seg_append[s][t] = out_cursor;
+    v.seg_alive[s][t] = out_cursor;
+    if (merged_count) atomicAdd(&v.counters[ti.gap * C_NCNT + C_MERGED], merged_count);
+  }
+}
+
+__global__ void k_merge_done(View v) { v.ctl->flags &= ~1; }
+
+void launch_merge(const View &v, cudaStream_t st) {
+  k_merge_check<<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
+  const size_t smem = (size_t)44 * kMergeKeys + (size_t)(v.tile + 8) * sizeof(int) + 64;
+  if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 256, smem, st>>>(v);
+  else k_merge<double><<<2 * v.n_tiles, 256, smem, st>>>(v);
+  k_merge_done<<<1, 1, 0, st>>>(v);
+}
+
+}  // namespace gapk

@@ -950,7 +950,7 @@ __global__ void k_photons(View v) {
     const int32_t n0 = v.pn0[cur][i];
     const int32_t dir = v.pdir[cur][i];
     if ((int64_t)n0 > step) {  // born during this step: untouched
-      photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir);
+      if (photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir)) atomicAdd(&v.ph_gap[nxt][gap], 1);
       continue;
     }
     if (X < g.Hc) {
@@ -988,8 +988,16 @@ __global__ void k_photons(View v) {
       atomicAdd(&v.counters[gap * C_NCNT + C_PAIRS], 1ull);
       continue;
     }
-    photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir);
+    if (photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir)) atomicAdd(&v.ph_gap[nxt][gap], 1);
   }
+}
+
+// Per-gap photon counts of the buffer k_photons fills (the photons emitted in
+// the push and the survivors of the step) start at 0.
+__global__ void k_photon_count_reset(View v) {
+  const int nxt = v.ctl->ph_cur ^ 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.n_gaps; i += gridDim.x * blockDim.x)
+    v.ph_gap[nxt][i] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1275,7 +1283,10 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
 
 template <class R>
 static void launch_after_push_impl(const View &v, cudaStream_t st) {
-  if (v.qed_any) k_photons<R><<<4 * 148, 256, 0, st>>>(v);
+  if (v.qed_any) {
+    k_photon_count_reset<<<(v.n_gaps + 255) / 256, 256, 0, st>>>(v);
+    k_photons<R><<<4 * 148, 256, 0, st>>>(v);
+  }
   if (v.surface_any) k_inject<R><<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
   k_house<<<(2 * v.n_tiles + 255) / 256, 256, 0, st>>>(v);
 }
@@ -1305,7 +1316,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 }
 
 int launches_per_step(const View &v) {
-  return 1 + (v.qed_any ? 1 : 0) + (v.surface_any ? 1 : 0) + 1 + 5;
+  return 1 + (v.qed_any ? 2 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5;
 }
 
 void launch_sync_used(const View &v, cudaStream_t st) {

@@ -75,7 +75,7 @@ def compare_field(Eg, Eo, rtol, what=""):
 
 
 COUNTER_KEYS = ("emit_events", "photons", "pairs", "injected", "absorbed", "escaped",
-                "photons_escaped", "emit_overflow", "inject_overflow")
+                "photons_escaped", "emit_overflow", "inject_overflow", "merged")
 
 
 def compare_counters(cg, co, what=""):
