@@ -244,7 +244,10 @@ typedef struct {
 } orc_params;
 
 typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
-typedef struct { uint64_t id; double X, x, w, tau_star, tau_acc; int32_t dir, n0, alive, pad; } orc_photon;
+/* A photon moves at c along h from X_ref, where it was at the start of step
+ * n_ref (its birth step n0 for photons born in the run); X is its current
+ * position, kept for export. */
+typedef struct { uint64_t id; double X, x, w, tau_star, tau_acc, X_ref; int32_t dir, n0, n_ref, alive; } orc_photon;
 
 /* Event counters and the energy ledger.  Energies are total energies (rest
  * mass included: w gamma for leptons, w x for photons) per unit area in
@@ -401,6 +404,7 @@ void orc_add_photon(orc_sim *s, uint64_t id, double X, double x, double w,
   orc_photon P = {0};
   P.id = id | ORC_PHOTON_BIT; P.X = X; P.x = x; P.w = w; P.dir = dir; P.n0 = n0;
   P.tau_star = tau_star; P.tau_acc = 0.0; P.alive = 1;
+  P.X_ref = X; P.n_ref = (int32_t)s->step;
   push_photon(s, P);
 }
 void orc_set_eta_bg(orc_sim *s, double eta) { s->eta_bg = eta; }
@@ -442,6 +446,15 @@ static double wrap(const orc_params *p, double X) {
   X = fmod(X, L);
   if (X < 0.0) X += L;
   if (X >= L) X -= L;
+  return X;
+}
+
+/* Position of a photon at the start of step m (Sect. 6.1: photons move at c
+ * along the field line): X_ref + dir (m - n_ref) c dt/dx, the closed form of
+ * the straight-line motion (one rounding of the product, one of the sum). */
+static double photon_pos(const orc_params *p, const orc_photon *P, int64_t m, double cdx) {
+  double X = P->X_ref + (double)P->dir * ((double)(m - (int64_t)P->n_ref) * cdx);
+  if (p->boundary == ORC_BC_PERIODIC) X = wrap(p, X);
   return X;
 }
 
@@ -632,6 +645,8 @@ void orc_step(orc_sim *s) {
     L->X = X1;
     for (int b = 0; b < nborn; ++b) {
       born[b].X = X1;
+      born[b].X_ref = X1;
+      born[b].n_ref = born[b].n0;
       if (p->boundary != ORC_BC_PERIODIC && !in_domain(p, X1)) {
         s->cnt.photons_escaped++; s->cnt.e_photon_escaped += born[b].w * born[b].x;
         continue;
@@ -645,14 +660,13 @@ void orc_step(orc_sim *s) {
   for (int64_t ip = 0; ip < nph_old; ++ip) {
     orc_photon *P = &s->ph[ip];
     if (!P->alive) continue;
-    if (P->X < Hc) {
+    if (photon_pos(p, P, n, cdx) < Hc) {
       double lmid = ((double)n - (double)P->n0 + 0.5) * dt;
       double sp = fabs(sin(lmid / p->rho_hat));
       double chi = P->x * p->b * sp;
       P->tau_acc += dt * p->rate_mult * ORC_ALPHA_EM / p->lambda_hat * p->b * sp * orc_tbw(chi);
     }
-    double X1 = P->X + (double)P->dir * cdx;
-    if (p->boundary == ORC_BC_PERIODIC) X1 = wrap(p, X1);
+    double X1 = photon_pos(p, P, n + 1, cdx);
     P->X = X1;
     if (p->boundary != ORC_BC_PERIODIC && !in_domain(p, X1)) {
       P->alive = 0; s->cnt.photons_escaped++; s->cnt.e_photon_escaped += P->w * P->x;
