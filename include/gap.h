@@ -244,14 +244,27 @@ int gap_power_spectrum_noalloc(const double *dev_E, int64_t n, double *dev_power
 int64_t gap_steps_done(const gap_handle *h);
 
 /* Live timing of the push kernel (the dominant kernel of a step).  With
- * on != 0, later gap_step calls bracket each push launch with CUDA events on
- * the launching stream.  Every call first returns, through the non-NULL
+ * on != 0, later gap_step calls bracket each phase of the step (the push
+ * launch among them) with CUDA events on the launching stream.  Every call first returns, through the non-NULL
  * outputs, the summed push duration (ms) and the number of push launches
  * timed since the previous call (synchronising on the last event), and the
  * number of kernel launches one step makes; then it resets the sums and sets
  * the mode.  Graph replays are not timed. */
 int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_launches,
                 int64_t *launches_per_step);
+
+/* Phases of a profiled step (gap_profile_phases). */
+#define GAP_PHASE_PUSH 0   /* the fused push / emission / deposit / Ampere kernel */
+#define GAP_PHASE_AFTER 1  /* photon propagation and conversion, injection, bookkeeping */
+#define GAP_PHASE_REBIN 2  /* store compaction (a no-op launch sequence between re-bins) */
+#define GAP_PHASE_MERGE 3  /* the over-cap check and merge */
+#define GAP_NPHASES 4
+
+/* Durations (ms) of each phase summed over the steps profiled since the last
+ * gap_profile call (which clears them), without clearing; ms_out holds
+ * GAP_NPHASES values, *steps_out the number of profiled steps.  Synchronises
+ * on the last recorded event.  The mode is switched by gap_profile. */
+int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out);
 
 /* Release host state.  The caller frees the workspace afterwards. */
 void gap_free(gap_handle *h);

@@ -28,3 +28,30 @@ def tune(params, precision="fp32", tiles=(128, 256, 512), threads=(128, 256), va
         torch.cuda.empty_cache()
     best = min(times, key=times.get)
     return best, times
+
+
+def tune_step(params, precision="fp32", tiles=(64, 128, 256), threads=(128, 256), rebins=(32, 64),
+              steps=60, warmup=20, graph_chunk=20, verbose=False):
+    """Whole-step objective for batched runs with QED (where the push kernel is
+    the general one and the photon, injection and compaction launches weigh
+    in): each (tile, threads, rebin_every) is timed over `steps` graph-replayed
+    steps.  Returns (best (tile, threads, rebin_every), {geometry: ms per step})."""
+    times = {}
+    s = torch.cuda.Stream()
+    for tile, thr, rb in itertools.product(tiles, threads, rebins):
+        g = Gap(params, precision=precision, tile=tile, threads=thr, rebin_every=rb)
+        with torch.cuda.stream(s):
+            g.step(warmup, graph_chunk=graph_chunk)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.step(steps, graph_chunk=graph_chunk)
+            e1.record(s)
+        e1.synchronize()
+        times[(tile, thr, rb)] = e0.elapsed_time(e1) / steps
+        if verbose:
+            print(f"tile {tile:5d} threads {thr:4d} rebin {rb:3d}: {times[(tile, thr, rb)]:.3f} ms/step", flush=True)
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    best = min(times, key=times.get)
+    return best, times

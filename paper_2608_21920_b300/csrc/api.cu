@@ -30,11 +30,15 @@ struct gap_handle {
   cudaStream_t graph_stream = nullptr;
   int status = GAP_OK;
   std::string err;
-  // live timing of the push kernel (gap_profile_*)
+  // live timing of the step phases (gap_profile, gap_profile_phases)
   bool profiling = false;
-  std::vector<cudaEvent_t> ev;  // pairs around each push launch
+  std::vector<cudaEvent_t> ev;  // kProfEvents per profiled step
   size_t ev_used = 0;
+  double phase_ms[GAP_NPHASES] = {0, 0, 0, 0};
+  int64_t phase_steps = 0;
 };
+
+static constexpr size_t kProfEvents = 5;
 
 namespace {
 
@@ -289,14 +293,17 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     v.new_start[s] = C.take<int64_t>(NT);
     v.new_cap[s] = C.take<int32_t>(NT);
     v.new_fill[s] = C.take<int32_t>(NT);
+    v.last_cnt[s] = C.take<int32_t>(NT);
+    v.gross[s] = C.take<int32_t>(NT);
   }
+  v.item_start = C.take<int32_t>((size_t)NT + 1);
+  v.tile_done = C.take<int32_t>(NT);
   v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);
   v.ledger = C.take<double>((size_t)n * L_NLED);
   v.q0 = C.take<unsigned long long>(n);
   v.merge_state = C.take<int32_t>(4 * (size_t)n);
   v.merge_width = C.take<double>(n);
-  v.ph_gap[0] = C.take<int32_t>(n);
-  v.ph_gap[1] = C.take<int32_t>(n);
+  v.ph_gap = C.take<int32_t>(n);
   const int spec_n = 1024;
   v.spec_n = spec_n;
   v.spec_tab = C.take<float2>(spec_n);
@@ -326,16 +333,21 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   }
   v.spill_capacity = spill_cap;
   for (int b = 0; b < 2; ++b) {
-    v.pX[b] = C.take<double>(ph_cap);
+    v.pXr[b] = C.take<double>(ph_cap);
     v.px[b] = C.take<double>(ph_cap);
     v.pw[b] = C.take<double>(ph_cap);
     v.pts[b] = C.take<double>(ph_cap);
     v.pta[b] = C.take<double>(ph_cap);
     v.pid[b] = C.take<uint64_t>(ph_cap);
     v.pn0[b] = C.take<int32_t>(ph_cap);
+    v.pnr[b] = C.take<int32_t>(ph_cap);
     v.pdir[b] = C.take<int32_t>(ph_cap);
     v.pgap[b] = C.take<int32_t>(ph_cap);
+    v.pm[b] = C.take<int32_t>(ph_cap);
+    v.pev[b] = C.take<int32_t>(ph_cap);
+    v.pkind[b] = C.take<int32_t>(ph_cap);
   }
+  v.ph_work = C.take<int64_t>(ph_cap);
   v.ph_capacity = ph_cap;
   char *bb[2];
   size_t bbytes = 0;
@@ -438,6 +450,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (c->error & 8) return fail(h, GAP_ECHECK, "store compaction overflowed a segment");
   if (c->error & 16) return fail(h, GAP_ETIMEOUT, "a bulk-copy stage of the push kernel never completed");
   if (c->error & 32) return fail(h, GAP_ECHECK, "a lepton outside its tile's nodes reached the merge");
+  if (c->error & 64) return fail(h, GAP_ECHECK, "a photon event was not taken at its step");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));
@@ -491,21 +504,29 @@ int gap_step(gap_handle *h, int64_t nsteps, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   for (int64_t i = 0; i < nsteps; ++i) {
     if (h->profiling) {
-      if (h->ev_used + 2 > h->ev.size()) {
-        for (int k = 0; k < 64; ++k) {
+      // five events per step: before the push, after it, after the photon /
+      // injection / bookkeeping launches, after the re-bin, after the merge
+      if (h->ev_used + kProfEvents > h->ev.size()) {
+        for (int k = 0; k < 16 * kProfEvents; ++k) {
           cudaEvent_t e;
           if (cudaEventCreate(&e) != cudaSuccess) return fail(h, GAP_ECUDA, "event create");
           h->ev.push_back(e);
         }
       }
-      cudaEventRecord(h->ev[h->ev_used], st);
+      cudaEvent_t *ev = &h->ev[h->ev_used];
+      cudaEventRecord(ev[0], st);
       launch_push(h->v, h->threads, st);
-      cudaEventRecord(h->ev[h->ev_used + 1], st);
-      h->ev_used += 2;
+      cudaEventRecord(ev[1], st);
       launch_after_push(h->v, st);
-    } else {
-      launch_step(h->v, h->threads, st);
+      cudaEventRecord(ev[2], st);
+      launch_rebin(h->v, h->slack, st);
+      cudaEventRecord(ev[3], st);
+      if (h->v.merge_any) launch_merge(h->v, st);
+      cudaEventRecord(ev[4], st);
+      h->ev_used += kProfEvents;
+      continue;
     }
+    launch_step(h->v, h->threads, st);
     launch_rebin(h->v, h->slack, st);
     if (h->v.merge_any) launch_merge(h->v, st);  // after the re-bin: no spilled leptons left
   }
@@ -758,27 +779,46 @@ int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int
 
 int64_t gap_steps_done(const gap_handle *h) { return h ? h->steps_done : 0; }
 
+// Sum the event intervals recorded since the last read into phase_ms.
+static int collect_phases(gap_handle *h) {
+  if (!h->ev_used) return GAP_OK;
+  cudaError_t e = cudaEventSynchronize(h->ev[h->ev_used - 1]);
+  if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+  for (size_t i = 0; i + kProfEvents <= h->ev_used; i += kProfEvents) {
+    for (int ph = 0; ph < GAP_NPHASES; ++ph) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, h->ev[i + ph], h->ev[i + ph + 1]);
+      if (e != cudaSuccess) return cuda_check(h, e, "profile read");
+      h->phase_ms[ph] += ms;
+    }
+    ++h->phase_steps;
+  }
+  h->ev_used = 0;
+  return GAP_OK;
+}
+
 int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_launches,
                 int64_t *launches_per_step) {
   if (!h) return GAP_EINVAL;
   if (launches_per_step) *launches_per_step = ::gapk::launches_per_step(h->v);
-  double tot = 0.0;
-  int64_t n = 0;
-  if (h->ev_used) {
-    cudaError_t e = cudaEventSynchronize(h->ev[h->ev_used - 1]);
-    if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
-    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]);
-      if (e != cudaSuccess) return cuda_check(h, e, "profile read");
-      tot += ms;
-      ++n;
-    }
-  }
+  const int r = collect_phases(h);
+  if (r) return r;
+  const double tot = h->phase_ms[GAP_PHASE_PUSH];
+  const int64_t n = h->phase_steps;
+  for (int ph = 0; ph < GAP_NPHASES; ++ph) h->phase_ms[ph] = 0.0;
+  h->phase_steps = 0;
   if (push_ms_total) *push_ms_total = tot;
   if (push_launches) *push_launches = n;
-  h->ev_used = 0;
   h->profiling = on != 0;
+  return GAP_OK;
+}
+
+int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out) {
+  if (!h || !ms_out) return GAP_EINVAL;
+  const int r = collect_phases(h);
+  if (r) return r;
+  for (int ph = 0; ph < GAP_NPHASES; ++ph) ms_out[ph] = h->phase_ms[ph];
+  if (steps_out) *steps_out = h->phase_steps;
   return GAP_OK;
 }
 

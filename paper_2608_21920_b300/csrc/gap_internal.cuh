@@ -22,6 +22,7 @@ constexpr int kPhiBits = 23;                   // FP32 offset grid 2^-23
 constexpr double kPhiUnit = 1.0 / 8388608.0;   // 2^-23
 constexpr int kWeightShift = 8;                // FP32 weight unit = w0 / 2^8
 constexpr int kMaxEmit = 16;                   // emission events per lepton-step (upper bound)
+constexpr int kPushChunk = 4096;  // leptons per push work item (multiple of 32)
 
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
@@ -56,6 +57,11 @@ struct Ctl {
   int32_t lep_cur, ph_cur, e_cur, need_rebin;
   int32_t error, flags;
   int64_t ph_count[2];
+  int64_t ph_work_n;  // photons on the scheduling work list this step
+  int64_t last_rebin_step;
+  int64_t ph_dead;  // photons dead since the last photon compaction
+  int32_t need_ph_compact, pad_c;
+  int32_t push_items, push_next;  // the push work list of this step and its counter
   int64_t spill_n[2];
   int64_t new_total[2];
 };
@@ -69,7 +75,7 @@ struct View {
   int32_t variant, merge_any;
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
-  int32_t *ph_gap[2];    // photons per gap in each photon buffer
+  int32_t *ph_gap;       // photons alive per gap
   Ctl *ctl;
   double *E[2];
   unsigned long long *Dg;  // int64 (FP32) or double (FP64) bit patterns
@@ -80,6 +86,10 @@ struct View {
   int32_t *seg_cap[2], *seg_used[2], *seg_append[2], *seg_alive[2], *spill_cnt[2];
   int64_t *new_start[2];
   int32_t *new_cap[2], *new_fill[2];
+  int32_t *last_cnt[2];  // per tile: alive count after the last re-bin
+  int32_t *gross[2];     // per tile: appends since the last re-bin
+  int32_t *item_start;   // [n_tiles + 1] first push item of each tile
+  int32_t *tile_done;    // [n_tiles] items of the tile finished this step
   // lepton stores [buffer][species]
   int32_t *lk[2][2];
   void *lphi[2][2], *lu[2][2], *lw[2][2], *ltau[2][2];
@@ -90,10 +100,15 @@ struct View {
   double *sphi[2], *su[2], *sw[2], *stau[2];
   uint64_t *sid[2];
   int64_t spill_capacity;
-  // photon stores [buffer]
-  double *pX[2], *px[2], *pw[2], *pts[2], *pta[2];
+  // photon stores [buffer]: the current buffer is append-only between
+  // compactions.  A photon moves from X_ref (its position at the start of
+  // step n_ref); its optical depth tau_acc holds the steps before pm; pev is
+  // the step of its next event (conversion, escape or re-schedule: pkind),
+  // kPhPending before it is scheduled, kPhDead after its event.
+  double *pXr[2], *px[2], *pw[2], *pts[2], *pta[2];
   uint64_t *pid[2];
-  int32_t *pn0[2], *pdir[2], *pgap[2];
+  int32_t *pn0[2], *pnr[2], *pdir[2], *pgap[2], *pm[2], *pev[2], *pkind[2];
+  int64_t *ph_work;  // photon indices to schedule this step
   int64_t ph_capacity;
   // per-gap accumulators
   unsigned long long *counters;  // [gap][C_NCNT]
@@ -138,6 +153,14 @@ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t id, uint32_t
   philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
   uint64_t m = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);
   return ((double)m + 1.0) * 1.1102230246251565e-16;  // 2^-53
+}
+
+// 24-bit uniform in (0, 1) from the same counter (the FP32 state's draws).
+__device__ __forceinline__ float uniform24(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
+                                           uint32_t k) {
+  uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, (channel << 16) | (k & 0xFFFFu)};
+  philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return ((float)(c[0] >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
 }
 
 // SplitMix64 output function (Steele, Lea, Flood 2014).
@@ -281,6 +304,55 @@ __device__ __forceinline__ void acc_add(long long *p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
 }
 __device__ __forceinline__ void acc_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_shared_add_u32(unsigned *p, unsigned v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_add_s32(int *p, int v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Exact 64-bit charge sums from 32-bit shared reductions: a contribution
+// c = q w F (|c| < 2^55: weight units w < 2^32, offset flux |F| <= 2^23) is
+// split as c = c2 2^38 + c1 2^19 + c0 with c0, c1 in [0, 2^19) and c2 =
+// floor(c / 2^38), |c2| <= 2^17, each added to its own 32-bit counter.  A
+// node receives at most 2 kPushChunk = 8192 contributions per push item, so
+// the unsigned limbs stay below 8192 (2^19 - 1) < 2^32 and the signed one
+// below 2^30: the node's exact sum is c2sum 2^38 + c1sum 2^19 + c0sum.
+__device__ __forceinline__ void limb_add(unsigned *L0, unsigned *L1, int *L2, int i, long long c) {
+  const unsigned long long u = (unsigned long long)c;
+  red_shared_add_u32(&L0[i], (unsigned)(u & 0x7FFFFull));
+  red_shared_add_u32(&L1[i], (unsigned)((u >> 19) & 0x7FFFFull));
+  red_shared_add_s32(&L2[i], (int)(c >> 38));
+}
+__device__ __forceinline__ long long limb_value(unsigned l0, unsigned l1, int l2) {
+  return (long long)l2 * (1ll << 38) + (long long)l1 * (1ll << 19) + (long long)l0;
+}
+
+// Warp-aggregated accumulation into shared memory: lanes that hold the same
+// key in a contiguous run of lanes sum their values into the run's last lane
+// (segmented inclusive scan over the lanes), which issues the one atomic;
+// key < 0 contributes nothing.  All 32 lanes of the warp must call it.  With
+// the store sorted by node most lanes of a warp share a few nodes, so this
+// replaces up to 32 same-address 64-bit atomics by one.
+template <class A>
+__device__ __forceinline__ void warp_run_add(A *base, int key, A val) {
+  const int lane = threadIdx.x & 31;
+  // run index: the number of run heads at or before this lane (non-decreasing
+  // over the lanes, so equal indices are one contiguous run)
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  const int run = __popc(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int r2 = __shfl_up_sync(0xffffffffu, run, o);
+    const A v2 = __shfl_up_sync(0xffffffffu, val, o);
+    if (lane >= o && r2 == run) val += v2;
+  }
+  const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  if (key >= 0 && last) acc_add(&base[key], val);
+}
 __device__ __forceinline__ void acc_add_global(unsigned long long *p, long long v) {
   atomicAdd(p, (unsigned long long)v);
 }
@@ -297,7 +369,7 @@ __device__ __forceinline__ double acc_take(unsigned long long *p, double *) {
 // Append one lepton to tile t of species s (current buffer); spills to the
 // overflow list when the segment is full.
 template <class R>
-__device__ void append_lepton(const View &v, int s, int t, int32_t k, R phi, R u,
+__device__ __noinline__ void append_lepton(const View &v, int s, int t, int32_t k, R phi, R u,
                               typename Prec<R>::W w, R tau, uint64_t id) {
   const int cur = v.ctl->lep_cur;
   int pos = atomicAdd(&v.seg_append[s][t], 1);
@@ -363,25 +435,73 @@ __device__ __forceinline__ void split_position(double X, int64_t nx, bool period
   phi = p;
 }
 
-__device__ __forceinline__ bool photon_append(const View &v, int buf, int gap, double X, double x,
-                                              double w, double tau_star, double tau_acc, uint64_t id,
-                                              int32_t n0, int32_t dir) {
+// Photon event kinds and markers of pev.
+enum PhotonEvent : int32_t { PH_CONVERT = 1, PH_ESCAPE = 2, PH_RESCHEDULE = 3, PH_INERT = 4 };
+constexpr int32_t kPhPending = -2, kPhDead = -1, kPhNever = 0x7fffffff;
+
+// Append a photon, unscheduled: it sits at X_ref at the start of step n_ref,
+// has accumulated tau_acc before step m, and will be scheduled by the next
+// photon pass.
+static __device__ __noinline__ bool photon_append(const View &v, int buf, int gap, double X_ref, int32_t n_ref,
+                                              double x, double w, double tau_star, double tau_acc,
+                                              uint64_t id, int32_t n0, int32_t dir, int32_t m) {
   long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[buf]));
   if (slot < v.ph_capacity) {
-    v.pX[buf][slot] = X;
+    v.pXr[buf][slot] = X_ref;
     v.px[buf][slot] = x;
     v.pw[buf][slot] = w;
     v.pts[buf][slot] = tau_star;
     v.pta[buf][slot] = tau_acc;
     v.pid[buf][slot] = id;
     v.pn0[buf][slot] = n0;
+    v.pnr[buf][slot] = n_ref;
     v.pdir[buf][slot] = dir;
     v.pgap[buf][slot] = gap;
+    v.pm[buf][slot] = m;
+    v.pkind[buf][slot] = 0;
+    v.pev[buf][slot] = kPhPending;
     return true;
   }
   atomicAdd(&v.counters[gap * C_NCNT + C_PH_OVF], 1ull);
   atomicOr(&v.ctl->error, 2);
   return false;
+}
+
+// Position of a photon at the start of step m: photons move at c along h
+// (Sect. 6.1), X = X_ref + dir (m - n_ref) c dt/dx, rounded once in the
+// product and once in the sum (never fused), wrapped into the box when
+// periodic.
+__device__ __forceinline__ double photon_pos(const GapDev &g, double Xr, int32_t nr, int32_t dir, int64_t m) {
+  const double t = __dmul_rn((double)(m - (int64_t)nr), g.cdx);
+  double X = __dadd_rn(Xr, dir > 0 ? t : -t);
+  if (g.periodic) {
+    const double L = (double)g.nx;
+    X = fmod(X, L);
+    if (X < 0.0) X += L;
+    if (X >= L) X -= L;
+  }
+  return X;
+}
+
+// Breit-Wheeler optical depth gained in step m (eq. tau_bw) at the mid-step
+// angle sin(psi) = |sin(l / R_curv)|, l = c (m - n0 + 1/2) dt (Sect. 6.1
+// virtual B_y), chi_x = x b sin(psi).  FP64: evaluated left to right as
+// dt rate_mult alpha_em / lambda_hat b sin(psi) T_BW(chi_x).
+__device__ __forceinline__ double bw_step_depth(const GapDev &g, double x, int32_t n0, int64_t m) {
+  const double lmid = ((double)m - (double)n0 + 0.5) * g.dt;
+  const double sp = fabs(sin(lmid / g.rho_hat));
+  const double chi = x * g.b * sp;
+  return g.dt * g.rate_mult * kAlphaEm / g.lambda_hat * g.b * sp * tbw_d(chi);
+}
+__device__ __forceinline__ float tbw_f(float chi) {
+  if (!(chi > 0.0f)) return 0.0f;
+  return 0.23f * expf(-8.0f / (3.0f * chi)) * exp2f(-log2f(1.0f + 0.22f * chi) * (1.0f / 3.0f));
+}
+__device__ __forceinline__ float bw_step_depth_f(const GapDev &g, float x, int32_t n0, int64_t m) {
+  const float lmid = ((float)(m - (int64_t)n0) + 0.5f) * g.f_dt;
+  const float sp = fabsf(sinf(lmid / g.f_rho));
+  const float chi = x * (float)g.b * sp;
+  return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * (float)g.b * sp * tbw_f(chi);
 }
 
 }  // namespace gapk

@@ -281,26 +281,6 @@ __global__ void k_moments(View v, int gap) {
   if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[16], en);
 }
 
-__global__ void k_photon_moments(View v, int gap) {
-  const int cur = v.ctl->ph_cur;
-  const int64_t n = v.ctl->ph_count[cur];
-  const GapDev &g = v.gaps[gap];
-  double en = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (v.pgap[cur][i] != gap) continue;
-    const double X = v.pX[cur][i];
-    int64_t c = (int64_t)floor(X);
-    if (c < 0) c = 0;
-    if (c >= g.nx) c = g.nx - 1;
-    atomicAdd(&v.dmom[7 * g.nx + c], v.pw[cur][i] / g.dx);
-    en += v.pw[cur][i] * v.px[cur][i];
-    atomicAdd(reinterpret_cast<unsigned long long *>(&v.dred[20]), 1ull);
-  }
-  for (int o = 16; o > 0; o >>= 1) en += __shfl_down_sync(0xffffffffu, en, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[17], en);
-}
-
 // One block: peak and mean multiplicity over the gap cells, <gamma^-3> at
 // the peak, E extrema, Gauss residual, field energy.  dred layout:
 // 0 M_peak, 1 M_avg, 2 peak cell, 3 g3_peak, 4-7 split, 8 E_min, 9 E_max,
@@ -463,7 +443,7 @@ void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st)
   cudaStreamSynchronize(st);
   if (v.precision == GAP_FP32_STATE) k_moments<float><<<gh.n_tiles, 256, 0, st>>>(v, gap);
   else k_moments<double><<<gh.n_tiles, 256, 0, st>>>(v, gap);
-  k_photon_moments<<<148, 256, 0, st>>>(v, gap);
+  launch_photon_moments(v, gap, st);
   k_reduce<<<1, 1024, 0, st>>>(v, gap);
   if (P >= 2) {
     double2 *a = reinterpret_cast<double2 *>(v.fft[0]);
@@ -517,25 +497,6 @@ __global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t 
   }
 }
 
-__global__ void k_export_photons(View v, int gap, double *stage, int64_t cap, unsigned long long *count) {
-  const int cur = v.ctl->ph_cur;
-  const int64_t n = v.ctl->ph_count[cur];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (v.pgap[cur][i] != gap) continue;
-    const unsigned long long o = atomicAdd(count, 1ull);
-    if ((int64_t)o >= cap) continue;
-    reinterpret_cast<uint64_t *>(stage)[o] = v.pid[cur][i];
-    stage[cap + o] = v.pX[cur][i];
-    stage[2 * cap + o] = v.px[cur][i];
-    stage[3 * cap + o] = v.pw[cur][i];
-    stage[4 * cap + o] = v.pta[cur][i];
-    stage[5 * cap + o] = v.pts[cur][i];
-    reinterpret_cast<int64_t *>(stage)[6 * cap + o] =
-        ((int64_t)v.pn0[cur][i] << 1) | (v.pdir[cur][i] > 0 ? 1 : 0);
-  }
-}
-
 template <class R>
 __global__ void k_import_leptons(View v, int gap, int s, int64_t n, const double *stage) {
   using W = typename Prec<R>::W;
@@ -554,18 +515,6 @@ __global__ void k_import_leptons(View v, int gap, int s, int64_t n, const double
     if (sizeof(R) == 4) wq = (W)llrint(w / g.w_unit);
     else wq = (W)w;
     append_lepton<R>(v, s, tile_of(v, g, k), k, phi, (R)u, wq, (R)tau, id);
-  }
-}
-
-__global__ void k_import_photons(View v, int gap, int64_t n, const double *stage) {
-  const int cur = v.ctl->ph_cur;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t id = reinterpret_cast<const uint64_t *>(stage)[i] | kPhotonBit;
-    const int64_t aux = reinterpret_cast<const int64_t *>(stage)[6 * n + i];
-    if (photon_append(v, cur, gap, stage[n + i], stage[2 * n + i], stage[3 * n + i], stage[5 * n + i],
-                      stage[4 * n + i], id, (int32_t)(aux >> 1), (aux & 1) ? 1 : -1))
-      atomicAdd(&v.ph_gap[cur][gap], 1);
   }
 }
 
@@ -588,7 +537,7 @@ void launch_import(const View &v, int gap, int kind, int64_t n, const double *st
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1184) blocks = 1184;
   if (kind == GAP_PHOTON) {
-    k_import_photons<<<blocks, 256, 0, st>>>(v, gap, n, stage);
+    launch_import_photons(v, gap, n, stage, st);
   } else if (v.precision == GAP_FP32_STATE) {
     k_import_leptons<float><<<blocks, 256, 0, st>>>(v, gap, kind, n, stage);
   } else {
@@ -599,7 +548,7 @@ void launch_import(const View &v, int gap, int kind, int64_t n, const double *st
 void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
                         unsigned long long *count, int n_tiles_gap, cudaStream_t st) {
   if (kind == GAP_PHOTON) {
-    k_export_photons<<<148, 256, 0, st>>>(v, gap, stage, cap, count);
+    launch_export_photons(v, gap, stage, cap, count, st);
   } else if (v.precision == GAP_FP32_STATE) {
     k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count);
   } else {

@@ -18,6 +18,12 @@ void launch_after_push(const View &v, cudaStream_t st);
 int launches_per_step(const View &v);
 void launch_rebin(const View &v, double slack, cudaStream_t st);
 void launch_merge(const View &v, cudaStream_t st);
+void launch_photon_step(const View &v, cudaStream_t st);
+void launch_photon_compact(const View &v, cudaStream_t st);
+void launch_export_photons(const View &v, int gap, double *stage, int64_t cap, unsigned long long *count,
+                           cudaStream_t st);
+void launch_import_photons(const View &v, int gap, int64_t n, const double *stage, cudaStream_t st);
+void launch_photon_moments(const View &v, int gap, cudaStream_t st);
 void launch_force_rebin(const View &v, cudaStream_t st);
 void launch_sync_used(const View &v, cudaStream_t st);
 

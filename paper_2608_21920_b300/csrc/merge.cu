@@ -34,7 +34,7 @@ __global__ void k_merge_check(View v) {
     st[0] = 0;
     return;
   }
-  int64_t total = v.ph_gap[v.ctl->ph_cur][gi];
+  int64_t total = v.ph_gap[gi];
   for (int t = g.tile_begin; t < g.tile_begin + g.n_tiles; ++t)
     total += (int64_t)v.seg_alive[0][t] + (int64_t)v.seg_alive[1][t];
   if (total > g.cap) {

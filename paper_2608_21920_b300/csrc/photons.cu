@@ -1,0 +1,378 @@
+// photons.cu -- photon propagation and one-photon pair creation (eq. tau_bw,
+// Sect. 6.1), with each photon's fate scheduled ahead of time.
+//
+// A photon's optical depth depends only on its energy, its direction and the
+// time since its birth (the angle to B grows with the path length), and its
+// position is a closed form of the step; so the step at which it converts,
+// or leaves the domain, follows from its birth record.  The photon pass
+// therefore reads one int32 (the event step) per stored photon and step; a
+// photon is touched only when it is scheduled (at birth, after an import, or
+// every kSchedIters accumulated steps) and at its event.  The accumulation is
+// the same sequence of per-step depths that a step-by-step integration adds,
+// in the same order, so the event step is the same.  Two shortcuts keep the
+// scheduling cheap, both exact: steps where the photon is above the gap
+// (QED inhibited, h > H_gap) add nothing and are skipped in closed form, and a
+// photon whose remaining depth cannot reach its threshold -- the per-step
+// depth is at most dt rate_mult alpha_em / lambda_hat b T_BW(x b), because
+// chi T_BW(chi) increases with chi -- goes straight to its escape step.
+#include "gap_internal.cuh"
+#include "kernels.h"
+
+namespace gapk {
+
+constexpr int kSchedIters = 256;  // accumulated steps per photon per scheduling pass
+
+// Smallest step j >= j0 with pos(j) >= T (dir > 0) or pos(j) < T (dir < 0),
+// for a non-periodic gap, where pos is monotone in j.
+__device__ int64_t first_step(const GapDev &g, double Xr, int32_t nr, int32_t dir, int64_t j0, double T) {
+  auto hit = [&](int64_t j) {
+    const double X = photon_pos(g, Xr, nr, dir, j);
+    return dir > 0 ? X >= T : X < T;
+  };
+  if (hit(j0)) return j0;
+  int64_t lo = j0;  // !hit(lo)
+  const double d = dir > 0 ? (T - Xr) / g.cdx : (Xr - T) / g.cdx;
+  int64_t hi = (int64_t)nr + (int64_t)ceil(d > 0.0 ? d : 0.0) + 2;
+  if (hi <= lo) hi = lo + 1;
+  for (int guard = 0; guard < 62 && !hit(hi); ++guard) hi = lo + 2 * (hi - lo);
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (hit(mid)) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
+template <class R>
+struct BwDepth;
+template <>
+struct BwDepth<double> {
+  static __device__ double step(const GapDev &g, double x, int32_t n0, int64_t m) {
+    return bw_step_depth(g, x, n0, m);
+  }
+  static __device__ double bound(const GapDev &g, double x) {
+    return g.dt * g.rate_mult * kAlphaEm / g.lambda_hat * g.b * tbw_d(x * g.b);
+  }
+  static __device__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static constexpr double margin = 1e-9;
+};
+template <>
+struct BwDepth<float> {
+  static __device__ float step(const GapDev &g, double x, int32_t n0, int64_t m) {
+    return bw_step_depth_f(g, (float)x, n0, m);
+  }
+  static __device__ float bound(const GapDev &g, double x) {
+    return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * (float)g.b * tbw_f((float)(x * g.b));
+  }
+  static __device__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static constexpr float margin = 2e-2f;  // covers FP32 rounding of sums of up to ~1e5 terms
+};
+
+// Optical depth accumulated over the steps [m, n) (active steps only), from
+// tau at the start of step m: the same sequence the scheduler adds.
+template <class R>
+__device__ R photon_depth_at(const GapDev &g, double Xr, int32_t nr, int32_t dir, double x, int32_t n0,
+                             int32_t m, R tau, int64_t n) {
+  for (int64_t j = m; j < n; ++j)
+    if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
+  return tau;
+}
+
+// Schedule photon i of buffer b from its checkpoint (tau_acc before step pm).
+template <class R>
+__device__ void schedule_photon(const View &v, int b, int64_t i) {
+  const int gap = v.pgap[b][i];
+  const GapDev &g = v.gaps[gap];
+  const double Xr = v.pXr[b][i], x = v.px[b][i];
+  const int32_t nr = v.pnr[b][i], dir = v.pdir[b][i], n0 = v.pn0[b][i];
+  const int64_t m = v.pm[b][i];
+  const R ts = (R)v.pts[b][i];
+  R tau = (R)v.pta[b][i];
+  int32_t kind, ev;
+  if (g.periodic) {
+    if (tau >= ts) {
+      kind = PH_CONVERT;
+      ev = (int32_t)m;
+    } else if (BwDepth<R>::bound(g, x) == (R)0) {
+      kind = PH_INERT;
+      ev = kPhNever;
+    } else {
+      int64_t j = m;
+      kind = 0;
+      for (int it = 0; it < kSchedIters; ++it, ++j) {
+        if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
+        if (tau >= ts) {
+          kind = PH_CONVERT;
+          break;
+        }
+      }
+      if (kind == PH_CONVERT) {
+        ev = (int32_t)j;
+      } else {
+        kind = PH_RESCHEDULE;
+        ev = (int32_t)(j - 1);
+        v.pm[b][i] = (int32_t)j;
+        v.pta[b][i] = (double)tau;
+      }
+    }
+  } else {
+    // escape step: the first step whose move ends outside [0, nx)
+    const int64_t jx = first_step(g, Xr, nr, dir, m + 1, dir > 0 ? (double)g.nx : 0.0) - 1;
+    // steps of the life with QED active (start-of-step position below H_gap)
+    int64_t lo, hi;
+    if (dir > 0) {
+      lo = m;
+      hi = first_step(g, Xr, nr, dir, m, g.Hc);
+    } else {
+      lo = first_step(g, Xr, nr, dir, m, g.Hc);
+      hi = jx;
+    }
+    if (hi > jx) hi = jx;
+    if (tau >= ts) {
+      kind = m == jx ? PH_ESCAPE : PH_CONVERT;
+      ev = (int32_t)m;
+    } else {
+      const R rmax = BwDepth<R>::bound(g, x) * ((R)1 + BwDepth<R>::margin);
+      int64_t j = lo > m ? lo : m;
+      kind = PH_ESCAPE;
+      ev = (int32_t)jx;
+      for (int it = 0; j < hi; ++it, ++j) {
+        if ((it & 63) == 0 && tau + (R)(hi - j) * rmax < ts) break;  // cannot reach its threshold
+        if (it == kSchedIters) {
+          kind = PH_RESCHEDULE;
+          ev = (int32_t)(j - 1);
+          v.pm[b][i] = (int32_t)j;
+          v.pta[b][i] = (double)tau;
+          break;
+        }
+        tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
+        if (tau >= ts) {
+          kind = PH_CONVERT;
+          ev = (int32_t)j;
+          break;
+        }
+      }
+    }
+  }
+  v.pkind[b][i] = kind;
+  v.pev[b][i] = ev;
+}
+
+// The event of photon i at step `step`: conversion into an e-e+ pair with
+// gamma = x/2 each at the photon's new position, or escape through a boundary.
+template <class R>
+__device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
+  using W = typename Prec<R>::W;
+  const int kind = v.pkind[b][i];
+  const int gap = v.pgap[b][i];
+  const GapDev &g = v.gaps[gap];
+  const double x = v.px[b][i], w = v.pw[b][i];
+  if (kind == PH_ESCAPE) {
+    atomicAdd(&v.counters[gap * C_NCNT + C_PH_ESCAPED], 1ull);
+    atomicAdd(&v.ledger[gap * L_NLED + L_PH_ESC], w * x);
+  } else if (kind == PH_CONVERT) {
+    const int32_t dir = v.pdir[b][i];
+    const double X1 = photon_pos(g, v.pXr[b][i], v.pnr[b][i], dir, step + 1);
+    const uint64_t id = v.pid[b][i];
+    const double gp = 0.5 * x;
+    const double up = (double)dir * sqrt((gp - 1.0) * (gp + 1.0));
+    int32_t k;
+    R phi;
+    split_position<R>(X1, g.nx, g.periodic != 0, k, phi);
+    const int tn = tile_of(v, g, k);
+    W wq;
+    if (sizeof(R) == 4) wq = (W)llrint(w / g.w_unit);
+    else wq = (W)w;
+    for (int s = 0; s < 2; ++s) {
+      const uint64_t lid = child_id(id, (uint32_t)step, CH_PAIR, (uint32_t)s) & ~kPhotonBit;
+      const R tau = (R)(-log(uniform53(g.seed, lid, (uint32_t)(step + 1), CH_TAU0, 0)));
+      append_lepton<R>(v, s, tn, k, phi, (R)up, wq, tau, lid);
+    }
+    atomicAdd(&v.counters[gap * C_NCNT + C_PAIRS], 1ull);
+  } else {
+    return;
+  }
+  v.pev[b][i] = kPhDead;
+  atomicSub(&v.ph_gap[gap], 1);
+  const unsigned mask = __activemask();  // one count per warp of the dead since the last compaction
+  if ((threadIdx.x & 31) == __ffs(mask) - 1)
+    atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->ph_dead), (unsigned long long)__popc(mask));
+}
+
+// Photon pass of step n, part 1: a scan of the event steps.  Events of this
+// step are applied; photons waiting to be scheduled (new, imported, or at
+// their re-schedule step) go to a dense work list.
+template <class R>
+__global__ void __launch_bounds__(256) k_photon_scan(View v) {
+  const int b = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_count[b];
+  const int64_t step = v.ctl->step;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ev = v.pev[b][i];
+    bool work = false;
+    if (ev == kPhPending) {
+      work = true;
+    } else if (ev == step) {
+      if (v.pkind[b][i] == PH_RESCHEDULE) work = true;
+      else photon_event<R>(v, b, i, step);
+    } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
+      atomicOr(&v.ctl->error, 64);
+    }
+    if (work) {
+      const long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n));
+      v.ph_work[slot] = (int64_t)i;
+    }
+  }
+}
+
+// Part 2: schedule the work list (one photon per thread, densely packed);
+// an imported photon may have its event in this very step.
+template <class R>
+__global__ void __launch_bounds__(256) k_photon_schedule(View v) {
+  const int b = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_work_n;
+  const int64_t step = v.ctl->step;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = v.ph_work[t];
+    schedule_photon<R>(v, b, i);
+    if (v.pev[b][i] == step) photon_event<R>(v, b, i, step);
+  }
+}
+
+__global__ void k_photon_work_reset(View v) { v.ctl->ph_work_n = 0; }
+
+// Compaction of the photon store into the other buffer (once a quarter of
+// the store is dead, or it is half full): the survivors keep their records;
+// the order is not kept.
+__global__ void k_photon_compact(View v) {
+  if (!v.ctl->need_ph_compact) return;
+  const int b = v.ctl->ph_cur, o = b ^ 1;
+  const int64_t n = v.ctl->ph_count[b];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pev[b][i] == kPhDead) continue;
+    const long long d = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[o]));
+    v.pXr[o][d] = v.pXr[b][i];
+    v.px[o][d] = v.px[b][i];
+    v.pw[o][d] = v.pw[b][i];
+    v.pts[o][d] = v.pts[b][i];
+    v.pta[o][d] = v.pta[b][i];
+    v.pid[o][d] = v.pid[b][i];
+    v.pn0[o][d] = v.pn0[b][i];
+    v.pnr[o][d] = v.pnr[b][i];
+    v.pdir[o][d] = v.pdir[b][i];
+    v.pgap[o][d] = v.pgap[b][i];
+    v.pm[o][d] = v.pm[b][i];
+    v.pkind[o][d] = v.pkind[b][i];
+    v.pev[o][d] = v.pev[b][i];
+  }
+}
+
+__global__ void k_photon_flip(View v) {
+  Ctl *c = v.ctl;
+  if (!c->need_ph_compact) return;
+  const int b = c->ph_cur;
+  c->ph_count[b] = 0;
+  c->ph_cur = b ^ 1;
+  c->ph_dead = 0;
+  c->need_ph_compact = 0;
+}
+
+void launch_photon_step(const View &v, cudaStream_t st) {
+  k_photon_work_reset<<<1, 1, 0, st>>>(v);
+  if (v.precision == GAP_FP32_STATE) {
+    k_photon_scan<float><<<4 * 148, 256, 0, st>>>(v);
+    k_photon_schedule<float><<<4 * 148, 256, 0, st>>>(v);
+  } else {
+    k_photon_scan<double><<<4 * 148, 256, 0, st>>>(v);
+    k_photon_schedule<double><<<4 * 148, 256, 0, st>>>(v);
+  }
+}
+
+void launch_photon_compact(const View &v, cudaStream_t st) {
+  k_photon_compact<<<4 * 148, 256, 0, st>>>(v);
+  k_photon_flip<<<1, 1, 0, st>>>(v);
+}
+
+// Photon state at the start of the current step for export: position and
+// optical depth replayed from the checkpoint.
+template <class R>
+__global__ void k_export_photons_t(View v, int gap, double *stage, int64_t cap, unsigned long long *count) {
+  const int b = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_count[b];
+  const int64_t step = v.ctl->step;
+  const GapDev &g = v.gaps[gap];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pgap[b][i] != gap || v.pev[b][i] == kPhDead) continue;
+    const unsigned long long o = atomicAdd(count, 1ull);
+    if ((int64_t)o >= cap) continue;
+    const double Xr = v.pXr[b][i], x = v.px[b][i];
+    const int32_t nr = v.pnr[b][i], dir = v.pdir[b][i], n0 = v.pn0[b][i];
+    const int64_t m = v.pm[b][i];
+    const double ta = (double)photon_depth_at<R>(g, Xr, nr, dir, x, n0, (int32_t)m, (R)v.pta[b][i],
+                                                 m < step ? step : m);
+    reinterpret_cast<uint64_t *>(stage)[o] = v.pid[b][i];
+    stage[cap + o] = photon_pos(g, Xr, nr, dir, step);
+    stage[2 * cap + o] = x;
+    stage[3 * cap + o] = v.pw[b][i];
+    stage[4 * cap + o] = ta;
+    stage[5 * cap + o] = v.pts[b][i];
+    reinterpret_cast<int64_t *>(stage)[6 * cap + o] = ((int64_t)n0 << 1) | (dir > 0 ? 1 : 0);
+  }
+}
+
+void launch_export_photons(const View &v, int gap, double *stage, int64_t cap, unsigned long long *count,
+                           cudaStream_t st) {
+  if (v.precision == GAP_FP32_STATE) k_export_photons_t<float><<<148, 256, 0, st>>>(v, gap, stage, cap, count);
+  else k_export_photons_t<double><<<148, 256, 0, st>>>(v, gap, stage, cap, count);
+}
+
+__global__ void k_import_photons(View v, int gap, int64_t n, const double *stage) {
+  const int b = v.ctl->ph_cur;
+  const int32_t step = (int32_t)v.ctl->step;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t id = reinterpret_cast<const uint64_t *>(stage)[i] | kPhotonBit;
+    const int64_t aux = reinterpret_cast<const int64_t *>(stage)[6 * n + i];
+    if (photon_append(v, b, gap, stage[n + i], step, stage[2 * n + i], stage[3 * n + i], stage[5 * n + i],
+                      stage[4 * n + i], id, (int32_t)(aux >> 1), (aux & 1) ? 1 : -1, step))
+      atomicAdd(&v.ph_gap[gap], 1);
+  }
+}
+
+void launch_import_photons(const View &v, int gap, int64_t n, const double *stage, cudaStream_t st) {
+  const int blocks = (int)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184);
+  if (n > 0) k_import_photons<<<blocks, 256, 0, st>>>(v, gap, n, stage);
+}
+
+// Photon moments of one gap at the start of the current step: density per
+// cell (dmom row 7), energy sum w x (dred[17]) and count (dred[20]).
+__global__ void k_photon_moments(View v, int gap) {
+  const int b = v.ctl->ph_cur;
+  const int64_t n = v.ctl->ph_count[b];
+  const int64_t step = v.ctl->step;
+  const GapDev &g = v.gaps[gap];
+  double en = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pgap[b][i] != gap || v.pev[b][i] == kPhDead) continue;
+    const double X = photon_pos(g, v.pXr[b][i], v.pnr[b][i], v.pdir[b][i], step);
+    int64_t c = (int64_t)floor(X);
+    if (c < 0) c = 0;
+    if (c >= g.nx) c = g.nx - 1;
+    atomicAdd(&v.dmom[7 * g.nx + c], v.pw[b][i] / g.dx);
+    en += v.pw[b][i] * v.px[b][i];
+    atomicAdd(reinterpret_cast<unsigned long long *>(&v.dred[20]), 1ull);
+  }
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_down_sync(0xffffffffu, en, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[17], en);
+}
+
+void launch_photon_moments(const View &v, int gap, cudaStream_t st) {
+  k_photon_moments<<<148, 256, 0, st>>>(v, gap);
+}
+
+}  // namespace gapk

@@ -2,7 +2,7 @@
 // (paper Sect. 6.1 cycle reduced to the field-aligned direction):
 //   k_push      gather, kick, curvature emission, drift, deposit, boundaries,
 //               Ampere update of E (one block per tile, fused)
-//   k_photons   photon propagation, Breit-Wheeler optical depth, pair creation
+//   (photon propagation and pair creation: photons.cu)
 //   k_inject    cold-electron surface injection (atmosphere, Sect. 2.3 / 6.1)
 //   k_house     per-step bookkeeping of the tile segments and buffers
 //   k_rebin_*   compaction of the particle store into the other buffer
@@ -12,30 +12,78 @@
 namespace gapk {
 
 // ---------------------------------------------------------------------------
-// k_push: one block per tile.  Shared memory holds E^n on the tile's nodes
-// k0-1 .. k0+nk (in the precision of the state) and the charge through the
-// same nodes.  Interior nodes are complete when the block finishes and get
-// E^{n+1} = E^n + (dt j_m - D) at once; the four edge nodes shared with the
-// neighbouring tiles are finished by whichever of the two blocks arrives
-// second (atomic arrival count, no waiting).
+// k_push: the work of a step is a list of items, each a chunk of at most
+// kPushChunk leptons of one species of one tile (every tile has at least one
+// item), taken by a persistent grid from an atomic counter so that the tiles
+// where a discharge concentrates its pairs are shared out over many blocks.
+// Shared memory holds E^n on the tile's nodes k0-1 .. k0+nk (in the precision
+// of the state) and the charge through the same nodes.  A tile with one item
+// finishes its interior nodes at once, E^{n+1} = E^n + (dt j_m - D); a tile
+// with several adds every node's charge to the global accumulators and the
+// last of its items to finish does the update.  The four edge nodes shared
+// with the neighbouring tiles are finished by whichever of the two tiles
+// arrives second (atomic arrival count, no waiting).
 template <class R, bool QED, bool HAS_W>
-__global__ void __launch_bounds__(256) k_push(View v) {
+__global__ void __launch_bounds__(256, 3) k_push(View v) {
   using W = typename Prec<R>::W;
   using Acc = typename Prec<R>::Acc;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Acc sQ0;
+  __shared__ unsigned sQl[2];
+  __shared__ int sQh;
   __shared__ unsigned long long sCnt[8];
   __shared__ double sLed[4];
   __shared__ int sDead[2];
+  __shared__ int s_item, s_last;
 
-  const int t = blockIdx.x;
+  for (;;) {
+  __syncthreads();  // the previous item is done with shared memory
+  if (threadIdx.x == 0) s_item = atomicAdd(&v.ctl->push_next, 1);
+  __syncthreads();
+  const int item = s_item;
+  if (item >= v.ctl->push_items) return;
+  int t;
+  {
+    int lo = 0, hi = v.n_tiles;  // item_start[t] <= item < item_start[t + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (v.item_start[mid] <= item) lo = mid;
+      else hi = mid;
+    }
+    t = lo;
+  }
+  const int nitems = v.item_start[t + 1] - v.item_start[t];
+  int s_only, r0, r1;
+  {
+    const int c = item - v.item_start[t];
+    const int u0 = v.seg_used[0][t], u1 = v.seg_used[1][t];
+    const int n0c = (u0 + kPushChunk - 1) / kPushChunk;
+    if (c < n0c) {
+      s_only = 0;
+      r0 = c * kPushChunk;
+      r1 = u0 < r0 + kPushChunk ? u0 : r0 + kPushChunk;
+    } else {
+      s_only = 1;
+      r0 = (c - n0c) * kPushChunk;
+      r1 = u1 < r0 + kPushChunk ? u1 : r0 + kPushChunk;
+    }
+  }
   const TileDev ti = v.tiles[t];
   const GapDev &g = v.gaps[ti.gap];
   const int nk = ti.nk, k0 = ti.k0;
   const int64_t nx = g.nx;
   const bool periodic = g.periodic != 0;
+  // charge through the nodes: FP64 state, one double per node; FP32 state,
+  // the exact integer in three 32-bit limbs per node (see limb_add)
   Acc *sD = reinterpret_cast<Acc *>(smem);
-  R *sE = reinterpret_cast<R *>(smem + sizeof(Acc) * (nk + 2));
+  unsigned *sL0 = reinterpret_cast<unsigned *>(smem);
+  unsigned *sL1 = sL0 + (nk + 2);
+  int *sL2 = reinterpret_cast<int *>(sL1 + (nk + 2));
+  R *sE = sizeof(R) == 4 ? reinterpret_cast<R *>(sL2 + (nk + 2)) : reinterpret_cast<R *>(smem + sizeof(Acc) * (nk + 2));
+  auto node_charge = [&](int i) -> Acc {
+    if (sizeof(R) == 4) return (Acc)limb_value(sL0[i], sL1[i], sL2[i]);
+    return sD[i];
+  };
 
   const Ctl *ctl = v.ctl;
   const int ecur = ctl->e_cur;
@@ -55,12 +103,22 @@ __global__ void __launch_bounds__(256) k_push(View v) {
       e = (R)Eo[node];
     }
     sE[i] = e;
-    sD[i] = (Acc)0;
+    if (sizeof(R) == 4) {
+      sL0[i] = 0u;
+      sL1[i] = 0u;
+      sL2[i] = 0;
+    } else {
+      sD[i] = (Acc)0;
+    }
   }
   if (threadIdx.x < 8) sCnt[threadIdx.x] = 0ull;
   if (threadIdx.x < 4) sLed[threadIdx.x] = 0.0;
   if (threadIdx.x < 2) sDead[threadIdx.x] = 0;
-  if (threadIdx.x == 0) sQ0 = (Acc)0;
+  if (threadIdx.x == 0) {
+    sQ0 = (Acc)0;
+    sQl[0] = sQl[1] = 0u;
+    sQh = 0;
+  }
   __syncthreads();
 
   const R dt = (R)g.dt;
@@ -68,12 +126,21 @@ __global__ void __launch_bounds__(256) k_push(View v) {
   const R Hc15 = (R)(g.Hc + 1.5);
   const bool q0_tile = !periodic && k0 == 0;
   const W w_def = HAS_W ? (W)0 : (sizeof(R) == 4 ? (W)(1u << kWeightShift) : (W)g.w0);
+  // FP32 state: emission constants converted once (chi = gamma^2 lambda/rho,
+  // rate = rate_mult alpha_em gamma T(chi) / rho)
+  const float chi_cf = g.f_lam / g.f_rho;
+  const float rate_cf = g.f_rate * (float)kAlphaEm / g.f_rho;
+  const double wunit = sizeof(R) == 4 ? g.w_unit : 1.0;
 
   constexpr int VEC = 16 / (int)sizeof(R);  // particles per 16-byte vector load
-  for (int s = 0; s < 2; ++s) {
+  // per-thread event counts and energies, reduced per warp at the end (one
+  // shared atomic per warp instead of one per event)
+  unsigned c_emit = 0, c_ovf = 0, c_abs = 0, c_esc = 0, c_phesc = 0, c_ph = 0;
+  double l_rad = 0.0, l_abs = 0.0, l_esc = 0.0, l_phesc = 0.0;
+  for (int s = s_only; s == s_only; ++s) {
     const int q = s == 0 ? -1 : 1;
-    const int64_t start = v.seg_start[s][t];  // multiple of 32 slots: 16-byte aligned
-    const int used = v.seg_used[s][t];
+    const int64_t start = v.seg_start[s][t] + r0;  // multiples of 32 slots: 16-byte aligned
+    const int used = r1 - r0;
     int32_t *Kp = v.lk[cur][s];
     R *Pp = as<R>(v.lphi[cur][s]);
     R *Up = as<R>(v.lu[cur][s]);
@@ -81,6 +148,10 @@ __global__ void __launch_bounds__(256) k_push(View v) {
     R *Tp = as<R>(v.ltau[cur][s]);
     uint64_t *Ip = v.lid[cur][s];
     int dead = 0;
+    // this lane's deposit (charge through up to two nodes) and its share of
+    // the cell-0 charge, accumulated warp-wide after each lepton
+    int dkey0, dkey1, qkey;
+    Acc dval0, dval1, qval;
 
     // One lepton: gather, kick, emission, drift, deposit, boundaries.  k is
     // set to -1 when the lepton leaves the tile (migrated or removed).
@@ -103,9 +174,14 @@ __global__ void __launch_bounds__(256) k_push(View v) {
         int kk = 0;
         for (;;) {
           R gm = sqrt((R)1 + u * u);
-          R chi = gm * gm * (R)g.lambda_hat / (R)g.rho_hat;
-          R ts = sizeof(R) == 4 ? (R)tsyn_f((float)chi) : (R)tsyn_d((double)chi);
-          R r = (R)g.rate_mult * (R)kAlphaEm * gm * ts / (R)g.rho_hat;
+          R chi, r;
+          if (sizeof(R) == 4) {
+            chi = gm * gm * (R)chi_cf;
+            r = (R)rate_cf * gm * (R)tsyn_f((float)chi);
+          } else {
+            chi = gm * gm * (R)g.lambda_hat / (R)g.rho_hat;
+            r = (R)g.rate_mult * (R)kAlphaEm * gm * (R)tsyn_d((double)chi) / (R)g.rho_hat;
+          }
           if (!(r > (R)0)) break;
           if (tau > r * trem) {
             tau -= r * trem;
@@ -116,8 +192,9 @@ __global__ void __launch_bounds__(256) k_push(View v) {
             id = Ip[slot];
             have_id = true;
           }
-          double U = uniform53(g.seed, id, (uint32_t)step, CH_EMIT_X, (uint32_t)kk);
-          R xi = sizeof(R) == 4 ? (R)spec_inverse_f(v, (float)U) : (R)spec_inverse_d(v, U);
+          R xi = sizeof(R) == 4
+                     ? (R)spec_inverse_f(v, uniform24(g.seed, id, (uint32_t)step, CH_EMIT_X, (uint32_t)kk))
+                     : (R)spec_inverse_d(v, uniform53(g.seed, id, (uint32_t)step, CH_EMIT_X, (uint32_t)kk));
           R x = xi * (R)1.5 * gm * chi;
           R gm1 = u * u / (gm + (R)1);
           R dir = u >= (R)0 ? (R)1 : (R)-1;
@@ -129,18 +206,18 @@ __global__ void __launch_bounds__(256) k_push(View v) {
             R pp = (g2 - (R)1) * (g2 + (R)1);
             u = pp > (R)0 ? dir * sqrt(pp) : (R)0;
           }
-          atomicAdd(&sCnt[0], 1ull);
+          ++c_emit;
           if (x >= (R)2) {
             ph_x[nph] = dir * x;  // the sign carries the direction
             ph_k[nph] = kk;
             ++nph;
           } else {
-            atomicAdd(&sLed[0], (double)w * (sizeof(R) == 4 ? g.w_unit : 1.0) * (double)x);
+            l_rad += (double)w * wunit * (double)x;
           }
-          double U2 = uniform53(g.seed, id, (uint32_t)step, CH_EMIT_TAU, (uint32_t)kk);
-          tau = (R)(-log(U2));
+          if (sizeof(R) == 4) tau = (R)(-__logf(uniform24(g.seed, id, (uint32_t)step, CH_EMIT_TAU, (uint32_t)kk)));
+          else tau = (R)(-log(uniform53(g.seed, id, (uint32_t)step, CH_EMIT_TAU, (uint32_t)kk)));
           if (++kk >= g.kmax_emit) {
-            atomicAdd(&sCnt[1], 1ull);
+            ++c_ovf;
             break;
           }
         }
@@ -172,33 +249,34 @@ __global__ void __launch_bounds__(256) k_push(View v) {
         const int Fn = __float2int_rn(((float)pn - 1.0f) * 8388608.0f);
         const int f0 = dk == 0 ? Fn - Fo : (dk > 0 ? (1 << kPhiBits) - Fo : -Fo);
         const long long qw = (long long)q * (long long)w;
-        acc_add(reinterpret_cast<long long *>(&sD[lk]), qw * (long long)f0);
+        limb_add(sL0, sL1, sL2, lk, qw * (long long)f0);
         if (dk != 0) {
           const int f1 = dk > 0 ? Fn : Fn - (1 << kPhiBits);
-          acc_add(reinterpret_cast<long long *>(&sD[lk + dk]), qw * (long long)f1);
+          limb_add(sL0, sL1, sL2, lk + dk, qw * (long long)f1);
         }
       } else {
         const double f0 = dk == 0 ? (double)pn - (double)phi
                                   : (dk > 0 ? 2.0 - (double)phi : 1.0 - (double)phi);
         const double qw = (double)q * (double)w;
-        acc_add(reinterpret_cast<double *>(&sD[lk]), qw * f0);
+        dkey0 = lk;
+        dval0 = (Acc)(qw * f0);
         if (dk != 0) {
           const double f1 = dk > 0 ? (double)pn - 1.0 : (double)pn - 2.0;
-          acc_add(reinterpret_cast<double *>(&sD[lk + dk]), qw * f1);
+          dkey1 = lk + dk;
+          dval1 = (Acc)(qw * f1);
         }
       }
       // a7: boundaries
       bool gone = false;
-      const double wd = (double)w * (sizeof(R) == 4 ? g.w_unit : 1.0);
       if (!periodic) {
         if (kn < 0 || (kn == 0 && pn < (R)1.5)) {
           gone = true;
-          atomicAdd(&sCnt[2], 1ull);
-          atomicAdd(&sLed[1], wd * (double)sqrt((R)1 + u * u));
+          ++c_abs;
+          l_abs += (double)w * wunit * (double)sqrt((R)1 + u * u);
         } else if ((int64_t)kn > nx || ((int64_t)kn == nx && pn >= (R)1.5)) {
           gone = true;
-          atomicAdd(&sCnt[3], 1ull);
-          atomicAdd(&sLed[2], wd * (double)sqrt((R)1 + u * u));
+          ++c_esc;
+          l_esc += (double)w * wunit * (double)sqrt((R)1 + u * u);
         }
       } else {
         if (kn < 0) kn += (int32_t)nx;
@@ -206,6 +284,7 @@ __global__ void __launch_bounds__(256) k_push(View v) {
       }
       // photons born this step sit at the lepton's new position
       if (QED && nph > 0) {
+        const double wd = (double)w * wunit;
         double Xn = (double)kn + ((double)pn - 1.5);
         if (periodic && Xn < 0.0) Xn += (double)nx;
         const bool inside = periodic || (Xn >= 0.0 && Xn < (double)nx);
@@ -214,14 +293,15 @@ __global__ void __launch_bounds__(256) k_push(View v) {
           int32_t dirb = xb >= 0.0 ? 1 : -1;
           xb = fabs(xb);
           if (!inside) {
-            atomicAdd(&sCnt[4], 1ull);
-            atomicAdd(&sLed[3], wd * xb);
+            ++c_phesc;
+            l_phesc += wd * xb;
             continue;
           }
           uint64_t pid = child_id(id, (uint32_t)step, CH_PHOTON, (uint32_t)ph_k[b]) | kPhotonBit;
           double tsb = -log(uniform53(g.seed, pid, (uint32_t)(step + 1), CH_BW_TAU, 0));
-          photon_append(v, phbuf, ti.gap, Xn, xb, wd, tsb, 0.0, pid, (int32_t)(step + 1), dirb);
-          atomicAdd(&sCnt[6], 1ull);
+          photon_append(v, phbuf, ti.gap, Xn, (int32_t)(step + 1), xb, wd, tsb, 0.0, pid, (int32_t)(step + 1),
+                        dirb, (int32_t)(step + 1));
+          ++c_ph;
         }
       }
       if (gone) {
@@ -230,13 +310,14 @@ __global__ void __launch_bounds__(256) k_push(View v) {
         return;
       }
       if (q0_tile && kn <= 1) {
+        qkey = 0;
         if (sizeof(R) == 4) {
           const int Fn = __float2int_rn(((float)pn - 1.0f) * 8388608.0f);
           const long long frac = kn == 0 ? Fn : (1 << kPhiBits) - Fn;
-          acc_add(reinterpret_cast<long long *>(&sQ0), (long long)q * (long long)w * frac);
+          limb_add(sQl, sQl + 1, &sQh, 0, (long long)q * (long long)w * frac);
         } else {
           const double frac = kn == 0 ? (double)pn - 1.0 : 2.0 - (double)pn;
-          acc_add(reinterpret_cast<double *>(&sQ0), (double)q * (double)w * frac);
+          qval = (Acc)((double)q * (double)w * frac);
         }
       }
       if (kn >= k0 && kn < k0 + nk) {
@@ -252,23 +333,38 @@ __global__ void __launch_bounds__(256) k_push(View v) {
     };
 
     const int ngroups = (used + VEC - 1) / VEC;
-    for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+    // warp-uniform trip count: every lane takes part in the warp-wide deposit
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
+      const int gi = g0 + lane;
       const int base = gi * VEC;
       const int64_t slot0 = start + base;
+      const int nvalid = gi >= ngroups ? 0 : (used - base < VEC ? used - base : VEC);
       // all loads of the group first (memory-level parallelism)
-      Vec<int32_t, VEC> kv = *reinterpret_cast<const Vec<int32_t, VEC> *>(Kp + slot0);
-      Vec<R, VEC> pv = *reinterpret_cast<const Vec<R, VEC> *>(Pp + slot0);
-      Vec<R, VEC> uv = *reinterpret_cast<const Vec<R, VEC> *>(Up + slot0);
+      Vec<int32_t, VEC> kv;
+      Vec<R, VEC> pv, uv, tv;
       Vec<W, VEC> wv;
-      Vec<R, VEC> tv;
-      if (HAS_W) wv = *reinterpret_cast<const Vec<W, VEC> *>(Wp + slot0);
-      if (QED) tv = *reinterpret_cast<const Vec<R, VEC> *>(Tp + slot0);
-      const int nvalid = used - base < VEC ? used - base : VEC;
+      if (nvalid > 0) {
+        kv = *reinterpret_cast<const Vec<int32_t, VEC> *>(Kp + slot0);
+        pv = *reinterpret_cast<const Vec<R, VEC> *>(Pp + slot0);
+        uv = *reinterpret_cast<const Vec<R, VEC> *>(Up + slot0);
+        if (HAS_W) wv = *reinterpret_cast<const Vec<W, VEC> *>(Wp + slot0);
+        if (QED) tv = *reinterpret_cast<const Vec<R, VEC> *>(Tp + slot0);
+      }
 #pragma unroll
       for (int jj = 0; jj < VEC; ++jj) {
+        dkey0 = dkey1 = qkey = -1;
+        dval0 = dval1 = qval = (Acc)0;
         if (jj < nvalid && kv.a[jj] >= 0)
           push_one(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj);
+        if (sizeof(R) == 8) {  // FP64 charge: warp-aggregated double atomics
+          __syncwarp();
+          warp_run_add(sD, dkey0, dval0);
+          if (__any_sync(0xffffffffu, dkey1 >= 0)) warp_run_add(sD, dkey1, dval1);
+          if (q0_tile && __any_sync(0xffffffffu, qkey >= 0)) warp_run_add(&sQ0, qkey, qval);
+        }
       }
+      if (nvalid == 0) continue;
       if (nvalid == VEC) {
         *reinterpret_cast<Vec<int32_t, VEC> *>(Kp + slot0) = kv;
         *reinterpret_cast<Vec<R, VEC> *>(Pp + slot0) = pv;
@@ -288,40 +384,82 @@ __global__ void __launch_bounds__(256) k_push(View v) {
     for (int o = 16; o > 0; o >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, o);
     if ((threadIdx.x & 31) == 0 && dead) atomicAdd(&sDead[s], dead);
   }
+  {
+    unsigned cc[6] = {c_emit, c_ovf, c_abs, c_esc, c_phesc, c_ph};
+    double ll[4] = {l_rad, l_abs, l_esc, l_phesc};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) cc[i] += __shfl_down_sync(0xffffffffu, cc[i], o);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ll[i] += __shfl_down_sync(0xffffffffu, ll[i], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      const int slot[6] = {0, 1, 2, 3, 4, 6};
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        if (cc[i]) atomicAdd(&sCnt[slot[i]], (unsigned long long)cc[i]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (ll[i] != 0.0) atomicAdd(&sLed[i], ll[i]);
+    }
+  }
   __syncthreads();
 
   // a9: Ampere on the tile's nodes
   const double scale = sizeof(R) == 4 ? g.w_unit * kPhiUnit : 1.0;
   const double djm = g.dt * g.jm;
   double work = 0.0;
-  for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
-    const int64_t node = (int64_t)k0 - 1 + i;
-    const double eo = Eo[node];
-    const double en = eo + (djm - (double)sD[i] * scale);
-    En[node] = en;
-    work += eo + en;
+  bool finish = true;  // this block completes the tile
+  if (nitems > 1) {
+    for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+      const Acc qi = node_charge(i);
+      if (qi == (Acc)0) continue;
+      int64_t node = (int64_t)k0 - 1 + i;
+      if (periodic) node = (node + nx) % nx;
+      else if (node < 0 || node > nx) continue;
+      acc_add_global(&v.Dg[g.node_off + node], qi);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&v.tile_done[t], 1) == nitems - 1;
+    __syncthreads();
+    finish = s_last != 0;
+    if (finish) __threadfence();
   }
-  if (threadIdx.x < 4) {
-    const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
-    int64_t node = (int64_t)k0 - 1 + local;
-    bool valid = true;
-    if (periodic) node = (node + nx) % nx;
-    else valid = node >= 0 && node <= nx;
-    if (valid) {
-      const int64_t gn = g.node_off + node;
-      acc_add_global(&v.Dg[gn], sD[local]);
-      __threadfence();
-      const int old = atomicAdd(&v.arrive[gn], 1);
-      if (old == (int)v.expect[gn] - 1) {
+  if (finish) {
+    for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
+      const int64_t node = (int64_t)k0 - 1 + i;
+      const double eo = Eo[node];
+      const double D = nitems > 1 ? acc_take(&v.Dg[g.node_off + node], (Acc *)nullptr) * scale
+                                  : (double)node_charge(i) * scale;
+      const double en = eo + (djm - D);
+      En[node] = en;
+      work += eo + en;
+    }
+    if (threadIdx.x < 4) {
+      const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
+      int64_t node = (int64_t)k0 - 1 + local;
+      bool valid = true;
+      if (periodic) node = (node + nx) % nx;
+      else valid = node >= 0 && node <= nx;
+      if (valid) {
+        const int64_t gn = g.node_off + node;
+        if (nitems == 1) acc_add_global(&v.Dg[gn], node_charge(local));
         __threadfence();
-        const double D = acc_take(&v.Dg[gn], (Acc *)nullptr) * scale;
-        const double eo = Eo[node];
-        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
-        En[node] = en;
-        v.arrive[gn] = 0;
-        work += eo + en;
+        const int old = atomicAdd(&v.arrive[gn], 1);
+        if (old == (int)v.expect[gn] - 1) {
+          __threadfence();
+          const double D = acc_take(&v.Dg[gn], (Acc *)nullptr) * scale;
+          const double eo = Eo[node];
+          const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
+          En[node] = en;
+          v.arrive[gn] = 0;
+          work += eo + en;
+        }
       }
     }
+    if (nitems > 1 && threadIdx.x == 0) v.tile_done[t] = 0;
   }
   for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
   if ((threadIdx.x & 31) == 0 && work != 0.0)
@@ -336,15 +474,20 @@ __global__ void __launch_bounds__(256) k_push(View v) {
     if (sCnt[3]) atomicAdd(&C[C_ESCAPED], sCnt[3]);
     if (sCnt[4]) atomicAdd(&C[C_PH_ESCAPED], sCnt[4]);
     if (sCnt[5]) atomicAdd(&C[C_PH_OVF], sCnt[5]);
-    if (sCnt[6]) atomicAdd(&C[C_PHOTONS], sCnt[6]);
+    if (sCnt[6]) {
+      atomicAdd(&C[C_PHOTONS], sCnt[6]);
+      atomicAdd(&v.ph_gap[ti.gap], (int)sCnt[6]);
+    }
     if (sLed[0] != 0.0) atomicAdd(&Lg[L_RAD], sLed[0]);
     if (sLed[1] != 0.0) atomicAdd(&Lg[L_ABS], sLed[1]);
     if (sLed[2] != 0.0) atomicAdd(&Lg[L_ESC], sLed[2]);
     if (sLed[3] != 0.0) atomicAdd(&Lg[L_PH_ESC], sLed[3]);
     for (int s = 0; s < 2; ++s)
       if (sDead[s]) atomicAdd(&v.seg_alive[s][t], -sDead[s]);
-    if (q0_tile) acc_add_global(&v.q0[ti.gap], sQ0);
+    const Acc q0v = sizeof(R) == 4 ? (Acc)limb_value(sQl[0], sQl[1], sQh) : sQ0;
+    if (q0_tile && q0v != (Acc)0) acc_add_global(&v.q0[ti.gap], q0v);
   }
+  }  // items
 }
 
 // ---------------------------------------------------------------------------
@@ -359,14 +502,6 @@ __global__ void __launch_bounds__(256) k_push(View v) {
 // neither of which can overflow below 2^20 contributions; the node total is
 // hi 2^12 + lo, and the uniform weight multiplies it once, when it leaves
 // shared memory.
-__device__ __forceinline__ void red_shared_add_u32(unsigned *p, unsigned v) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ void red_shared_add_s32(int *p, int v) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
 __device__ __forceinline__ void deposit_split(unsigned *lo, int *hi, int c) {
   red_shared_add_u32(lo, (unsigned)(c & 4095));
   red_shared_add_s32(hi, c >> 12);
@@ -926,81 +1061,6 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
 }
 
 // ---------------------------------------------------------------------------
-// k_photons: every photon alive at step start moves by c dt, accumulates the
-// Breit-Wheeler optical depth at the mid-step angle sin(psi) = |sin(l/R_curv)|
-// (eq. tau_bw, Sect. 6.1) inside the gap, and converts into an e-e+ pair with
-// gamma = x/2 each once the depth reaches its threshold.  Survivors and the
-// photons born during this step are copied into the other buffer.
-template <class R>
-__global__ void k_photons(View v) {
-  using W = typename Prec<R>::W;
-  const int cur = v.ctl->ph_cur, nxt = cur ^ 1;
-  const int64_t n = v.ctl->ph_count[cur];
-  const int64_t step = v.ctl->step;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int gap = v.pgap[cur][i];
-    const GapDev &g = v.gaps[gap];
-    double X = v.pX[cur][i];
-    const double x = v.px[cur][i];
-    const double w = v.pw[cur][i];
-    const double ts = v.pts[cur][i];
-    double ta = v.pta[cur][i];
-    const uint64_t id = v.pid[cur][i];
-    const int32_t n0 = v.pn0[cur][i];
-    const int32_t dir = v.pdir[cur][i];
-    if ((int64_t)n0 > step) {  // born during this step: untouched
-      if (photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir)) atomicAdd(&v.ph_gap[nxt][gap], 1);
-      continue;
-    }
-    if (X < g.Hc) {
-      const double lmid = ((double)step - (double)n0 + 0.5) * g.dt;
-      const double sp = fabs(sin(lmid / g.rho_hat));
-      const double chi = x * g.b * sp;
-      ta += g.dt * g.rate_mult * kAlphaEm / g.lambda_hat * g.b * sp * tbw_d(chi);
-    }
-    X += (double)dir * g.cdx;
-    if (g.periodic) {
-      const double L = (double)g.nx;
-      X = fmod(X, L);
-      if (X < 0.0) X += L;
-      if (X >= L) X -= L;
-    } else if (X < 0.0 || X >= (double)g.nx) {
-      atomicAdd(&v.counters[gap * C_NCNT + C_PH_ESCAPED], 1ull);
-      atomicAdd(&v.ledger[gap * L_NLED + L_PH_ESC], w * x);
-      continue;
-    }
-    if (ta >= ts) {
-      const double gp = 0.5 * x;
-      const double up = (double)dir * sqrt((gp - 1.0) * (gp + 1.0));
-      int32_t k;
-      R phi;
-      split_position<R>(X, g.nx, g.periodic != 0, k, phi);
-      const int tn = tile_of(v, g, k);
-      W wq;
-      if (sizeof(R) == 4) wq = (W)llrint(w / g.w_unit);
-      else wq = (W)w;
-      for (int s = 0; s < 2; ++s) {
-        const uint64_t lid = child_id(id, (uint32_t)step, CH_PAIR, (uint32_t)s) & ~kPhotonBit;
-        const R tau = (R)(-log(uniform53(g.seed, lid, (uint32_t)(step + 1), CH_TAU0, 0)));
-        append_lepton<R>(v, s, tn, k, phi, (R)up, wq, tau, lid);
-      }
-      atomicAdd(&v.counters[gap * C_NCNT + C_PAIRS], 1ull);
-      continue;
-    }
-    if (photon_append(v, nxt, gap, X, x, w, ts, ta, id, n0, dir)) atomicAdd(&v.ph_gap[nxt][gap], 1);
-  }
-}
-
-// Per-gap photon counts of the buffer k_photons fills (the photons emitted in
-// the push and the survivors of the step) start at 0.
-__global__ void k_photon_count_reset(View v) {
-  const int nxt = v.ctl->ph_cur ^ 1;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.n_gaps; i += gridDim.x * blockDim.x)
-    v.ph_gap[nxt][i] = 0;
-}
-
-// ---------------------------------------------------------------------------
 // k_inject: one thread per gap with a surface.  Cell 0 must hold the
 // co-rotation charge eta_co dx = -dx; while its deficit exceeds half a
 // macro-particle charge a cold electron is added at X = U/2 in (0, 1/2].
@@ -1041,38 +1101,42 @@ __global__ void k_inject(View v) {
   }
 }
 
+
 // k_house: the appends of this step become part of the next step's work;
-// buffers of E and photons flip; the step counter advances.
+// the E buffers flip; the step counter advances; a re-bin is due every
+// rebin_every steps, after a spill, or when the photon store is half full.
 __global__ void k_house(View v) {
   const int n = 2 * v.n_tiles;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int s = i / v.n_tiles, t = i % v.n_tiles;
     const int a = v.seg_append[s][t], c = v.seg_cap[s][t];
+    v.gross[s][t] += a - v.seg_used[s][t];  // appends of this step (migrants, pairs, injected)
     v.seg_used[s][t] = a < c ? a : c;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl *c = v.ctl;
     c->step += 1;
     c->e_cur ^= 1;
-    if (v.qed_any) {
-      const int old = c->ph_cur;
-      c->ph_cur = old ^ 1;
-      c->ph_count[old] = 0;
-    }
     if (c->spill_n[0] > 0 || c->spill_n[1] > 0 || (v.rebin_every > 0 && c->step % v.rebin_every == 0))
       c->need_rebin = 1;
+    // the photon store is compacted once a quarter of it is dead, or it is half full
+    if (v.qed_any && (4 * c->ph_dead > c->ph_count[c->ph_cur] || 2 * c->ph_count[c->ph_cur] > v.ph_capacity))
+      c->need_ph_compact = 1;
   }
 }
 
 // k_sync_used: appends made outside a step (initial load, import) become
-// visible to the next compaction and push.
+// visible to the next compaction and push, and are not counted as growth.
 __global__ void k_sync_used(View v) {
   const int n = 2 * v.n_tiles;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int s = i / v.n_tiles, t = i % v.n_tiles;
     const int a = v.seg_append[s][t], c = v.seg_cap[s][t];
     v.seg_used[s][t] = a < c ? a : c;
+    v.last_cnt[s][t] = v.seg_alive[s][t] + v.spill_cnt[s][t];
+    v.gross[s][t] = 0;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.ctl->last_rebin_step = v.ctl->step;
 }
 
 // ---------------------------------------------------------------------------
@@ -1082,19 +1146,59 @@ __global__ void __launch_bounds__(1024) k_rebin_layout(View v, double slack) {
   if (!v.ctl->need_rebin) return;
   __shared__ long long warp_sums[32];
   __shared__ long long carry;
+  __shared__ double s_base, s_extra;
   const int n = v.n_tiles;
+  // a tile also gets room for the appends it saw since the last re-bin,
+  // projected over the next rebin_every steps, so that beams crossing tile
+  // edges and a filling discharge do not spill (and force a re-bin) every
+  // few steps; the extra room is scaled down to what the store holds
+  const long long elapsed = v.ctl->step - v.ctl->last_rebin_step > 0 ? v.ctl->step - v.ctl->last_rebin_step : 1;
+  const double horizon = 1.25 * (double)(v.rebin_every > 0 ? v.rebin_every : 64) / (double)elapsed;
   for (int s = 0; s < 2; ++s) {
+    auto counts = [&](int t, long long &cnt, long long &head, double &extra) {
+      cnt = (long long)v.seg_alive[s][t] + (long long)v.spill_cnt[s][t];
+      if (cnt < 0) cnt = 0;
+      head = (long long)(cnt * slack);
+      if (head < 64) head = 64;
+      // appends since the last re-bin (migrants from the neighbours, pairs,
+      // injected electrons: the slots a segment fills between re-bins), or
+      // the net growth if larger
+      long long grow = cnt - (long long)v.last_cnt[s][t];
+      if ((long long)v.gross[s][t] > grow) grow = v.gross[s][t];
+      extra = grow > 0 ? horizon * (double)grow : 0.0;
+    };
+    if (threadIdx.x == 0) {
+      s_base = 0.0;
+      s_extra = 0.0;
+    }
+    __syncthreads();
+    double b_loc = 0.0, e_loc = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      long long cnt, head;
+      double extra;
+      counts(t, cnt, head, extra);
+      b_loc += (double)(cnt + head + 64);
+      e_loc += extra;
+    }
+    atomicAdd(&s_base, b_loc);
+    atomicAdd(&s_extra, e_loc);
+    __syncthreads();
+    double f = 0.0;
+    if (s_extra > 0.0) {
+      f = ((double)v.lep_capacity - s_base) / s_extra;
+      f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+    }
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < n; base += blockDim.x) {
       const int t = base + threadIdx.x;
       long long cap = 0;
       if (t < n) {
-        long long cnt = (long long)v.seg_alive[s][t] + (long long)v.spill_cnt[s][t];
-        if (cnt < 0) cnt = 0;
-        long long head = (long long)(cnt * slack);
-        if (head < 64) head = 64;
-        cap = (cnt + head + 31) & ~31ll;
+        long long cnt, head;
+        double extra;
+        counts(t, cnt, head, extra);
+        cap = (cnt + head + (long long)(f * extra) + 31) & ~31ll;
+        if (cap > 0x7fffffe0ll) cap = 0x7fffffe0ll;
         v.new_cap[s][t] = (int32_t)cap;
       }
       // block exclusive scan of cap
@@ -1230,6 +1334,8 @@ __global__ void k_rebin_adopt(View v) {
     v.seg_append[s][t] = f;
     v.seg_alive[s][t] = f;
     v.spill_cnt[s][t] = 0;
+    v.last_cnt[s][t] = f;
+    v.gross[s][t] = 0;
   }
 }
 
@@ -1241,11 +1347,58 @@ __global__ void k_rebin_finish(View v) {
     c->lep_cur ^= 1;
     c->spill_n[0] = 0;
     c->spill_n[1] = 0;
+    c->last_rebin_step = c->step;
   }
   c->need_rebin = 0;
 }
 
 // ---------------------------------------------------------------------------
+// The push work list of this step: per tile max(1, chunks of species 0 +
+// chunks of species 1), their exclusive scan, and the shared item counter.
+__global__ void __launch_bounds__(1024) k_push_items(View v) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int n = v.n_tiles;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    int c = 0;
+    if (t < n) {
+      const int u0 = v.seg_used[0][t], u1 = v.seg_used[1][t];
+      c = (u0 + kPushChunk - 1) / kPushChunk + (u1 + kPushChunk - 1) / kPushChunk;
+      if (c < 1) c = 1;
+    }
+    int x = c;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sums[lane] = ws;
+    }
+    __syncthreads();
+    const int before = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + x - c;
+    if (t < n) v.item_start[t] = before;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + c;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v.item_start[n] = carry;
+    v.ctl->push_items = carry;
+    v.ctl->push_next = 0;
+  }
+}
+
 template <class R>
 static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
   if (sizeof(R) == 4 && !v.qed_any && !v.has_w) {
@@ -1267,26 +1420,25 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     }
     return;
   }
-  const size_t smem = (size_t)(v.tile + 8) * (sizeof(typename Prec<R>::Acc) + sizeof(R)) + 64;
+  const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
+  k_push_items<<<1, 1024, 0, st>>>(v);
+  const int grid = 148 * 4;  // persistent: blocks take items until the list is empty
   if (v.qed_any) {
     if (v.has_w)
-      k_push<R, true, true><<<v.n_tiles, threads, smem, st>>>(v);
+      k_push<R, true, true><<<grid, threads, smem, st>>>(v);
     else
-      k_push<R, true, false><<<v.n_tiles, threads, smem, st>>>(v);
+      k_push<R, true, false><<<grid, threads, smem, st>>>(v);
   } else {
     if (v.has_w)
-      k_push<R, false, true><<<v.n_tiles, threads, smem, st>>>(v);
+      k_push<R, false, true><<<grid, threads, smem, st>>>(v);
     else
-      k_push<R, false, false><<<v.n_tiles, threads, smem, st>>>(v);
+      k_push<R, false, false><<<grid, threads, smem, st>>>(v);
   }
 }
 
 template <class R>
 static void launch_after_push_impl(const View &v, cudaStream_t st) {
-  if (v.qed_any) {
-    k_photon_count_reset<<<(v.n_gaps + 255) / 256, 256, 0, st>>>(v);
-    k_photons<R><<<4 * 148, 256, 0, st>>>(v);
-  }
+  if (v.qed_any) launch_photon_step(v, st);
   if (v.surface_any) k_inject<R><<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
   k_house<<<(2 * v.n_tiles + 255) / 256, 256, 0, st>>>(v);
 }
@@ -1297,6 +1449,7 @@ static void launch_rebin_impl(const View &v, double slack, cudaStream_t st) {
   k_rebin_compact<R><<<2 * v.n_tiles, 256, 0, st>>>(v);
   k_rebin_spill<R><<<64, 256, 0, st>>>(v);
   k_rebin_adopt<<<(2 * v.n_tiles + 255) / 256, 256, 0, st>>>(v);
+  if (v.qed_any) launch_photon_compact(v, st);
   k_rebin_finish<<<1, 1, 0, st>>>(v);
 }
 
@@ -1316,7 +1469,9 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 }
 
 int launches_per_step(const View &v) {
-  return 1 + (v.qed_any ? 2 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5;
+  const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
+  return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
+         (v.qed_any ? 2 : 0);
 }
 
 void launch_sync_used(const View &v, cudaStream_t st) {

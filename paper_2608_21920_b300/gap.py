@@ -116,6 +116,16 @@ class Gap:
                 "gap_profile")
         return ms.value, n.value, lps.value
 
+    PHASES = ("push", "photons+inject+house", "rebin", "merge")
+
+    def profile_phases(self) -> tuple[dict, int]:
+        """Per-phase durations (ms, summed) of the steps profiled since the
+        last profile() call, and the number of those steps."""
+        ms = (C.c_double * len(self.PHASES))()
+        n = C.c_int64(0)
+        A.check(A.lib().gap_profile_phases(self._h, ms, C.byref(n)), self._h, "gap_profile_phases")
+        return {k: ms[i] for i, k in enumerate(self.PHASES)}, n.value
+
     def spectrum_inverse(self, U, precision: str | None = None):
         """xi with P(xi' > xi) = U for a CUDA tensor of uniforms (float64)."""
         U = U.to(device=self.device, dtype=torch.float64).contiguous()
