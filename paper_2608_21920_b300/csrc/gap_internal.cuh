@@ -330,29 +330,6 @@ __device__ __forceinline__ long long limb_value(unsigned l0, unsigned l1, int l2
   return (long long)l2 * (1ll << 38) + (long long)l1 * (1ll << 19) + (long long)l0;
 }
 
-// Warp-aggregated accumulation into shared memory: lanes that hold the same
-// key in a contiguous run of lanes sum their values into the run's last lane
-// (segmented inclusive scan over the lanes), which issues the one atomic;
-// key < 0 contributes nothing.  All 32 lanes of the warp must call it.  With
-// the store sorted by node most lanes of a warp share a few nodes, so this
-// replaces up to 32 same-address 64-bit atomics by one.
-template <class A>
-__device__ __forceinline__ void warp_run_add(A *base, int key, A val) {
-  const int lane = threadIdx.x & 31;
-  // run index: the number of run heads at or before this lane (non-decreasing
-  // over the lanes, so equal indices are one contiguous run)
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
-  const int run = __popc(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int r2 = __shfl_up_sync(0xffffffffu, run, o);
-    const A v2 = __shfl_up_sync(0xffffffffu, val, o);
-    if (lane >= o && r2 == run) val += v2;
-  }
-  const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (key >= 0 && last) acc_add(&base[key], val);
-}
 __device__ __forceinline__ void acc_add_global(unsigned long long *p, long long v) {
   atomicAdd(p, (unsigned long long)v);
 }

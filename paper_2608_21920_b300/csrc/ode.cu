@@ -173,7 +173,8 @@ extern "C" int ode_forward(const void *dev_p, const void *dev_y0, const void *de
       (dev_ckpt && ckpt_every <= 0) || delta < 0)
     return GAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const int threads = 64, blocks = (B + threads - 1) / threads;
+  // one thread per parameter set; small batches spread over more SMs
+  const int threads = B >= 148 * 64 ? 64 : 32, blocks = (B + threads - 1) / threads;
   if (dtype == 0)
     k_ode_forward<double><<<blocks, threads, 0, st>>>((const double *)dev_p, (const double *)dev_y0,
                                                       (const double *)dev_dt, B, nsteps, every,
@@ -194,7 +195,8 @@ extern "C" int ode_adjoint(const void *dev_p, const void *dev_dt, const void *de
       nsteps < 0 || every <= 0 || ckpt_every <= 0 || delta < 0)
     return GAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const int threads = 64, blocks = (B + threads - 1) / threads;
+  // one thread per parameter set; small batches spread over more SMs
+  const int threads = B >= 148 * 64 ? 64 : 32, blocks = (B + threads - 1) / threads;
   if (dtype == 0)
     k_ode_adjoint<double><<<blocks, threads, 0, st>>>(
         (const double *)dev_p, (const double *)dev_dt, (const double *)dev_ckpt, (const double *)dev_gout, B,

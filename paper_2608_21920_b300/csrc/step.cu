@@ -148,10 +148,6 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
     R *Tp = as<R>(v.ltau[cur][s]);
     uint64_t *Ip = v.lid[cur][s];
     int dead = 0;
-    // this lane's deposit (charge through up to two nodes) and its share of
-    // the cell-0 charge, accumulated warp-wide after each lepton
-    int dkey0, dkey1, qkey;
-    Acc dval0, dval1, qval;
 
     // One lepton: gather, kick, emission, drift, deposit, boundaries.  k is
     // set to -1 when the lepton leaves the tile (migrated or removed).
@@ -258,12 +254,10 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
         const double f0 = dk == 0 ? (double)pn - (double)phi
                                   : (dk > 0 ? 2.0 - (double)phi : 1.0 - (double)phi);
         const double qw = (double)q * (double)w;
-        dkey0 = lk;
-        dval0 = (Acc)(qw * f0);
+        acc_add(reinterpret_cast<double *>(&sD[lk]), qw * f0);
         if (dk != 0) {
           const double f1 = dk > 0 ? (double)pn - 1.0 : (double)pn - 2.0;
-          dkey1 = lk + dk;
-          dval1 = (Acc)(qw * f1);
+          acc_add(reinterpret_cast<double *>(&sD[lk + dk]), qw * f1);
         }
       }
       // a7: boundaries
@@ -310,14 +304,13 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
         return;
       }
       if (q0_tile && kn <= 1) {
-        qkey = 0;
         if (sizeof(R) == 4) {
           const int Fn = __float2int_rn(((float)pn - 1.0f) * 8388608.0f);
           const long long frac = kn == 0 ? Fn : (1 << kPhiBits) - Fn;
           limb_add(sQl, sQl + 1, &sQh, 0, (long long)q * (long long)w * frac);
         } else {
           const double frac = kn == 0 ? (double)pn - 1.0 : 2.0 - (double)pn;
-          qval = (Acc)((double)q * (double)w * frac);
+          acc_add(reinterpret_cast<double *>(&sQ0), (double)q * (double)w * frac);
         }
       }
       if (kn >= k0 && kn < k0 + nk) {
@@ -333,7 +326,7 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
     };
 
     const int ngroups = (used + VEC - 1) / VEC;
-    // warp-uniform trip count: every lane takes part in the warp-wide deposit
+    // warp-uniform trip count (lanes past the end load nothing)
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
       const int gi = g0 + lane;
@@ -353,16 +346,9 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
       }
 #pragma unroll
       for (int jj = 0; jj < VEC; ++jj) {
-        dkey0 = dkey1 = qkey = -1;
-        dval0 = dval1 = qval = (Acc)0;
         if (jj < nvalid && kv.a[jj] >= 0)
           push_one(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj);
-        if (sizeof(R) == 8) {  // FP64 charge: warp-aggregated double atomics
-          __syncwarp();
-          warp_run_add(sD, dkey0, dval0);
-          if (__any_sync(0xffffffffu, dkey1 >= 0)) warp_run_add(sD, dkey1, dval1);
-          if (q0_tile && __any_sync(0xffffffffu, qkey >= 0)) warp_run_add(&sQ0, qkey, qval);
-        }
+
       }
       if (nvalid == 0) continue;
       if (nvalid == VEC) {
