@@ -135,6 +135,23 @@ def traffic_record(kernel, precision):
     return rec.get("bytes_per_launch")
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's time (every rank gets it); x alone without a
+    process group."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank, steps, ms_max, world):
+    """Whole-job rate of independent replicas (weak scaling): the units
+    all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -150,12 +167,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    def rank_max(x):
+        return max_over_ranks(x, dist if world > 1 else None, "cuda")
 
     peaks, peak_kind = measured_peaks()
     cfg = dict(WORKLOAD, seed=rank, gap_index=rank)
@@ -185,7 +198,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         push_ms, push_n, lps = g.profile(False)
         clk = clocks.stop() if precision == "fp32" else None
-        ms = max_over_ranks(ms)
+        ms = rank_max(ms)
         d = g.diag(spectrum=False)
         r = dict(ms=ms, K=K, push_ms=push_ms / max(push_n, 1), push_n=push_n, launches=lps * K,
                  gauss=d["gauss_residual"], E_abs_max=d["E_abs_max"],
@@ -209,7 +222,7 @@ def run_ours(args):
                 A.check(A.lib().gap_get_field(g.handle, 0, C.c_void_p(Ehost.data_ptr()), NX, g.stream()),
                         g.handle, "get_field")
             barrier()
-            t_e2e = max_over_ranks(time.perf_counter() - t0)
+            t_e2e = rank_max(time.perf_counter() - t0)
             # host->device bytes of gap_init: gap and tile tables, tile-edge
             # counts, segment layout, spectrum tables (the plasma is loaded on
             # the device from the parameters); device->host per step: E and
@@ -227,7 +240,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     r32 = results["fp32"]
-    value = world * N_PARTICLES * r32["K"] / (r32["ms"] / 1e3)
+    value = job_throughput(N_PARTICLES, r32["K"], r32["ms"], world)
     bpp = BYTES_PER_PARTICLE["fp32"]
     achieved = bpp * N_PARTICLES / (r32["push_ms"] / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
@@ -261,7 +274,7 @@ def run_ours(args):
                        "includes": "gap_init from host parameters + per-step E readback to pinned host"}
     if "fp64" in results:
         r64 = results["fp64"]
-        v64 = world * N_PARTICLES * r64["K"] / (r64["ms"] / 1e3)
+        v64 = job_throughput(N_PARTICLES, r64["K"], r64["ms"], world)
         a64 = BYTES_PER_PARTICLE["fp64"] * N_PARTICLES / (r64["push_ms"] / 1e3) / 1e9
         line["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": r64["K"], "ms_per_step": r64["ms"] / r64["K"],
                               "achieved_gbs": a64, "frac": a64 / peak, "gauss_residual": r64["gauss"],
