@@ -12,6 +12,34 @@
 namespace gapk {
 
 // ---------------------------------------------------------------------------
+// One curvature-emission event (a3): the photon energy from the classical
+// spectrum at x_c = (3/2) gamma chi (eq. xcurv), the recoil (the whole kinetic
+// energy when the draw exceeds it: the lepton is then at rest), and the next
+// optical depth.  Returns x with the emission direction as its sign.  Kept out
+// of line: events are rare per lepton-step, and the push inlines its lepton
+// body once per vector lane.
+template <class R>
+__device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t id, uint32_t step, uint32_t kk,
+                                         R gm, R chi, R &u, R &tau) {
+  R xi = sizeof(R) == 4 ? (R)spec_inverse_f(v, uniform24(seed, id, step, CH_EMIT_X, kk))
+                        : (R)spec_inverse_d(v, uniform53(seed, id, step, CH_EMIT_X, kk));
+  R x = xi * (R)1.5 * gm * chi;
+  R gm1 = u * u / (gm + (R)1);
+  R dir = u >= (R)0 ? (R)1 : (R)-1;
+  if (x >= gm1) {  // the photon takes the whole kinetic energy
+    x = gm1;
+    u = (R)0;
+  } else {
+    R g2 = gm - x;
+    R pp = (g2 - (R)1) * (g2 + (R)1);
+    u = pp > (R)0 ? dir * sqrt(pp) : (R)0;
+  }
+  if (sizeof(R) == 4) tau = (R)(-__logf(uniform24(seed, id, step, CH_EMIT_TAU, kk)));
+  else tau = (R)(-log(uniform53(seed, id, step, CH_EMIT_TAU, kk)));
+  return dir * x;
+}
+
+// ---------------------------------------------------------------------------
 // k_push: the work of a step is a list of items, each a chunk of at most
 // kPushChunk leptons of one species of one tile (every tile has at least one
 // item), taken by a persistent grid from an atomic counter so that the tiles
@@ -132,7 +160,10 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
   const float rate_cf = g.f_rate * (float)kAlphaEm / g.f_rho;
   const double wunit = sizeof(R) == 4 ? g.w_unit : 1.0;
 
-  constexpr int VEC = 16 / (int)sizeof(R);  // particles per 16-byte vector load
+  // leptons per thread and group: 16-byte vectors without QED; one lepton
+  // (coalesced scalar loads) with QED, whose lepton body is large and
+  // instruction-bound, so that it is inlined once
+  constexpr int VEC = QED ? 1 : 16 / (int)sizeof(R);
   // per-thread event counts and energies, reduced per warp at the end (one
   // shared atomic per warp instead of one per event)
   unsigned c_emit = 0, c_ovf = 0, c_abs = 0, c_esc = 0, c_phesc = 0, c_ph = 0;
@@ -188,30 +219,16 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
             id = Ip[slot];
             have_id = true;
           }
-          R xi = sizeof(R) == 4
-                     ? (R)spec_inverse_f(v, uniform24(g.seed, id, (uint32_t)step, CH_EMIT_X, (uint32_t)kk))
-                     : (R)spec_inverse_d(v, uniform53(g.seed, id, (uint32_t)step, CH_EMIT_X, (uint32_t)kk));
-          R x = xi * (R)1.5 * gm * chi;
-          R gm1 = u * u / (gm + (R)1);
-          R dir = u >= (R)0 ? (R)1 : (R)-1;
-          if (x >= gm1) {  // the photon takes the whole kinetic energy: lepton at rest
-            x = gm1;
-            u = (R)0;
-          } else {
-            R g2 = gm - x;
-            R pp = (g2 - (R)1) * (g2 + (R)1);
-            u = pp > (R)0 ? dir * sqrt(pp) : (R)0;
-          }
+          const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau);
+          const R x = xs >= (R)0 ? xs : -xs;
           ++c_emit;
           if (x >= (R)2) {
-            ph_x[nph] = dir * x;  // the sign carries the direction
+            ph_x[nph] = xs;  // the sign carries the direction
             ph_k[nph] = kk;
             ++nph;
           } else {
             l_rad += (double)w * wunit * (double)x;
           }
-          if (sizeof(R) == 4) tau = (R)(-__logf(uniform24(g.seed, id, (uint32_t)step, CH_EMIT_TAU, (uint32_t)kk)));
-          else tau = (R)(-log(uniform53(g.seed, id, (uint32_t)step, CH_EMIT_TAU, (uint32_t)kk)));
           if (++kk >= g.kmax_emit) {
             ++c_ovf;
             break;
