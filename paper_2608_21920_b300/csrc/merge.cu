@@ -21,6 +21,7 @@ namespace gapk {
 
 constexpr int kMergeBins = 256;
 constexpr int kMergeKeys = 2 * kMergeBins;  // direction x bin
+constexpr int kMergeWarpBytes = 46 * kMergeKeys;  // one warp's key table and touched list
 constexpr uint32_t CH_MERGE = 10;
 
 // One thread per gap: decide whether the gap merges this step.
@@ -60,8 +61,21 @@ struct MergeAcc<float> {  // FP32 state: exact integer sums of m and m Phi (2^-2
   using T = unsigned long long;
 };
 
+constexpr int kMergeWarps = 4;  // warps per merge block, each with its own key table
+
+// An output slot for each lane of a warp that asks for one.
+__device__ __forceinline__ int warp_slot(int *cursor) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(cursor, __popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
 template <class R>
-__global__ void __launch_bounds__(256) k_merge(View v) {
+__global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
   using W = typename Prec<R>::W;
   using A = typename MergeAcc<R>::T;
   if (!(v.ctl->flags & 1)) return;
@@ -74,21 +88,36 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
   const int cur = v.ctl->lep_cur, nxt = cur ^ 1;
   const int64_t step = v.ctl->step;  // the step just completed is step - 1
   const int q = s == 0 ? -1 : 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
+  // per warp: a direct-mapped table over the 512 (direction, bin) keys and
+  // the list of keys the current node touched (only those are reset)
   extern __shared__ __align__(16) unsigned char msm[];
-  int *cnt = reinterpret_cast<int *>(msm);                                            // [kMergeKeys]
-  unsigned long long *minid = reinterpret_cast<unsigned long long *>(msm + 4 * kMergeKeys);
-  A *sw = reinterpret_cast<A *>(msm + 12 * kMergeKeys);                                // sum w
-  A *sphi = reinterpret_cast<A *>(msm + 20 * kMergeKeys);                              // sum w phi
-  double *sp = reinterpret_cast<double *>(msm + 28 * kMergeKeys);                      // sum w (g+u)
-  double *sm = reinterpret_cast<double *>(msm + 36 * kMergeKeys);                      // sum w (g-u)
-  int *hist = reinterpret_cast<int *>(msm + 44 * kMergeKeys);                          // [nk + 1]
-  __shared__ int wsum[8];
+  unsigned char *wb = msm + (size_t)wid * kMergeWarpBytes;
+  int *cnt = reinterpret_cast<int *>(wb);
+  unsigned long long *minid = reinterpret_cast<unsigned long long *>(wb + 4 * kMergeKeys);
+  A *sw = reinterpret_cast<A *>(wb + 12 * kMergeKeys);                                // sum w
+  A *sphi = reinterpret_cast<A *>(wb + 20 * kMergeKeys);                              // sum w phi
+  double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then eta
+  double *sm = reinterpret_cast<double *>(wb + 36 * kMergeKeys);                      // sum w (g-u), then D
+  short *touched = reinterpret_cast<short *>(wb + 44 * kMergeKeys);                   // [kMergeKeys]
+  int *hist = reinterpret_cast<int *>(msm + (size_t)kMergeWarps * kMergeWarpBytes);  // [nk + 1]
+  __shared__ int wsum[kMergeWarps];
+  __shared__ int ntouched[kMergeWarps];
   __shared__ int carry, out_cursor;
   __shared__ unsigned long long merged_count;
 
   const int64_t seg0 = v.seg_start[s][t];
   const int used = v.seg_used[s][t];
+  for (int i = lane; i < kMergeKeys; i += 32) {
+    cnt[i] = 0;
+    minid[i] = ~0ull;
+    sw[i] = (A)0;
+    sphi[i] = (A)0;
+    sp[i] = 0.0;
+    sm[i] = 0.0;
+  }
+  if (lane == 0) ntouched[wid] = 0;
   // 1. counting sort of the segment by node into the other buffer
   for (int i = threadIdx.x; i <= nk; i += blockDim.x) hist[i] = 0;
   if (threadIdx.x == 0) {
@@ -111,7 +140,6 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
     const int i = base + threadIdx.x;
     const int x = i < nk ? hist[i] : 0;
     int y = x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
       const int z = __shfl_up_sync(0xffffffffu, y, o);
       if (lane >= o) y += z;
@@ -141,56 +169,51 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
   }
   __syncthreads();
   // after the scatter hist[i] holds the end of node i's run = start of node i+1
-  // 2. node by node: group, merge, write back into the current buffer
-  for (int node = 0; node < nk; ++node) {
+
+  auto copy_out = [&](int64_t src) {
+    const int64_t d = seg0 + warp_slot(&out_cursor);
+    v.lk[cur][s][d] = v.lk[nxt][s][src];
+    as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
+    as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
+    as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
+    as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
+    v.lid[cur][s][d] = v.lid[nxt][s][src];
+  };
+  auto key_of = [&](int64_t src) -> int {
+    const double u = (double)as<R>(v.lu[nxt][s])[src];
+    const double gm = sqrt(1.0 + u * u);
+    int64_t b = (int64_t)floor(log(gm) / width);
+    if (b < 0) b = 0;
+    if (b > kMergeBins - 1) b = kMergeBins - 1;
+    return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
+  };
+  auto weight_of = [&](int64_t src) -> double {
+    const W wq = as<W>(v.lw[nxt][s])[src];
+    return sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+  };
+
+  // 2. one warp per node: group, merge, write back into the current buffer
+  for (int node = wid; node < nk; node += kMergeWarps) {
     const int r0 = node == 0 ? 0 : hist[node - 1], r1 = hist[node];
     if (r1 - r0 < 3) {  // nothing to merge: copy through
-      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const int64_t src = seg0 + i;
-        const int o = atomicAdd(&out_cursor, 1);
-        const int64_t d = seg0 + o;
-        v.lk[cur][s][d] = v.lk[nxt][s][src];
-        as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
-        as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
-        as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
-        as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
-        v.lid[cur][s][d] = v.lid[nxt][s][src];
-      }
-      __syncthreads();
+      for (int i = r0 + lane; i < r1; i += 32) copy_out(seg0 + i);
       continue;
     }
-    for (int i = threadIdx.x; i < kMergeKeys; i += blockDim.x) {
-      cnt[i] = 0;
-      minid[i] = ~0ull;
-      sw[i] = (A)0;
-      sphi[i] = (A)0;
-      sp[i] = 0.0;
-      sm[i] = 0.0;
-    }
-    __syncthreads();
-    auto key_of = [&](int64_t src) -> int {
-      const double u = (double)as<R>(v.lu[nxt][s])[src];
-      const double gm = sqrt(1.0 + u * u);
-      int64_t b = (int64_t)floor(log(gm) / width);
-      if (b < 0) b = 0;
-      if (b > kMergeBins - 1) b = kMergeBins - 1;
-      return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
-    };
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
       const double u = (double)as<R>(v.lu[nxt][s])[src];
-      const W wq = as<W>(v.lw[nxt][s])[src];
-      const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
+      const double w = weight_of(src);
       const double gm = sqrt(1.0 + u * u);
       const double big = gm + fabs(u);
       const double gp = u >= 0.0 ? big : 1.0 / big, gmn = u >= 0.0 ? 1.0 / big : big;
       const R phi = as<R>(v.lphi[nxt][s])[src];
-      atomicAdd(&cnt[key], 1);
+      if (atomicAdd(&cnt[key], 1) == 0) touched[atomicAdd(&ntouched[wid], 1)] = (short)key;
       atomicMin(&minid[key], (unsigned long long)v.lid[nxt][s][src]);
       atomicAdd(&sp[key], w * gp);
       atomicAdd(&sm[key], w * gmn);
       if (sizeof(R) == 4) {
+        const W wq = as<W>(v.lw[nxt][s])[src];
         const long long F = __float2int_rn(((float)phi - 1.0f) * 8388608.0f);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sw[key]), (unsigned long long)wq);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sphi[key]), (unsigned long long)((long long)wq * F));
@@ -199,60 +222,52 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
         atomicAdd(reinterpret_cast<double *>(&sphi[key]), w * ((double)phi - 1.0));
       }
     }
-    __syncthreads();
+    __syncwarp();
+    const int nt = ntouched[wid];
     // centre rapidity eta into sp[]; sm[] then accumulates
     // D = sum w 2 sinh^2((asinh u - eta)/2), so that M = W + D and
     // M^2 - W^2 = D (2W + D) carry no cancellation for nearly cold groups
-    for (int key = threadIdx.x; key < kMergeKeys; key += blockDim.x) {
+    for (int j = lane; j < nt; j += 32) {
+      const int key = touched[j];
       if (cnt[key] < 3) continue;
       sp[key] = 0.5 * log(sp[key] / sm[key]);
       sm[key] = 0.0;
     }
-    __syncthreads();
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    __syncwarp();
+    for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
       if (cnt[key] < 3) continue;
       const double u = (double)as<R>(v.lu[nxt][s])[src];
-      const W wq = as<W>(v.lw[nxt][s])[src];
-      const double w = sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
       const double h = sinh(0.5 * (asinh(u) - sp[key]));
-      atomicAdd(&sm[key], w * 2.0 * h * h);
+      atomicAdd(&sm[key], weight_of(src) * 2.0 * h * h);
     }
-    __syncthreads();
+    __syncwarp();
     // leptons of small groups are copied through
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
-      if (cnt[key_of(src)] >= 3) continue;
-      const int o = atomicAdd(&out_cursor, 1);
-      const int64_t d = seg0 + o;
-      v.lk[cur][s][d] = v.lk[nxt][s][src];
-      as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
-      as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
-      as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
-      as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
-      v.lid[cur][s][d] = v.lid[nxt][s][src];
+      if (cnt[key_of(src)] < 3) copy_out(src);
     }
     // groups of three or more become two
     const int32_t kn = k0 + node;
-    for (int key = threadIdx.x; key < kMergeKeys; key += blockDim.x) {
+    for (int j = lane; j < nt; j += 32) {
+      const int key = touched[j];
       const int n = cnt[key];
       if (n < 3) continue;
-      double Wt, phim, flux;
+      double Wt, flux;
       W wa, wb;
       R phi_store;
       if (sizeof(R) == 4) {
         const long long Wi = (long long)sw[key], Si = (long long)sphi[key];
         const long long Fm = (2 * Si + Wi) / (2 * Wi);  // round(S/W) for S >= 0
         flux = (double)q * (double)(Wi * Fm - Si) * g.w_unit * kPhiUnit;
-        phim = (double)Fm * kPhiUnit;
         phi_store = (R)(1.0f + (float)Fm * (float)kPhiUnit);
         wa = (W)(Wi / 2);
         wb = (W)(Wi - Wi / 2);
         Wt = (double)Wi * g.w_unit;
       } else {
         const double Wd = (double)sw[key], Sd = (double)sphi[key];
-        phim = Sd / Wd;
+        const double phim = Sd / Wd;
         flux = (double)q * (Wd * phim - Sd);
         phi_store = (R)(1.0 + phim);
         if (phi_store >= (R)2) phi_store = (R)2 - (R)2.220446049250313e-16;
@@ -260,7 +275,6 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
         wb = (W)(Wd - 0.5 * Wd);
         Wt = Wd;
       }
-      (void)phim;
       const double wad = sizeof(R) == 4 ? (double)wa * g.w_unit : (double)wa;
       const double wbd = sizeof(R) == 4 ? (double)wb * g.w_unit : (double)wb;
       const double eta = sp[key], D = sm[key], M = Wt + D;
@@ -285,8 +299,22 @@ __global__ void __launch_bounds__(256) k_merge(View v) {
       }
       atomicAdd(&merged_count, (unsigned long long)(n - 2));
     }
-    __syncthreads();
+    __syncwarp();
+    // reset the touched keys for the warp's next node
+    for (int j = lane; j < nt; j += 32) {
+      const int key = touched[j];
+      cnt[key] = 0;
+      minid[key] = ~0ull;
+      sw[key] = (A)0;
+      sphi[key] = (A)0;
+      sp[key] = 0.0;
+      sm[key] = 0.0;
+    }
+    __syncwarp();
+    if (lane == 0) ntouched[wid] = 0;
+    __syncwarp();
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     v.seg_used[s][t] = out_cursor;
     v.seg_append[s][t] = out_cursor;
@@ -299,9 +327,17 @@ __global__ void k_merge_done(View v) { v.ctl->flags &= ~1; }
 
 void launch_merge(const View &v, cudaStream_t st) {
   k_merge_check<<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
-  const size_t smem = (size_t)44 * kMergeKeys + (size_t)(v.tile + 8) * sizeof(int) + 64;
-  if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 256, smem, st>>>(v);
-  else k_merge<double><<<2 * v.n_tiles, 256, smem, st>>>(v);
+  const size_t smem = (size_t)kMergeWarps * kMergeWarpBytes + (size_t)(v.tile + 8) * sizeof(int) + 64;
+  // shared memory above 48 KB is opted into once, for the largest tile
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int most = (int)((size_t)kMergeWarps * kMergeWarpBytes + (size_t)(4096 + 8) * sizeof(int) + 64);
+    cudaFuncSetAttribute(k_merge<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_merge<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    attr_set = true;
+  }
+  if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
+  else k_merge<double><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
   k_merge_done<<<1, 1, 0, st>>>(v);
 }
 

@@ -203,26 +203,44 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
 // step are applied; photons waiting to be scheduled (new, imported, or at
 // their re-schedule step) go to a dense work list.
 template <class R>
+__device__ __forceinline__ void photon_scan_one(const View &v, int b, int64_t i, int32_t ev, int64_t step) {
+  bool work = false;
+  if (ev == kPhPending) {
+    work = true;
+  } else if (ev == step) {
+    if (v.pkind[b][i] == PH_RESCHEDULE) work = true;
+    else photon_event<R>(v, b, i, step);
+  } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
+    atomicOr(&v.ctl->error, 64);
+  }
+  if (work) {
+    const long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n));
+    v.ph_work[slot] = (int64_t)i;
+  }
+}
+
+template <class R>
 __global__ void __launch_bounds__(256) k_photon_scan(View v) {
   const int b = v.ctl->ph_cur;
   const int64_t n = v.ctl->ph_count[b];
   const int64_t step = v.ctl->step;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  // four event steps per 16-byte load; most photons are dead or not due
+  auto idle = [&](int32_t ev) { return ev == kPhDead || ev > step; };
+  const int4 *ev4 = reinterpret_cast<const int4 *>(v.pev[b]);
+  const int64_t n4 = n / 4;
+  for (int64_t q = tid; q < n4; q += stride) {
+    const int4 e = ev4[q];
+    if (idle(e.x) && idle(e.y) && idle(e.z) && idle(e.w)) continue;
+    const int64_t i = 4 * q;
+    if (!idle(e.x)) photon_scan_one<R>(v, b, i, e.x, step);
+    if (!idle(e.y)) photon_scan_one<R>(v, b, i + 1, e.y, step);
+    if (!idle(e.z)) photon_scan_one<R>(v, b, i + 2, e.z, step);
+    if (!idle(e.w)) photon_scan_one<R>(v, b, i + 3, e.w, step);
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
     const int32_t ev = v.pev[b][i];
-    bool work = false;
-    if (ev == kPhPending) {
-      work = true;
-    } else if (ev == step) {
-      if (v.pkind[b][i] == PH_RESCHEDULE) work = true;
-      else photon_event<R>(v, b, i, step);
-    } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
-      atomicOr(&v.ctl->error, 64);
-    }
-    if (work) {
-      const long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n));
-      v.ph_work[slot] = (int64_t)i;
-    }
+    if (!idle(ev)) photon_scan_one<R>(v, b, i, ev, step);
   }
 }
 

@@ -1064,46 +1064,67 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
 }
 
 // ---------------------------------------------------------------------------
-// k_inject: one thread per gap with a surface.  Cell 0 must hold the
+// k_inject: one warp per gap with a surface.  Cell 0 must hold the
 // co-rotation charge eta_co dx = -dx; while its deficit exceeds half a
 // macro-particle charge a cold electron is added at X = U/2 in (0, 1/2].
+// The lanes make the draws of up to 32 candidate electrons at once; the
+// deficit recurrence then runs over them in order (every lane runs it on the
+// broadcast offsets, so all agree), and the accepted lanes append.
 template <class R>
 __global__ void k_inject(View v) {
   using W = typename Prec<R>::W;
-  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= v.n_gaps) return;
+  const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gi >= v.n_gaps) return;  // whole warp
   const GapDev &g = v.gaps[gi];
   if (g.periodic) return;
   const int64_t step = v.ctl->step;
-  double Q0;
-  if (sizeof(R) == 4) Q0 = (double)(long long)atomicExch(&v.q0[gi], 0ull) * g.w_unit * kPhiUnit;
-  else Q0 = __longlong_as_double((long long)atomicExch(&v.q0[gi], 0ull));
+  double Q0 = 0.0;
+  if (lane == 0) {
+    if (sizeof(R) == 4) Q0 = (double)(long long)atomicExch(&v.q0[gi], 0ull) * g.w_unit * kPhiUnit;
+    else Q0 = __longlong_as_double((long long)atomicExch(&v.q0[gi], 0ull));
+  }
+  Q0 = __shfl_sync(0xffffffffu, Q0, 0);
   if (!(g.w0 > 0.0)) return;
   double deficit = Q0 + g.dx;
-  int j = 0;
   unsigned long long *C = v.counters + gi * C_NCNT;
-  while (deficit > 0.5 * g.w0) {
-    if (j >= g.kmax_inject) {
-      atomicAdd(&C[C_INJ_OVF], 1ull);
-      break;
+  int injected = 0;
+  for (int base = 0; base < g.kmax_inject && deficit > 0.5 * g.w0; base += 32) {
+    const int j = base + lane;
+    uint64_t id = 0;
+    double o = 0.0;
+    if (j < g.kmax_inject) {
+      id = child_id(g.inj_root, (uint32_t)step, CH_INJECT, (uint32_t)j) & ~kPhotonBit;
+      o = 0.5 * uniform53(g.seed, id, (uint32_t)(step + 1), CH_INJECT, 0);
     }
-    const uint64_t id = child_id(g.inj_root, (uint32_t)step, CH_INJECT, (uint32_t)j) & ~kPhotonBit;
-    const double o = 0.5 * uniform53(g.seed, id, (uint32_t)(step + 1), CH_INJECT, 0);
-    int32_t k;
-    R phi;
-    split_position<R>(o, g.nx, false, k, phi);
-    const R tau = (R)(-log(uniform53(g.seed, id, (uint32_t)(step + 1), CH_TAU0, 0)));
-    W w;
-    if (sizeof(R) == 4) w = (W)(1u << kWeightShift);
-    else w = (W)g.w0;
-    append_lepton<R>(v, 0, tile_of(v, g, k), k, phi, (R)0, w, tau, id);
-    deficit -= g.w0 * (o + 0.5);
-    atomicAdd(&C[C_INJECTED], 1ull);
-    atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0);
-    ++j;
+    int take = 0;  // candidates accepted in this chunk
+    for (int i = 0; i < 32; ++i) {
+      const double oi = __shfl_sync(0xffffffffu, o, i);
+      if (base + i < g.kmax_inject && deficit > 0.5 * g.w0) {
+        deficit = __dsub_rn(deficit, __dmul_rn(g.w0, oi + 0.5));  // a separate product and difference
+        take = i + 1;
+      }
+    }
+    if (lane < take) {
+      int32_t k;
+      R phi;
+      split_position<R>(o, g.nx, false, k, phi);
+      const R tau = (R)(-log(uniform53(g.seed, id, (uint32_t)(step + 1), CH_TAU0, 0)));
+      W w;
+      if (sizeof(R) == 4) w = (W)(1u << kWeightShift);
+      else w = (W)g.w0;
+      append_lepton<R>(v, 0, tile_of(v, g, k), k, phi, (R)0, w, tau, id);
+    }
+    injected += take;
+  }
+  if (lane == 0) {
+    if (deficit > 0.5 * g.w0) atomicAdd(&C[C_INJ_OVF], 1ull);  // kmax_inject reached
+    if (injected) {
+      atomicAdd(&C[C_INJECTED], (unsigned long long)injected);
+      atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0 * (double)injected);
+    }
   }
 }
-
 
 // k_house: the appends of this step become part of the next step's work;
 // the E buffers flip; the step counter advances; a re-bin is due every
@@ -1442,7 +1463,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
 template <class R>
 static void launch_after_push_impl(const View &v, cudaStream_t st) {
   if (v.qed_any) launch_photon_step(v, st);
-  if (v.surface_any) k_inject<R><<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
+  if (v.surface_any) k_inject<R><<<(v.n_gaps + 3) / 4, 128, 0, st>>>(v);  // a warp per gap
   k_house<<<(2 * v.n_tiles + 255) / 256, 256, 0, st>>>(v);
 }
 
