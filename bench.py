@@ -335,8 +335,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-BATCH_NAME = ("cfg4 batch: 256 independent gaps, Nx~U[1024,8192], alpha~U[-1,3], b~logU[0.03,0.3], "
-              "rho_c~logU[1e6,1e8] cm, 8-64 cold e-/cell, QED on, per-gap seeds 0..255, cap 16x initial")
+BATCH_NAME = ("cfg4 batch: {n} independent gaps, Nx~U[1024,8192], alpha~U[-1,3], b~logU[0.03,0.3], "
+              "rho_c~logU[1e6,1e8] cm, 8-64 cold e-/cell, QED on, per-gap seeds 0..{last}, cap 16x initial")
 
 
 def _total_leptons(g):
@@ -361,7 +361,12 @@ def run_batch(args):
     if args.autotune:
         (tile, threads, rebin), times = autotune.tune_step(params, "fp32", verbose=(rank == 0))
         tuned = {f"{t}x{th}r{rb}": round(ms, 4) for (t, th, rb), ms in times.items()}
-    g = Gap(params, precision="fp32", tile=tile, threads=threads, rebin_every=rebin)
+    cap_kw = {}
+    if args.capacity_factor > 0:  # smaller stores for profiling captures (a few GB)
+        init = sum(p["nx"] * p["ppc"] for p in params)
+        cap_kw = dict(lepton_capacity=int(args.capacity_factor * init),
+                      photon_capacity=int(4 * args.capacity_factor * init // 3))
+    g = Gap(params, precision="fp32", tile=tile, threads=threads, rebin_every=rebin, **cap_kw)
     s = torch.cuda.Stream()
     chunk = args.graph_chunk
     with torch.cuda.stream(s):
@@ -399,7 +404,8 @@ def run_batch(args):
         "metric": METRIC, "value": world * nmean * K / (ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup * chunk, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": BATCH_NAME, "gaps": args.gaps, "graph_chunk": chunk, "tile": tile,
+        "config": {"workload": BATCH_NAME.format(n=args.gaps, last=args.gaps - 1), "gaps": args.gaps,
+                   "capacity_factor": args.capacity_factor or None, "graph_chunk": chunk, "tile": tile,
                    "threads": threads, "rebin_every": rebin, "advanced_before_timing": args.batch_advance,
                    "leptons_mean": nmean, "l2": "inputs larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -440,6 +446,8 @@ def main():
     ap.add_argument("--gaps", type=int, default=256)
     ap.add_argument("--graph-chunk", type=int, default=50)
     ap.add_argument("--batch-advance", type=int, default=1500)
+    ap.add_argument("--capacity-factor", type=float, default=0.0,
+                    help="batch: lepton store = factor x initial count (profiling captures only; 0: caps)")
     args = ap.parse_args()
     if args.nx:
         set_size(args.nx)

@@ -301,10 +301,10 @@ __global__ void k_photon_flip(View v) {
 void launch_photon_step(const View &v, cudaStream_t st) {
   k_photon_work_reset<<<1, 1, 0, st>>>(v);
   if (v.precision == GAP_FP32_STATE) {
-    k_photon_scan<float><<<4 * 148, 256, 0, st>>>(v);
+    k_photon_scan<float><<<16 * 148, 256, 0, st>>>(v);  // many loads in flight: the scan is latency-bound
     k_photon_schedule<float><<<4 * 148, 256, 0, st>>>(v);
   } else {
-    k_photon_scan<double><<<4 * 148, 256, 0, st>>>(v);
+    k_photon_scan<double><<<16 * 148, 256, 0, st>>>(v);
     k_photon_schedule<double><<<4 * 148, 256, 0, st>>>(v);
   }
 }
