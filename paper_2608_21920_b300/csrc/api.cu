@@ -346,6 +346,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     v.pm[b] = C.take<int32_t>(ph_cap);
     v.pev[b] = C.take<int32_t>(ph_cap);
     v.pkind[b] = C.take<int32_t>(ph_cap);
+    v.pmn[b] = C.take<int32_t>(ph_cap);
+    v.ptan[b] = C.take<double>(ph_cap);
   }
   v.ph_work = C.take<int64_t>(ph_cap);
   v.ph_capacity = ph_cap;

@@ -108,6 +108,8 @@ struct View {
   double *pXr[2], *px[2], *pw[2], *pts[2], *pta[2];
   uint64_t *pid[2];
   int32_t *pn0[2], *pnr[2], *pdir[2], *pgap[2], *pm[2], *pev[2], *pkind[2];
+  int32_t *pmn[2];   // checkpoint a pending re-schedule starts from (step, tau
+  double *ptan[2];   // before it), adopted when the re-schedule is taken
   int64_t *ph_work;  // photon indices to schedule this step
   int64_t ph_capacity;
   // per-gap accumulators

@@ -20,7 +20,7 @@
 
 namespace gapk {
 
-constexpr int kSchedIters = 256;  // accumulated steps per photon per scheduling pass
+constexpr int kSchedIters = 64;  // accumulated steps per photon per scheduling pass (a multiple of 4)
 
 // Smallest step j >= j0 with pos(j) >= T (dir > 0) or pos(j) < T (dir < 0),
 // for a non-periodic gap, where pos is monotone in j.
@@ -30,8 +30,24 @@ __device__ int64_t first_step(const GapDev &g, double Xr, int32_t nr, int32_t di
     return dir > 0 ? X >= T : X < T;
   };
   if (hit(j0)) return j0;
-  int64_t lo = j0;  // !hit(lo)
   const double d = dir > 0 ? (T - Xr) / g.cdx : (Xr - T) / g.cdx;
+  // the exact motion puts the answer within rounding of the estimate: walk
+  // the last steps; a long walk falls back to bisection
+  {
+    int64_t j = (int64_t)nr + (int64_t)ceil(d > 0.0 ? d : 0.0);
+    if (j <= j0) j = j0 + 1;
+    int guard = 0;
+    while (j > j0 + 1 && guard < 8 && hit(j - 1)) {
+      --j;
+      ++guard;
+    }
+    while (guard < 16 && !hit(j)) {
+      ++j;
+      ++guard;
+    }
+    if (hit(j) && (j == j0 + 1 || !hit(j - 1))) return j;
+  }
+  int64_t lo = j0;  // !hit(lo)
   int64_t hi = (int64_t)nr + (int64_t)ceil(d > 0.0 ? d : 0.0) + 2;
   if (hi <= lo) hi = lo + 1;
   for (int guard = 0; guard < 62 && !hit(hi); ++guard) hi = lo + 2 * (hi - lo);
@@ -85,6 +101,10 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
   const GapDev &g = v.gaps[gap];
   const double Xr = v.pXr[b][i], x = v.px[b][i];
   const int32_t nr = v.pnr[b][i], dir = v.pdir[b][i], n0 = v.pn0[b][i];
+  if (v.pkind[b][i] == PH_RESCHEDULE) {  // the walk so far becomes the checkpoint
+    v.pm[b][i] = v.pmn[b][i];
+    v.pta[b][i] = v.ptan[b][i];
+  }
   const int64_t m = v.pm[b][i];
   const R ts = (R)v.pts[b][i];
   R tau = (R)v.pta[b][i];
@@ -111,8 +131,8 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
       } else {
         kind = PH_RESCHEDULE;
         ev = (int32_t)(j - 1);
-        v.pm[b][i] = (int32_t)j;
-        v.pta[b][i] = (double)tau;
+        v.pmn[b][i] = (int32_t)j;
+        v.ptan[b][i] = (double)tau;
       }
     }
   } else {
@@ -136,21 +156,34 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
       int64_t j = lo > m ? lo : m;
       kind = PH_ESCAPE;
       ev = (int32_t)jx;
-      for (int it = 0; j < hi; ++it, ++j) {
+      for (int it = 0; j < hi;) {
         if ((it & 63) == 0 && tau + (R)(hi - j) * rmax < ts) break;  // cannot reach its threshold
         if (it == kSchedIters) {
           kind = PH_RESCHEDULE;
           ev = (int32_t)(j - 1);
-          v.pm[b][i] = (int32_t)j;
-          v.pta[b][i] = (double)tau;
+          v.pmn[b][i] = (int32_t)j;
+          v.ptan[b][i] = (double)tau;
           break;
         }
-        tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
-        if (tau >= ts) {
-          kind = PH_CONVERT;
-          ev = (int32_t)j;
-          break;
+        // four steps' depths at once (independent), added in step order
+        const int nb = hi - j < 4 ? (int)(hi - j) : 4;
+        R r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = q < nb ? BwDepth<R>::step(g, x, n0, j + q) : (R)0;
+        bool conv = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q >= nb || conv) continue;
+          tau = BwDepth<R>::add(tau, r[q]);
+          if (tau >= ts) {
+            kind = PH_CONVERT;
+            ev = (int32_t)(j + q);
+            conv = true;
+          }
         }
+        if (conv) break;
+        j += nb;
+        it += nb;
       }
     }
   }
@@ -283,6 +316,8 @@ __global__ void k_photon_compact(View v) {
     v.pdir[o][d] = v.pdir[b][i];
     v.pgap[o][d] = v.pgap[b][i];
     v.pm[o][d] = v.pm[b][i];
+    v.pmn[o][d] = v.pmn[b][i];
+    v.ptan[o][d] = v.ptan[b][i];
     v.pkind[o][d] = v.pkind[b][i];
     v.pev[o][d] = v.pev[b][i];
   }
