@@ -23,6 +23,7 @@ constexpr double kPhiUnit = 1.0 / 8388608.0;   // 2^-23
 constexpr int kWeightShift = 8;                // FP32 weight unit = w0 / 2^8
 constexpr int kMaxEmit = 16;                   // emission events per lepton-step (upper bound)
 constexpr int kPushChunk = 4096;  // leptons per push work item (multiple of 32)
+static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 contributions per node");
 
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
@@ -319,9 +320,10 @@ __device__ __forceinline__ void red_shared_add_s32(int *p, int v) {
 // c = q w F (|c| < 2^55: weight units w < 2^32, offset flux |F| <= 2^23) is
 // split as c = c2 2^38 + c1 2^19 + c0 with c0, c1 in [0, 2^19) and c2 =
 // floor(c / 2^38), |c2| <= 2^17, each added to its own 32-bit counter.  A
-// node receives at most 2 kPushChunk = 8192 contributions per push item, so
-// the unsigned limbs stay below 8192 (2^19 - 1) < 2^32 and the signed one
-// below 2^30: the node's exact sum is c2sum 2^38 + c1sum 2^19 + c0sum.
+// node receives at most one contribution per lepton of a push item (a move
+// crosses a node at most once), at most kPushChunk <= 8192, so the unsigned
+// limbs stay below 8192 (2^19 - 1) < 2^32 and the signed one below 2^30: the
+// node's exact sum is c2sum 2^38 + c1sum 2^19 + c0sum.
 __device__ __forceinline__ void limb_add(unsigned *L0, unsigned *L1, int *L2, int i, long long c) {
   const unsigned long long u = (unsigned long long)c;
   red_shared_add_u32(&L0[i], (unsigned)(u & 0x7FFFFull));
