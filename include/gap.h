@@ -191,6 +191,15 @@ int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uin
                       double *host_X, double *host_u, double *host_w, double *host_tau,
                       double *host_aux, int64_t *host_aux2, int64_t *n_out, void *stream);
 
+/* Export the leptons of one species (kind 0 electrons, 1 positrons) of one
+ * gap whose id is a multiple of `stride` (>= 1), as gap_get_particles does:
+ * a fixed sample of a large gap that stays the same from step to step (ids
+ * do not change when leptons move between tiles or the store is compacted).
+ * GAP_EINVAL for photons or stride < 1.  Synchronises `stream`. */
+int gap_sample_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
+                         uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
+                         int64_t *n_out, void *stream);
+
 /* Append n particles of one kind to gap `gap` (tests build hand-checkable
  * states).  Photons: host_u is x, host_tau is tau_star, host_aux2 packs
  * (n0 << 1) | (dir > 0).  In a handle without QED and without a cap

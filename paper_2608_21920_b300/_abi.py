@@ -77,6 +77,7 @@ def lib():
     L.gap_get_field.argtypes = [vp, i32, vp, i64, vp]
     L.gap_set_field.argtypes = [vp, i32, vp, i64, vp]
     L.gap_get_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
+    L.gap_sample_particles.argtypes = [vp, i32, i32, i64, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_add_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
     L.gap_solve_gauss.argtypes = [vp, i32, vp]
     L.gap_set_background.argtypes = [vp, i32, d]
@@ -99,7 +100,7 @@ def lib():
 
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
-            "gap_get_field", "gap_set_field", "gap_get_particles", "gap_add_particles",
+            "gap_get_field", "gap_set_field", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
             "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_spectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 

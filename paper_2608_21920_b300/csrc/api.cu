@@ -614,9 +614,31 @@ int gap_set_background(gap_handle *h, int32_t gap, double eta_bg) {
   return cuda_check(h, e, "set background");
 }
 
+// Shared by gap_get_particles (stride 1) and gap_sample_particles.
+static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
+                            uint64_t *host_id, double *host_X, double *host_u, double *host_w,
+                            double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
+                            void *stream);
+
 int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uint64_t *host_id,
                       double *host_X, double *host_u, double *host_w, double *host_tau, double *host_aux,
                       int64_t *host_aux2, int64_t *n_out, void *stream) {
+  return export_particles(h, gap, kind, 1, cap, host_id, host_X, host_u, host_w, host_tau, host_aux,
+                          host_aux2, n_out, stream);
+}
+
+int gap_sample_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
+                         uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
+                         int64_t *n_out, void *stream) {
+  if (kind == GAP_PHOTON || stride < 1) return GAP_EINVAL;
+  return export_particles(h, gap, kind, stride, cap, host_id, host_X, host_u, host_w, host_tau, nullptr,
+                          nullptr, n_out, stream);
+}
+
+static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
+                            uint64_t *host_id, double *host_X, double *host_u, double *host_w,
+                            double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
+                            void *stream) {
   if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > 2 || !n_out) return GAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Ctl c;
@@ -625,7 +647,7 @@ int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uin
   const int64_t scap = (int64_t)(h->buf_bytes / (8 * 7));
   double *stage = reinterpret_cast<double *>(h->buf_base[c.lep_cur ^ 1]);
   cudaError_t e = cudaMemsetAsync(h->export_count, 0, sizeof(unsigned long long), st);
-  launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st);
+  launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st, stride);
   if (e == cudaSuccess) e = cudaGetLastError();
   unsigned long long cnt = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, h->export_count, sizeof(cnt), cudaMemcpyDeviceToHost, st);

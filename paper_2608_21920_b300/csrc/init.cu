@@ -472,7 +472,7 @@ void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st)
 // Photon stage: id | X | x | w | tau_acc | tau_star | aux2.
 template <class R>
 __global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t cap,
-                                 unsigned long long *count) {
+                                 unsigned long long *count, int64_t stride) {
   using W = typename Prec<R>::W;
   const GapDev &g = v.gaps[gap];
   const int t = g.tile_begin + blockIdx.x;
@@ -483,6 +483,7 @@ __global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t 
     const int64_t slot = start + i;
     const int32_t k = v.lk[cur][s][slot];
     if (k < 0) continue;
+    if (stride > 1 && v.lid[cur][s][slot] % (uint64_t)stride != 0) continue;  // a sample by id
     const unsigned long long o = atomicAdd(count, 1ull);
     if ((int64_t)o >= cap) continue;
     const R phi = as<R>(v.lphi[cur][s])[slot];
@@ -546,13 +547,13 @@ void launch_import(const View &v, int gap, int kind, int64_t n, const double *st
 }
 
 void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
-                        unsigned long long *count, int n_tiles_gap, cudaStream_t st) {
+                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride) {
   if (kind == GAP_PHOTON) {
     launch_export_photons(v, gap, stage, cap, count, st);
   } else if (v.precision == GAP_FP32_STATE) {
-    k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count);
+    k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride);
   } else {
-    k_export_leptons<double><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count);
+    k_export_leptons<double><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride);
   }
 }
 

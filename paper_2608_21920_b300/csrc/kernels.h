@@ -33,7 +33,7 @@ void launch_gauss(const View &v, int set_background, cudaStream_t st);
 void launch_spec_inverse(const View &v, const double *U, double *xi, int64_t n, int fp32, cudaStream_t st);
 void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st);
 void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
-                        unsigned long long *count, int n_tiles_gap, cudaStream_t st);
+                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride = 1);
 void launch_import(const View &v, int gap, int kind, int64_t n, const double *stage,
                    cudaStream_t st);
 

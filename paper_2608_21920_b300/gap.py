@@ -176,6 +176,21 @@ class Gap:
                        dir=np.where(aux2[:m] & 1, 1, -1).astype(np.int32))
         return res
 
+    def sample_particles(self, kind: int, stride: int, gap: int = 0) -> dict:
+        """Leptons of one species whose id is a multiple of `stride`: the same
+        sample from step to step, for large gaps."""
+        L = A.lib()
+        n = C.c_int64(0)
+        L.gap_sample_particles(self._h, gap, kind, int(stride), 0, None, None, None, None, None, C.byref(n),
+                               self.stream())
+        cap = n.value
+        out = dict(id=np.empty(cap, np.uint64), X=np.empty(cap), u=np.empty(cap), w=np.empty(cap),
+                   tau=np.empty(cap))
+        A.check(L.gap_sample_particles(self._h, gap, kind, int(stride), cap, _ptr(out["id"]), _ptr(out["X"]),
+                                       _ptr(out["u"]), _ptr(out["w"]), _ptr(out["tau"]), C.byref(n),
+                                       self.stream()), self._h, "gap_sample_particles")
+        return {k: v[:n.value] for k, v in out.items()}
+
     def add_particles(self, kind: int, id, X, u, w, tau, n0=None, direction=None, gap: int = 0):
         id = np.ascontiguousarray(id, dtype=np.uint64)
         X, u, w, tau = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, u, w, tau))

@@ -1,0 +1,58 @@
+"""The roofline workload at its full size, in the launch configuration the
+bench times: Nx = 2^20 periodic cells, 200 e- + 200 e+ per cell (4.19e8
+leptons), Maxwell-Juttner theta = 0.1, 1e-3 Langmuir seed, FP32 state, tile
+256, 256 threads, the lean push.  The oracle cannot step 4e8 leptons, but it
+can push any one of them: a fixed sample (ids divisible by 20000, about 1e4
+per species) is pushed one step by the oracle from the GPU's own state and
+field E^n, and must match the GPU's step to FP32 rounding.  Gauss's law,
+which holds at any size, is checked on the whole gap."""
+import numpy as np
+import pytest
+
+import bench
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+STRIDE = 20000
+
+
+def test_config2_full_size_sampled_push_and_gauss():
+    from paper_2608_21920_b300 import Gap
+    cfg = dict(bench.WORKLOAD, nx=1 << 20, seed=0, gap_index=0)
+    nx = cfg["nx"]
+    g = Gap(cfg, precision="fp32", tile=256, threads=256, variant=0)
+    try:
+        g.step(3)
+        E = g.field()
+        before = [g.sample_particles(kind, STRIDE) for kind in (0, 1)]
+        g.step(1)
+        after = [g.sample_particles(kind, STRIDE) for kind in (0, 1)]
+        d = g.diag(spectrum=False)
+    finally:
+        g.close()
+    assert d["n_electrons"] + d["n_positrons"] == 2 * nx * cfg["ppc"]
+    assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+
+    o = O.Sim(nx=nx, boundary=O.BC_PERIODIC, dx=cfg["dx"], dt=cfg["dt"], init=O.INIT_EMPTY)
+    o.set_E(E)
+    for kind, q in ((0, -1), (1, 1)):
+        b = before[kind]
+        assert b["id"].size > 9000  # about 1e4 per species
+        for i in range(b["id"].size):
+            o.add_lepton(int(b["id"][i]), q, float(b["X"][i]), float(b["u"][i]), float(b["w"][i]))
+    o.step(1)
+    L = o.leptons()
+    got = {k: np.concatenate([a[k] for a in after]) for k in ("id", "X", "u")}
+    gi, oi = np.argsort(got["id"]), np.argsort(L["id"])
+    assert np.array_equal(got["id"][gi], L["id"][oi])  # periodic: every sampled lepton is still there
+    dX = got["X"][gi] - L["X"][oi]
+    dX -= nx * np.round(dX / nx)
+    du = got["u"][gi] - L["u"][oi]
+    # FP32 offsets (2^-23 cells) and momenta; the kick of this step is ~1e-4,
+    # the drift ~0.2 cells, so a wrong sign or term is far outside these
+    assert np.abs(dX).max() < 2e-6
+    assert np.abs(du).max() < 2e-6 * max(1.0, np.abs(L["u"]).max())
+    moved = np.abs((L["X"][oi] - np.concatenate([b["X"] for b in before])[np.argsort(
+        np.concatenate([b["id"] for b in before]))]))
+    assert np.median(np.minimum(moved, nx - moved)) > 1e-3  # the leptons did move
