@@ -448,6 +448,13 @@ static __device__ __noinline__ bool photon_append(const View &v, int buf, int ga
   return false;
 }
 
+// Photons stored in buffer b.  The fill counter keeps counting appends that
+// found the store full (they are refused and flagged), so readers clamp it.
+__device__ __forceinline__ int64_t photon_fill(const View &v, int b) {
+  const int64_t n = v.ctl->ph_count[b];
+  return n < v.ph_capacity ? n : v.ph_capacity;
+}
+
 // Position of a photon at the start of step m: photons move at c along h
 // (Sect. 6.1), X = X_ref + dir (m - n_ref) c dt/dx, rounded once in the
 // product and once in the sum (never fused), wrapped into the box when

@@ -255,7 +255,7 @@ __device__ __forceinline__ void photon_scan_one(const View &v, int b, int64_t i,
 template <class R>
 __global__ void __launch_bounds__(256) k_photon_scan(View v) {
   const int b = v.ctl->ph_cur;
-  const int64_t n = v.ctl->ph_count[b];
+  const int64_t n = photon_fill(v, b);
   const int64_t step = v.ctl->step;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
   // four event steps per 16-byte load; most photons are dead or not due
@@ -300,7 +300,7 @@ __global__ void k_photon_work_reset(View v) { v.ctl->ph_work_n = 0; }
 __global__ void k_photon_compact(View v) {
   if (!v.ctl->need_ph_compact) return;
   const int b = v.ctl->ph_cur, o = b ^ 1;
-  const int64_t n = v.ctl->ph_count[b];
+  const int64_t n = photon_fill(v, b);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (v.pev[b][i] == kPhDead) continue;
@@ -354,7 +354,7 @@ void launch_photon_compact(const View &v, cudaStream_t st) {
 template <class R>
 __global__ void k_export_photons_t(View v, int gap, double *stage, int64_t cap, unsigned long long *count) {
   const int b = v.ctl->ph_cur;
-  const int64_t n = v.ctl->ph_count[b];
+  const int64_t n = photon_fill(v, b);
   const int64_t step = v.ctl->step;
   const GapDev &g = v.gaps[gap];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -405,7 +405,7 @@ void launch_import_photons(const View &v, int gap, int64_t n, const double *stag
 // cell (dmom row 7), energy sum w x (dred[17]) and count (dred[20]).
 __global__ void k_photon_moments(View v, int gap) {
   const int b = v.ctl->ph_cur;
-  const int64_t n = v.ctl->ph_count[b];
+  const int64_t n = photon_fill(v, b);
   const int64_t step = v.ctl->step;
   const GapDev &g = v.gaps[gap];
   double en = 0.0;
