@@ -275,6 +275,15 @@ int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_
  * on the last recorded event.  The mode is switched by gap_profile. */
 int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out);
 
+/* Test hook for the timeout path of the bulk-copy push variants (config
+ * variant 4 or 5): with on != 0, later push launches leave the first copy
+ * stage of every tile unissued and poll its barrier only 2^14 times, so the
+ * wait runs out; the kernel records the failure and returns, the next call
+ * that reads the control block returns GAP_ETIMEOUT, and the GPU context
+ * stays usable.  The handle's state is then invalid and the handle is to be
+ * freed.  For tests of error handling only; other variants ignore it. */
+int gap_hold_copies(gap_handle *h, int32_t on);
+
 /* Release host state.  The caller frees the workspace afterwards. */
 void gap_free(gap_handle *h);
 

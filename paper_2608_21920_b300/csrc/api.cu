@@ -837,6 +837,13 @@ int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_
   return GAP_OK;
 }
 
+int gap_hold_copies(gap_handle *h, int32_t on) {
+  if (!h) return GAP_EINVAL;
+  const int32_t flag = on != 0;
+  return cuda_check(h, cudaMemcpy(&h->v.ctl->hold_copies, &flag, sizeof(flag), cudaMemcpyHostToDevice),
+                    "hold copies");
+}
+
 int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out) {
   if (!h || !ms_out) return GAP_EINVAL;
   const int r = collect_phases(h);

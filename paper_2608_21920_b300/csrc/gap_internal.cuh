@@ -61,7 +61,8 @@ struct Ctl {
   int64_t ph_work_n;  // photons on the scheduling work list this step
   int64_t last_rebin_step;
   int64_t ph_dead;  // photons dead since the last photon compaction
-  int32_t need_ph_compact, pad_c;
+  int32_t need_ph_compact;
+  int32_t hold_copies;  // test hook: bulk-copy pushes leave their first stage unissued
   int32_t push_items, push_next;  // the push work list of this step and its counter
   int64_t spill_n[2];
   int64_t new_total[2];
