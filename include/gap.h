@@ -284,6 +284,20 @@ int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out);
  * freed.  For tests of error handling only; other variants ignore it. */
 int gap_hold_copies(gap_handle *h, int32_t on);
 
+/* Checkpoint and resume.  A handle's whole state (particles, photons and
+ * their schedules, E, counters, ledgers, step number) lives in its
+ * workspace and holds no device addresses, so gap_save copies the
+ * gap_state_bytes(h) bytes in use to host memory and gap_load copies such a
+ * state into a handle made with the same parameters and configuration (any
+ * workspace address): stepping on continues exactly as the saved handle
+ * would (the random draws are keyed by particle id and step, with no
+ * generator state).  gap_load returns GAP_EINVAL, copying nothing, for a
+ * state of another layout or size; it clears an error status of the handle
+ * and returns that of the loaded state.  Both synchronise `stream`. */
+size_t gap_state_bytes(const gap_handle *h);
+int gap_save(gap_handle *h, void *host_dst, size_t bytes, void *stream);
+int gap_load(gap_handle *h, const void *host_src, size_t bytes, void *stream);
+
 /* Release host state.  The caller frees the workspace afterwards. */
 void gap_free(gap_handle *h);
 

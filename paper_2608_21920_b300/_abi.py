@@ -88,6 +88,10 @@ def lib():
     L.gap_profile.argtypes = [vp, i32, C.POINTER(d), C.POINTER(i64), C.POINTER(i64)]
     L.gap_profile_phases.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
     L.gap_hold_copies.argtypes = [vp, i32]
+    L.gap_state_bytes.argtypes = [vp]
+    L.gap_state_bytes.restype = sz
+    L.gap_save.argtypes = [vp, vp, sz, vp]
+    L.gap_load.argtypes = [vp, vp, sz, vp]
     L.gap_free.argtypes = [vp]
     L.gap_free.restype = None
     L.gap_last_error.argtypes = [vp]
@@ -102,7 +106,7 @@ def lib():
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
             "gap_get_field", "gap_set_field", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
-            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_spectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
+            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 
 

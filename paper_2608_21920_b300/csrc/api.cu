@@ -22,6 +22,7 @@ struct gap_handle {
   int64_t total_nodes = 0, steps_done = 0;
   char *ws = nullptr;
   size_t ws_bytes = 0;
+  size_t ws_need = 0;  // bytes of the workspace the layout uses
   char *buf_base[2] = {nullptr, nullptr};
   size_t buf_bytes = 0;
   unsigned long long *export_count = nullptr;
@@ -485,6 +486,7 @@ int gap_init(const gap_params *params, int32_t n_gaps, const gap_config *cfg, vo
   gap_handle *h = new gap_handle();
   h->ws = (char *)dev_workspace;
   h->ws_bytes = bytes;
+  h->ws_need = need;
   r = build_layout(params, n_gaps, c, (char *)dev_workspace, h, &need);
   if (r) { *out = h; return r; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -802,6 +804,48 @@ int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int
 }
 
 int64_t gap_steps_done(const gap_handle *h) { return h ? h->steps_done : 0; }
+
+size_t gap_state_bytes(const gap_handle *h) { return h ? h->ws_need : 0; }
+
+int gap_save(gap_handle *h, void *host_dst, size_t bytes, void *stream) {
+  if (!h || !host_dst) return GAP_EINVAL;
+  if (h->status) return h->status;
+  if (bytes < h->ws_need) return GAP_ENOSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host_dst, h->ws, h->ws_need, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "save");
+}
+
+int gap_load(gap_handle *h, const void *host_src, size_t bytes, void *stream) {
+  if (!h || !host_src || bytes != h->ws_need) return GAP_EINVAL;
+  // the gap and tile tables follow from the parameters and the configuration;
+  // a state from another layout is refused before anything is copied (only
+  // the mutable background density of a gap may differ)
+  const char *src = static_cast<const char *>(host_src);
+  const size_t og = (size_t)(reinterpret_cast<char *>(h->v.gaps) - h->ws);
+  const size_t ot = (size_t)(reinterpret_cast<char *>(h->v.tiles) - h->ws);
+  std::vector<GapDev> gs((size_t)h->n_gaps);
+  std::memcpy(gs.data(), src + og, sizeof(GapDev) * gs.size());
+  for (size_t i = 0; i < gs.size(); ++i) {
+    GapDev a = gs[i], b = h->gaps_h[i];
+    a.eta_bg = b.eta_bg = 0.0;
+    if (std::memcmp(&a, &b, sizeof(GapDev)) != 0) return GAP_EINVAL;
+  }
+  if (std::memcmp(src + ot, h->tiles_h.data(), sizeof(TileDev) * h->tiles_h.size()) != 0) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h->ws, host_src, h->ws_need, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(h, e, "load");
+  for (size_t i = 0; i < gs.size(); ++i) h->gaps_h[i].eta_bg = gs[i].eta_bg;
+  h->status = GAP_OK;
+  h->err.clear();
+  Ctl c;
+  const int r = read_ctl(h, &c, st);
+  if (r) return r;
+  h->steps_done = c.step;
+  return GAP_OK;
+}
 
 // Sum the event intervals recorded since the last read into phase_ms.
 static int collect_phases(gap_handle *h) {

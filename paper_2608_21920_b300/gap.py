@@ -176,6 +176,20 @@ class Gap:
                        dir=np.where(aux2[:m] & 1, 1, -1).astype(np.int32))
         return res
 
+    def save(self) -> np.ndarray:
+        """The handle's whole state as host bytes (checkpoint)."""
+        L = A.lib()
+        n = L.gap_state_bytes(self._h)
+        buf = np.empty(n, np.uint8)
+        A.check(L.gap_save(self._h, _ptr(buf), n, self.stream()), self._h, "gap_save")
+        return buf
+
+    def load(self, state: np.ndarray):
+        """Resume from a state saved by a handle with the same parameters and
+        configuration."""
+        buf = np.ascontiguousarray(state, dtype=np.uint8)
+        A.check(A.lib().gap_load(self._h, _ptr(buf), buf.size, self.stream()), self._h, "gap_load")
+
     def sample_particles(self, kind: int, stride: int, gap: int = 0) -> dict:
         """Leptons of one species whose id is a multiple of `stride`: the same
         sample from step to step, for large gaps."""
