@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("gap_index", C.c_int32), ("qed", C.c_int32), ("boundary", C.c_int32),
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
+        ("inject_theta", C.c_double),
     ]
 
 
@@ -78,6 +79,7 @@ def lib():
         for f in ("orc_tsyn", "orc_tbw", "orc_spec_survival", "orc_spec_inverse"):
             getattr(L, f).argtypes = [d]; getattr(L, f).restype = d
         L.orc_mj_sample.argtypes = [u64, u64, d, C.POINTER(C.c_int)]; L.orc_mj_sample.restype = d
+        L.orc_mj_draw.argtypes = [u64, u64, u32, u32, d, C.POINTER(C.c_int)]; L.orc_mj_draw.restype = d
         L.orc_create.argtypes = [C.POINTER(Params)]; L.orc_create.restype = vp
         L.orc_destroy.argtypes = [vp]
         L.orc_step.argtypes = [vp]
@@ -147,6 +149,12 @@ def spec_inverse(U):
     return lib().orc_spec_inverse(float(U))
 
 
+def mj_draw(seed, pid, step, channel, theta):
+    ok = C.c_int(0)
+    u = lib().orc_mj_draw(seed, pid, step, channel, float(theta), C.byref(ok))
+    return u, bool(ok.value)
+
+
 def mj_sample(seed, pid, theta):
     ok = C.c_int(0)
     u = lib().orc_mj_sample(seed, pid, float(theta), C.byref(ok))
@@ -157,7 +165,7 @@ def mj_sample(seed, pid, theta):
 DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
-                init=INIT_EMPTY, kmax_emit=16, kmax_inject=64)
+                init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0)
 
 
 class Sim:

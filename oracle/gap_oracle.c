@@ -106,7 +106,8 @@ uint64_t orc_child_id(uint64_t parent, uint32_t step, uint32_t channel,
 /* Draw channels (shared interface with the library; values only). */
 enum {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
-  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_MERGE = 10
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_MERGE = 10,
+  CH_INJECT_U = 12
 };
 
 /* ------------------------------------------------------------------------- */
@@ -198,20 +199,25 @@ double orc_spec_inverse(double U) {
  * the ratio-of-uniforms method (Kinderman & Monahan 1977): (a, v) uniform on
  * (0,1] x [-bmax, bmax], u = v/a accepted when a^2 <= f(u).  bmax =
  * sup |u| sqrt(f(u)), attained at u^2 = 2 theta gamma, gamma = theta +
- * sqrt(theta^2+1).  Draws: channel CH_INIT_U, k = 2r, 2r+1 for round r. */
-double orc_mj_sample(uint64_t seed, uint64_t id, double theta, int *ok) {
+ * sqrt(theta^2+1).  Draws: (id, step, channel), k = 2r, 2r+1 for round r. */
+double orc_mj_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t ch, double theta, int *ok) {
   double gs = theta + sqrt(theta * theta + 1.0);
   double us = sqrt(2.0 * theta * gs);
   double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
   for (uint32_t r = 0; r < 64; ++r) {
-    double a = orc_uniform(seed, id, 0, CH_INIT_U, 2 * r);
-    double v = bmax * (2.0 * orc_uniform(seed, id, 0, CH_INIT_U, 2 * r + 1) - 1.0);
+    double a = orc_uniform(seed, id, step, ch, 2 * r);
+    double v = bmax * (2.0 * orc_uniform(seed, id, step, ch, 2 * r + 1) - 1.0);
     double u = v / a;
     double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
     if (2.0 * log(a) <= -gm1 / theta) { *ok = 1; return u; }
   }
   *ok = 0;
   return 0.0;
+}
+
+/* The loader's draw: step 0, channel CH_INIT_U. */
+double orc_mj_sample(uint64_t seed, uint64_t id, double theta, int *ok) {
+  return orc_mj_draw(seed, id, 0, CH_INIT_U, theta, ok);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -241,6 +247,7 @@ typedef struct {
   int32_t init;      /* ORC_INIT_* */
   int32_t kmax_emit; /* emission events per lepton per step (sub-cycling cap) */
   int32_t kmax_inject; /* injected electrons per step cap */
+  double inject_theta; /* temperature of the injected atmosphere (m_e c^2); 0 = cold */
 } orc_params;
 
 typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
@@ -709,8 +716,12 @@ void orc_step(orc_sim *s) {
 
   /* a7: surface injection.  Cell 0 must hold the co-rotation charge
    * eta_co dx = -dx; while its deficit exceeds half a macro-particle charge,
-   * add a cold electron at X = U/2 in (0, 1/2] (cloud inside cell 0 and the
-   * conductor only, so no other cell's Gauss balance changes). */
+   * add an electron at X = U/2 in (0, 1/2] (cloud inside cell 0 and the
+   * conductor only, so no other cell's Gauss balance changes).  The
+   * atmosphere has a temperature (Sect. 6.1): with inject_theta > 0 the
+   * electron's momentum is |u| of a 1D Maxwell-Juttner draw at that
+   * temperature, pointing into the gap (the half of the distribution that
+   * leaves the surface); otherwise it starts at rest. */
   if (p->boundary == ORC_BC_SURFACE && s->w0 > 0.0) {
     double Q0 = orc_cell_charge(s, 0);
     double deficit = Q0 - (-1.0) * dx;
@@ -721,11 +732,16 @@ void orc_step(orc_sim *s) {
       L.id = orc_child_id(inject_root(p->gap_index), n, CH_INJECT, (uint32_t)j) & ~ORC_PHOTON_BIT;
       double o = 0.5 * orc_uniform(p->seed, L.id, n + 1, CH_INJECT, 0);
       L.q = -1; L.X = o; L.u = 0.0; L.w = s->w0; L.alive = 1;
+      if (p->inject_theta > 0.0) {
+        int ok = 1;
+        L.u = fabs(orc_mj_draw(p->seed, L.id, (uint32_t)(n + 1), CH_INJECT_U, p->inject_theta, &ok));
+        if (!ok) s->cnt.load_overflow++;
+      }
       L.tau = -log(orc_uniform(p->seed, L.id, n + 1, CH_TAU0, 0));
       push_lepton(s, L);
       deficit -= s->w0 * (o + 0.5);
       s->cnt.injected++;
-      s->cnt.e_injected += s->w0; /* rest energy of a cold electron */
+      s->cnt.e_injected += s->w0 * sqrt(1.0 + L.u * L.u); /* total energy w gamma */
       ++j;
     }
   }

@@ -307,6 +307,46 @@ def test_surface_injection_restores_cell0():
     assert s.counters()["injected"] > 0
 
 
+def _injected_once(seed, theta):
+    """The electrons injected at the end of the first step of an empty
+    surface gap (not yet pushed: the push of the next step moves them)."""
+    s = O.Sim(nx=16, ppc=256, kmax_inject=512, boundary=O.BC_SURFACE, init=O.INIT_EMPTY,
+              dx=0.1, dt=0.045, seed=seed, inject_theta=theta)
+    s.step(1)
+    return s.leptons(), s.counters(), s.w0
+
+
+def test_hot_atmosphere_half_maxwell_juttner():
+    """Sect. 6.1: the atmosphere has k_B T = 0.3 m_e c^2.  Injected momenta
+    follow the upward half of the 1D Maxwell-Juttner law: KS against the
+    quadrature CDF, the closed-form mean E|u| = theta (1 + theta) e^{-1/theta}
+    / K_1(1/theta) (u du = gamma dgamma), all u > 0, positions independent of
+    momenta, and the energy ledger credits w gamma, not the rest energy."""
+    theta = 0.3
+    us, Xs = [], []
+    for seed in range(12):
+        L, c, w0 = _injected_once(seed, theta)
+        assert c["injected"] == L["id"].size > 200 and c["load_overflow"] == 0
+        assert np.all(L["q"] == -1) and np.all((L["X"] > 0) & (L["X"] <= 0.5))
+        g = np.sqrt(1 + L["u"] ** 2)
+        assert c["e_injected"] == pytest.approx(np.sum(L["w"] * g), rel=1e-13)
+        assert c["e_injected"] > 1.05 * w0 * L["id"].size
+        us.append(L["u"]); Xs.append(L["X"])
+    u, X = np.concatenate(us), np.concatenate(Xs)
+    assert np.all(u > 0)
+    full = _mj_cdf(theta)
+    half = np.vectorize(lambda x: 2.0 * full(x) - 1.0)
+    assert stats.kstest(u, half).pvalue > 1e-3
+    mean_abs = theta * (1 + theta) / special.k1e(1 / theta)
+    assert np.mean(u) == pytest.approx(mean_abs, abs=4 * np.std(u) / math.sqrt(u.size))
+    assert abs(np.corrcoef(X, u)[0, 1]) < 4 / math.sqrt(u.size)
+
+
+def test_cold_atmosphere_injects_at_rest():
+    L, c, w0 = _injected_once(5, 0.0)
+    assert np.all(L["u"] == 0.0) and c["e_injected"] == pytest.approx(w0 * L["id"].size, rel=1e-14)
+
+
 def test_boundaries_absorb_and_escape():
     s = O.Sim(nx=16, boundary=O.BC_SURFACE, dx=0.1, dt=0.045)
     s.add_lepton(1, -1, 0.2, -5.0, 1e-30)   # falls back onto the star
@@ -390,8 +430,9 @@ def test_pair_energy_and_charge_conservation():
     assert L["X"][0] == L["X"][1]
 
 
-def test_energy_ledger_closes():
-    s = _discharge_sim()
+@pytest.mark.parametrize("inject_theta", [0.0, 0.3])
+def test_energy_ledger_closes(inject_theta):
+    s = _discharge_sim(inject_theta=inject_theta)
 
     def total():
         L, P, c = s.leptons(), s.photons(), s.counters()
