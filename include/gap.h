@@ -98,6 +98,10 @@ typedef struct gap_params {
   int32_t kmax_emit; /* emission events per lepton per step (0 -> 16) */
   int32_t kmax_inject; /* injected electrons per step (0 -> 64) */
   int32_t gap_index; /* enters the ids of loaded and injected particles */
+  double inject_theta; /* temperature of the surface atmosphere (m_e c^2, Sect. 6.1):
+                          injected electrons get |u| of a 1D Maxwell-Juttner draw
+                          at this temperature, moving into the gap; 0 -> at rest.
+                          In [0, 1e3], else GAP_EINVAL */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */

@@ -96,6 +96,7 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.kmax_emit < 0 || q.kmax_emit > kMaxEmit) { msg = "kmax_emit must be <= 16"; return GAP_EINVAL; }
     if (q.qed && (!(q.lambda_hat > 0) || !(q.rho_hat > 0) || q.rate_mult < 0)) { msg = "QED scales"; return GAP_EINVAL; }
     if (q.init == GAP_INIT_PAIR_THERMAL && q.boundary != GAP_BC_PERIODIC) { msg = "thermal pair load needs a periodic gap"; return GAP_EINVAL; }
+    if (!(q.inject_theta >= 0.0) || q.inject_theta > 1e3) { msg = "inject_theta must be in [0, 1e3]"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -206,6 +207,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.f_rate = (float)g.rate_mult;
     g.seed = q.seed;
     g.cap = q.cap > 0 ? q.cap : 0;
+    g.inject_theta = q.inject_theta;
     merge_any |= q.cap > 0;
     g.inj_root = ((uint64_t)(uint32_t)q.gap_index << 40) | (1ull << 38);
     qed_any |= g.qed != 0;

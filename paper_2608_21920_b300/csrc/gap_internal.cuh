@@ -28,7 +28,7 @@ static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 con
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
-  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_INJECT_U = 12
 };
 
 enum Counter {
@@ -45,6 +45,7 @@ struct GapDev {
   float f_dt, f_cdx, f_Hc, f_lam, f_rho, f_rate;
   uint64_t seed, inj_root;
   int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
+  double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold
 };
 
 struct TileDev {
@@ -168,6 +169,31 @@ __device__ __forceinline__ float uniform24(uint64_t seed, uint64_t id, uint32_t 
 }
 
 // SplitMix64 output function (Steele, Lea, Flood 2014).
+// 1D Maxwell-Juttner deviate, f(u) ~ exp(-(gamma - 1)/theta), by the
+// ratio-of-uniforms method (Kinderman & Monahan 1977): (a, v) uniform on
+// (0,1] x [-bmax, bmax] with bmax = sup |u| sqrt(f(u)) (at u^2 = 2 theta
+// gamma, gamma = theta + sqrt(theta^2 + 1)); u = v/a is accepted when
+// a^2 <= f(u).  Round r draws k = 2r, 2r+1 of (id, step, channel); after 64
+// rejected rounds ok is false and u = 0.
+__device__ __noinline__ static double mj_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
+                                              double theta, bool &ok) {
+  const double gs = theta + sqrt(theta * theta + 1.0);
+  const double us = sqrt(2.0 * theta * gs);
+  const double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
+  for (uint32_t r = 0; r < 64; ++r) {
+    const double a = uniform53(seed, id, step, channel, 2 * r);
+    const double vv = bmax * (2.0 * uniform53(seed, id, step, channel, 2 * r + 1) - 1.0);
+    const double u = vv / a;
+    const double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
+    if (2.0 * log(a) <= -gm1 / theta) {
+      ok = true;
+      return u;
+    }
+  }
+  ok = false;
+  return 0.0;
+}
+
 __device__ __host__ __forceinline__ uint64_t mix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

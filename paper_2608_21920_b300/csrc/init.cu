@@ -9,25 +9,7 @@ namespace gapk {
 // Loader: quiet start X = cell + (j + 1/2)/ppc; for the thermal pair load the
 // electrons are displaced by (A/k1) sin(k1 X), k1 = 2 pi/nx (a Langmuir seed
 // of relative density amplitude A) and momenta are 1D Maxwell-Juttner by the
-// ratio-of-uniforms method (Kinderman & Monahan 1977).
-__device__ double mj_sample(uint64_t seed, uint64_t id, double theta, bool &ok) {
-  const double gs = theta + sqrt(theta * theta + 1.0);
-  const double us = sqrt(2.0 * theta * gs);
-  const double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
-  for (uint32_t r = 0; r < 64; ++r) {
-    const double a = uniform53(seed, id, 0, CH_INIT_U, 2 * r);
-    const double vv = bmax * (2.0 * uniform53(seed, id, 0, CH_INIT_U, 2 * r + 1) - 1.0);
-    const double u = vv / a;
-    const double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
-    if (2.0 * log(a) <= -gm1 / theta) {
-      ok = true;
-      return u;
-    }
-  }
-  ok = false;
-  return 0.0;
-}
-
+// mj_draw (step 0, channel CH_INIT_U).
 template <class R>
 __global__ void k_load(View v, LoadSpec sp) {
   using W = typename Prec<R>::W;
@@ -51,7 +33,7 @@ __global__ void k_load(View v, LoadSpec sp) {
       }
       if (sp.theta > 0.0) {
         bool ok = true;
-        u = mj_sample(g.seed, id, sp.theta, ok);
+        u = mj_draw(g.seed, id, 0, CH_INIT_U, sp.theta, ok);
         if (!ok) atomicAdd(&v.counters[sp.gap * C_NCNT + C_LOAD_OVF], 1ull);
       }
     }

@@ -1071,10 +1071,13 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
 // ---------------------------------------------------------------------------
 // k_inject: one warp per gap with a surface.  Cell 0 must hold the
 // co-rotation charge eta_co dx = -dx; while its deficit exceeds half a
-// macro-particle charge a cold electron is added at X = U/2 in (0, 1/2].
-// The lanes make the draws of up to 32 candidate electrons at once; the
-// deficit recurrence then runs over them in order (every lane runs it on the
-// broadcast offsets, so all agree), and the accepted lanes append.
+// macro-particle charge an electron is added at X = U/2 in (0, 1/2], at rest
+// or, for a hot atmosphere (Sect. 6.1, inject_theta > 0), with |u| of a 1D
+// Maxwell-Juttner draw, moving into the gap.  The lanes make the draws of up
+// to 32 candidate electrons at once; the deficit recurrence then runs over
+// them in order (every lane runs it on the broadcast offsets, so all agree),
+// and the accepted lanes append.  The injected energy w gamma enters the
+// ledger as a fixed-order warp sum.
 template <class R>
 __global__ void k_inject(View v) {
   using W = typename Prec<R>::W;
@@ -1094,6 +1097,7 @@ __global__ void k_inject(View v) {
   double deficit = Q0 + g.dx;
   unsigned long long *C = v.counters + gi * C_NCNT;
   int injected = 0;
+  double e_inj = 0.0;  // sum of gamma over the accepted electrons (lane 0 holds it)
   for (int base = 0; base < g.kmax_inject && deficit > 0.5 * g.w0; base += 32) {
     const int j = base + lane;
     uint64_t id = 0;
@@ -1110,7 +1114,15 @@ __global__ void k_inject(View v) {
         take = i + 1;
       }
     }
+    double gam = 0.0;
     if (lane < take) {
+      R u = (R)0;
+      if (g.inject_theta > 0.0) {
+        bool ok = true;
+        u = (R)fabs(mj_draw(g.seed, id, (uint32_t)(step + 1), CH_INJECT_U, g.inject_theta, ok));
+        if (!ok) atomicAdd(&C[C_LOAD_OVF], 1ull);
+      }
+      gam = sqrt(1.0 + (double)u * (double)u);
       int32_t k;
       R phi;
       split_position<R>(o, g.nx, false, k, phi);
@@ -1118,15 +1130,17 @@ __global__ void k_inject(View v) {
       W w;
       if (sizeof(R) == 4) w = (W)(1u << kWeightShift);
       else w = (W)g.w0;
-      append_lepton<R>(v, 0, tile_of(v, g, k), k, phi, (R)0, w, tau, id);
+      append_lepton<R>(v, 0, tile_of(v, g, k), k, phi, u, w, tau, id);
     }
+    for (int off = 16; off > 0; off >>= 1) gam += __shfl_down_sync(0xffffffffu, gam, off);
+    e_inj += gam;
     injected += take;
   }
   if (lane == 0) {
     if (deficit > 0.5 * g.w0) atomicAdd(&C[C_INJ_OVF], 1ull);  // kmax_inject reached
     if (injected) {
       atomicAdd(&C[C_INJECTED], (unsigned long long)injected);
-      atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0 * (double)injected);
+      atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0 * e_inj);
     }
   }
 }
