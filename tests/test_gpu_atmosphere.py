@@ -75,3 +75,24 @@ def test_hot_atmosphere_fp32_gauss():
     assert d["counters"]["injected"] > 0
     assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
     g.close()
+
+
+def test_negative_alpha_parity():
+    """alpha = -2 with a hot atmosphere: the injected electrons fall back onto
+    the star and E grows as -alpha t in the bulk; parity to 1e-10 with
+    identical injection and absorption counts over 1500 steps."""
+    cfg = dict(HOT, alpha=-2.0)
+    g, o = P.make_pair(cfg, "fp64", tile=16)
+    n_prev = 0
+    for n in (100, 600, 1500):
+        g.step(n - n_prev)
+        o.step(n - n_prev)
+        n_prev = n
+        d = g.diag(spectrum=False)
+        P.compare_counters(d["counters"], o.counters(), f"step {n}")
+        _compare_ledgers(d["counters"], o.counters(), 1e-10, f"step {n}")
+        P.compare_field(g.field(), o.E(), RTOL64, f"step {n}")
+        P.compare_leptons(P.leptons_gpu(g), P.leptons_oracle(o), RTOL64, f"step {n}")
+    c = o.counters()
+    assert c["injected"] > 1000 and c["absorbed"] > 1000
+    g.close()

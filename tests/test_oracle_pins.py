@@ -347,6 +347,26 @@ def test_cold_atmosphere_injects_at_rest():
     assert np.all(L["u"] == 0.0) and c["e_injected"] == pytest.approx(w0 * L["id"].size, rel=1e-14)
 
 
+def test_negative_alpha_field_grows_linearly():
+    """alpha = -2 (Sect. 6.1's counter-aligned case) with only an electron
+    atmosphere: j_m = alpha j_co with j_co < 0 points up, electrons cannot
+    carry it and fall back onto the star.  Once the gap is empty, Ampere gives
+    dE/dt = -alpha at every node there and Gauss a slope dE/dx = -eta_co = 1
+    (E_{i+1} - E_i = dx)."""
+    s = _discharge_sim(alpha=-2.0, inject_theta=0.3, qed=0)
+    s.step(1000)
+    E1 = s.E()
+    s.step(500)
+    E2 = s.E()
+    X = s.leptons()["X"]
+    assert X.size == 0 or X.max() < 20
+    t = 500 * s.cfg["dt"]
+    assert np.allclose(E2[40:] - E1[40:], 2.0 * t, rtol=1e-12, atol=0)
+    assert np.allclose(np.diff(E2[40:]), s.cfg["dx"], rtol=0, atol=1e-10)
+    c = s.counters()
+    assert c["injected"] > 1000 and c["absorbed"] > 1000 and c["escaped"] == 0
+
+
 def test_boundaries_absorb_and_escape():
     s = O.Sim(nx=16, boundary=O.BC_SURFACE, dx=0.1, dt=0.045)
     s.add_lepton(1, -1, 0.2, -5.0, 1e-30)   # falls back onto the star
