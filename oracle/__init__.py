@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("gap_index", C.c_int32), ("qed", C.c_int32), ("boundary", C.c_int32),
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
-        ("inject_theta", C.c_double),
+        ("inject_theta", C.c_double), ("filter_passes", C.c_int32),
     ]
 
 
@@ -79,6 +79,7 @@ def lib():
         for f in ("orc_tsyn", "orc_tbw", "orc_spec_survival", "orc_spec_inverse"):
             getattr(L, f).argtypes = [d]; getattr(L, f).restype = d
         L.orc_mj_sample.argtypes = [u64, u64, d, C.POINTER(C.c_int)]; L.orc_mj_sample.restype = d
+        L.orc_binomial_smooth.argtypes = [C.POINTER(d), i64, C.c_int32, C.c_int32]
         L.orc_mj_draw.argtypes = [u64, u64, u32, u32, d, C.POINTER(C.c_int)]; L.orc_mj_draw.restype = d
         L.orc_create.argtypes = [C.POINTER(Params)]; L.orc_create.restype = vp
         L.orc_destroy.argtypes = [vp]
@@ -149,6 +150,16 @@ def spec_inverse(U):
     return lib().orc_spec_inverse(float(U))
 
 
+EXT_PERIODIC, EXT_NODE_EVEN, EXT_CELL_ODD = 0, 1, 2
+
+
+def binomial_smooth(a, passes, ext):
+    """The oracle's binomial current/charge smoother on a copy of a."""
+    b = np.ascontiguousarray(a, dtype=np.float64).copy()
+    lib().orc_binomial_smooth(b.ctypes.data_as(C.POINTER(C.c_double)), b.size, passes, ext)
+    return b
+
+
 def mj_draw(seed, pid, step, channel, theta):
     ok = C.c_int(0)
     u = lib().orc_mj_draw(seed, pid, step, channel, float(theta), C.byref(ok))
@@ -165,7 +176,8 @@ def mj_sample(seed, pid, theta):
 DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
-                init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0)
+                init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0,
+                filter_passes=0)
 
 
 class Sim:

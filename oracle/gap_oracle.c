@@ -248,6 +248,7 @@ typedef struct {
   int32_t kmax_emit; /* emission events per lepton per step (sub-cycling cap) */
   int32_t kmax_inject; /* injected electrons per step cap */
   double inject_theta; /* temperature of the injected atmosphere (m_e c^2); 0 = cold */
+  int32_t filter_passes; /* binomial smoothing passes of the current per step; 0 = none */
 } orc_params;
 
 typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
@@ -308,6 +309,28 @@ static uint64_t inject_root(int32_t gap) { return ((uint64_t)gap << 40) | (1ull 
 
 double orc_cell_charge(const orc_sim *s, int64_t c);
 
+/* Binomial smoothing (Sect. 6.1: the current is smoothed by a 3-point
+ * binomial filter, 8 passes per step): each pass replaces a[i] by
+ * (a[i-1] + 2 a[i] + a[i+1]) / 4.  Values beyond the ends, re-derived before
+ * every pass: a periodic gap wraps; on a surface gap a node array is
+ * mirrored evenly about its end nodes (a[-1] = a[1], a[n] = a[n-2]) and a
+ * cell array oddly about the same nodes (q[-1] = -q[0], q[n] = -q[n-1]).
+ * Under that pair of rules smoothing commutes with the node-to-cell
+ * difference (D_c - D_{c+1}), so Gauss's law holds for the smoothed charge
+ * (image charges of opposite sign behind each end). */
+enum { ORC_EXT_PERIODIC = 0, ORC_EXT_NODE_EVEN = 1, ORC_EXT_CELL_ODD = 2 };
+static void binomial_smooth(double *a, int64_t n, int passes, int ext) {
+  double *e = (double *)malloc((size_t)(n + 2) * sizeof(double));
+  for (int pass = 0; pass < passes; ++pass) {
+    for (int64_t i = 0; i < n; ++i) e[i + 1] = a[i];
+    if (ext == ORC_EXT_PERIODIC) { e[0] = a[n - 1]; e[n + 1] = a[0]; }
+    else if (ext == ORC_EXT_NODE_EVEN) { e[0] = a[1]; e[n + 1] = a[n - 2]; }
+    else { e[0] = -a[0]; e[n + 1] = -a[n - 1]; }
+    for (int64_t i = 0; i < n; ++i) a[i] = 0.25 * (e[i] + 2.0 * e[i + 1] + e[i + 2]);
+  }
+  free(e);
+}
+
 /* Gauss's law (Sect. 2.2) on the grid: E_{c+1} - E_c = Q_c - eta_bg dx, with
  * Q_c the cloud-in-cell charge of cell c (between nodes c and c+1).  Surface:
  * E_0 = 0 (conductor).  Periodic: zero-mean E. */
@@ -328,7 +351,14 @@ void orc_solve_gauss(orc_sim *s) {
   }
   s->E[0] = 0.0;
   int64_t last = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx;
-  for (int64_t c = 0; c < last; ++c) s->E[c + 1] = s->E[c] + Q[c] - s->eta_bg * p->dx;
+  if (p->filter_passes > 0) { /* the field of the smoothed charge */
+    for (int64_t c = 0; c < p->nx; ++c) Q[c] -= s->eta_bg * p->dx;
+    binomial_smooth(Q, p->nx, p->filter_passes,
+                    p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_CELL_ODD);
+    for (int64_t c = 0; c < last; ++c) s->E[c + 1] = s->E[c] + Q[c];
+  } else {
+    for (int64_t c = 0; c < last; ++c) s->E[c + 1] = s->E[c] + Q[c] - s->eta_bg * p->dx;
+  }
   if (p->boundary == ORC_BC_PERIODIC) {
     double m = 0.0;
     for (int64_t i = 0; i < s->nnode; ++i) m += s->E[i];
@@ -415,6 +445,7 @@ void orc_add_photon(orc_sim *s, uint64_t id, double X, double x, double w,
   push_photon(s, P);
 }
 void orc_set_eta_bg(orc_sim *s, double eta) { s->eta_bg = eta; }
+void orc_binomial_smooth(double *a, int64_t n, int32_t passes, int32_t ext) { binomial_smooth(a, n, passes, ext); }
 void orc_set_E(orc_sim *s, const double *E) { memcpy(s->E, E, (size_t)s->nnode * sizeof(double)); }
 
 /* Deposit of one move X0 -> X1 (unwrapped): the charge through node i is
@@ -703,7 +734,11 @@ void orc_step(orc_sim *s) {
   for (int64_t i = 0; i < s->nph; ++i) if (s->ph[i].alive) s->ph[m++] = s->ph[i];
   s->nph = m;
 
-  /* a9: Ampere, with the work of the imposed current on the field */
+  /* a9: Ampere, with the work of the imposed current on the field; the
+   * current is smoothed first when filter_passes > 0 */
+  if (p->filter_passes > 0)
+    binomial_smooth(s->D, s->nnode, p->filter_passes,
+                    p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_NODE_EVEN);
   int64_t i0 = p->boundary == ORC_BC_PERIODIC ? 0 : 1;
   double work = 0.0;
   for (int64_t i = i0; i < s->nnode; ++i) {
@@ -771,7 +806,10 @@ double orc_cell_charge(const orc_sim *s, int64_t c) {
 }
 
 /* Largest |Gauss residual| (E_{c+1} - E_c) - (Q_c - eta_bg dx) over the cells
- * that touch no boundary (surface: 1..nx-2; periodic: all). */
+ * that touch no boundary (surface: 1..nx-2; periodic: all).  With smoothing
+ * the charge term is smoothed like the current, and on a surface gap the
+ * cells within filter_passes of a boundary cell are left out too (charge
+ * that enters or leaves through an end without a flux spreads that far). */
 double orc_gauss_residual(const orc_sim *s, double *max_abs_E) {
   const orc_params *p = &s->p;
   double *Q = (double *)calloc((size_t)p->nx, sizeof(double));
@@ -788,11 +826,14 @@ double orc_gauss_residual(const orc_sim *s, double *max_abs_E) {
     }
   }
   double r = 0.0, em = 0.0;
-  int64_t c_lo = p->boundary == ORC_BC_PERIODIC ? 0 : 1;
-  int64_t c_hi = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx - 2;
+  const int P = p->filter_passes;
+  for (int64_t c = 0; c < p->nx; ++c) Q[c] -= s->eta_bg * p->dx;
+  if (P > 0) binomial_smooth(Q, p->nx, P, p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_CELL_ODD);
+  int64_t c_lo = p->boundary == ORC_BC_PERIODIC ? 0 : 1 + P;
+  int64_t c_hi = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx - 2 - P;
   for (int64_t c = c_lo; c <= c_hi; ++c) {
     int64_t c1 = p->boundary == ORC_BC_PERIODIC ? imod(c + 1, p->nx) : c + 1;
-    double res = (s->E[c1] - s->E[c]) - (Q[c] - s->eta_bg * p->dx);
+    double res = (s->E[c1] - s->E[c]) - Q[c];
     if (fabs(res) > r) r = fabs(res);
   }
   for (int64_t i = 0; i < s->nnode; ++i) if (fabs(s->E[i]) > em) em = fabs(s->E[i]);

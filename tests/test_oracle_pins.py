@@ -249,6 +249,110 @@ def test_cold_langmuir_frequency():
     assert omega == pytest.approx(expect, rel=1e-3)
 
 
+def _langmuir_omega(nx, passes, steps=1500):
+    ppc, dx, dt = 16, 0.1, 0.045
+    s = O.Sim(nx=nx, boundary=O.BC_PERIODIC, dx=dx, dt=dt, filter_passes=passes)
+    w = dx / ppc
+    k = 2 * math.pi / nx
+    A = 0.01
+    pid = 0
+    for c in range(nx):
+        for j in range(ppc):
+            X0 = c + (j + 0.5) / ppc
+            s.add_lepton(pid, -1, (X0 + A / k * math.sin(k * X0)) % nx, 0.0, w)
+            pid += 1
+    s.set_eta_bg(-1.0)
+    s.solve_gauss()
+    node = nx // 4
+    tr = [s.E()[node]]
+    for _ in range(steps):
+        s.step(1)
+        tr.append(s.E()[node])
+    tr = np.array(tr)
+    zc = np.where(np.sign(tr[:-1]) != np.sign(tr[1:]))[0]
+    tz = zc + tr[zc] / (tr[zc] - tr[zc + 1])
+    return math.pi / (np.mean(np.diff(tz)) * dt), dt
+
+
+def test_filter_lowers_langmuir_frequency_by_its_response():
+    """Sect. 6.1's 8-pass binomial current filter: one pass multiplies mode k
+    (per cell) by cos^2(k/2), so the restoring field of a cold plasma wave is
+    cut by cos^16(k/2) and its frequency by cos^8(k/2); the deposit and gather
+    shapes are common to both runs.  Leapfrog: omega = (2/dt) asin(Omega dt/2)."""
+    nx = 32
+    w_u, dt = _langmuir_omega(nx, 0)
+    w_f, _ = _langmuir_omega(nx, 8)
+    Om_u = 2 / dt * math.sin(w_u * dt / 2)
+    Om_f = Om_u * math.cos(math.pi / nx) ** 8
+    assert w_f == pytest.approx(2 / dt * math.asin(Om_f * dt / 2), rel=1e-3)
+    assert w_f < 0.97 * w_u
+
+
+def _binomial_closed_form(a, P):
+    """P passes of (1, 2, 1)/4 on a periodic array: circular convolution with
+    C(2P, j) / 4^P, j = 0..2P, centred."""
+    n = a.size
+    out = np.zeros(n)
+    for j in range(2 * P + 1):
+        out += special.comb(2 * P, j, exact=True) / 4.0 ** P * np.roll(a, j - P)
+    return out
+
+
+@pytest.mark.parametrize("P", [1, 3, 8])
+def test_binomial_smoother_closed_forms(P):
+    rng = np.random.default_rng(P)
+    n = 37
+    a = rng.normal(size=n)
+    # periodic: the binomial convolution
+    assert np.allclose(O.binomial_smooth(a, P, O.EXT_PERIODIC), _binomial_closed_form(a, P),
+                       rtol=0, atol=1e-14)
+    # node array, even about both end nodes: the periodic smoothing of the
+    # mirror image a_0..a_{n-1}, a_{n-2}..a_1 (period 2n - 2)
+    ext = np.concatenate([a, a[-2:0:-1]])
+    assert np.allclose(O.binomial_smooth(a, P, O.EXT_NODE_EVEN), _binomial_closed_form(ext, P)[:n],
+                       rtol=0, atol=1e-14)
+    # cell array, odd about the end nodes: q_0..q_{n-1}, -q_{n-1}..-q_0 (period 2n)
+    ext = np.concatenate([a, -a[::-1]])
+    assert np.allclose(O.binomial_smooth(a, P, O.EXT_CELL_ODD), _binomial_closed_form(ext, P)[:n],
+                       rtol=0, atol=1e-14)
+    # a constant passes a periodic or node-even smoother unchanged
+    assert np.allclose(O.binomial_smooth(np.full(n, 2.5), P, O.EXT_NODE_EVEN), 2.5, rtol=0, atol=1e-15)
+
+
+def test_binomial_smoother_commutes_with_the_difference():
+    """The node (even) and cell (odd) rules are paired: smoothing the node
+    flux D and then differencing equals differencing and then smoothing the
+    cell charge change, D_c - D_{c+1}, so Gauss's law survives the filter."""
+    rng = np.random.default_rng(5)
+    D = rng.normal(size=41)  # nodes 0..40, cells 0..39
+    for P in (1, 8):
+        lhs = -np.diff(O.binomial_smooth(D, P, O.EXT_NODE_EVEN))
+        rhs = O.binomial_smooth(-np.diff(D), P, O.EXT_CELL_ODD)
+        assert np.allclose(lhs, rhs, rtol=0, atol=1e-14)
+
+
+def test_filtered_discharge_keeps_smoothed_gauss_law():
+    """A surface discharge with pairs and an 8-pass filter: Gauss's law holds
+    to round-off for the smoothed charge, and fails for the raw charge (the
+    filter acts)."""
+    s = _discharge_sim(filter_passes=8)
+    s.step(700)
+    r, emax = s.gauss_residual()
+    assert s.counters()["pairs"] > 0
+    assert r < 1e-12 * max(1.0, emax)
+    raw_r = _raw_residual(s)
+    assert raw_r > 1e-6 * max(1.0, emax)
+
+
+def _raw_residual(s):
+    """Unsmoothed Gauss residual of a sim's state on cells 9..nx-10."""
+    nx, dx = s.cfg["nx"], s.cfg["dx"]
+    Q = np.array([s.cell_charge(c) for c in range(nx)])
+    E = s.E()
+    r = (E[1:nx + 1] - E[:nx]) - (Q + dx)
+    return np.abs(r[9:nx - 9]).max()
+
+
 def test_warm_pair_langmuir_frequency():
     """Thermal pair plasma: omega^2 -> omega_p^2 <gamma^-3> for k -> 0
     (eq. omega_osc, App. B.5), with <gamma^-3> of the 1D Maxwell-Juttner.
