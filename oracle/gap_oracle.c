@@ -538,6 +538,9 @@ static void merge(orc_sim *s, uint32_t n) {
     key[i].id = L->id; key[i].idx = i;
   }
   qsort(key, (size_t)nl, sizeof(mkey), mkey_cmp);
+  /* with smoothing, the re-centring flux is gathered per node, smoothed like
+   * the current and then applied (Gauss's law for the smoothed charge) */
+  double *mflux = p->filter_passes > 0 ? (double *)calloc((size_t)s->nnode, sizeof(double)) : NULL;
   int64_t a = 0;
   while (a < nl) {
     int64_t e = a + 1;
@@ -562,7 +565,8 @@ static void merge(orc_sim *s, uint32_t n) {
       /* charge moved across node k by re-centring: q (W phim - sum w phi) */
       const double flux = (double)key[a].q * (W * phim - Sphi);
       int64_t node = k;
-      if (p->boundary == ORC_BC_PERIODIC || (node > 0 && node <= p->nx)) s->E[node] -= flux;
+      if (mflux) { if (p->boundary == ORC_BC_PERIODIC || node <= p->nx) mflux[node] += flux; }
+      else if (p->boundary == ORC_BC_PERIODIC || (node > 0 && node <= p->nx)) s->E[node] -= flux;
       /* centre rapidity; the invariant mass as M = sum w cosh(a - eta) with
        * a = asinh(u) the rapidity of each member, written as W + D with
        * D = sum w 2 sinh^2((a - eta)/2) >= 0, so that M^2 - W^2 = D (2W + D)
@@ -594,6 +598,12 @@ static void merge(orc_sim *s, uint32_t n) {
     a = e;
   }
   free(key);
+  if (mflux) {
+    binomial_smooth(mflux, s->nnode, p->filter_passes,
+                    p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_NODE_EVEN);
+    for (int64_t i = p->boundary == ORC_BC_PERIODIC ? 0 : 1; i < s->nnode; ++i) s->E[i] -= mflux[i];
+    free(mflux);
+  }
   int64_t m = 0;
   for (int64_t i = 0; i < s->nlep; ++i) if (s->lep[i].alive) s->lep[m++] = s->lep[i];
   s->nlep = m;
@@ -606,8 +616,9 @@ static void merge(orc_sim *s, uint32_t n) {
  *  2. every photon alive at step start: propagate at c, accumulate the
  *     Breit-Wheeler optical depth (eq. tau_bw) at the accumulated angle of
  *     Sect. 6.1, convert into an e-e+ pair when it reaches its threshold;
- *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface;
- *  4. surface injection of cold electrons (Sect. 2.3 / 6.1 atmosphere);
+ *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface (D
+ *     smoothed by filter_passes binomial passes first, when asked);
+ *  4. surface injection of electrons (Sect. 2.3 / 6.1 atmosphere);
  *  5. merge when leptons + photons exceed the cap (see merge()). */
 void orc_step(orc_sim *s) {
   const orc_params *p = &s->p;

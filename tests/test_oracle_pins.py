@@ -749,8 +749,9 @@ def test_merge_cold_group_keeps_internal_energy():
     assert sum(L["w"]) == pytest.approx(sum(ws), rel=1e-15)
 
 
-def test_merge_keeps_gauss_and_cap_in_a_discharge():
-    s = _discharge_sim(cap=450)
+@pytest.mark.parametrize("filter_passes", [0, 8])
+def test_merge_keeps_gauss_and_cap_in_a_discharge(filter_passes):
+    s = _discharge_sim(cap=450, filter_passes=filter_passes)
     s.step(900)
     c = s.counters()
     r, emax = s.gauss_residual()
