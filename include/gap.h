@@ -102,6 +102,12 @@ typedef struct gap_params {
                           injected electrons get |u| of a 1D Maxwell-Juttner draw
                           at this temperature, moving into the gap; 0 -> at rest.
                           In [0, 1e3], else GAP_EINVAL */
+  int32_t filter_passes; /* passes of the binomial (1/4, 1/2, 1/4) current filter per
+                            step (Sect. 6.1 uses 8); 0 -> none.  Ends of a surface
+                            gap: node arrays mirror evenly about the end nodes,
+                            cell charge oddly, so Gauss's law holds for the
+                            smoothed charge (the Gauss solve and residual use it).
+                            In [0, 16] with nx >= 2 passes + 2, else GAP_EINVAL */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */

@@ -23,7 +23,7 @@ class GapParams(C.Structure):
         ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("qed", C.c_int32), ("boundary", C.c_int32), ("init", C.c_int32),
         ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32), ("gap_index", C.c_int32),
-        ("inject_theta", C.c_double),
+        ("inject_theta", C.c_double), ("filter_passes", C.c_int32),
     ]
 
 

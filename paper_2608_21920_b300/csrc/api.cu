@@ -97,6 +97,8 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.qed && (!(q.lambda_hat > 0) || !(q.rho_hat > 0) || q.rate_mult < 0)) { msg = "QED scales"; return GAP_EINVAL; }
     if (q.init == GAP_INIT_PAIR_THERMAL && q.boundary != GAP_BC_PERIODIC) { msg = "thermal pair load needs a periodic gap"; return GAP_EINVAL; }
     if (!(q.inject_theta >= 0.0) || q.inject_theta > 1e3) { msg = "inject_theta must be in [0, 1e3]"; return GAP_EINVAL; }
+    if (q.filter_passes < 0 || q.filter_passes > 16) { msg = "filter_passes must be in [0, 16]"; return GAP_EINVAL; }
+    if (q.filter_passes > 0 && q.nx < 2 * (int64_t)q.filter_passes + 2) { msg = "filter_passes needs nx >= 2 passes + 2"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -170,7 +172,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<LoadSpec> loads;
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
-  bool qed_any = false, surface_any = false, merge_any = false;
+  bool qed_any = false, surface_any = false, merge_any = false, filter_any = false;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     GapDev &g = gaps[i];
@@ -208,6 +210,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.seed = q.seed;
     g.cap = q.cap > 0 ? q.cap : 0;
     g.inject_theta = q.inject_theta;
+    g.filter_passes = q.filter_passes;
+    filter_any |= q.filter_passes > 0;
     merge_any |= q.cap > 0;
     g.inj_root = ((uint64_t)(uint32_t)q.gap_index << 40) | (1ull << 38);
     qed_any |= g.qed != 0;
@@ -276,6 +280,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.surface_any = surface_any;
   v.has_w = (qed_any || merge_any) ? 1 : 0;  // merging makes weights unequal
   v.merge_any = merge_any ? 1 : 0;
+  v.filter_any = filter_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
   v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
@@ -320,6 +325,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.dmom = C.take<double>(8 * (size_t)max_nx);
   v.dcharge = C.take<unsigned long long>(dchg);
   v.dcharge_len = dchg;
+  v.Dflt = C.take<double>(filter_any ? 2 * (size_t)dchg : 0);
   v.fft[0] = C.take<double>(2 * (size_t)max_P);
   v.fft[1] = C.take<double>(2 * (size_t)max_P);
   v.dred = C.take<double>(32);

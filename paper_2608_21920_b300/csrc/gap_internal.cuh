@@ -46,6 +46,8 @@ struct GapDev {
   uint64_t seed, inj_root;
   int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
   double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold
+  int32_t filter_passes;  // binomial current-smoothing passes per step; 0 = none
+  int32_t pad2;
 };
 
 struct TileDev {
@@ -76,6 +78,8 @@ struct View {
   int32_t n_gaps, n_tiles, tile, precision;
   int32_t qed_any, surface_any, has_w, rebin_every;
   int32_t variant, merge_any;
+  int32_t filter_any, pad_f;  // some gap smooths its current
+  double *Dflt;               // [2 x dcharge_len] smoothing scratch (node flux; two cell buffers)
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
   int32_t *ph_gap;       // photons alive per gap

@@ -149,8 +149,29 @@ __device__ double block_exclusive_scan(double x, double *total) {
   return before;
 }
 
+// P binomial passes over the cell array a[0..n) of one gap, run by one block
+// (a periodic gap wraps; a surface gap mirrors the charge oddly about its end
+// nodes: a[-1] = -a[0], a[n] = -a[n-1]), ping-ponging between a and b in
+// global memory.  Returns the buffer that holds the result.
+__device__ double *filter_cells_block(double *a, double *b, int64_t n, int P, bool periodic) {
+  for (int p = 0; p < P; ++p) {
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double l = i > 0 ? a[i - 1] : (periodic ? a[n - 1] : -a[0]);
+      const double r = i < n - 1 ? a[i + 1] : (periodic ? a[0] : -a[n - 1]);
+      b[i] = 0.25 * (l + 2.0 * a[i] + r);
+    }
+    double *t = a;
+    a = b;
+    b = t;
+  }
+  __syncthreads();
+  return a;
+}
+
 // Gauss's law (Sect. 2.2) per gap, one block each: E_0 = 0 and
-// E_{c+1} = E_c + Q_c - eta_bg dx; periodic gaps take zero-mean E.
+// E_{c+1} = E_c + Q_c - eta_bg dx; periodic gaps take zero-mean E.  A gap
+// with a current filter takes the field of the smoothed Q_c - eta_bg dx.
 __global__ void __launch_bounds__(1024) k_gauss_scan(View v, int set_background) {
   const int gi = blockIdx.x;
   GapDev &g = v.gaps[gi];
@@ -172,14 +193,21 @@ __global__ void __launch_bounds__(1024) k_gauss_scan(View v, int set_background)
   }
   __syncthreads();
   const double bg = eta * g.dx;
+  const double *Qs = nullptr;  // smoothed Q_c - bg of a filter gap
+  if (g.filter_passes > 0) {
+    double *A = v.Dflt + g.node_off, *B = v.Dflt + v.dcharge_len + g.node_off;
+    for (int64_t c = threadIdx.x; c < nx; c += T) A[c] = charge_value(v, g, Q[c]) - bg;
+    Qs = filter_cells_block(A, B, nx, g.filter_passes, g.periodic != 0);
+  }
+  auto qv = [&](int64_t c) { return Qs ? Qs[c] : charge_value(v, g, Q[c]) - bg; };
   // prefix of (Q_c - bg) over the cells of the preceding threads
   double mine = 0.0;
-  for (int64_t c = c0; c < c1; ++c) mine += charge_value(v, g, Q[c]) - bg;
+  for (int64_t c = c0; c < c1; ++c) mine += qv(c);
   double run = block_exclusive_scan(mine, nullptr);
   const int64_t last = g.periodic ? nx - 1 : nx;  // E has nodes 0..last
   if (threadIdx.x == 0) E[0] = 0.0;
   for (int64_t c = c0; c < c1; ++c) {
-    run += charge_value(v, g, Q[c]) - bg;
+    run += qv(c);
     if (c + 1 <= last) E[c + 1] = run;
   }
   if (g.periodic) {
@@ -321,13 +349,22 @@ __global__ void __launch_bounds__(1024) k_reduce(View v, int gap) {
     eabs = fmax(eabs, fabs(e));
     fe += 0.5 * g.dx * e * e;
   }
-  // Gauss residual over cells touching no boundary
+  // Gauss residual over cells touching no boundary; with a current filter,
+  // against the smoothed charge and P cells further from each end
+  const int P = g.filter_passes;
+  const double *Qs = nullptr;
+  if (P > 0) {
+    double *A = v.Dflt, *B = v.Dflt + v.dcharge_len;
+    for (int64_t c = threadIdx.x; c < nx; c += blockDim.x)
+      A[c] = charge_value(v, g, v.dcharge[c]) - g.eta_bg * g.dx;
+    Qs = filter_cells_block(A, B, nx, P, g.periodic != 0);
+  }
   double gr = 0.0;
-  const int64_t clo = g.periodic ? 0 : 1, chi = g.periodic ? nx - 1 : nx - 2;
+  const int64_t clo = g.periodic ? 0 : 1 + P, chi = g.periodic ? nx - 1 : nx - 2 - P;
   for (int64_t c = clo + threadIdx.x; c <= chi; c += blockDim.x) {
     const int64_t c1 = g.periodic ? (c + 1) % nx : c + 1;
-    const double Qc = charge_value(v, g, v.dcharge[c]);
-    const double r = (E[c1] - E[c]) - (Qc - g.eta_bg * g.dx);
+    const double q = Qs ? Qs[c] : charge_value(v, g, v.dcharge[c]) - g.eta_bg * g.dx;
+    const double r = (E[c1] - E[c]) - q;
     gr = fmax(gr, fabs(r));
   }
   sv[threadIdx.x] = emin;

@@ -18,6 +18,7 @@ void launch_after_push(const View &v, cudaStream_t st);
 int launches_per_step(const View &v);
 void launch_rebin(const View &v, double slack, cudaStream_t st);
 void launch_merge(const View &v, cudaStream_t st);
+void launch_filter(const View &v, int mode, cudaStream_t st);
 void launch_photon_step(const View &v, cudaStream_t st);
 void launch_photon_compact(const View &v, cudaStream_t st);
 void launch_export_photons(const View &v, int gap, double *stage, int64_t cap, unsigned long long *count,

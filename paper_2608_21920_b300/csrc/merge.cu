@@ -255,12 +255,14 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       const int n = cnt[key];
       if (n < 3) continue;
       double Wt, flux;
+      long long flux_units = 0;  // FP32 state: the moved charge in integer units
       W wa, wb;
       R phi_store;
       if (sizeof(R) == 4) {
         const long long Wi = (long long)sw[key], Si = (long long)sphi[key];
         const long long Fm = (2 * Si + Wi) / (2 * Wi);  // round(S/W) for S >= 0
-        flux = (double)q * (double)(Wi * Fm - Si) * g.w_unit * kPhiUnit;
+        flux_units = (long long)q * (Wi * Fm - Si);
+        flux = (double)flux_units * g.w_unit * kPhiUnit;
         phi_store = (R)(1.0f + (float)Fm * (float)kPhiUnit);
         wa = (W)(Wi / 2);
         wb = (W)(Wi - Wi / 2);
@@ -281,11 +283,16 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       const double q2 = D * (2.0 * Wt + D) * (M * M - (wad - wbd) * (wad - wbd));
       const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
       const double ua = sinh(eta + asinh(ps / wad)), ub = sinh(eta - asinh(ps / wbd));
-      // the charge moved across node kn by re-centring
+      // the charge moved across node kn by re-centring; a gap with a current
+      // filter collects it for smoothing (k_filter_apply, mode 1)
       int64_t node_g = kn;
       if (g.periodic) node_g %= g.nx;
-      if (flux != 0.0 && (g.periodic || node_g > 0))
+      if (flux != 0.0 && g.filter_passes > 0) {
+        if (sizeof(R) == 4) acc_add_global(&v.Dg[g.node_off + node_g], flux_units);
+        else acc_add_global(&v.Dg[g.node_off + node_g], flux);
+      } else if (flux != 0.0 && (g.periodic || node_g > 0)) {
         atomicAdd(&v.E[v.ctl->e_cur][g.node_off + node_g], -flux);
+      }
       const int o = atomicAdd(&out_cursor, 2);
       for (int c = 0; c < 2; ++c) {
         const int64_t d = seg0 + o + c;
@@ -339,6 +346,7 @@ void launch_merge(const View &v, cudaStream_t st) {
   if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
   else k_merge<double><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
   k_merge_done<<<1, 1, 0, st>>>(v);
+  launch_filter(v, 1, st);  // smoothed re-centring correction of filter gaps
 }
 
 }  // namespace gapk

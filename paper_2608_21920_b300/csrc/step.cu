@@ -409,12 +409,23 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
   }
   __syncthreads();
 
-  // a9: Ampere on the tile's nodes
+  // a9: Ampere on the tile's nodes (a gap with a current filter leaves it to
+  // k_filter_apply: every node's flux goes to the global accumulators)
   const double scale = sizeof(R) == 4 ? g.w_unit * kPhiUnit : 1.0;
   const double djm = g.dt * g.jm;
   double work = 0.0;
   bool finish = true;  // this block completes the tile
-  if (nitems > 1) {
+  if (g.filter_passes > 0) {
+    for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+      const Acc qi = node_charge(i);
+      if (qi == (Acc)0) continue;
+      int64_t node = (int64_t)k0 - 1 + i;
+      if (periodic) node = (node + nx) % nx;
+      else if (node < 0 || node > nx) continue;
+      acc_add_global(&v.Dg[g.node_off + node], qi);
+    }
+    finish = false;
+  } else if (nitems > 1) {
     for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
       const Acc qi = node_charge(i);
       if (qi == (Acc)0) continue;
@@ -1523,7 +1534,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
 
 template <class R>
 static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
-  if (sizeof(R) == 4 && !v.qed_any && !v.has_w) {
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w && !v.filter_any) {
     const size_t smem_lean = (size_t)(v.tile + 8) * (2 * sizeof(unsigned) + sizeof(float2)) + 64;
     switch (v.variant) {
       case 1: k_push_lean<4, 6><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
@@ -1556,6 +1567,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     else
       k_push<R, false, false><<<grid, threads, smem, st>>>(v);
   }
+  launch_filter(v, 0, st);  // Ampere of the gaps with a current filter
 }
 
 template <class R>
@@ -1568,7 +1580,7 @@ static void launch_after_push_impl(const View &v, cudaStream_t st) {
 template <class R>
 static void launch_rebin_impl(const View &v, double slack, cudaStream_t st) {
   k_rebin_layout<<<1, 1024, 0, st>>>(v, slack);
-  if (sizeof(R) == 4 && !v.qed_any && !v.has_w)
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w && !v.filter_any)
     k_rebin_interleave<<<2 * v.n_tiles, 256, (size_t)(v.tile + 8) * sizeof(int), st>>>(v);
   else
     k_rebin_compact<R><<<2 * v.n_tiles, 256, 0, st>>>(v);
@@ -1594,9 +1606,9 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 }
 
 int launches_per_step(const View &v) {
-  const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
+  const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w && !v.filter_any;
   return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
-         (v.qed_any ? 2 : 0);
+         (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0);
 }
 
 void launch_sync_used(const View &v, cudaStream_t st) {
