@@ -47,6 +47,22 @@ def set_size(nx):
     N_PARTICLES = 2 * NX * PPC
 WORKLOAD_NAME = ("cfg2 push+deposit roofline: Nx=2^20 periodic, 4.19e8 e+- (200+200 per cell, "
                  "0.5 n_co each), Maxwell-Juttner theta=0.1, 1e-3 Langmuir seed, QED off")
+SETUP = {"filter_passes": 0, "inject_theta": 0.0}  # Sect. 6.1 set-up options (off for the headline)
+
+
+def set_setup(filter_passes, inject_theta):
+    """Sect. 6.1's binomial current filter and hot atmosphere, applied to the
+    workloads (the atmosphere only matters for surface gaps: the batch)."""
+    global WORKLOAD_NAME, BATCH_NAME
+    SETUP.update(filter_passes=filter_passes, inject_theta=inject_theta)
+    if filter_passes:
+        WORKLOAD["filter_passes"] = filter_passes
+        WORKLOAD_NAME += f", {filter_passes}-pass binomial current filter"
+        BATCH_NAME += f", {filter_passes}-pass binomial current filter"
+    if inject_theta:
+        BATCH_NAME += f", atmosphere T={inject_theta:g} m_e c^2"
+
+
 # algorithmic bytes of the push kernel per particle-step (no QED, uniform
 # weights): read cell int32 + offset + momentum, write them back
 BYTES_PER_PARTICLE = {"fp32": 24, "fp64": 40}
@@ -254,9 +270,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "kernel": "k_push_lean (FP32, no QED, uniform weights)", "bytes_per_particle": bpp,
-                     "push_ms_per_launch": r32["push_ms"],
-                     "traffic": traffic_record("k_push", "fp32")},
+                     "kernel": ("k_push_lean (FP32, no QED, uniform weights)" if not SETUP["filter_passes"] else
+                                "k_push (FP32 generic, no QED) + k_flux_take + k_filter_apply"),
+                     "bytes_per_particle": bpp, "push_ms_per_launch": r32["push_ms"],
+                     "traffic": traffic_record("k_push", "fp32") if not SETUP["filter_passes"] else None},
         "gpu_launches": int(r32["launches"]),
         "clocks": r32["clocks"],
         "gauss_residual": r32["gauss"], "E_abs_max": r32["E_abs_max"],
@@ -289,7 +306,8 @@ def run_ours(args):
 def _oracle_sample(nx, steps, warmup):
     import oracle as O
     s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
-              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0)
+              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0,
+              filter_passes=SETUP["filter_passes"])
     if warmup:
         s.step(warmup)
     t0 = time.perf_counter()
@@ -317,7 +335,8 @@ def run_reference(args):
     nx = 1 << max(8, int(math.log2(max(256, 1.5e9 / (2 * PPC * max(total, 1))))))
     import oracle as O
     s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
-              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0)
+              init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0,
+              filter_passes=SETUP["filter_passes"])
     s.step(args.warmup)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -354,7 +373,7 @@ def run_batch(args):
     from paper_2608_21920_b300 import Gap, autotune, workloads
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
-    params = workloads.batch(args.gaps)
+    params = [dict(p, **SETUP) for p in workloads.batch(args.gaps)]
     peaks, peak_kind = measured_peaks()
     tuned = None
     tile, threads, rebin = args.tile if args.tile != 256 else 128, args.threads, args.rebin_every or 64
@@ -448,9 +467,14 @@ def main():
     ap.add_argument("--batch-advance", type=int, default=1500)
     ap.add_argument("--capacity-factor", type=float, default=0.0,
                     help="batch: lepton store = factor x initial count (profiling captures only; 0: caps)")
+    ap.add_argument("--filter-passes", type=int, default=0,
+                    help="binomial current-filter passes per step (Sect. 6.1 uses 8; 0: off)")
+    ap.add_argument("--inject-theta", type=float, default=0.0,
+                    help="batch: temperature of the surface atmosphere (Sect. 6.1 uses 0.3; 0: cold)")
     args = ap.parse_args()
     if args.nx:
         set_size(args.nx)
+    set_setup(args.filter_passes, args.inject_theta)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
