@@ -2,9 +2,11 @@
 // smoothed by a 3-point binomial filter, 8 passes per step).
 //
 //   k_flux_take     the node flux a step (or a merge) left in the global
-//                   accumulators -> doubles; the accumulators are zeroed
-//   k_filter_apply  P passes of (1/4, 1/2, 1/4) in shared memory over chunks
-//                   of a tile's nodes with P-node halos, then Ampere
+//                   accumulators -> scratch; the accumulators are zeroed
+//   k_filter_apply  P passes of (1/4, 1/2, 1/4), as the equal binomial
+//                   convolution, over chunks of each tile's nodes held in
+//                   shared memory with P-node halos (exact integers for the
+//                   FP32 state's integer flux, doubles otherwise), then Ampere
 //                   E^{n+1} = E^n + (dt j_m - S D) (mode 0) or the merge's
 //                   re-centring correction E -= S F (mode 1)
 //
@@ -13,8 +15,10 @@
 // and residual is mirrored oddly about the same nodes (init.cu), the pairing
 // under which smoothing commutes with the node-to-cell difference, so Gauss's
 // law holds for the smoothed charge.  Both kernels touch only gaps with
-// filter_passes > 0; one block per tile, and the tiles of a gap cover its
-// nodes k0 .. k0 + nk - 1 without overlap.
+// filter_passes > 0, and the tiles of a gap cover its nodes k0 .. k0 + nk - 1
+// without overlap.
+#include <algorithm>
+
 #include "gap_internal.cuh"
 #include "kernels.h"
 
@@ -22,6 +26,7 @@ namespace gapk {
 
 constexpr int kFilterChunk = 1024;  // nodes smoothed per shared-memory round
 constexpr int kMaxPasses = 16;      // upper bound of filter_passes (checked at init)
+static_assert(kMaxPasses <= 16, "the integer smoothing of the FP32 flux holds 16 passes");
 
 // Source index of position j of a node array of n values extended beyond its
 // ends (|j| and j - n stay below n: the init check nx >= 2 P + 2 keeps every
@@ -36,73 +41,165 @@ __device__ __forceinline__ int64_t node_source(int64_t j, int64_t n, bool period
   return j;
 }
 
+// The push has finished: every node has one owner here, so plain loads and
+// stores take and clear the accumulators.  FP32 state: the exact integer
+// flux is kept as is (the smoothing runs in integers); FP64 state: doubles.
 template <class R>
 __global__ void k_flux_take(View v) {
-  using Acc = typename Prec<R>::Acc;
   const TileDev ti = v.tiles[blockIdx.x];
   const GapDev &g = v.gaps[ti.gap];
   if (g.filter_passes <= 0) return;
-  const double scale = sizeof(R) == 4 ? g.w_unit * kPhiUnit : 1.0;
+  unsigned long long *out = reinterpret_cast<unsigned long long *>(v.Dflt);
   for (int i = threadIdx.x; i < ti.nk; i += blockDim.x) {
     const int64_t gn = g.node_off + ti.k0 + i;
-    v.Dflt[gn] = acc_take(&v.Dg[gn], (Acc *)nullptr) * scale;
+    out[gn] = v.Dg[gn];
+    v.Dg[gn] = 0ull;
   }
 }
 
-__global__ void __launch_bounds__(256) k_filter_apply(View v, int mode) {
-  __shared__ double sa[kFilterChunk + 2 * kMaxPasses], sb[kFilterChunk + 2 * kMaxPasses];
-  const TileDev ti = v.tiles[blockIdx.x];
-  const GapDev &g = v.gaps[ti.gap];
-  const int P = g.filter_passes;
-  if (P <= 0) return;
-  const bool periodic = g.periodic != 0;
-  const int64_t n = g.nnode;
-  const double *D = v.Dflt + g.node_off;
-  const int ecur = v.ctl->e_cur;
-  const double *Eo = v.E[ecur] + g.node_off;
-  double *En = v.E[mode == 0 ? ecur ^ 1 : ecur] + g.node_off;
-  const double djm = g.dt * g.jm;
-  double work = 0.0;
-  for (int c0 = 0; c0 < ti.nk; c0 += kFilterChunk) {
-    const int len = min(kFilterChunk, ti.nk - c0);
-    const int64_t first = (int64_t)ti.k0 + c0 - P;  // node held by sa[0]
-    const int w = len + 2 * P;
-    __syncthreads();  // the previous chunk is done with sa / sb
-    for (int i = threadIdx.x; i < w; i += blockDim.x) sa[i] = D[node_source(first + i, n, periodic)];
-    __syncthreads();
-    double *a = sa, *b = sb;
-    for (int p = 1; p <= P; ++p) {  // pass p is valid on [p, w - p)
-      for (int i = p + threadIdx.x; i < w - p; i += blockDim.x) b[i] = 0.25 * (a[i - 1] + 2.0 * a[i] + a[i + 1]);
-      __syncthreads();
-      double *t = a;
-      a = b;
-      b = t;
+// Block-wide sum of one double per thread, added to *dst by thread 0.
+__device__ void block_add(double x, double *dst) {
+  __shared__ double part[32];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  __syncthreads();  // part[] is free
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    if (t != 0.0) atomicAdd(dst, t);
+  }
+}
+
+// P passes of (a + 2 b + c) / 4 equal one convolution with the binomial
+// weights C(2P, k) / 4^P, k = 0..2P, so each output is formed directly from
+// the chunk in shared memory (one barrier per chunk instead of one per
+// pass).  coef[k] = C(2P, k) < 2^30 for P <= 16.
+//
+// FP64 state: doubles, weights C(2P, k) 2^-2P (exact dyadic numbers).
+struct SmoothF64 {
+  double a[kFilterChunk + 2 * kMaxPasses];
+  __device__ void load(int i, unsigned long long bits) { a[i] = __longlong_as_double((long long)bits); }
+  __device__ double value(int i, int P, const int *coef, double) const {
+    const double inv = ldexp(1.0, -2 * P);
+    double s = 0.0;
+    for (int k = 0; k <= 2 * P; ++k) s += ((double)coef[k] * inv) * a[i - P + k];
+    return s;
+  }
+};
+
+// FP32 state: the flux is an exact integer, split into a signed high and an
+// unsigned low 32-bit word; each is convolved in 64-bit integers (32 x 32 ->
+// 64-bit products).  The weights sum to 4^P <= 2^32, so the high sum stays
+// within int64 and the low sum within uint64, and the result
+// (hi 2^32 + lo) / 4^P is exact until its conversion to double.  (Double
+// arithmetic here would run on the FP64 units, a small fraction of the
+// integer rate.)
+struct SmoothI64 {
+  int hi[kFilterChunk + 2 * kMaxPasses];
+  unsigned lo[kFilterChunk + 2 * kMaxPasses];
+  __device__ void load(int i, unsigned long long bits) {
+    hi[i] = (int)((long long)bits >> 32);
+    lo[i] = (unsigned)bits;
+  }
+  __device__ double value(int i, int P, const int *coef, double scale) const {
+    long long sh = 0;
+    unsigned long long sl = 0;
+    for (int k = 0; k <= 2 * P; ++k) {
+      sh += (long long)coef[k] * (long long)hi[i - P + k];
+      sl += (unsigned long long)(unsigned)coef[k] * (unsigned long long)lo[i - P + k];
     }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-      const int64_t node = (int64_t)ti.k0 + c0 + i;
-      const double sd = a[P + i];
-      if (mode == 0) {
-        const double eo = Eo[node];
-        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - sd);
-        En[node] = en;
-        work += eo + en;
-      } else if (periodic || node > 0) {
-        En[node] -= sd;
+    return ((double)sh * 4294967296.0 + (double)sl) * (scale * ldexp(1.0, -2 * P));
+  }
+};
+
+template <class R>
+struct Smoother;
+template <>
+struct Smoother<double> { using T = SmoothF64; };
+template <>
+struct Smoother<float> { using T = SmoothI64; };
+
+// A persistent grid: block b smooths the contiguous tiles [t0, t1), so a gap's
+// work of j_m reaches the ledger once per block (one address per gap takes
+// the atomics of every block on it).
+template <class R>
+__global__ void __launch_bounds__(256) k_filter_apply(View v, int mode) {
+  using S = typename Smoother<R>::T;
+  __shared__ S sm;
+  __shared__ int coef[2 * kMaxPasses + 1];
+  int coef_P = -1;  // passes the weights in coef[] belong to
+  const unsigned long long *D0 = reinterpret_cast<const unsigned long long *>(v.Dflt);
+  const int t0 = (int)((int64_t)blockIdx.x * v.n_tiles / gridDim.x);
+  const int t1 = (int)((int64_t)(blockIdx.x + 1) * v.n_tiles / gridDim.x);
+  double work = 0.0;
+  int work_gap = -1;
+  for (int t = t0; t < t1; ++t) {
+    const TileDev ti = v.tiles[t];
+    const GapDev &g = v.gaps[ti.gap];
+    const int P = g.filter_passes;
+    if (P <= 0) continue;
+    if (mode == 0 && ti.gap != work_gap) {  // block-uniform
+      if (work_gap >= 0) {
+        const GapDev &gw = v.gaps[work_gap];
+        block_add(0.5 * work * gw.dt * gw.dx * gw.jm, &v.ledger[work_gap * L_NLED + L_WORK]);
+      }
+      work = 0.0;
+      work_gap = ti.gap;
+    }
+    const bool periodic = g.periodic != 0;
+    const int64_t n = g.nnode;
+    const unsigned long long *D = D0 + g.node_off;
+    const int ecur = v.ctl->e_cur;
+    const double *Eo = v.E[ecur] + g.node_off;
+    double *En = v.E[mode == 0 ? ecur ^ 1 : ecur] + g.node_off;
+    const double djm = g.dt * g.jm;
+    const double scale = sizeof(R) == 4 ? g.w_unit * kPhiUnit : 1.0;
+    for (int c0 = 0; c0 < ti.nk; c0 += kFilterChunk) {
+      const int len = min(kFilterChunk, ti.nk - c0);
+      const int64_t first = (int64_t)ti.k0 + c0 - P;  // node held by position 0
+      const int w = len + 2 * P;
+      __syncthreads();  // the previous chunk is done with the shared buffers
+      if (P != coef_P && threadIdx.x == 0) {  // C(2P, k) by the exact recurrence
+        long long c = 1;
+        for (int k = 0; k <= 2 * P; ++k) {
+          coef[k] = (int)c;
+          c = c * (2 * P - k) / (k + 1);
+        }
+      }
+      coef_P = P;
+      for (int i = threadIdx.x; i < w; i += blockDim.x) sm.load(i, D[node_source(first + i, n, periodic)]);
+      __syncthreads();
+      for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int64_t node = (int64_t)ti.k0 + c0 + i;
+        const double sd = sm.value(P + i, P, coef, scale);
+        if (mode == 0) {
+          const double eo = Eo[node];
+          const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - sd);
+          En[node] = en;
+          work += eo + en;
+        } else if (periodic || node > 0) {
+          En[node] -= sd;
+        }
       }
     }
   }
-  if (mode == 0) {
-    for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
-    if ((threadIdx.x & 31) == 0 && work != 0.0)
-      atomicAdd(&v.ledger[ti.gap * L_NLED + L_WORK], 0.5 * work * g.dt * g.dx * g.jm);
+  if (mode == 0 && work_gap >= 0) {
+    const GapDev &gw = v.gaps[work_gap];
+    block_add(0.5 * work * gw.dt * gw.dx * gw.jm, &v.ledger[work_gap * L_NLED + L_WORK]);
   }
 }
 
 void launch_filter(const View &v, int mode, cudaStream_t st) {
   if (!v.filter_any) return;
-  if (v.precision == GAP_FP32_STATE) k_flux_take<float><<<v.n_tiles, 256, 0, st>>>(v);
-  else k_flux_take<double><<<v.n_tiles, 256, 0, st>>>(v);
-  k_filter_apply<<<v.n_tiles, 256, 0, st>>>(v, mode);
+  const int grid = std::min(v.n_tiles, 148 * 8);
+  if (v.precision == GAP_FP32_STATE) {
+    k_flux_take<float><<<v.n_tiles, 256, 0, st>>>(v);
+    k_filter_apply<float><<<grid, 256, 0, st>>>(v, mode);
+  } else {
+    k_flux_take<double><<<v.n_tiles, 256, 0, st>>>(v);
+    k_filter_apply<double><<<grid, 256, 0, st>>>(v, mode);
+  }
 }
 
 }  // namespace gapk

@@ -698,33 +698,46 @@ __global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
-    const int64_t node = (int64_t)k0 - 1 + i;
-    const double eo = Eo[node];
-    const double en = eo + (djm - (double)node_sum(i) * scale);
-    En[node] = en;
-    work += eo + en;
-  }
-  if (threadIdx.x < 4) {
-    const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
-    int64_t node = (int64_t)k0 - 1 + local;
-    bool valid = true;
-    if (periodic) node = (node + nx) % nx;
-    else valid = node >= 0 && node <= nx;
-    if (valid) {
-      const int64_t gn = g.node_off + node;
-      // global edge sums are in the units of k_push: weight units x 2^-23
-      atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
-      __threadfence();
-      const int old = atomicAdd(&v.arrive[gn], 1);
-      if (old == (int)v.expect[gn] - 1) {
+  if (g.filter_passes > 0) {
+    // a gap with a current filter: every node's flux goes to the global
+    // accumulators (k_push units) and k_filter_apply finishes E
+    for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+      const long long c = node_sum(i);
+      if (c == 0) continue;
+      int64_t node = (int64_t)k0 - 1 + i;
+      if (periodic) node = (node + nx) % nx;
+      else if (node < 0 || node > nx) continue;
+      atomicAdd(&v.Dg[g.node_off + node], (unsigned long long)(c * (long long)m0));
+    }
+  } else {
+    for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
+      const int64_t node = (int64_t)k0 - 1 + i;
+      const double eo = Eo[node];
+      const double en = eo + (djm - (double)node_sum(i) * scale);
+      En[node] = en;
+      work += eo + en;
+    }
+    if (threadIdx.x < 4) {
+      const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
+      int64_t node = (int64_t)k0 - 1 + local;
+      bool valid = true;
+      if (periodic) node = (node + nx) % nx;
+      else valid = node >= 0 && node <= nx;
+      if (valid) {
+        const int64_t gn = g.node_off + node;
+        // global edge sums are in the units of k_push: weight units x 2^-23
+        atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
         __threadfence();
-        const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
-        const double eo = Eo[node];
-        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
-        En[node] = en;
-        v.arrive[gn] = 0;
-        work += eo + en;
+        const int old = atomicAdd(&v.arrive[gn], 1);
+        if (old == (int)v.expect[gn] - 1) {
+          __threadfence();
+          const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
+          const double eo = Eo[node];
+          const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
+          En[node] = en;
+          v.arrive[gn] = 0;
+          work += eo + en;
+        }
       }
     }
   }
@@ -1033,32 +1046,45 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
-    const int64_t node = (int64_t)k0 - 1 + i;
-    const double eo = Eo[node];
-    const double en = eo + (djm - (double)node_sum(i) * scale);
-    En[node] = en;
-    work += eo + en;
-  }
-  if (threadIdx.x < 4) {
-    const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
-    int64_t node = (int64_t)k0 - 1 + local;
-    bool valid = true;
-    if (periodic) node = (node + nx) % nx;
-    else valid = node >= 0 && node <= nx;
-    if (valid) {
-      const int64_t gn = g.node_off + node;
-      atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
-      __threadfence();
-      const int old = atomicAdd(&v.arrive[gn], 1);
-      if (old == (int)v.expect[gn] - 1) {
+  if (g.filter_passes > 0) {
+    // a gap with a current filter: every node's flux goes to the global
+    // accumulators (k_push units) and k_filter_apply finishes E
+    for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+      const long long c = node_sum(i);
+      if (c == 0) continue;
+      int64_t node = (int64_t)k0 - 1 + i;
+      if (periodic) node = (node + nx) % nx;
+      else if (node < 0 || node > nx) continue;
+      atomicAdd(&v.Dg[g.node_off + node], (unsigned long long)(c * (long long)m0));
+    }
+  } else {
+    for (int i = 2 + threadIdx.x; i <= nk - 1; i += blockDim.x) {
+      const int64_t node = (int64_t)k0 - 1 + i;
+      const double eo = Eo[node];
+      const double en = eo + (djm - (double)node_sum(i) * scale);
+      En[node] = en;
+      work += eo + en;
+    }
+    if (threadIdx.x < 4) {
+      const int local = threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 1 : (threadIdx.x == 2 ? nk : nk + 1));
+      int64_t node = (int64_t)k0 - 1 + local;
+      bool valid = true;
+      if (periodic) node = (node + nx) % nx;
+      else valid = node >= 0 && node <= nx;
+      if (valid) {
+        const int64_t gn = g.node_off + node;
+        atomicAdd(&v.Dg[gn], (unsigned long long)(node_sum(local) * (long long)m0));
         __threadfence();
-        const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
-        const double eo = Eo[node];
-        const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
-        En[node] = en;
-        v.arrive[gn] = 0;
-        work += eo + en;
+        const int old = atomicAdd(&v.arrive[gn], 1);
+        if (old == (int)v.expect[gn] - 1) {
+          __threadfence();
+          const double D = (double)(long long)atomicExch(&v.Dg[gn], 0ull) * g.w_unit * kPhiUnit;
+          const double eo = Eo[node];
+          const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - D);
+          En[node] = en;
+          v.arrive[gn] = 0;
+          work += eo + en;
+        }
       }
     }
   }
@@ -1534,7 +1560,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
 
 template <class R>
 static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
-  if (sizeof(R) == 4 && !v.qed_any && !v.has_w && !v.filter_any) {
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w) {
     const size_t smem_lean = (size_t)(v.tile + 8) * (2 * sizeof(unsigned) + sizeof(float2)) + 64;
     switch (v.variant) {
       case 1: k_push_lean<4, 6><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
@@ -1551,6 +1577,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       }
       default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
     }
+    launch_filter(v, 0, st);  // Ampere of the gaps with a current filter
     return;
   }
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
@@ -1580,7 +1607,7 @@ static void launch_after_push_impl(const View &v, cudaStream_t st) {
 template <class R>
 static void launch_rebin_impl(const View &v, double slack, cudaStream_t st) {
   k_rebin_layout<<<1, 1024, 0, st>>>(v, slack);
-  if (sizeof(R) == 4 && !v.qed_any && !v.has_w && !v.filter_any)
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w)
     k_rebin_interleave<<<2 * v.n_tiles, 256, (size_t)(v.tile + 8) * sizeof(int), st>>>(v);
   else
     k_rebin_compact<R><<<2 * v.n_tiles, 256, 0, st>>>(v);
@@ -1606,7 +1633,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 }
 
 int launches_per_step(const View &v) {
-  const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w && !v.filter_any;
+  const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
   return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
          (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0);
 }

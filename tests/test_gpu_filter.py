@@ -119,3 +119,43 @@ def test_filter_rejects_bad_pass_counts():
     for bad in (dict(filter_passes=17), dict(filter_passes=-1), dict(nx=16, filter_passes=8)):
         with pytest.raises(GapError):
             Gap(P.gpu_params(dict(P.SMALL_DISCHARGE, **bad)), precision="fp64")
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+def test_filtered_fp32_push_variants_are_bit_identical(variant):
+    """The lean and bulk-copy (TMA) FP32 pushes defer Ampere to the filter
+    the same way: states and E agree bit for bit with variant 0 (integer
+    charge accumulators make the smoothed field order-free)."""
+    from paper_2608_21920_b300 import Gap
+    for cfg, tile in ((dict(P.THERMAL_PAIRS, filter_passes=8), 32),
+                      (dict(P.SMALL_DISCHARGE, qed=0, nx=300, filter_passes=8), 64)):
+        ref = Gap(P.gpu_params(cfg), precision="fp32", tile=tile, variant=0)
+        alt = Gap(P.gpu_params(cfg), precision="fp32", tile=tile, variant=variant)
+        ref.step(70)
+        alt.step(70)
+        assert np.array_equal(ref.field(), alt.field())
+        a, b = P.leptons_gpu(ref), P.leptons_gpu(alt)
+        assert np.array_equal(a["id"], b["id"])
+        assert np.array_equal(a["X"], b["X"]) and np.array_equal(a["u"], b["u"])
+        d = alt.diag(spectrum=False)
+        assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+        ref.close()
+        alt.close()
+
+
+@pytest.mark.parametrize("passes", [1, 16])
+def test_integer_smoothing_of_fp32_flux(passes):
+    """The FP32 state smooths its integer flux in integers (split words, no
+    division until the end): the smoothed Gauss law to round-off, the field
+    within the FP32 bound of the FP64 oracle, at 1 and at the maximum 16
+    passes, on a periodic and on a surface gap."""
+    for cfg in (dict(P.THERMAL_PAIRS, filter_passes=passes),
+                dict(P.SMALL_DISCHARGE, qed=0, filter_passes=passes)):
+        g, o = P.make_pair(cfg, "fp32", tile=32)
+        g.step(60)
+        o.step(60)
+        d = g.diag(spectrum=False)
+        assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+        Eg, Eo = g.field(), o.E()
+        assert np.abs(Eg - Eo).max() <= 1e-3 * np.abs(Eo).max()
+        g.close()
