@@ -60,6 +60,26 @@ def batch(n_gaps: int = 256) -> list[dict]:
     return [batch_row(i) for i in range(n_gaps)]
 
 
+# Concurrency-model scan (App. B empirical fit): 36 parameter sets in five
+# one-at-a-time sweeps around the Fig. 2 point (alpha = 2, t_x = t_pm = 1e-3,
+# t_acc = 4e-8, g3 = 8e-8, units of t_esc).  The paper names the sweeps and
+# the count but not their ranges; these span a factor 10 either way in g3
+# and t_acc, about 3 in t_x and t_pm, and alpha in [1.25, 4].
+SCAN_BASE = dict(alpha=2.0, t_x=1e-3, t_pm=1e-3, t_acc=4e-8, g3=8e-8)
+
+
+def concurrency_scan() -> list[dict]:
+    """The 36 sets, each with the name of its sweep."""
+    out = []
+    sweeps = (("g3", np.geomspace(8e-9, 8e-7, 8)), ("t_pm", np.geomspace(3e-4, 3e-3, 7)),
+              ("t_x", np.geomspace(3e-4, 3e-3, 7)), ("t_acc", np.geomspace(4e-9, 4e-7, 7)),
+              ("alpha", np.linspace(1.25, 4.0, 7)))
+    for name, values in sweeps:
+        for v in values:
+            out.append(dict(SCAN_BASE, **{name: float(v)}, sweep=name))
+    return out
+
+
 TRACE_KEYS = ("M_avg", "M_peak", "E_min", "E_max", "E_abs_max", "n_electrons", "n_positrons", "n_photons")
 
 

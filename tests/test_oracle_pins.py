@@ -680,6 +680,35 @@ def test_ode_empirical_peak_multiplicity_fit():
         assert abs(mp[1:].mean() - pred) / pred < tol
 
 
+@pytest.mark.slow
+def test_ode_36_solution_scan_tracks_empirical_formula():
+    """App. B: across 36 solutions of five one-at-a-time sweeps the peak
+    multiplicity follows 11 t_acc/(t_x g3) alpha^(1/4) to <~30 %, is set by
+    t_acc/(g3 t_x) and hardly depends on t_pm.  Sets and step rule of the
+    scan recipe; the fit is an ordinary least squares in log space."""
+    from oracle import ode
+    from paper_2608_21920_b300.workloads import concurrency_scan
+    sets = concurrency_scan()
+    M = []
+    for q in sets:
+        dt = min(2e-4, 0.2 * min(q["t_x"], q["t_pm"]))
+        t, Y = ode.rk4_scalar([1.0, 0.0, 1.0, 0.0], q, dt, int(30.0 / dt), record_every=5)
+        m = Y[:, 0]
+        i = ode.peaks(t, m)
+        i = i[m[i] > 100.0]
+        assert i.size >= 3
+        M.append(m[i[1:]].mean())
+    M = np.array(M)
+    X = np.array([q["t_acc"] / (q["t_x"] * q["g3"]) for q in sets])
+    al = np.array([q["alpha"] for q in sets])
+    c, tol = _paper("empirical_fit_coeff")
+    assert np.all(np.abs(M / (c * X * al ** 0.25) - 1.0) < tol)
+    cols = [np.ones(36)] + [np.log([q[k] for q in sets]) for k in ("t_acc", "g3", "t_x", "t_pm", "alpha")]
+    coef = np.linalg.lstsq(np.stack(cols, axis=1), np.log(M), rcond=None)[0]
+    assert abs(coef[1] - 1) < 0.1 and abs(coef[2] + 1) < 0.1 and abs(coef[3] + 1) < 0.1
+    assert abs(coef[4]) < 0.1
+
+
 # ------------------------------------------------------------------ merge
 def _sums(L):
     g = np.sqrt(1 + L["u"] ** 2)
