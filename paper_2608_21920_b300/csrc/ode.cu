@@ -20,21 +20,24 @@ namespace {
 template <class R>
 struct Model {
   R alpha, tx, tpm, tacc, g3, delta;
+  // reciprocals and the ratio g3/t_acc, formed once per set: the right-hand
+  // side then has no division (FP64 division is a long dependent sequence)
+  R itx, itpm, itacc, gt, idelta;
   __device__ __forceinline__ R gate(R z) const {
     if (delta == (R)0) return z > (R)0 ? (R)1 : (R)0;
-    return (R)0.5 * ((R)1 + tanh(z / delta));
+    return (R)0.5 * ((R)1 + tanh(z * idelta));
   }
   __device__ __forceinline__ R dgate(R z) const {
     if (delta == (R)0) return (R)0;
-    const R th = tanh(z / delta);
-    return ((R)1 - th * th) / ((R)2 * delta);
+    const R th = tanh(z * idelta);
+    return ((R)1 - th * th) * ((R)0.5 * idelta);
   }
   __device__ __forceinline__ void f(const R y[4], R k[4]) const {
     const R H = gate(fabs(y[2]) - (R)1);
-    k[0] = (R)2 * y[1] / tpm - y[0];
-    k[1] = -y[1] / tpm + H * y[0] / tx - y[1];
+    k[0] = (R)2 * y[1] * itpm - y[0];
+    k[1] = -y[1] * itpm + H * y[0] * itx - y[1];
     k[2] = alpha - y[3];
-    k[3] = -y[3] + y[0] * y[2] * g3 / tacc;
+    k[3] = -y[3] + y[0] * y[2] * gt;
   }
   // lam_y += J(y)^T a ; lam_p += Jp(y)^T a
   __device__ __forceinline__ void vjp(const R y[4], const R a[4], R ly[4], R lp[5]) const {
@@ -42,15 +45,15 @@ struct Model {
     const R H = gate(z);
     const R sg = y[2] > (R)0 ? (R)1 : (y[2] < (R)0 ? (R)-1 : (R)0);
     const R dH = dgate(z) * sg;
-    ly[0] += -a[0] + a[1] * H / tx + a[3] * y[2] * g3 / tacc;
-    ly[1] += a[0] * (R)2 / tpm + a[1] * ((R)-1 / tpm - (R)1);
-    ly[2] += a[1] * dH * y[0] / tx + a[3] * y[0] * g3 / tacc;
+    ly[0] += -a[0] + a[1] * H * itx + a[3] * y[2] * gt;
+    ly[1] += a[0] * (R)2 * itpm + a[1] * (-itpm - (R)1);
+    ly[2] += a[1] * dH * y[0] * itx + a[3] * y[0] * gt;
     ly[3] += -a[2] - a[3];
     lp[0] += a[2];
-    lp[1] += -a[1] * H * y[0] / (tx * tx);
-    lp[2] += (-a[0] * (R)2 * y[1] + a[1] * y[1]) / (tpm * tpm);
-    lp[3] += -a[3] * y[0] * y[2] * g3 / (tacc * tacc);
-    lp[4] += a[3] * y[0] * y[2] / tacc;
+    lp[1] += -a[1] * H * y[0] * (itx * itx);
+    lp[2] += (-a[0] * (R)2 * y[1] + a[1] * y[1]) * (itpm * itpm);
+    lp[3] += -a[3] * y[0] * y[2] * gt * itacc;
+    lp[4] += a[3] * y[0] * y[2] * itacc;
   }
   __device__ __forceinline__ void step(R y[4], R h) const {
     R k1[4], k2[4], k3[4], k4[4], t[4];
@@ -101,6 +104,11 @@ __device__ __forceinline__ Model<R> load_model(const R *p, int b, double delta) 
   m.tacc = p[5 * b + 3];
   m.g3 = p[5 * b + 4];
   m.delta = (R)delta;
+  m.itx = (R)1 / m.tx;
+  m.itpm = (R)1 / m.tpm;
+  m.itacc = (R)1 / m.tacc;
+  m.gt = m.g3 / m.tacc;
+  m.idelta = m.delta != (R)0 ? (R)1 / m.delta : (R)0;
   return m;
 }
 
