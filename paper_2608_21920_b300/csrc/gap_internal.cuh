@@ -177,25 +177,47 @@ __device__ __forceinline__ float uniform24(uint64_t seed, uint64_t id, uint32_t 
 // ratio-of-uniforms method (Kinderman & Monahan 1977): (a, v) uniform on
 // (0,1] x [-bmax, bmax] with bmax = sup |u| sqrt(f(u)) (at u^2 = 2 theta
 // gamma, gamma = theta + sqrt(theta^2 + 1)); u = v/a is accepted when
-// a^2 <= f(u).  Round r draws k = 2r, 2r+1 of (id, step, channel); after 64
-// rejected rounds ok is false and u = 0.
-__device__ __noinline__ static double mj_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
-                                              double theta, bool &ok) {
+// 2 ln a <= -(gamma - 1)/theta.  Round r draws k = 2r, 2r+1 of (id, step,
+// channel); after 64 rejected rounds ok is false and u = 0.
+__device__ __forceinline__ double mj_bmax(double theta) {
   const double gs = theta + sqrt(theta * theta + 1.0);
   const double us = sqrt(2.0 * theta * gs);
-  const double bmax = us * exp(-(gs - 1.0) / (2.0 * theta));
+  return us * exp(-(gs - 1.0) / (2.0 * theta));
+}
+
+// The draw with bmax given (a loader forms it once).  The bounds
+// 1 - 1/a <= ln a <= a - 1 settle about 70 % of the rounds without the
+// logarithm; only where a bound lies within a relative 1e-12 of the
+// threshold is ln a taken, so every decision is the one the logarithm gives.
+__device__ __noinline__ static double mj_draw_b(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
+                                                double theta, double bmax, bool &ok) {
   for (uint32_t r = 0; r < 64; ++r) {
     const double a = uniform53(seed, id, step, channel, 2 * r);
     const double vv = bmax * (2.0 * uniform53(seed, id, step, channel, 2 * r + 1) - 1.0);
     const double u = vv / a;
     const double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
-    if (2.0 * log(a) <= -gm1 / theta) {
+    const double rhs = -gm1 / theta;
+    const double up = 2.0 * (a - 1.0);  // >= 2 ln a
+    bool accept;
+    if (up <= rhs - 1e-12 * (fabs(rhs) + fabs(up))) {
+      accept = true;
+    } else if (up - rhs * a > 1e-12 * (fabs(rhs) * a + fabs(up))) {  // 2 (1 - 1/a) > rhs, times a > 0
+      accept = false;
+    } else {
+      accept = 2.0 * log(a) <= rhs;
+    }
+    if (accept) {
       ok = true;
       return u;
     }
   }
   ok = false;
   return 0.0;
+}
+
+__device__ __forceinline__ double mj_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
+                                          double theta, bool &ok) {
+  return mj_draw_b(seed, id, step, channel, theta, mj_bmax(theta), ok);
 }
 
 __device__ __host__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -396,6 +418,56 @@ __device__ __noinline__ void append_lepton(const View &v, int s, int t, int32_t 
     v.lk[cur][s][slot] = k;
     atomicAdd(&v.seg_alive[s][t], 1);
   } else {
+    long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->spill_n[s]), 1ull);
+    if (i < v.spill_capacity) {
+      v.sk[s][i] = k;
+      v.stile[s][i] = t;
+      v.sphi[s][i] = (double)phi;
+      v.su[s][i] = (double)u;
+      v.sw[s][i] = (double)w;
+      v.stau[s][i] = (double)tau;
+      v.sid[s][i] = id;
+      atomicAdd(&v.spill_cnt[s][t], 1);
+    } else {
+      atomicOr(&v.ctl->error, 1);  // storage exhausted
+    }
+    v.ctl->need_rebin = 1;
+    atomicAdd(&v.counters[v.tiles[t].gap * C_NCNT + C_SPILL], 1ull);
+  }
+}
+
+// append_lepton for a loader, where whole warps append to few tiles: the
+// lanes that append to the same (species, tile) reserve their slots with one
+// atomic (slots in lane order) and count the stored ones with one more.  The
+// whole warp calls it together; lanes with valid == false append nothing.
+template <class R>
+__device__ __forceinline__ void append_lepton_warp(const View &v, bool valid, int s, int t, int32_t k, R phi,
+                                                   R u, typename Prec<R>::W w, R tau, uint64_t id) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? s * v.n_tiles + t : -1);
+  if (!valid) return;  // the invalid lanes form their own group
+  const int leader = __ffs(peers) - 1;
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&v.seg_append[s][t], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int pos = base + rank;
+  const bool fits = pos < v.seg_cap[s][t];
+  const unsigned stored = __ballot_sync(peers, fits) & peers;
+  if (fits) {
+    const int cur = v.ctl->lep_cur;
+    const int64_t slot = v.seg_start[s][t] + pos;
+    as<R>(v.lphi[cur][s])[slot] = phi;
+    as<R>(v.lu[cur][s])[slot] = u;
+    as<typename Prec<R>::W>(v.lw[cur][s])[slot] = w;
+    as<R>(v.ltau[cur][s])[slot] = tau;
+    v.lid[cur][s][slot] = id;
+    __threadfence_block();
+    v.lk[cur][s][slot] = k;
+  }
+  if (lane == leader && stored) atomicAdd(&v.seg_alive[s][t], __popc(stored));
+  if (!fits) {  // the segment is full: the single-lepton path spills (its reservation fails too)
     long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->spill_n[s]), 1ull);
     if (i < v.spill_capacity) {
       v.sk[s][i] = k;

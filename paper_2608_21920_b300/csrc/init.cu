@@ -9,7 +9,7 @@ namespace gapk {
 // Loader: quiet start X = cell + (j + 1/2)/ppc; for the thermal pair load the
 // electrons are displaced by (A/k1) sin(k1 X), k1 = 2 pi/nx (a Langmuir seed
 // of relative density amplitude A) and momenta are 1D Maxwell-Juttner by the
-// mj_draw (step 0, channel CH_INIT_U).
+// mj_draw_b (step 0, channel CH_INIT_U, the bound formed once).
 template <class R>
 __global__ void k_load(View v, LoadSpec sp) {
   using W = typename Prec<R>::W;
@@ -17,34 +17,50 @@ __global__ void k_load(View v, LoadSpec sp) {
   const int64_t total = sp.n_per_species * sp.species_count;
   const double w = (sp.init == GAP_INIT_PAIR_THERMAL ? 0.5 : 1.0) * sp.density * g.dx / (double)sp.ppc;
   const double k1 = 2.0 * 3.141592653589793 / (double)g.nx;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int s = (int)(p / sp.n_per_species);
-    const int64_t idx = p % sp.n_per_species;
-    const int64_t cell = idx / sp.ppc, j = idx % sp.ppc;
-    const uint64_t id = ((uint64_t)g.gap_index << 40) | ((uint64_t)s << 39) | (uint64_t)(cell * sp.ppc + j);
-    double X = (double)cell + ((double)j + 0.5) / (double)sp.ppc;
-    double u = 0.0;
-    if (sp.init == GAP_INIT_PAIR_THERMAL) {
-      if (s == 0 && sp.seed_amp != 0.0) {
-        X += sp.seed_amp / k1 * sin(k1 * X);
-        X = fmod(X, (double)g.nx);
-        if (X < 0.0) X += (double)g.nx;
+  const double bmax = sp.theta > 0.0 ? mj_bmax(sp.theta) : 0.0;
+  const bool full_state = v.qed_any || v.has_w;  // the lean store keeps no optical depth
+  // warp-uniform grid-stride loop (the append is a warp collective); lanes
+  // past the end take part without appending
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; p0 < total; p0 += stride) {
+    const int64_t p = p0 + lane;
+    const bool valid = p < total;
+    int s = 0, t = 0;
+    int32_t k = 0;
+    R phi = (R)1;
+    double u = 0.0, tau = 0.0;
+    uint64_t id = 0;
+    if (valid) {
+      s = (int)(p / sp.n_per_species);
+      const int64_t idx = p % sp.n_per_species;
+      const int64_t cell = idx / sp.ppc, j = idx % sp.ppc;
+      id = ((uint64_t)g.gap_index << 40) | ((uint64_t)s << 39) | (uint64_t)(cell * sp.ppc + j);
+      double X = (double)cell + ((double)j + 0.5) / (double)sp.ppc;
+      if (sp.init == GAP_INIT_PAIR_THERMAL) {
+        if (s == 0 && sp.seed_amp != 0.0) {
+          X += sp.seed_amp / k1 * sin(k1 * X);
+          // X mod nx: within (-nx, 2 nx) one exact subtraction or addition
+          // gives fmod's result (fmod is a long FP64 sequence)
+          const double L = (double)g.nx;
+          if (X >= L && X < 2.0 * L) X -= L;
+          else if (!(X >= 0.0 && X < L)) X = fmod(X, L);
+          if (X < 0.0) X += L;
+        }
+        if (sp.theta > 0.0) {
+          bool ok = true;
+          u = mj_draw_b(g.seed, id, 0, CH_INIT_U, sp.theta, bmax, ok);
+          if (!ok) atomicAdd(&v.counters[sp.gap * C_NCNT + C_LOAD_OVF], 1ull);
+        }
       }
-      if (sp.theta > 0.0) {
-        bool ok = true;
-        u = mj_draw(g.seed, id, 0, CH_INIT_U, sp.theta, ok);
-        if (!ok) atomicAdd(&v.counters[sp.gap * C_NCNT + C_LOAD_OVF], 1ull);
-      }
+      if (full_state) tau = -log(uniform53(g.seed, id, 0, CH_TAU0, 0));
+      split_position<R>(X, g.nx, g.periodic != 0, k, phi);
+      t = tile_of(v, g, k);
     }
-    const double tau = -log(uniform53(g.seed, id, 0, CH_TAU0, 0));
-    int32_t k;
-    R phi;
-    split_position<R>(X, g.nx, g.periodic != 0, k, phi);
     W wq;
     if (sizeof(R) == 4) wq = (W)(1u << kWeightShift);
     else wq = (W)w;
-    append_lepton<R>(v, s, tile_of(v, g, k), k, phi, (R)u, wq, (R)tau, id);
+    append_lepton_warp<R>(v, valid, s, t, k, phi, (R)u, wq, (R)tau, id);
   }
 }
 
