@@ -318,6 +318,20 @@ def _oracle_sample(nx, steps, warmup):
     return 2 * nx * PPC * steps / dt, dt
 
 
+def host_cpu():
+    """CPU model and logical core count of the host (for the baseline record)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
 def cpu_baseline(seconds):
     """The FP64 oracle as it stands, single-threaded on the host, on a bounded
     sample of the workload (same density, temperature and seed; fewer cells)."""
@@ -326,7 +340,8 @@ def cpu_baseline(seconds):
     steps = max(2, int(seconds * rate / (2 * nx * PPC)))
     rate, dt = _oracle_sample(nx, steps, 1)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Nx=2^14 periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), {steps} steps, {dt:.1f} s"}
+            "sample": f"Nx=2^14 periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), {steps} steps, {dt:.1f} s",
+            **host_cpu()}
 
 
 def run_reference(args):
@@ -351,7 +366,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "precision": "FP64 oracle (plain C, 1 thread)",
                        "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
