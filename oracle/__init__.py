@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("gap_index", C.c_int32), ("qed", C.c_int32), ("boundary", C.c_int32),
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
-        ("inject_theta", C.c_double), ("filter_passes", C.c_int32),
+        ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
     ]
 
 
@@ -79,6 +79,8 @@ def lib():
         for f in ("orc_tsyn", "orc_tbw", "orc_spec_survival", "orc_spec_inverse"):
             getattr(L, f).argtypes = [d]; getattr(L, f).restype = d
         L.orc_mj_sample.argtypes = [u64, u64, d, C.POINTER(C.c_int)]; L.orc_mj_sample.restype = d
+        for f in ("orc_qspec_density", "orc_qspec_survival", "orc_qspec_inverse"):
+            getattr(L, f).argtypes = [d, d]; getattr(L, f).restype = d
         L.orc_binomial_smooth.argtypes = [C.POINTER(d), i64, C.c_int32, C.c_int32]
         L.orc_mj_draw.argtypes = [u64, u64, u32, u32, d, C.POINTER(C.c_int)]; L.orc_mj_draw.restype = d
         L.orc_create.argtypes = [C.POINTER(Params)]; L.orc_create.restype = vp
@@ -150,6 +152,18 @@ def spec_inverse(U):
     return lib().orc_spec_inverse(float(U))
 
 
+def qspec_density(chi, xi):
+    return lib().orc_qspec_density(float(chi), float(xi))
+
+
+def qspec_survival(chi, xi):
+    return lib().orc_qspec_survival(float(chi), float(xi))
+
+
+def qspec_inverse(chi, U):
+    return lib().orc_qspec_inverse(float(chi), float(U))
+
+
 EXT_PERIODIC, EXT_NODE_EVEN, EXT_CELL_ODD = 0, 1, 2
 
 
@@ -177,7 +191,7 @@ DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
                 init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0,
-                filter_passes=0)
+                filter_passes=0, qed_quantum=0)
 
 
 class Sim:

@@ -195,6 +195,107 @@ double orc_spec_inverse(double U) {
   return exp(y);
 }
 
+/* Quantum photon spectrum of a lepton with quantum parameter chi (an option;
+ * Sect. 3.1 leaves the shape S(gamma, x) unspecified and the default is the
+ * classical shape above).  Photon energy fraction xi = x/gamma in (0, 1);
+ * the number per unit xi is proportional to (Baier & Katkov 1968)
+ *   n(xi) = (1 - xi + 1/(1 - xi)) K_{2/3}(d) - int_d^inf K_{1/3}(s) ds,
+ *   d = 2 xi / (3 chi (1 - xi)),
+ * whose chi -> 0 limit is int_y^inf K_{5/3}, y = x/x_c, x_c = (3/2) gamma chi.
+ * With K_nu(d) = int_0^inf exp(-d cosh t) cosh(nu t) dt and
+ * int_d^inf K_nu = int_0^inf exp(-d cosh t) cosh(nu t) / cosh t dt, n is one
+ * integral over t (trapezoid rule, h = 1/8, to exp(-745)).  In the variable
+ * s = d^(1/3) both ends of the xi range are smooth: xi = 3 chi s^3 /
+ * (2 + 3 chi s^3), dxi/ds = 18 chi s^2 / (2 + 3 chi s^3)^2. */
+static double qspec_density_d(double d, double xi) {
+  const double B = 1.0 - xi + 1.0 / (1.0 - xi);
+  const double h = 0.125;
+  double sum = 0.0;
+  for (int k = 0;; ++k) {
+    const double t = k * h, ch = cosh(t), arg = d * ch;
+    if (arg > 745.0 || t > 700.0) break;
+    const double f = exp(-arg) * (B * cosh(2.0 * t / 3.0) - cosh(t / 3.0) / ch);
+    sum += (k == 0 ? 0.5 : 1.0) * f;
+  }
+  return h * sum;
+}
+
+double orc_qspec_density(double chi, double xi) {
+  if (!(xi > 0.0 && xi < 1.0)) return 0.0;
+  return qspec_density_d(2.0 * xi / (3.0 * chi * (1.0 - xi)), xi);
+}
+
+/* n(xi(s)) dxi/ds */
+static double qspec_ds(double chi, double s) {
+  const double d = s * s * s, w = 2.0 + 3.0 * chi * d;
+  const double xi = 3.0 * chi * d / w;
+  if (!(s > 0.0) || xi >= 1.0) return 0.0;
+  return qspec_density_d(d, xi) * 18.0 * chi * s * s / (w * w);
+}
+
+/* 8-point Gauss-Legendre nodes and weights on [-1, 1], by Newton's method on
+ * the Legendre polynomial P_8 (three-term recurrence). */
+static void gauss_legendre8(double *x, double *w) {
+  const int n = 8;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* S_q(xi) = int_xi^1 n: composite 8-point Gauss-Legendre in s over
+ * [s(xi), (d(xi) + 60)^(1/3)] in 64 panels (the rest is below exp(-60) of
+ * the integrand at the lower end). */
+double orc_qspec_survival(double chi, double xi) {
+  double gx[8], gw[8];
+  gauss_legendre8(gx, gw);
+  const double d0 = xi > 0.0 ? 2.0 * xi / (3.0 * chi * (1.0 - xi)) : 0.0;
+  const double s0 = cbrt(d0), s1 = cbrt(d0 + 60.0);
+  const int panels = 64;
+  const double hp = (s1 - s0) / panels;
+  double sum = 0.0;
+  for (int pnl = 0; pnl < panels; ++pnl) {
+    const double a = s0 + pnl * hp;
+    for (int i = 0; i < 8; ++i) sum += gw[i] * qspec_ds(chi, a + 0.5 * hp * (gx[i] + 1.0));
+  }
+  return 0.5 * hp * sum;
+}
+
+/* Inverse: the xi with S_q(xi) = U S_q(0), U in (0, 1].  Newton in s,
+ * safeguarded by a bracket (bisection when a step leaves it). */
+double orc_qspec_inverse(double chi, double U) {
+  const double target = U * orc_qspec_survival(chi, 0.0);
+  double lo = 0.0, hi = cbrt(800.0);
+  double s = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double d = s * s * s, w = 2.0 + 3.0 * chi * d;
+    const double xi = 3.0 * chi * d / w;
+    const double S = orc_qspec_survival(chi, xi);
+    if (S > target) lo = s; else hi = s;
+    const double dS = -qspec_ds(chi, s);
+    double sn = dS < 0.0 ? s - (S - target) / dS : 0.5 * (lo + hi);
+    if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+    const double step = fabs(sn - s);
+    s = sn;
+    if (step < 1e-14 * (s > 1e-300 ? s : 1.0) || hi - lo < 1e-15) break;
+  }
+  const double d = s * s * s;
+  return 3.0 * chi * d / (2.0 + 3.0 * chi * d);
+}
+
 /* 1D Maxwell-Juttner deviate, f(u) proportional to exp(-(gamma-1)/theta), by
  * the ratio-of-uniforms method (Kinderman & Monahan 1977): (a, v) uniform on
  * (0,1] x [-bmax, bmax], u = v/a accepted when a^2 <= f(u).  bmax =
@@ -249,6 +350,7 @@ typedef struct {
   int32_t kmax_inject; /* injected electrons per step cap */
   double inject_theta; /* temperature of the injected atmosphere (m_e c^2); 0 = cold */
   int32_t filter_passes; /* binomial smoothing passes of the current per step; 0 = none */
+  int32_t qed_quantum;   /* 1: quantum photon spectrum (orc_qspec_*); 0: classical */
 } orc_params;
 
 typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
@@ -648,8 +750,9 @@ void orc_step(orc_sim *s) {
         if (tau > r * trem) { tau -= r * trem; break; }
         trem -= tau / r;
         double U = orc_uniform(p->seed, L->id, n, CH_EMIT_X, (uint32_t)k);
-        double xi = orc_spec_inverse(U);
-        double x = xi * 1.5 * g * chi;
+        /* photon energy: classical shape (x = xi x_c), or with qed_quantum the
+         * quantum shape (x = xi gamma, xi the energy fraction) */
+        double x = p->qed_quantum ? orc_qspec_inverse(chi, U) * g : orc_spec_inverse(U) * 1.5 * g * chi;
         double gm1 = u * u / (g + 1.0);
         double dir = u >= 0.0 ? 1.0 : -1.0;
         if (x >= gm1) {

@@ -520,6 +520,83 @@ def test_photon_energy_spectrum_ks():
     assert stats.kstest(xi, lambda v: 1.0 - np.vectorize(O.spec_survival)(v)).pvalue > 1e-3
 
 
+# ----------------------------------------------------- quantum photon spectrum
+def _qdensity_ref(chi, xi):
+    """Quantum photon number spectrum per unit energy fraction from scipy's
+    Bessel functions: (1 - xi + 1/(1 - xi)) K_2/3(d) - int_d^inf K_1/3,
+    d = 2 xi / (3 chi (1 - xi))."""
+    d = 2.0 * xi / (3.0 * chi * (1.0 - xi))
+    tail = integrate.quad(lambda s: special.kv(1.0 / 3.0, s), d, np.inf, limit=200, epsrel=1e-12)[0]
+    return (1.0 - xi + 1.0 / (1.0 - xi)) * special.kv(2.0 / 3.0, d) - tail
+
+
+def test_quantum_spectrum_density_against_bessel():
+    for chi in (0.05, 1.0, 20.0):
+        for xi in (1e-4, 0.01, 0.2, 0.6, 0.95):
+            assert O.qspec_density(chi, xi) == pytest.approx(_qdensity_ref(chi, xi), rel=1e-9)
+
+
+def test_quantum_spectrum_number_rate_matches_paper_tsyn():
+    """The photon number per unit time is proportional to T_syn (eq. tau_syn):
+    the quantum spectrum integrated over the energy fraction, over its
+    classical value 5 pi chi / 2 (int_0^inf t K_5/3 = 5 pi / 3), follows the
+    paper's fit of T_syn(chi)/T_syn(0) within its stated ~1 % up to chi = 30,
+    with the paper's exact first-order slope 8 sqrt3 / 15."""
+    for chi in (0.01, 0.1, 1.0, 3.0, 10.0, 30.0):
+        ratio = O.qspec_survival(chi, 0.0) / (2.5 * math.pi * chi)
+        assert ratio == pytest.approx(O.tsyn(chi) / O.tsyn(0.0), rel=0.01)
+    slope, tol = _paper("tsyn_slope")
+    chi = 1e-4
+    measured = -(O.qspec_survival(chi, 0.0) / (2.5 * math.pi * chi) - 1.0) / chi * (5.0 / (2.0 * math.sqrt(3.0)))
+    assert measured == pytest.approx(-slope, rel=2e-3)
+
+
+def test_quantum_spectrum_power_suppression():
+    """Emitted power over the classical 2 pi chi^2 / sqrt3 (int_0^inf t^2 K_5/3
+    = 16 pi / (9 sqrt3)): g_Q = 1 - (55 sqrt3 / 16) chi + O(chi^2)."""
+    chi = 1e-4
+    pts = [chi * k for k in (1e-3, 1e-2, 0.1, 1, 3, 10, 30)]
+    P = integrate.quad(lambda x: x * O.qspec_density(chi, x), 0, 1, points=pts, limit=400, epsrel=1e-11)[0]
+    g = P / (2.0 * math.pi * chi * chi / math.sqrt(3.0))
+    assert (1.0 - g) / chi == pytest.approx(55.0 * math.sqrt(3.0) / 16.0, rel=3e-3)
+
+
+def test_quantum_spectrum_classical_limit_and_support():
+    chi = 1e-6
+    for U in (0.05, 0.5, 0.95):
+        assert O.qspec_inverse(chi, U) / (1.5 * chi) == pytest.approx(O.spec_inverse(U), rel=1e-4)
+    for chi in (0.3, 100.0):
+        for U in (1e-12, 0.3, 1 - 1e-6):
+            xi = O.qspec_inverse(chi, U)
+            assert 0.0 < xi < 1.0
+            assert O.qspec_survival(chi, xi) / O.qspec_survival(chi, 0.0) == pytest.approx(U, rel=1e-10)
+
+
+def test_quantum_photon_energy_ks():
+    """With qed_quantum the emitted energy fraction x / gamma of a lepton at
+    chi = 2 follows the quantum spectrum (KS against scipy's Bessel CDF)."""
+    lam, rho, g0 = 2e-4, 100.0, 1000.0
+    chi = g0 * g0 * lam / rho
+    s = O.Sim(nx=64, boundary=O.BC_PERIODIC, qed=1, qed_quantum=1, lambda_hat=lam, rho_hat=rho,
+              rate_mult=1e-3, dx=0.1, dt=0.045, gap_length=6.4)
+    u0 = math.sqrt(g0 * g0 - 1)
+    N = 3000
+    for i in range(N):
+        s.add_lepton(i, -1, 1.0, u0, 1e-30, tau=0.0)
+    s.step(1)
+    g = np.sqrt(1 + s.leptons()["u"] ** 2)
+    xi = (g0 - g) / g0
+    assert N <= s.counters()["emit_events"] <= N + 3
+    grid = np.concatenate([[0.0], np.geomspace(1e-7, 0.999, 300)])
+    dens = [_qdensity_ref(chi, x) for x in grid[1:]]
+    pieces = [integrate.quad(lambda x: _qdensity_ref(chi, x), a, b, epsrel=1e-9)[0]
+              for a, b in zip(grid[:-1], grid[1:])]
+    cdf = np.concatenate([[0.0], np.cumsum(pieces)])
+    cdf /= cdf[-1]
+    assert stats.kstest(xi, lambda v: np.interp(v, grid, cdf)).pvalue > 1e-3
+    assert dens[0] > 0
+
+
 def test_pair_conversion_length_distribution():
     """Photons accumulate tau_BW (eq. tau_bw) at the angle sin psi = |sin(l/R)|
     (Sect. 6.1) and convert at tau = -ln U: P(converted by l) = 1 - exp(-tau(l))."""
