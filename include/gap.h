@@ -108,6 +108,14 @@ typedef struct gap_params {
                             cell charge oddly, so Gauss's law holds for the
                             smoothed charge (the Gauss solve and residual use it).
                             In [0, 16] with nx >= 2 passes + 2, else GAP_EINVAL */
+  int32_t qed_quantum;   /* 1: the photon energy of an emission follows the quantum
+                            spectrum n(xi) ~ (1 - xi + 1/(1 - xi)) K_2/3(d)
+                            - int_d^inf K_1/3, d = 2 xi / (3 chi (1 - xi)),
+                            xi = x/gamma (Baier & Katkov; Sect. 3.1 leaves the
+                            shape open), read from a table of the inverse
+                            distribution built at init (relative error of xi
+                            about 1e-5; chi above 1e5 uses the chi = 1e5 row);
+                            0: the classical shape.  0 or 1, else GAP_EINVAL */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */
@@ -313,6 +321,14 @@ void gap_free(gap_handle *h);
 
 const char *gap_last_error(const gap_handle *h);
 const char *gap_status_string(int status);
+
+/* The photon energy fraction xi in (0, 1) of the quantum spectrum for
+ * emission parameter chi and draw U in (0, 1] (n values, device arrays; the
+ * inverse the emissions of qed_quantum gaps use), in the FP64 (precision =
+ * GAP_FP64_PLAIN) or the FP32 (GAP_FP32_STATE) evaluation.  GAP_EINVAL when
+ * no gap of the handle has qed_quantum.  Enqueued on `stream`. */
+int gap_qspectrum_inverse(gap_handle *h, const double *dev_chi, const double *dev_U, double *dev_xi, int64_t n,
+                          int32_t precision, void *stream);
 
 /* ------------------------------------------------------------------------
  * Concurrency model (Sect. 5.2, eq. dis1-dis4) -- batched RK4 integrator

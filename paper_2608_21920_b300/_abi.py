@@ -23,7 +23,7 @@ class GapParams(C.Structure):
         ("nx", C.c_int64), ("ppc", C.c_int64), ("cap", C.c_int64), ("seed", C.c_uint64),
         ("qed", C.c_int32), ("boundary", C.c_int32), ("init", C.c_int32),
         ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32), ("gap_index", C.c_int32),
-        ("inject_theta", C.c_double), ("filter_passes", C.c_int32),
+        ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
     ]
 
 
@@ -85,6 +85,7 @@ def lib():
     L.gap_steps_done.argtypes = [vp]
     L.gap_steps_done.restype = i64
     L.gap_spectrum_inverse.argtypes = [vp, vp, vp, i64, i32, vp]
+    L.gap_qspectrum_inverse.argtypes = [vp, vp, vp, vp, i64, i32, vp]
     L.gap_power_spectrum_noalloc.argtypes = [vp, i64, vp, vp]
     L.gap_profile.argtypes = [vp, i32, C.POINTER(d), C.POINTER(i64), C.POINTER(i64)]
     L.gap_profile_phases.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
@@ -107,7 +108,7 @@ def lib():
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
             "gap_get_field", "gap_set_field", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
-            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
+            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 
 

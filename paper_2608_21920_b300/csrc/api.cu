@@ -99,6 +99,7 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (!(q.inject_theta >= 0.0) || q.inject_theta > 1e3) { msg = "inject_theta must be in [0, 1e3]"; return GAP_EINVAL; }
     if (q.filter_passes < 0 || q.filter_passes > 16) { msg = "filter_passes must be in [0, 16]"; return GAP_EINVAL; }
     if (q.filter_passes > 0 && q.nx < 2 * (int64_t)q.filter_passes + 2) { msg = "filter_passes needs nx >= 2 passes + 2"; return GAP_EINVAL; }
+    if (q.qed_quantum != 0 && q.qed_quantum != 1) { msg = "qed_quantum must be 0 or 1"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -155,6 +156,88 @@ struct SpecQuad {
 
 }  // namespace
 
+// Quantum photon spectrum (gaps with qed_quantum), built on the host.  The
+// photon number per unit energy fraction xi is proportional to
+//   n(xi) = (1 - xi + 1/(1 - xi)) K_2/3(d) - int_d^inf K_1/3,
+//   d = 2 xi / (3 chi (1 - xi))   (Baier & Katkov 1968),
+// with K_nu(d) = int_0^inf e^{-d cosh t} cosh(nu t) dt and
+// int_d^inf K_nu = int_0^inf e^{-d cosh t} cosh(nu t) / cosh t dt (trapezoid
+// in t, h = 1/8).  In s = d^(1/3), xi = 3 chi s^3 / (2 + 3 chi s^3) and the
+// survival S(s) = int_s^inf n dxi/ds' ds' is smooth at both ends; each panel
+// between nodes is one 8-point Gauss-Legendre rule.  Row r holds chi =
+// exp(kQsLchi0 + r kQsDlchi); node k holds (S(s_k)/S(0), dS/ds(s_k)/S(0)).
+struct QSpecHost {
+  static constexpr double kH = 0.125;
+  double gx[8], gw[8];
+  std::vector<double> c, c2, c1;  // cosh t, cosh(2t/3), cosh(t/3)/cosh t at t = k h
+  QSpecHost() {
+    for (int i = 0; i < 8; ++i) {  // Gauss-Legendre nodes: Newton on P_8 (three-term recurrence)
+      double z = std::cos(M_PI * (i + 0.75) / 8.5), dp = 1.0;
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= 8; ++k) {
+          const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = 8.0 * (z * p1 - p0) / (z * z - 1.0);
+        const double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      gx[i] = z;
+      gw[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    for (int k = 0; k * kH <= 120.0; ++k) {
+      const double t = k * kH;
+      c.push_back(std::cosh(t));
+      c2.push_back(std::cosh(2.0 * t / 3.0));
+      c1.push_back(std::cosh(t / 3.0) / std::cosh(t));
+    }
+  }
+  // n(d, xi); the t-sum stops once a term is below e^-40 of the first
+  // (d (cosh t - 1) - 2t/3 > 40: the node weights grow at most like e^(2t/3))
+  double density(double d, double xi) const {
+    const double B = 1.0 - xi + 1.0 / (1.0 - xi);
+    double sum = 0.0;
+    for (size_t k = 0; k < c.size(); ++k) {
+      const double arg = d * c[k];
+      if (arg > 745.0 || d * (c[k] - 1.0) - (2.0 / 3.0) * k * kH > 40.0) break;
+      sum += (k == 0 ? 0.5 : 1.0) * std::exp(-arg) * (B * c2[k] - c1[k]);
+    }
+    return kH * sum;
+  }
+  double per_s(double chi, double s) const {  // n(xi(s)) dxi/ds
+    const double d = s * s * s, w = 2.0 + 3.0 * chi * d, xi = 3.0 * chi * d / w;
+    if (!(s > 0.0) || xi >= 1.0) return 0.0;
+    return density(d, xi) * 18.0 * chi * s * s / (w * w);
+  }
+  void row(double chi, double2 *out) const {
+    std::vector<double> S(kQsNodes, 0.0);
+    double acc = 0.0;  // the rest beyond the last node (below e^-60 of the total)
+    {
+      const double a = (kQsNodes - 1) * kQsDs;
+      for (int i = 0; i < 8; ++i) acc += 0.5 * gw[i] * per_s(chi, a + 0.5 * (gx[i] + 1.0));
+    }
+    S[kQsNodes - 1] = acc;
+    for (int k = kQsNodes - 2; k >= 0; --k) {
+      const double a = k * kQsDs;
+      double p = 0.0;
+      for (int i = 0; i < 8; ++i) p += gw[i] * per_s(chi, a + 0.5 * kQsDs * (gx[i] + 1.0));
+      acc += 0.5 * kQsDs * p;
+      S[k] = acc;
+    }
+    const double S0 = S[0];
+    for (int k = 0; k < kQsNodes; ++k) {
+      // dS/ds has a finite limit at s = 0 (n ~ d^(-2/3), dxi/ds ~ s^2)
+      const double sk = k > 0 ? k * kQsDs : 1e-6 * kQsDs;
+      out[k].x = S[k] / S0;
+      out[k].y = -per_s(chi, sk) / S0;
+    }
+    out[0].x = 1.0;
+  }
+};
+
 static int64_t next_pow2(int64_t n) {
   int64_t p = 1;
   while (p < n) p <<= 1;
@@ -172,7 +255,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<LoadSpec> loads;
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
-  bool qed_any = false, surface_any = false, merge_any = false, filter_any = false;
+  bool qed_any = false, surface_any = false, merge_any = false, filter_any = false, qs_any = false;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     GapDev &g = gaps[i];
@@ -212,6 +295,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.inject_theta = q.inject_theta;
     g.filter_passes = q.filter_passes;
     filter_any |= q.filter_passes > 0;
+    g.qed_quantum = q.qed && q.qed_quantum ? 1 : 0;
+    qs_any |= g.qed_quantum != 0;
     merge_any |= q.cap > 0;
     g.inj_root = ((uint64_t)(uint32_t)q.gap_index << 40) | (1ull << 38);
     qed_any |= g.qed != 0;
@@ -320,6 +405,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.quad_n = (int32_t)(quad_tmax / quad_h) + 1;
   v.quad_c = C.take<double>(v.quad_n);
   v.quad_a = C.take<double>(v.quad_n);
+  v.qs_any = qs_any ? 1 : 0;
+  v.qs_rows = kQsRows;
+  v.qs_tab_d = C.take<double2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
+  v.qs_tab_f = C.take<float2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
   v.max_nx = max_nx;
   v.max_P = max_P;
   v.dmom = C.take<double>(8 * (size_t)max_nx);
@@ -450,6 +539,19 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.spec_tab, tab.data(), sizeof(float2) * spec_n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_c, qc.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_a, qa.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
+  std::vector<double2> qtab_d;
+  std::vector<float2> qtab_f;
+  if (qs_any) {  // the quantum spectrum table, only when a gap asks for it
+    qtab_d.resize((size_t)kQsRows * kQsNodes);
+    qtab_f.resize(qtab_d.size());
+    const QSpecHost qh;  // about 0.05 s for all rows
+    for (int r = 0; r < kQsRows; ++r) qh.row(std::exp(kQsLchi0 + r * kQsDlchi), &qtab_d[(size_t)r * kQsNodes]);
+    for (size_t i = 0; i < qtab_d.size(); ++i) qtab_f[i] = make_float2((float)qtab_d[i].x, (float)qtab_d[i].y);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v.qs_tab_d, qtab_d.data(), sizeof(double2) * qtab_d.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v.qs_tab_f, qtab_f.data(), sizeof(float2) * qtab_f.size(), cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_check(h, e, "layout upload");
 }
@@ -809,6 +911,15 @@ int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int
   if (precision != GAP_FP64_PLAIN && precision != GAP_FP32_STATE) return GAP_EINVAL;
   launch_spec_inverse(h->v, dev_U, dev_xi, n, precision == GAP_FP32_STATE, (cudaStream_t)stream);
   return cuda_check(h, cudaGetLastError(), "spectrum inverse");
+}
+
+int gap_qspectrum_inverse(gap_handle *h, const double *dev_chi, const double *dev_U, double *dev_xi, int64_t n,
+                          int32_t precision, void *stream) {
+  if (!h || n < 0 || (n > 0 && (!dev_chi || !dev_U || !dev_xi))) return GAP_EINVAL;
+  if (precision != GAP_FP64_PLAIN && precision != GAP_FP32_STATE) return GAP_EINVAL;
+  if (!h->v.qs_any) return fail(h, GAP_EINVAL, "no gap of this handle has qed_quantum");
+  launch_qspec_inverse(h->v, dev_chi, dev_U, dev_xi, n, precision == GAP_FP32_STATE, (cudaStream_t)stream);
+  return cuda_check(h, cudaGetLastError(), "quantum spectrum inverse");
 }
 
 int64_t gap_steps_done(const gap_handle *h) { return h ? h->steps_done : 0; }

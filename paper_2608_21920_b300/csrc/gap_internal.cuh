@@ -25,6 +25,15 @@ constexpr int kMaxEmit = 16;                   // emission events per lepton-ste
 constexpr int kPushChunk = 4096;  // leptons per push work item (multiple of 32)
 static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 contributions per node");
 
+// Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
+// ln 10 / 8 (89 rows to chi = 1e5), nodes s = k kQsDs, k < kQsNodes (s <= 4,
+// d <= 64: the survival there is below e^-60).
+constexpr int kQsNodes = 257;
+constexpr int kQsRows = 89;
+constexpr double kQsLchi0 = -13.815510557964274;  // ln 1e-6
+constexpr double kQsDlchi = 0.28782313662425574;  // ln 10 / 8
+constexpr double kQsDs = 4.0 / 256.0;
+
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
@@ -47,7 +56,7 @@ struct GapDev {
   int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
   double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold
   int32_t filter_passes;  // binomial current-smoothing passes per step; 0 = none
-  int32_t pad2;
+  int32_t qed_quantum;    // 1: quantum photon spectrum (table below); 0: classical
 };
 
 struct TileDev {
@@ -80,6 +89,12 @@ struct View {
   int32_t variant, merge_any;
   int32_t filter_any, pad_f;  // some gap smooths its current
   double *Dflt;               // [2 x dcharge_len] smoothing scratch (node flux; two cell buffers)
+  // quantum photon spectrum (some gap with qed_quantum): per row of ln chi,
+  // the normalised survival S(s)/S(0) and its s-derivative on kQsNodes nodes
+  // of s = d^(1/3), d = 2 xi / (3 chi (1 - xi)); FP64 and FP32 copies
+  int32_t qs_any, qs_rows;
+  double2 *qs_tab_d;
+  float2 *qs_tab_f;
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
   int32_t *ph_gap;       // photons alive per gap
@@ -314,6 +329,77 @@ __device__ __forceinline__ double spec_inverse_d(const View &v, double U) {
     if (fabs(step) < 1e-14) break;
   }
   return exp(y);
+}
+
+// Quantum photon spectrum: the photon energy fraction xi of an emission at
+// chi for a draw U.  In each table row the node with S_k >= U > S_{k+1} is
+// found by bisection and the cubic Hermite interpolant of S(s) on that
+// panel is solved by Newton steps; ln s is blended over four rows of ln chi
+// (Catmull-Rom).  Below chi = 1e-6 the classical inverse gives d (the
+// quantum correction is O(chi)); above 1e5 the last row is used.
+template <class R>
+struct QsRow;
+template <>
+struct QsRow<double> {
+  __device__ static double2 at(const View &v, int r, int k) { return v.qs_tab_d[r * kQsNodes + k]; }
+};
+template <>
+struct QsRow<float> {
+  __device__ static float2 at(const View &v, int r, int k) { return v.qs_tab_f[r * kQsNodes + k]; }
+};
+
+template <class R>
+__device__ R qs_row_s(const View &v, int r, R U) {
+  int lo = 0, hi = kQsNodes - 1;
+  if (!(U > QsRow<R>::at(v, r, hi).x)) return (R)(hi * kQsDs);
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (QsRow<R>::at(v, r, mid).x >= U) lo = mid;
+    else hi = mid;
+  }
+  const auto a = QsRow<R>::at(v, r, lo), b = QsRow<R>::at(v, r, hi);
+  const R h = (R)kQsDs;
+  R t = (a.x - U) / (a.x - b.x);  // linear start, in [0, 1]
+  for (int it = 0; it < 4; ++it) {
+    const R t2 = t * t, t3 = t2 * t;
+    const R H = ((R)2 * t3 - (R)3 * t2 + (R)1) * a.x + (t3 - (R)2 * t2 + t) * h * a.y +
+                ((R)-2 * t3 + (R)3 * t2) * b.x + (t3 - t2) * h * b.y;
+    const R dH = ((R)6 * t2 - (R)6 * t) * a.x + ((R)3 * t2 - (R)4 * t + (R)1) * h * a.y +
+                 ((R)-6 * t2 + (R)6 * t) * b.x + ((R)3 * t2 - (R)2 * t) * h * b.y;
+    if (!(dH < (R)0)) break;
+    R tn = t - (H - U) / dH;
+    tn = tn < (R)0 ? (R)0 : (tn > (R)1 ? (R)1 : tn);
+    if (tn == t) break;
+    t = tn;
+  }
+  return ((R)lo + t) * h;
+}
+
+template <class R>
+__device__ __noinline__ R qspec_inverse(const View &v, R chi, R U) {
+  if (!(U < (R)1)) return (R)0;
+  R d;
+  if (chi < (R)1e-6) {
+    d = sizeof(R) == 4 ? (R)spec_inverse_f(v, (float)U) : (R)spec_inverse_d(v, (double)U);
+  } else {
+    R rr = (log(chi) - (R)kQsLchi0) / (R)kQsDlchi;
+    if (rr > (R)(v.qs_rows - 1)) rr = (R)(v.qs_rows - 1);
+    int i = (int)rr;
+    if (i > v.qs_rows - 2) i = v.qs_rows - 2;
+    const R t = rr - (R)i;
+    R p[4];
+    for (int j = 0; j < 4; ++j) {
+      int r = i - 1 + j;
+      r = r < 0 ? 0 : (r > v.qs_rows - 1 ? v.qs_rows - 1 : r);
+      const R sr = qs_row_s<R>(v, r, U);
+      p[j] = sr > (R)0 ? log(sr) : (R)-700;
+    }
+    const R ls = (R)0.5 * ((R)2 * p[1] + (-p[0] + p[2]) * t + ((R)2 * p[0] - (R)5 * p[1] + (R)4 * p[2] - p[3]) * t * t +
+                           (-p[0] + (R)3 * p[1] - (R)3 * p[2] + p[3]) * t * t * t);
+    d = exp((R)3 * ls);
+  }
+  const R w = (R)3 * chi * d;
+  return w / ((R)2 + w);
 }
 
 // ---------------------------------------------------------------------------

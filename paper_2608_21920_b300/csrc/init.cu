@@ -562,6 +562,17 @@ __global__ void k_spec_inverse(View v, const double *U, double *xi, int64_t n, i
     xi[i] = fp32 ? (double)spec_inverse_f(v, (float)U[i]) : spec_inverse_d(v, U[i]);
 }
 
+__global__ void k_qspec_inverse(View v, const double *chi, const double *U, double *xi, int64_t n, int fp32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    xi[i] = fp32 ? (double)qspec_inverse<float>(v, (float)chi[i], (float)U[i]) : qspec_inverse<double>(v, chi[i], U[i]);
+}
+
+void launch_qspec_inverse(const View &v, const double *chi, const double *U, double *xi, int64_t n, int fp32,
+                          cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  if (n > 0) k_qspec_inverse<<<blocks, 256, 0, st>>>(v, chi, U, xi, n, fp32);
+}
+
 void launch_spec_inverse(const View &v, const double *U, double *xi, int64_t n, int fp32, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1184) blocks = 1184;

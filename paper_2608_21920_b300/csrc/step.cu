@@ -13,17 +13,22 @@ namespace gapk {
 
 // ---------------------------------------------------------------------------
 // One curvature-emission event (a3): the photon energy from the classical
-// spectrum at x_c = (3/2) gamma chi (eq. xcurv), the recoil (the whole kinetic
-// energy when the draw exceeds it: the lepton is then at rest), and the next
-// optical depth.  Returns x with the emission direction as its sign.  Kept out
+// spectrum at x_c = (3/2) gamma chi (eq. xcurv) or, for qed_quantum, from
+// the quantum one; the recoil (the whole kinetic energy when the draw
+// exceeds it: the lepton is then at rest); and the next optical depth.  Returns x with the emission direction as its sign.  Kept out
 // of line: events are rare per lepton-step, and the push inlines its lepton
 // body once per vector lane.
 template <class R>
 __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t id, uint32_t step, uint32_t kk,
-                                         R gm, R chi, R &u, R &tau) {
-  R xi = sizeof(R) == 4 ? (R)spec_inverse_f(v, uniform24(seed, id, step, CH_EMIT_X, kk))
-                        : (R)spec_inverse_d(v, uniform53(seed, id, step, CH_EMIT_X, kk));
-  R x = xi * (R)1.5 * gm * chi;
+                                         R gm, R chi, R &u, R &tau, bool quantum) {
+  const R U = sizeof(R) == 4 ? (R)uniform24(seed, id, step, CH_EMIT_X, kk) : (R)uniform53(seed, id, step, CH_EMIT_X, kk);
+  R x;
+  if (quantum) {  // quantum spectrum: x = xi gamma, xi the energy fraction
+    x = qspec_inverse<R>(v, chi, U) * gm;
+  } else {
+    const R xi = sizeof(R) == 4 ? (R)spec_inverse_f(v, (float)U) : (R)spec_inverse_d(v, (double)U);
+    x = xi * (R)1.5 * gm * chi;
+  }
   R gm1 = u * u / (gm + (R)1);
   R dir = u >= (R)0 ? (R)1 : (R)-1;
   if (x >= gm1) {  // the photon takes the whole kinetic energy
@@ -219,7 +224,8 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
             id = Ip[slot];
             have_id = true;
           }
-          const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau);
+          const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau,
+                                         g.qed_quantum != 0);
           const R x = xs >= (R)0 ? xs : -xs;
           ++c_emit;
           if (x >= (R)2) {

@@ -18,7 +18,7 @@ PARAM_DEFAULTS = dict(
     alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0, gap_length=0.0,
     density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0, nx=64, ppc=0, cap=0, seed=0,
     qed=0, boundary=A.GAP_BC_SURFACE, init=A.GAP_INIT_EMPTY, kmax_emit=16, kmax_inject=64,
-    gap_index=0, inject_theta=0.0, filter_passes=0)
+    gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0)
 
 PRECISION = {"fp64": A.GAP_FP64_PLAIN, "fp32": A.GAP_FP32_STATE}
 
@@ -133,6 +133,17 @@ class Gap:
         prec = PRECISION[precision or self.precision]
         A.check(A.lib().gap_spectrum_inverse(self._h, _ptr(U), _ptr(xi), U.numel(), prec, self.stream()),
                 self._h, "gap_spectrum_inverse")
+        return xi
+
+    def qspectrum_inverse(self, chi, U, precision: str | None = None):
+        """Energy fraction xi of the quantum spectrum (qed_quantum gaps) for
+        CUDA tensors of chi and uniforms U (float64)."""
+        chi = chi.to(device=self.device, dtype=torch.float64).contiguous()
+        U = U.to(device=self.device, dtype=torch.float64).contiguous()
+        xi = torch.empty_like(U)
+        prec = PRECISION[precision or self.precision]
+        A.check(A.lib().gap_qspectrum_inverse(self._h, _ptr(chi), _ptr(U), _ptr(xi), U.numel(), prec,
+                                              self.stream()), self._h, "gap_qspectrum_inverse")
         return xi
 
     @property

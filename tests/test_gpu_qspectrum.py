@@ -1,0 +1,79 @@
+"""The quantum photon spectrum option (qed_quantum) on the CUDA path: the
+table inverse against the oracle's exact inverse, and one emission of each of
+3000 leptons at chi = 2 against the oracle's emissions from the same draws.
+
+Tolerance: the table interpolates ln s = ln d / 3 over rows of ln chi (eight
+per decade, cubic) and the survival over 256 panels of s (cubic Hermite);
+its emulation against the exact inverse stays below 1e-4 relative in xi, so
+the FP64 bound is 2e-4.  The FP32 evaluation adds float rounding of the
+survival (1e-7 absolute): relative 1e-3 for draws U <= 0.999."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from tests import _pair as P
+
+pytestmark = pytest.mark.gpu
+
+QCFG = dict(nx=64, boundary=O.BC_PERIODIC, qed=1, qed_quantum=1, lambda_hat=2e-4, rho_hat=100.0,
+            rate_mult=1e-3, dx=0.1, dt=0.045, gap_length=6.4)
+
+
+def _gap(precision="fp64"):
+    from paper_2608_21920_b300 import Gap
+    return Gap(P.gpu_params(QCFG), precision=precision, tile=16)
+
+
+@pytest.mark.parametrize("precision,rtol,umax", [("fp64", 2e-4, 1.0 - 1e-9), ("fp32", 1e-3, 0.999)])
+def test_qspectrum_inverse_matches_oracle(precision, rtol, umax):
+    g = _gap(precision)
+    rng = np.random.default_rng(3)
+    chis = [1e-7, 3e-6, 0.013, 0.7, 5.3, 77.0, 1e4]
+    Us = np.concatenate([rng.random(12) * umax, [1e-9, 1e-3, 0.5, umax]])
+    chi = np.repeat(chis, Us.size)
+    U = np.tile(Us, len(chis))
+    xi = g.qspectrum_inverse(torch.tensor(chi), torch.tensor(U), precision).cpu().numpy()
+    ref = np.array([O.qspec_inverse(c, u) for c, u in zip(chi, U)])
+    assert np.all((xi > 0) & (xi < 1))
+    rel = np.abs(xi / ref - 1.0)
+    assert rel.max() <= rtol, (rel.max(), chi[rel.argmax()], U[rel.argmax()])
+    g.close()
+
+
+def test_qspectrum_inverse_needs_a_quantum_gap():
+    from paper_2608_21920_b300 import Gap
+    from paper_2608_21920_b300._abi import GapError
+    g = Gap(P.gpu_params(dict(QCFG, qed_quantum=0)), precision="fp64", tile=16)
+    with pytest.raises(GapError):
+        g.qspectrum_inverse(torch.tensor([1.0]), torch.tensor([0.5]))
+    g.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 2e-4), ("fp32", 2e-3)])
+def test_quantum_emission_matches_oracle(precision, rtol):
+    """tau = 0 makes every lepton emit once at the start of the step (a second
+    event in the step is improbable: rate x dt ~ 3e-6); the recoil gives the
+    photon's energy fraction xi = (gamma0 - gamma)/gamma0."""
+    g0, N = 1000.0, 3000
+    u0 = math.sqrt(g0 * g0 - 1.0)
+    gpu = _gap(precision)
+    o = O.Sim(**{k: v for k, v in QCFG.items() if k in O.DEFAULTS})
+    ids = np.arange(1, N + 1)
+    gpu.add_particles(0, ids, np.full(N, 1.0), np.full(N, u0), np.full(N, 1e-30), np.zeros(N))
+    for i in ids:
+        o.add_lepton(int(i), -1, 1.0, u0, 1e-30, tau=0.0)
+    gpu.step(1)
+    o.step(1)
+    a, b = P.leptons_gpu(gpu), P.leptons_oracle(o)
+    assert np.array_equal(a["id"], b["id"])
+    xa = (g0 - np.sqrt(1.0 + a["u"] ** 2)) / g0
+    xb = (g0 - np.sqrt(1.0 + b["u"] ** 2)) / g0
+    assert gpu.diag(spectrum=False)["counters"]["emit_events"] == o.counters()["emit_events"]
+    big = xb > 1e-3  # softer photons leave gamma unchanged to the state's rounding
+    assert big.sum() > N // 2
+    rel = np.abs(xa[big] / xb[big] - 1.0)
+    assert rel.max() <= rtol, rel.max()
+    gpu.close()
