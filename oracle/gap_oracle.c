@@ -257,21 +257,25 @@ static void gauss_legendre8(double *x, double *w) {
 }
 
 /* S_q(xi) = int_xi^1 n: composite 8-point Gauss-Legendre in s over
- * [s(xi), (d(xi) + 60)^(1/3)] in 64 panels (the rest is below exp(-60) of
- * the integrand at the lower end). */
+ * [s(xi), (d(xi) + 60)^(1/3)] (the rest is below exp(-60) of the integrand
+ * at the lower end), in 160 panels whose ends s0 + (s1 - s0)(j/160)^2 crowd
+ * towards s0: at large chi the spectrum's scale in s, (2/(3 chi))^(1/3),
+ * is a small part of the range. */
 double orc_qspec_survival(double chi, double xi) {
   double gx[8], gw[8];
   gauss_legendre8(gx, gw);
   const double d0 = xi > 0.0 ? 2.0 * xi / (3.0 * chi * (1.0 - xi)) : 0.0;
   const double s0 = cbrt(d0), s1 = cbrt(d0 + 60.0);
-  const int panels = 64;
-  const double hp = (s1 - s0) / panels;
+  const int panels = 160;
   double sum = 0.0;
   for (int pnl = 0; pnl < panels; ++pnl) {
-    const double a = s0 + pnl * hp;
-    for (int i = 0; i < 8; ++i) sum += gw[i] * qspec_ds(chi, a + 0.5 * hp * (gx[i] + 1.0));
+    const double fa = (double)pnl / panels, fb = (double)(pnl + 1) / panels;
+    const double a = s0 + (s1 - s0) * fa * fa, hp = (s1 - s0) * (fb * fb - fa * fa);
+    double part = 0.0;
+    for (int i = 0; i < 8; ++i) part += gw[i] * qspec_ds(chi, a + 0.5 * hp * (gx[i] + 1.0));
+    sum += 0.5 * hp * part;
   }
-  return 0.5 * hp * sum;
+  return sum;
 }
 
 /* Inverse: the xi with S_q(xi) = U S_q(0), U in (0, 1].  Newton in s,

@@ -536,6 +536,20 @@ def test_quantum_spectrum_density_against_bessel():
             assert O.qspec_density(chi, xi) == pytest.approx(_qdensity_ref(chi, xi), rel=1e-9)
 
 
+def test_quantum_spectrum_survival_against_scipy():
+    """S_q(xi) = int_xi^1 n against scipy's adaptive quadrature of the Bessel
+    form, up to chi = 1e5, where the spectrum's scale in s = d^(1/3) is a
+    small part of the integration range."""
+    import warnings
+    for chi in (1.0, 1e5):
+        for xi0 in (0.0, 0.3):
+            pts = [p for p in (1e-12, 1e-9, 1e-6, 1e-4, 1e-2, 0.1, 0.5, 0.9, 0.99, 0.999, 0.9999, 0.99999) if p > xi0]
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore")
+                ref = integrate.quad(lambda x: _qdensity_ref(chi, x), xi0, 1, points=pts, limit=500, epsrel=1e-10)[0]
+            assert O.qspec_survival(chi, xi0) == pytest.approx(ref, rel=1e-8)
+
+
 def test_quantum_spectrum_number_rate_matches_paper_tsyn():
     """The photon number per unit time is proportional to T_syn (eq. tau_syn):
     the quantum spectrum integrated over the energy fraction, over its
