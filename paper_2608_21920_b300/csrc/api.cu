@@ -164,7 +164,7 @@ struct SpecQuad {
 // int_d^inf K_nu = int_0^inf e^{-d cosh t} cosh(nu t) / cosh t dt (trapezoid
 // in t, h = 1/8).  In s = d^(1/3), xi = 3 chi s^3 / (2 + 3 chi s^3) and the
 // survival S(s) = int_s^inf n dxi/ds' ds' is smooth at both ends; each panel
-// between nodes is one 8-point Gauss-Legendre rule.  Row r holds chi =
+// between nodes s_k = qs_node(k) is one 8-point Gauss-Legendre rule.  Row r holds chi =
 // exp(kQsLchi0 + r kQsDlchi); node k holds (S(s_k)/S(0), dS/ds(s_k)/S(0)).
 struct QSpecHost {
   static constexpr double kH = 0.125;
@@ -216,21 +216,21 @@ struct QSpecHost {
     std::vector<double> S(kQsNodes, 0.0);
     double acc = 0.0;  // the rest beyond the last node (below e^-60 of the total)
     {
-      const double a = (kQsNodes - 1) * kQsDs;
+      const double a = qs_node(kQsNodes - 1);
       for (int i = 0; i < 8; ++i) acc += 0.5 * gw[i] * per_s(chi, a + 0.5 * (gx[i] + 1.0));
     }
     S[kQsNodes - 1] = acc;
     for (int k = kQsNodes - 2; k >= 0; --k) {
-      const double a = k * kQsDs;
+      const double a = qs_node(k), hp = qs_node(k + 1) - a;
       double p = 0.0;
-      for (int i = 0; i < 8; ++i) p += gw[i] * per_s(chi, a + 0.5 * kQsDs * (gx[i] + 1.0));
-      acc += 0.5 * kQsDs * p;
+      for (int i = 0; i < 8; ++i) p += gw[i] * per_s(chi, a + 0.5 * hp * (gx[i] + 1.0));
+      acc += 0.5 * hp * p;
       S[k] = acc;
     }
     const double S0 = S[0];
     for (int k = 0; k < kQsNodes; ++k) {
       // dS/ds has a finite limit at s = 0 (n ~ d^(-2/3), dxi/ds ~ s^2)
-      const double sk = k > 0 ? k * kQsDs : 1e-6 * kQsDs;
+      const double sk = k > 0 ? qs_node(k) : 1e-12;
       out[k].x = S[k] / S0;
       out[k].y = -per_s(chi, sk) / S0;
     }

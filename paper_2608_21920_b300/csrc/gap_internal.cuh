@@ -26,13 +26,17 @@ constexpr int kPushChunk = 4096;  // leptons per push work item (multiple of 32)
 static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 contributions per node");
 
 // Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
-// ln 10 / 8 (89 rows to chi = 1e5), nodes s = k kQsDs, k < kQsNodes (s <= 4,
-// d <= 64: the survival there is below e^-60).
+// ln 10 / 8 (89 rows to chi = 1e5); nodes s_k = 4 (k/256)^2, k < kQsNodes
+// (s <= 4, d <= 64: the survival there is below e^-60), crowded towards
+// s = 0, where the spectrum of a large chi lies (s ~ (2/(3 chi))^(1/3)).
 constexpr int kQsNodes = 257;
 constexpr int kQsRows = 89;
 constexpr double kQsLchi0 = -13.815510557964274;  // ln 1e-6
 constexpr double kQsDlchi = 0.28782313662425574;  // ln 10 / 8
-constexpr double kQsDs = 4.0 / 256.0;
+__host__ __device__ __forceinline__ double qs_node(int k) {
+  const double f = (double)k / (kQsNodes - 1);
+  return 4.0 * f * f;
+}
 
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
@@ -334,7 +338,7 @@ __device__ __forceinline__ double spec_inverse_d(const View &v, double U) {
 // Quantum photon spectrum: the photon energy fraction xi of an emission at
 // chi for a draw U.  In each table row the node with S_k >= U > S_{k+1} is
 // found by bisection and the cubic Hermite interpolant of S(s) on that
-// panel is solved by Newton steps; ln s is blended over four rows of ln chi
+// panel (nodes s_k = qs_node(k)) is solved by Newton steps; ln s is blended over four rows of ln chi
 // (Catmull-Rom).  Below chi = 1e-6 the classical inverse gives d (the
 // quantum correction is O(chi)); above 1e5 the last row is used.
 template <class R>
@@ -351,14 +355,14 @@ struct QsRow<float> {
 template <class R>
 __device__ R qs_row_s(const View &v, int r, R U) {
   int lo = 0, hi = kQsNodes - 1;
-  if (!(U > QsRow<R>::at(v, r, hi).x)) return (R)(hi * kQsDs);
+  if (!(U > QsRow<R>::at(v, r, hi).x)) return (R)qs_node(hi);
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (QsRow<R>::at(v, r, mid).x >= U) lo = mid;
     else hi = mid;
   }
   const auto a = QsRow<R>::at(v, r, lo), b = QsRow<R>::at(v, r, hi);
-  const R h = (R)kQsDs;
+  const R s_lo = (R)qs_node(lo), h = (R)qs_node(hi) - s_lo;
   R t = (a.x - U) / (a.x - b.x);  // linear start, in [0, 1]
   for (int it = 0; it < 4; ++it) {
     const R t2 = t * t, t3 = t2 * t;
@@ -372,7 +376,7 @@ __device__ R qs_row_s(const View &v, int r, R U) {
     if (tn == t) break;
     t = tn;
   }
-  return ((R)lo + t) * h;
+  return s_lo + t * h;
 }
 
 template <class R>

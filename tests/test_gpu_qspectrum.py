@@ -3,10 +3,11 @@ table inverse against the oracle's exact inverse, and one emission of each of
 3000 leptons at chi = 2 against the oracle's emissions from the same draws.
 
 Tolerance: the table interpolates ln s = ln d / 3 over rows of ln chi (eight
-per decade, cubic) and the survival over 256 panels of s (cubic Hermite);
-its emulation against the exact inverse stays below 1e-4 relative in xi, so
-the FP64 bound is 2e-4.  The FP32 evaluation adds float rounding of the
-survival (1e-7 absolute): relative 1e-3 for draws U <= 0.999."""
+per decade, cubic) and the survival over 256 panels of s (cubic Hermite,
+panels crowded towards s = 0); its emulation against the exact inverse stays
+below 2e-5 relative in xi for chi in [1e-6, 1e5], so the FP64 bound is 1e-4.
+The FP32 evaluation adds float rounding of the survival (1e-7 absolute):
+relative 1e-3 for draws U <= 0.999."""
 import math
 
 import numpy as np
@@ -27,11 +28,11 @@ def _gap(precision="fp64"):
     return Gap(P.gpu_params(QCFG), precision=precision, tile=16)
 
 
-@pytest.mark.parametrize("precision,rtol,umax", [("fp64", 2e-4, 1.0 - 1e-9), ("fp32", 1e-3, 0.999)])
+@pytest.mark.parametrize("precision,rtol,umax", [("fp64", 1e-4, 1.0 - 1e-9), ("fp32", 1e-3, 0.999)])
 def test_qspectrum_inverse_matches_oracle(precision, rtol, umax):
     g = _gap(precision)
     rng = np.random.default_rng(3)
-    chis = [1e-7, 3e-6, 0.013, 0.7, 5.3, 77.0, 1e4]
+    chis = [1e-7, 3e-6, 0.013, 0.7, 5.3, 77.0, 1e4, 1e5]
     Us = np.concatenate([rng.random(12) * umax, [1e-9, 1e-3, 0.5, umax]])
     chi = np.repeat(chis, Us.size)
     U = np.tile(Us, len(chis))
@@ -52,7 +53,7 @@ def test_qspectrum_inverse_needs_a_quantum_gap():
     g.close()
 
 
-@pytest.mark.parametrize("precision,rtol", [("fp64", 2e-4), ("fp32", 2e-3)])
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-4), ("fp32", 2e-3)])
 def test_quantum_emission_matches_oracle(precision, rtol):
     """tau = 0 makes every lepton emit once at the start of the step (a second
     event in the step is improbable: rate x dt ~ 3e-6); the recoil gives the
