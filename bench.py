@@ -47,14 +47,17 @@ def set_size(nx):
     N_PARTICLES = 2 * NX * PPC
 WORKLOAD_NAME = ("cfg2 push+deposit roofline: Nx=2^20 periodic, 4.19e8 e+- (200+200 per cell, "
                  "0.5 n_co each), Maxwell-Juttner theta=0.1, 1e-3 Langmuir seed, QED off")
-SETUP = {"filter_passes": 0, "inject_theta": 0.0}  # Sect. 6.1 set-up options (off for the headline)
+SETUP = {"filter_passes": 0, "inject_theta": 0.0, "qed_quantum": 0}  # options (off for the headline)
 
 
-def set_setup(filter_passes, inject_theta):
-    """Sect. 6.1's binomial current filter and hot atmosphere, applied to the
-    workloads (the atmosphere only matters for surface gaps: the batch)."""
+def set_setup(filter_passes, inject_theta, qed_quantum=0):
+    """Sect. 6.1's binomial current filter and hot atmosphere, and the quantum
+    photon spectrum, applied to the workloads (the atmosphere and the
+    spectrum only matter for the QED surface gaps of the batch)."""
     global WORKLOAD_NAME, BATCH_NAME
-    SETUP.update(filter_passes=filter_passes, inject_theta=inject_theta)
+    SETUP.update(filter_passes=filter_passes, inject_theta=inject_theta, qed_quantum=qed_quantum)
+    if qed_quantum:
+        BATCH_NAME += ", quantum photon spectrum"
     if filter_passes:
         WORKLOAD["filter_passes"] = filter_passes
         WORKLOAD_NAME += f", {filter_passes}-pass binomial current filter"
@@ -489,10 +492,12 @@ def main():
                     help="binomial current-filter passes per step (Sect. 6.1 uses 8; 0: off)")
     ap.add_argument("--inject-theta", type=float, default=0.0,
                     help="batch: temperature of the surface atmosphere (Sect. 6.1 uses 0.3; 0: cold)")
+    ap.add_argument("--qed-quantum", action="store_true",
+                    help="batch: photon energies from the quantum spectrum (default: classical shape)")
     args = ap.parse_args()
     if args.nx:
         set_size(args.nx)
-    set_setup(args.filter_passes, args.inject_theta)
+    set_setup(args.filter_passes, args.inject_theta, 1 if args.qed_quantum else 0)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -1,6 +1,6 @@
 """The quantum photon spectrum option (qed_quantum) on the CUDA path: the
 table inverse against the oracle's exact inverse, and one emission of each of
-3000 leptons at chi = 2 against the oracle's emissions from the same draws.
+800 leptons at chi = 2 against the oracle's emissions from the same draws.
 
 Tolerance: the table interpolates ln s = ln d / 3 over rows of ln chi (eight
 per decade, cubic) and the survival over 256 panels of s (cubic Hermite,
@@ -58,7 +58,7 @@ def test_quantum_emission_matches_oracle(precision, rtol):
     """tau = 0 makes every lepton emit once at the start of the step (a second
     event in the step is improbable: rate x dt ~ 3e-6); the recoil gives the
     photon's energy fraction xi = (gamma0 - gamma)/gamma0."""
-    g0, N = 1000.0, 3000
+    g0, N = 1000.0, 800
     u0 = math.sqrt(g0 * g0 - 1.0)
     gpu = _gap(precision)
     o = O.Sim(**{k: v for k, v in QCFG.items() if k in O.DEFAULTS})
