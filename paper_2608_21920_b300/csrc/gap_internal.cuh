@@ -33,9 +33,10 @@ constexpr int kQsNodes = 257;
 constexpr int kQsRows = 89;
 constexpr double kQsLchi0 = -13.815510557964274;  // ln 1e-6
 constexpr double kQsDlchi = 0.28782313662425574;  // ln 10 / 8
-__host__ __device__ __forceinline__ double qs_node(int k) {
-  const double f = (double)k / (kQsNodes - 1);
-  return 4.0 * f * f;
+template <class R = double>
+__host__ __device__ __forceinline__ R qs_node(int k) {  // in the precision of the caller
+  const R f = (R)k / (R)(kQsNodes - 1);
+  return (R)4 * f * f;
 }
 
 // Draw channels of the counter-based generator (interface values).
@@ -336,9 +337,10 @@ __device__ __forceinline__ double spec_inverse_d(const View &v, double U) {
 }
 
 // Quantum photon spectrum: the photon energy fraction xi of an emission at
-// chi for a draw U.  In each table row the node with S_k >= U > S_{k+1} is
-// found by bisection and the cubic Hermite interpolant of S(s) on that
-// panel (nodes s_k = qs_node(k)) is solved by Newton steps; ln s is blended over four rows of ln chi
+// chi for a draw U.  In each of four table rows the node with
+// S_k >= U > S_{k+1} is found by bisection and the cubic Hermite
+// interpolant of S(s) on that panel (nodes s_k = qs_node(k)) is solved by
+// Newton steps; ln s is blended over four rows of ln chi
 // (Catmull-Rom).  Below chi = 1e-6 the classical inverse gives d (the
 // quantum correction is O(chi)); above 1e5 the last row is used.
 template <class R>
@@ -352,31 +354,49 @@ struct QsRow<float> {
   __device__ static float2 at(const View &v, int r, int k) { return v.qs_tab_f[r * kQsNodes + k]; }
 };
 
+// The four rows are searched in lockstep, so each bisection level issues four
+// independent loads (the emissions of a discharge are frequent: a serial
+// chain of dependent loads would dominate the push).
 template <class R>
-__device__ R qs_row_s(const View &v, int r, R U) {
-  int lo = 0, hi = kQsNodes - 1;
-  if (!(U > QsRow<R>::at(v, r, hi).x)) return (R)qs_node(hi);
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (QsRow<R>::at(v, r, mid).x >= U) lo = mid;
-    else hi = mid;
+__device__ void qs_rows_s(const View &v, const int r[4], R U, R s[4]) {
+  int lo[4], hi[4];
+  bool live[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    lo[j] = 0;
+    hi[j] = kQsNodes - 1;
+    live[j] = U > QsRow<R>::at(v, r[j], kQsNodes - 1).x;
+    if (!live[j]) s[j] = qs_node<R>(kQsNodes - 1);
   }
-  const auto a = QsRow<R>::at(v, r, lo), b = QsRow<R>::at(v, r, hi);
-  const R s_lo = (R)qs_node(lo), h = (R)qs_node(hi) - s_lo;
-  R t = (a.x - U) / (a.x - b.x);  // linear start, in [0, 1]
-  for (int it = 0; it < 4; ++it) {
-    const R t2 = t * t, t3 = t2 * t;
-    const R H = ((R)2 * t3 - (R)3 * t2 + (R)1) * a.x + (t3 - (R)2 * t2 + t) * h * a.y +
-                ((R)-2 * t3 + (R)3 * t2) * b.x + (t3 - t2) * h * b.y;
-    const R dH = ((R)6 * t2 - (R)6 * t) * a.x + ((R)3 * t2 - (R)4 * t + (R)1) * h * a.y +
-                 ((R)-6 * t2 + (R)6 * t) * b.x + ((R)3 * t2 - (R)2 * t) * h * b.y;
-    if (!(dH < (R)0)) break;
-    R tn = t - (H - U) / dH;
-    tn = tn < (R)0 ? (R)0 : (tn > (R)1 ? (R)1 : tn);
-    if (tn == t) break;
-    t = tn;
+  for (int level = 0; level < 8; ++level) {  // 2^8 panels
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!live[j] || hi[j] - lo[j] <= 1) continue;
+      const int mid = (lo[j] + hi[j]) >> 1;
+      if (QsRow<R>::at(v, r[j], mid).x >= U) lo[j] = mid;
+      else hi[j] = mid;
+    }
   }
-  return s_lo + t * h;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!live[j]) continue;
+    const auto a = QsRow<R>::at(v, r[j], lo[j]), b = QsRow<R>::at(v, r[j], hi[j]);
+    const R s_lo = qs_node<R>(lo[j]), h = qs_node<R>(hi[j]) - s_lo;
+    R t = (a.x - U) / (a.x - b.x);  // linear start, in [0, 1]
+    for (int it = 0; it < 4; ++it) {
+      const R t2 = t * t, t3 = t2 * t;
+      const R H = ((R)2 * t3 - (R)3 * t2 + (R)1) * a.x + (t3 - (R)2 * t2 + t) * h * a.y +
+                  ((R)-2 * t3 + (R)3 * t2) * b.x + (t3 - t2) * h * b.y;
+      const R dH = ((R)6 * t2 - (R)6 * t) * a.x + ((R)3 * t2 - (R)4 * t + (R)1) * h * a.y +
+                   ((R)-6 * t2 + (R)6 * t) * b.x + ((R)3 * t2 - (R)2 * t) * h * b.y;
+      if (!(dH < (R)0)) break;
+      R tn = t - (H - U) / dH;
+      tn = tn < (R)0 ? (R)0 : (tn > (R)1 ? (R)1 : tn);
+      if (tn == t) break;
+      t = tn;
+    }
+    s[j] = s_lo + t * h;
+  }
 }
 
 template <class R>
@@ -391,13 +411,14 @@ __device__ __noinline__ R qspec_inverse(const View &v, R chi, R U) {
     int i = (int)rr;
     if (i > v.qs_rows - 2) i = v.qs_rows - 2;
     const R t = rr - (R)i;
+    int rows[4];
     R p[4];
     for (int j = 0; j < 4; ++j) {
-      int r = i - 1 + j;
-      r = r < 0 ? 0 : (r > v.qs_rows - 1 ? v.qs_rows - 1 : r);
-      const R sr = qs_row_s<R>(v, r, U);
-      p[j] = sr > (R)0 ? log(sr) : (R)-700;
+      const int r = i - 1 + j;
+      rows[j] = r < 0 ? 0 : (r > v.qs_rows - 1 ? v.qs_rows - 1 : r);
     }
+    qs_rows_s<R>(v, rows, U, p);
+    for (int j = 0; j < 4; ++j) p[j] = p[j] > (R)0 ? log(p[j]) : (R)-700;
     const R ls = (R)0.5 * ((R)2 * p[1] + (-p[0] + p[2]) * t + ((R)2 * p[0] - (R)5 * p[1] + (R)4 * p[2] - p[3]) * t * t +
                            (-p[0] + (R)3 * p[1] - (R)3 * p[2] + p[3]) * t * t * t);
     d = exp((R)3 * ls);
