@@ -107,7 +107,7 @@ uint64_t orc_child_id(uint64_t parent, uint32_t step, uint32_t channel,
 enum {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
   CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_MERGE = 10,
-  CH_INJECT_U = 12
+  CH_INJECT_U = 12, CH_PAIR_E = 13
 };
 
 /* ------------------------------------------------------------------------- */
@@ -298,6 +298,75 @@ double orc_qspec_inverse(double chi, double U) {
   }
   const double d = s * s * s;
   return 3.0 * chi * d / (2.0 + 3.0 * chi * d);
+}
+
+/* Energy split of one-photon pair creation (with qed_quantum; the default
+ * gives each lepton x/2).  The electron's fraction e of the photon energy
+ * has density (Baier & Katkov 1968)
+ *   p(e) = (e/(1 - e) + (1 - e)/e) K_{2/3}(y) + int_y^inf K_{1/3},
+ *   y = 2 / (3 chi e (1 - e)),
+ * symmetric about 1/2, with (1/(pi sqrt3 chi)) int_0^1 p de the T_BW of
+ * eq. tau_bw (its asymptotes 0.23 e^(-8/(3 chi)) and 0.38 chi^(-1/3)).  The
+ * Bessel integrals as for the photon spectrum (trapezoid in t, h = 1/8). */
+static double bw_density_y(double y, double e) {
+  const double A = e / (1.0 - e) + (1.0 - e) / e;
+  const double h = 0.125;
+  double sum = 0.0;
+  for (int k = 0;; ++k) {
+    const double t = k * h, ch = cosh(t), arg = y * ch;
+    if (arg > 745.0 || t > 700.0) break;
+    sum += (k == 0 ? 0.5 : 1.0) * exp(-arg) * (A * cosh(2.0 * t / 3.0) + cosh(t / 3.0) / ch);
+  }
+  return h * sum;
+}
+
+double orc_bw_density(double chi, double e) {
+  if (!(e > 0.0 && e < 1.0) || !(chi > 0.0)) return 0.0;
+  return bw_density_y(2.0 / (3.0 * chi * e * (1.0 - e)), e);
+}
+
+/* int_e0^(1/2) p de: 200 Gauss-Legendre panels, uniform in tau of the map
+ * e = e0 + (1/2 - e0)(3 tau^2 - 2 tau^3), which crowds them towards both
+ * ends (the narrow peak at 1/2 of a small chi, the structure near e ~ 1/chi
+ * of a large one). */
+double orc_bw_half(double chi, double e0) {
+  double gx[8], gw[8];
+  gauss_legendre8(gx, gw);
+  const int panels = 200;
+  const double L = 0.5 - e0, ht = 1.0 / panels;
+  double sum = 0.0;
+  for (int pnl = 0; pnl < panels; ++pnl) {
+    double part = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      const double tau = (pnl + 0.5 * (gx[i] + 1.0)) * ht;
+      const double e = e0 + L * tau * tau * (3.0 - 2.0 * tau);
+      part += gw[i] * orc_bw_density(chi, e) * L * 6.0 * tau * (1.0 - tau);
+    }
+    sum += 0.5 * ht * part;
+  }
+  return sum;
+}
+
+/* The electron's fraction for a draw U in (0, 1]: F(e) = U with F the
+ * distribution of p, i.e. e = 1/2 -+ eta where int_(1/2 - eta)^(1/2) p is
+ * |2U - 1| times the half integral (minus for U < 1/2); Newton in eta with
+ * a bracket (bisection when a step leaves it). */
+double orc_bw_split(double chi, double U) {
+  if (!(chi > 0.0)) return 0.5;
+  const double half = orc_bw_half(chi, 0.0);
+  const double target = fabs(2.0 * U - 1.0) * half;
+  double lo = 0.0, hi = 0.5, eta = 0.25 * sqrt(chi / (chi + 1.0));
+  for (int it = 0; it < 200; ++it) {
+    const double H = orc_bw_half(chi, 0.5 - eta);
+    if (H < target) lo = eta; else hi = eta;
+    const double dH = orc_bw_density(chi, 0.5 - eta);
+    double en = dH > 0.0 ? eta - (H - target) / dH : 0.5 * (lo + hi);
+    if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
+    const double step = fabs(en - eta);
+    eta = en;
+    if (step < 1e-15 || hi - lo < 1e-15) break;
+  }
+  return U < 0.5 ? 0.5 - eta : 0.5 + eta;
 }
 
 /* 1D Maxwell-Juttner deviate, f(u) proportional to exp(-(gamma-1)/theta), by
@@ -830,9 +899,20 @@ void orc_step(orc_sim *s) {
     }
     if (P->tau_acc >= P->tau_star) {
       P->alive = 0;
-      double gp = 0.5 * P->x;
-      double up = (double)P->dir * sqrt((gp - 1.0) * (gp + 1.0));
+      /* energies: x/2 each, or with qed_quantum the electron takes e x with e
+       * from the differential rate at this step's chi (both at least 1) */
+      double ge = 0.5 * P->x;
+      if (p->qed_quantum) {
+        const double lmid = ((double)n - (double)P->n0 + 0.5) * dt;
+        const double chi = P->x * p->b * fabs(sin(lmid / p->rho_hat));
+        double e = orc_bw_split(chi, orc_uniform(p->seed, P->id, n, CH_PAIR_E, 0));
+        if (e * P->x < 1.0) e = 1.0 / P->x;
+        if ((1.0 - e) * P->x < 1.0) e = 1.0 - 1.0 / P->x;
+        ge = e * P->x;
+      }
       for (int k = 0; k < 2; ++k) {
+        const double gk = k == 0 ? ge : P->x - ge;
+        const double up = (double)P->dir * sqrt((gk - 1.0) * (gk + 1.0));
         orc_lepton L = {0};
         L.id = orc_child_id(P->id, n, CH_PAIR, (uint32_t)k) & ~ORC_PHOTON_BIT;
         L.q = k == 0 ? -1 : +1;

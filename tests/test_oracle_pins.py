@@ -611,6 +611,62 @@ def test_quantum_photon_energy_ks():
     assert dens[0] > 0
 
 
+# ------------------------------------------------ pair energy split (quantum)
+def _bw_ref(chi, e):
+    """Differential one-photon pair rate in the electron's energy fraction
+    from scipy's Bessel functions: (e/(1-e) + (1-e)/e) K_2/3(y) + int_y^inf K_1/3,
+    y = 2 / (3 chi e (1 - e))."""
+    y = 2.0 / (3.0 * chi * e * (1.0 - e))
+    tail = integrate.quad(lambda s: special.kv(1.0 / 3.0, s), y, np.inf, limit=200, epsrel=1e-12)[0]
+    return (e / (1.0 - e) + (1.0 - e) / e) * special.kv(2.0 / 3.0, y) + tail
+
+
+def test_bw_split_density_against_bessel():
+    for chi in (0.05, 1.0, 100.0):
+        for e in (0.01, 0.2, 0.45, 0.5, 0.8):
+            assert O.bw_density(chi, e) == pytest.approx(_bw_ref(chi, e), rel=1e-9)
+
+
+def test_bw_split_integrates_to_paper_tbw():
+    """(1/(pi sqrt3 chi)) int_0^1 p de is T_BW of eq. tau_bw: the paper's
+    asymptotes 0.23 e^(-8/(3 chi)) (chi << 1) and 0.38 chi^(-1/3) (chi >> 1),
+    and its fit within the stated ~10 % in between."""
+    T = lambda chi: 2.0 * O.bw_half(chi, 0.0) / (math.pi * math.sqrt(3.0) * chi)
+    a, _ = _paper("tbw_small_coeff")
+    b, _ = _paper("tbw_large_coeff")
+    assert T(0.02) == pytest.approx(a * math.exp(-8.0 / (3.0 * 0.02)), rel=0.01)
+    assert T(1e4) == pytest.approx(b * 1e4 ** (-1.0 / 3.0), rel=0.01)
+    for chi in (0.05, 0.5, 5.0, 50.0):
+        assert T(chi) == pytest.approx(O.tbw(chi), rel=0.1)
+
+
+def test_bw_split_gaussian_limit_and_symmetry():
+    """chi << 1: y ~ (8/(3 chi))(1 + 4 (e - 1/2)^2), a Gaussian of variance
+    3 chi / 64 around 1/2; F(e(U)) = U and e(U) + e(1 - U) = 1."""
+    chi = 0.005
+    es = np.array([O.bw_split(chi, u) for u in (np.arange(300) + 0.5) / 300])
+    assert es.std() == pytest.approx(math.sqrt(3.0 * chi / 64.0), rel=0.02)
+    for chi in (0.5, 100.0):
+        for U in (0.01, 0.3, 0.77):
+            e = O.bw_split(chi, U)
+            assert e + O.bw_split(chi, 1.0 - U) == pytest.approx(1.0, abs=1e-12)
+            F = 0.5 - O.bw_half(chi, e) / (2.0 * O.bw_half(chi, 0.0)) if e < 0.5 else \
+                0.5 + O.bw_half(chi, 1.0 - e) / (2.0 * O.bw_half(chi, 0.0))
+            assert F == pytest.approx(U, abs=1e-12)
+
+
+def test_bw_split_pair_conserves_energy():
+    s = O.Sim(nx=512, boundary=O.BC_SURFACE, qed=1, qed_quantum=1, b=0.1, lambda_hat=1e-4, rho_hat=20.0,
+              rate_mult=10.0, dx=0.1, dt=0.045, gap_length=51.2)
+    s.add_photon(1, 5.0, 80.0, 1e-3, -1, 0, 0.0)  # threshold 0: converts at its first step
+    s.step(1)
+    L = s.leptons()
+    g = np.sqrt(1 + L["u"] ** 2)
+    assert L["id"].size == 2 and sorted(L["q"]) == [-1, 1] and np.all(L["u"] < 0)
+    assert g.sum() == pytest.approx(80.0, rel=1e-13)
+    assert abs(g[0] - 40.0) > 1e-6  # split off the half
+
+
 def test_pair_conversion_length_distribution():
     """Photons accumulate tau_BW (eq. tau_bw) at the angle sin psi = |sin(l/R)|
     (Sect. 6.1) and convert at tau = -ln U: P(converted by l) = 1 - exp(-tau(l))."""
