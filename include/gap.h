@@ -115,7 +115,14 @@ typedef struct gap_params {
                             shape open), read from a table of the inverse
                             distribution built at init (relative error of xi
                             about 1e-5; chi above 1e5 uses the chi = 1e5 row);
-                            0: the classical shape.  0 or 1, else GAP_EINVAL */
+                            and a converting photon gives the electron e x of
+                            its energy x, e from the differential one-photon
+                            pair rate (e/(1-e) + (1-e)/e) K_2/3(y)
+                            + int_y^inf K_1/3, y = 2 / (3 chi e (1 - e)), at
+                            the conversion step's chi (table, Gaussian limit
+                            below chi = 1e-3), the positron the rest;
+                            0: the classical shape and x/2 each.  0 or 1,
+                            else GAP_EINVAL */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */
@@ -329,6 +336,13 @@ const char *gap_status_string(int status);
  * no gap of the handle has qed_quantum.  Enqueued on `stream`. */
 int gap_qspectrum_inverse(gap_handle *h, const double *dev_chi, const double *dev_U, double *dev_xi, int64_t n,
                           int32_t precision, void *stream);
+
+/* The electron's fraction e of a converting photon's energy for
+ * conversion parameter chi and draw U in (0, 1] (n values, device arrays;
+ * the split of qed_quantum gaps, FP64).  GAP_EINVAL when no gap of the
+ * handle has qed_quantum.  Enqueued on `stream`. */
+int gap_pair_split(gap_handle *h, const double *dev_chi, const double *dev_U, double *dev_e, int64_t n,
+                   void *stream);
 
 /* ------------------------------------------------------------------------
  * Concurrency model (Sect. 5.2, eq. dis1-dis4) -- batched RK4 integrator

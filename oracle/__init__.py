@@ -80,7 +80,7 @@ def lib():
             getattr(L, f).argtypes = [d]; getattr(L, f).restype = d
         L.orc_mj_sample.argtypes = [u64, u64, d, C.POINTER(C.c_int)]; L.orc_mj_sample.restype = d
         for f in ("orc_qspec_density", "orc_qspec_survival", "orc_qspec_inverse", "orc_bw_density",
-                  "orc_bw_half", "orc_bw_split"):
+                  "orc_bw_tail", "orc_bw_split"):
             getattr(L, f).argtypes = [d, d]; getattr(L, f).restype = d
         L.orc_binomial_smooth.argtypes = [C.POINTER(d), i64, C.c_int32, C.c_int32]
         L.orc_mj_draw.argtypes = [u64, u64, u32, u32, d, C.POINTER(C.c_int)]; L.orc_mj_draw.restype = d
@@ -169,8 +169,8 @@ def bw_density(chi, e):
     return lib().orc_bw_density(float(chi), float(e))
 
 
-def bw_half(chi, e0):
-    return lib().orc_bw_half(float(chi), float(e0))
+def bw_tail(chi, e0):
+    return lib().orc_bw_tail(float(chi), float(e0))
 
 
 def bw_split(chi, U):

@@ -325,48 +325,68 @@ double orc_bw_density(double chi, double e) {
   return bw_density_y(2.0 / (3.0 * chi * e * (1.0 - e)), e);
 }
 
-/* int_e0^(1/2) p de: 200 Gauss-Legendre panels, uniform in tau of the map
- * e = e0 + (1/2 - e0)(3 tau^2 - 2 tau^3), which crowds them towards both
- * ends (the narrow peak at 1/2 of a small chi, the structure near e ~ 1/chi
- * of a large one). */
-double orc_bw_half(double chi, double e0) {
+/* p e^(y0), y0 = 8/(3 chi) the smallest y (at e = 1/2): the same ratios
+ * without underflow (p itself is below the smallest double for chi < 0.0036). */
+static double bw_density_scaled(double chi, double e) {
+  if (!(e > 0.0 && e < 1.0)) return 0.0;
+  const double y = 2.0 / (3.0 * chi * e * (1.0 - e)), y0 = 8.0 / (3.0 * chi);
+  const double A = e / (1.0 - e) + (1.0 - e) / e;
+  const double h = 0.125;
+  double sum = 0.0;
+  for (int k = 0;; ++k) {
+    const double t = k * h, ch = cosh(t), arg = y * ch - y0;
+    if (arg > 745.0 || t > 700.0) break;
+    sum += (k == 0 ? 0.5 : 1.0) * exp(-arg) * (A * cosh(2.0 * t / 3.0) + cosh(t / 3.0) / ch);
+  }
+  return h * sum;
+}
+
+/* int_0^e0 p de e^(y0), e0 <= 1/2: 200 Gauss-Legendre panels uniform in tau
+ * of the map e = e0 (3 tau^2 - 2 tau^3), which crowds them towards both
+ * ends (the structure near e ~ 1/chi of a large chi, the narrow peak at 1/2
+ * of a small one).  Integrating from e = 0 keeps the far tail (a lepton
+ * with a small share) free of cancellation. */
+static double bw_tail_scaled(double chi, double e0) {
   double gx[8], gw[8];
   gauss_legendre8(gx, gw);
   const int panels = 200;
-  const double L = 0.5 - e0, ht = 1.0 / panels;
+  const double ht = 1.0 / panels;
   double sum = 0.0;
   for (int pnl = 0; pnl < panels; ++pnl) {
     double part = 0.0;
     for (int i = 0; i < 8; ++i) {
       const double tau = (pnl + 0.5 * (gx[i] + 1.0)) * ht;
-      const double e = e0 + L * tau * tau * (3.0 - 2.0 * tau);
-      part += gw[i] * orc_bw_density(chi, e) * L * 6.0 * tau * (1.0 - tau);
+      const double e = e0 * tau * tau * (3.0 - 2.0 * tau);
+      part += gw[i] * bw_density_scaled(chi, e) * e0 * 6.0 * tau * (1.0 - tau);
     }
     sum += 0.5 * ht * part;
   }
   return sum;
 }
 
-/* The electron's fraction for a draw U in (0, 1]: F(e) = U with F the
- * distribution of p, i.e. e = 1/2 -+ eta where int_(1/2 - eta)^(1/2) p is
- * |2U - 1| times the half integral (minus for U < 1/2); Newton in eta with
- * a bracket (bisection when a step leaves it). */
+/* int_0^e0 p de (unscaled; zero below chi ~ 0.0036 by underflow). */
+double orc_bw_tail(double chi, double e0) { return bw_tail_scaled(chi, e0) * exp(-8.0 / (3.0 * chi)); }
+
+/* The electron's fraction for a draw U in (0, 1]: F(e) = U, F the
+ * distribution of p.  With u = min(U, 1 - U) the e <= 1/2 with
+ * int_0^e p = 2 u int_0^(1/2) p is found by Newton steps in e, bracketed
+ * (bisection when a step leaves the bracket); U > 1/2 takes 1 - e. */
 double orc_bw_split(double chi, double U) {
   if (!(chi > 0.0)) return 0.5;
-  const double half = orc_bw_half(chi, 0.0);
-  const double target = fabs(2.0 * U - 1.0) * half;
-  double lo = 0.0, hi = 0.5, eta = 0.25 * sqrt(chi / (chi + 1.0));
+  const double u = U < 0.5 ? U : 1.0 - U;
+  const double target = 2.0 * u * bw_tail_scaled(chi, 0.5);
+  double lo = 0.0, hi = 0.5, e = 0.5 - 0.25 * sqrt(chi / (chi + 1.0));
   for (int it = 0; it < 200; ++it) {
-    const double H = orc_bw_half(chi, 0.5 - eta);
-    if (H < target) lo = eta; else hi = eta;
-    const double dH = orc_bw_density(chi, 0.5 - eta);
-    double en = dH > 0.0 ? eta - (H - target) / dH : 0.5 * (lo + hi);
+    const double T = bw_tail_scaled(chi, e);
+    if (T < target) lo = e; else hi = e;
+    const double dT = bw_density_scaled(chi, e);
+    double en = dT > 0.0 ? e - (T - target) / dT : 0.5 * (lo + hi);
     if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
-    const double step = fabs(en - eta);
-    eta = en;
-    if (step < 1e-15 || hi - lo < 1e-15) break;
+    const double step = fabs(en - e);
+    e = en;
+    if (step < 1e-16 * (e > 1e-300 ? e : 1.0) || hi - lo < 1e-16 * hi) break;
   }
-  return U < 0.5 ? 0.5 - eta : 0.5 + eta;
+  return U < 0.5 ? e : 1.0 - e;
 }
 
 /* 1D Maxwell-Juttner deviate, f(u) proportional to exp(-(gamma-1)/theta), by

@@ -86,6 +86,7 @@ def lib():
     L.gap_steps_done.restype = i64
     L.gap_spectrum_inverse.argtypes = [vp, vp, vp, i64, i32, vp]
     L.gap_qspectrum_inverse.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+    L.gap_pair_split.argtypes = [vp, vp, vp, vp, i64, vp]
     L.gap_power_spectrum_noalloc.argtypes = [vp, i64, vp, vp]
     L.gap_profile.argtypes = [vp, i32, C.POINTER(d), C.POINTER(i64), C.POINTER(i64)]
     L.gap_profile_phases.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
@@ -108,7 +109,7 @@ def lib():
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
             "gap_get_field", "gap_set_field", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
-            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_power_spectrum_noalloc", "gap_free",
+            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 
 

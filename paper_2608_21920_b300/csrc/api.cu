@@ -238,6 +238,49 @@ struct QSpecHost {
   }
 };
 
+// Pair energy split (qed_quantum), built on the host: the electron's
+// fraction e of the photon energy has density
+//   p(e) = (e/(1 - e) + (1 - e)/e) K_2/3(y) + int_y^inf K_1/3,
+//   y = 2 / (3 chi e (1 - e))   (Baier & Katkov 1968),
+// symmetric about 1/2 (Bessel integrals as for the photon spectrum), taken
+// times e^(y0), y0 = 8/(3 chi), so that small chi do not underflow.  Row r
+// holds chi = exp(kBwLchi0 + r ln10/8); node k holds G = F(1/2 - eta_k) / F(1/2)
+// (F(e) = int_0^e p, summed from the e = 0 end, free of cancellation in the
+// far tail) and dG/deta, eta_k = bw_node(k), one 8-point Gauss-Legendre rule
+// per panel.
+struct BwHost {
+  const QSpecHost &q;  // Gauss-Legendre nodes and the t-node values
+  explicit BwHost(const QSpecHost &qq) : q(qq) {}
+  double density_scaled(double chi, double e) const {
+    if (!(e > 0.0 && e < 1.0)) return 0.0;
+    const double y = 2.0 / (3.0 * chi * e * (1.0 - e)), y0 = 8.0 / (3.0 * chi);
+    const double A = e / (1.0 - e) + (1.0 - e) / e;
+    double sum = 0.0;
+    for (size_t k = 0; k < q.c.size(); ++k) {
+      const double arg = y * q.c[k] - y0;
+      if (arg > 745.0 || y * (q.c[k] - 1.0) - (2.0 / 3.0) * k * QSpecHost::kH > 40.0) break;
+      sum += (k == 0 ? 0.5 : 1.0) * std::exp(-arg) * (A * q.c2[k] + q.c1[k]);
+    }
+    return QSpecHost::kH * sum;
+  }
+  void row(double chi, double2 *out) const {
+    std::vector<double> T(kQsNodes, 0.0);  // int over [eta_k, 1/2] of p(1/2 - eta)
+    for (int k = kQsNodes - 2; k >= 0; --k) {
+      const double a = bw_node(k), hp = bw_node(k + 1) - a;
+      double p = 0.0;
+      for (int i = 0; i < 8; ++i) p += q.gw[i] * density_scaled(chi, 0.5 - (a + 0.5 * hp * (q.gx[i] + 1.0)));
+      T[k] = T[k + 1] + 0.5 * hp * p;
+    }
+    const double Ht = T[0];
+    for (int k = 0; k < kQsNodes; ++k) {
+      out[k].x = T[k] / Ht;
+      out[k].y = -density_scaled(chi, 0.5 - bw_node(k)) / Ht;
+    }
+    out[0].x = 1.0;
+    out[kQsNodes - 1].x = 0.0;
+  }
+};
+
 static int64_t next_pow2(int64_t n) {
   int64_t p = 1;
   while (p < n) p <<= 1;
@@ -409,6 +452,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.qs_rows = kQsRows;
   v.qs_tab_d = C.take<double2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
   v.qs_tab_f = C.take<float2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
+  v.bw_tab = C.take<double2>(qs_any ? (size_t)kBwRows * kQsNodes : 0);
   v.max_nx = max_nx;
   v.max_P = max_P;
   v.dmom = C.take<double>(8 * (size_t)max_nx);
@@ -539,7 +583,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.spec_tab, tab.data(), sizeof(float2) * spec_n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_c, qc.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_a, qa.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
-  std::vector<double2> qtab_d;
+  std::vector<double2> qtab_d, bwtab;
   std::vector<float2> qtab_f;
   if (qs_any) {  // the quantum spectrum table, only when a gap asks for it
     qtab_d.resize((size_t)kQsRows * kQsNodes);
@@ -551,6 +595,11 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
       e = cudaMemcpyAsync(v.qs_tab_d, qtab_d.data(), sizeof(double2) * qtab_d.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(v.qs_tab_f, qtab_f.data(), sizeof(float2) * qtab_f.size(), cudaMemcpyHostToDevice, st);
+    bwtab.resize((size_t)kBwRows * kQsNodes);
+    const BwHost bh(qh);
+    for (int r = 0; r < kBwRows; ++r) bh.row(std::exp(kBwLchi0 + r * kQsDlchi), &bwtab[(size_t)r * kQsNodes]);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v.bw_tab, bwtab.data(), sizeof(double2) * bwtab.size(), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_check(h, e, "layout upload");
@@ -920,6 +969,14 @@ int gap_qspectrum_inverse(gap_handle *h, const double *dev_chi, const double *de
   if (!h->v.qs_any) return fail(h, GAP_EINVAL, "no gap of this handle has qed_quantum");
   launch_qspec_inverse(h->v, dev_chi, dev_U, dev_xi, n, precision == GAP_FP32_STATE, (cudaStream_t)stream);
   return cuda_check(h, cudaGetLastError(), "quantum spectrum inverse");
+}
+
+int gap_pair_split(gap_handle *h, const double *dev_chi, const double *dev_U, double *dev_e, int64_t n,
+                   void *stream) {
+  if (!h || n < 0 || (n > 0 && (!dev_chi || !dev_U || !dev_e))) return GAP_EINVAL;
+  if (!h->v.qs_any) return fail(h, GAP_EINVAL, "no gap of this handle has qed_quantum");
+  launch_pair_split(h->v, dev_chi, dev_U, dev_e, n, (cudaStream_t)stream);
+  return cuda_check(h, cudaGetLastError(), "pair split");
 }
 
 int64_t gap_steps_done(const gap_handle *h) { return h ? h->steps_done : 0; }

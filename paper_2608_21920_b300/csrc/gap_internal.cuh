@@ -38,11 +38,22 @@ __host__ __device__ __forceinline__ R qs_node(int k) {  // in the precision of t
   const R f = (R)k / (R)(kQsNodes - 1);
   return (R)4 * f * f;
 }
+// Pair energy split table (qed_quantum): rows of ln chi from ln 1e-3 in steps
+// of ln 10 / 8 (57 rows to chi = 1e4); nodes eta_k = |e - 1/2| on a quintic
+// smootherstep of [0, 1/2] (cubic crowding towards both ends: the narrow
+// peak of a small chi at e = 1/2, the structure near e ~ 1/chi of a large one).
+constexpr int kBwRows = 57;
+constexpr double kBwLchi0 = -6.907755278982137;  // ln 1e-3
+template <class R = double>
+__host__ __device__ __forceinline__ R bw_node(int k) {
+  const R f = (R)k / (R)(kQsNodes - 1);
+  return (R)0.5 * f * f * f * (f * ((R)6 * f - (R)15) + (R)10);
+}
 
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
-  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_INJECT_U = 12
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_INJECT_U = 12, CH_PAIR_E = 13
 };
 
 enum Counter {
@@ -100,6 +111,7 @@ struct View {
   int32_t qs_any, qs_rows;
   double2 *qs_tab_d;
   float2 *qs_tab_f;
+  double2 *bw_tab;  // pair energy split: per row of ln chi, (G, dG/deta) on kQsNodes nodes
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
   int32_t *ph_gap;       // photons alive per gap
@@ -343,52 +355,45 @@ __device__ __forceinline__ double spec_inverse_d(const View &v, double U) {
 // Newton steps; ln s is blended over four rows of ln chi
 // (Catmull-Rom).  Below chi = 1e-6 the classical inverse gives d (the
 // quantum correction is O(chi)); above 1e5 the last row is used.
-template <class R>
-struct QsRow;
-template <>
-struct QsRow<double> {
-  __device__ static double2 at(const View &v, int r, int k) { return v.qs_tab_d[r * kQsNodes + k]; }
-};
-template <>
-struct QsRow<float> {
-  __device__ static float2 at(const View &v, int r, int k) { return v.qs_tab_f[r * kQsNodes + k]; }
-};
-
-// The four rows are searched in lockstep, so each bisection level issues four
+// Inversion of a decreasing tabulated function G (G(node 0) = 1) for the
+// target U in four rows at once: each bisection level issues four
 // independent loads (the emissions of a discharge are frequent: a serial
-// chain of dependent loads would dominate the push).
-template <class R>
-__device__ void qs_rows_s(const View &v, const int r[4], R U, R s[4]) {
+// chain of dependent loads would dominate the push); then the cubic Hermite
+// interpolant of the panel found is solved by Newton steps.  T2 holds
+// (G, dG/dnode); Node gives the node positions.
+template <class R, class T2, class Node>
+__device__ void rows_invert(const T2 *tab, const int r[4], R U, R s[4]) {
   int lo[4], hi[4];
   bool live[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     lo[j] = 0;
     hi[j] = kQsNodes - 1;
-    live[j] = U > QsRow<R>::at(v, r[j], kQsNodes - 1).x;
-    if (!live[j]) s[j] = qs_node<R>(kQsNodes - 1);
+    live[j] = U > (R)tab[r[j] * kQsNodes + kQsNodes - 1].x;
+    if (!live[j]) s[j] = Node::template at<R>(kQsNodes - 1);
   }
   for (int level = 0; level < 8; ++level) {  // 2^8 panels
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (!live[j] || hi[j] - lo[j] <= 1) continue;
       const int mid = (lo[j] + hi[j]) >> 1;
-      if (QsRow<R>::at(v, r[j], mid).x >= U) lo[j] = mid;
+      if ((R)tab[r[j] * kQsNodes + mid].x >= U) lo[j] = mid;
       else hi[j] = mid;
     }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (!live[j]) continue;
-    const auto a = QsRow<R>::at(v, r[j], lo[j]), b = QsRow<R>::at(v, r[j], hi[j]);
-    const R s_lo = qs_node<R>(lo[j]), h = qs_node<R>(hi[j]) - s_lo;
-    R t = (a.x - U) / (a.x - b.x);  // linear start, in [0, 1]
+    const T2 a = tab[r[j] * kQsNodes + lo[j]], b = tab[r[j] * kQsNodes + hi[j]];
+    const R ax = (R)a.x, ay = (R)a.y, bx = (R)b.x, by = (R)b.y;
+    const R s_lo = Node::template at<R>(lo[j]), h = Node::template at<R>(hi[j]) - s_lo;
+    R t = (ax - U) / (ax - bx);  // linear start, in [0, 1]
     for (int it = 0; it < 4; ++it) {
       const R t2 = t * t, t3 = t2 * t;
-      const R H = ((R)2 * t3 - (R)3 * t2 + (R)1) * a.x + (t3 - (R)2 * t2 + t) * h * a.y +
-                  ((R)-2 * t3 + (R)3 * t2) * b.x + (t3 - t2) * h * b.y;
-      const R dH = ((R)6 * t2 - (R)6 * t) * a.x + ((R)3 * t2 - (R)4 * t + (R)1) * h * a.y +
-                   ((R)-6 * t2 + (R)6 * t) * b.x + ((R)3 * t2 - (R)2 * t) * h * b.y;
+      const R H = ((R)2 * t3 - (R)3 * t2 + (R)1) * ax + (t3 - (R)2 * t2 + t) * h * ay +
+                  ((R)-2 * t3 + (R)3 * t2) * bx + (t3 - t2) * h * by;
+      const R dH = ((R)6 * t2 - (R)6 * t) * ax + ((R)3 * t2 - (R)4 * t + (R)1) * h * ay +
+                   ((R)-6 * t2 + (R)6 * t) * bx + ((R)3 * t2 - (R)2 * t) * h * by;
       if (!(dH < (R)0)) break;
       R tn = t - (H - U) / dH;
       tn = tn < (R)0 ? (R)0 : (tn > (R)1 ? (R)1 : tn);
@@ -397,6 +402,22 @@ __device__ void qs_rows_s(const View &v, const int r[4], R U, R s[4]) {
     }
     s[j] = s_lo + t * h;
   }
+}
+struct QsNode {
+  template <class R>
+  __device__ static R at(int k) { return qs_node<R>(k); }
+};
+struct BwNode {
+  template <class R>
+  __device__ static R at(int k) { return bw_node<R>(k); }
+};
+
+// Catmull-Rom blend of four row values over ln chi (t in [0, 1] between the
+// middle two)
+template <class R>
+__device__ __forceinline__ R catmull_rom(const R p[4], R t) {
+  return (R)0.5 * ((R)2 * p[1] + (-p[0] + p[2]) * t + ((R)2 * p[0] - (R)5 * p[1] + (R)4 * p[2] - p[3]) * t * t +
+                   (-p[0] + (R)3 * p[1] - (R)3 * p[2] + p[3]) * t * t * t);
 }
 
 template <class R>
@@ -417,14 +438,45 @@ __device__ __noinline__ R qspec_inverse(const View &v, R chi, R U) {
       const int r = i - 1 + j;
       rows[j] = r < 0 ? 0 : (r > v.qs_rows - 1 ? v.qs_rows - 1 : r);
     }
-    qs_rows_s<R>(v, rows, U, p);
+    if (sizeof(R) == 4) rows_invert<R, float2, QsNode>(v.qs_tab_f, rows, U, p);
+    else rows_invert<R, double2, QsNode>(v.qs_tab_d, rows, U, p);
     for (int j = 0; j < 4; ++j) p[j] = p[j] > (R)0 ? log(p[j]) : (R)-700;
-    const R ls = (R)0.5 * ((R)2 * p[1] + (-p[0] + p[2]) * t + ((R)2 * p[0] - (R)5 * p[1] + (R)4 * p[2] - p[3]) * t * t +
-                           (-p[0] + (R)3 * p[1] - (R)3 * p[2] + p[3]) * t * t * t);
-    d = exp((R)3 * ls);
+    d = exp((R)3 * catmull_rom<R>(p, t));
   }
   const R w = (R)3 * chi * d;
   return w / ((R)2 + w);
+}
+
+// Pair energy split (qed_quantum): the electron's fraction e of the photon
+// energy for a conversion at chi and a draw U, e = 1/2 -+ eta (minus for
+// U < 1/2) with G(eta) = 2 min(U, 1 - U) inverted in four rows of the table
+// and ln eta blended over ln chi.  Below chi = 1e-3 the Gaussian limit
+// (variance 3 chi / 64) applies; above 1e4 the last row.
+__device__ __noinline__ static double bw_split(const View &v, double chi, double U) {
+  const double u = U < 0.5 ? U : 1.0 - U;
+  double eta;
+  if (!(chi > 0.0)) {
+    eta = 0.0;
+  } else if (chi < 1e-3) {
+    eta = sqrt(3.0 * chi / 64.0) * 1.4142135623730951 * erfinv(1.0 - 2.0 * u);
+  } else {
+    double rr = (log(chi) - kBwLchi0) / kQsDlchi;
+    if (rr > (double)(kBwRows - 1)) rr = (double)(kBwRows - 1);
+    int i = (int)rr;
+    if (i > kBwRows - 2) i = kBwRows - 2;
+    const double t = rr - (double)i;
+    int rows[4];
+    double p[4];
+    for (int j = 0; j < 4; ++j) {
+      const int r = i - 1 + j;
+      rows[j] = r < 0 ? 0 : (r > kBwRows - 1 ? kBwRows - 1 : r);
+    }
+    rows_invert<double, double2, BwNode>(v.bw_tab, rows, 2.0 * u, p);
+    for (int j = 0; j < 4; ++j) p[j] = p[j] > 0.0 ? log(p[j]) : -700.0;
+    eta = exp(catmull_rom<double>(p, t));
+    if (eta > 0.5) eta = 0.5;
+  }
+  return U < 0.5 ? 0.5 - eta : 0.5 + eta;
 }
 
 // ---------------------------------------------------------------------------

@@ -573,6 +573,16 @@ void launch_qspec_inverse(const View &v, const double *chi, const double *U, dou
   if (n > 0) k_qspec_inverse<<<blocks, 256, 0, st>>>(v, chi, U, xi, n, fp32);
 }
 
+__global__ void k_pair_split(View v, const double *chi, const double *U, double *e, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    e[i] = bw_split(v, chi[i], U[i]);
+}
+
+void launch_pair_split(const View &v, const double *chi, const double *U, double *e, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  if (n > 0) k_pair_split<<<blocks, 256, 0, st>>>(v, chi, U, e, n);
+}
+
 void launch_spec_inverse(const View &v, const double *U, double *xi, int64_t n, int fp32, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 1184) blocks = 1184;

@@ -32,6 +32,7 @@ void launch_load(const View &v, const LoadSpec *specs_dev, int n_specs, int64_t 
                  cudaStream_t st);
 void launch_gauss(const View &v, int set_background, cudaStream_t st);
 void launch_spec_inverse(const View &v, const double *U, double *xi, int64_t n, int fp32, cudaStream_t st);
+void launch_pair_split(const View &v, const double *chi, const double *U, double *e, int64_t n, cudaStream_t st);
 void launch_qspec_inverse(const View &v, const double *chi, const double *U, double *xi, int64_t n, int fp32,
                           cudaStream_t st);
 void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st);

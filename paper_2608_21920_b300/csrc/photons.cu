@@ -191,8 +191,10 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
   v.pev[b][i] = ev;
 }
 
-// The event of photon i at step `step`: conversion into an e-e+ pair with
-// gamma = x/2 each at the photon's new position, or escape through a boundary.
+// The event of photon i at step `step`: conversion into an e-e+ pair at the
+// photon's new position (gamma = x/2 each, or with qed_quantum the electron
+// e x with e from the differential rate at this step's chi, both at least 1),
+// or escape through a boundary.
 template <class R>
 __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
   using W = typename Prec<R>::W;
@@ -207,8 +209,15 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     const int32_t dir = v.pdir[b][i];
     const double X1 = photon_pos(g, v.pXr[b][i], v.pnr[b][i], dir, step + 1);
     const uint64_t id = v.pid[b][i];
-    const double gp = 0.5 * x;
-    const double up = (double)dir * sqrt((gp - 1.0) * (gp + 1.0));
+    double ge = 0.5 * x;
+    if (g.qed_quantum) {
+      const double lmid = ((double)step - (double)v.pn0[b][i] + 0.5) * g.dt;
+      const double chi = x * g.b * fabs(sin(lmid / g.rho_hat));
+      double e = bw_split(v, chi, uniform53(g.seed, id, (uint32_t)step, CH_PAIR_E, 0));
+      if (e * x < 1.0) e = 1.0 / x;
+      if ((1.0 - e) * x < 1.0) e = 1.0 - 1.0 / x;
+      ge = e * x;
+    }
     int32_t k;
     R phi;
     split_position<R>(X1, g.nx, g.periodic != 0, k, phi);
@@ -217,6 +226,8 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     if (sizeof(R) == 4) wq = (W)llrint(w / g.w_unit);
     else wq = (W)w;
     for (int s = 0; s < 2; ++s) {
+      const double gs = s == 0 ? ge : x - ge;
+      const double up = (double)dir * sqrt((gs - 1.0) * (gs + 1.0));
       const uint64_t lid = child_id(id, (uint32_t)step, CH_PAIR, (uint32_t)s) & ~kPhotonBit;
       const R tau = (R)(-log(uniform53(g.seed, lid, (uint32_t)(step + 1), CH_TAU0, 0)));
       append_lepton<R>(v, s, tn, k, phi, (R)up, wq, tau, lid);

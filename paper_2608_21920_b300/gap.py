@@ -146,6 +146,16 @@ class Gap:
                                               self.stream()), self._h, "gap_qspectrum_inverse")
         return xi
 
+    def pair_split(self, chi, U):
+        """Electron's energy fraction of a conversion (qed_quantum gaps) for
+        CUDA tensors of chi and uniforms U (float64)."""
+        chi = chi.to(device=self.device, dtype=torch.float64).contiguous()
+        U = U.to(device=self.device, dtype=torch.float64).contiguous()
+        e = torch.empty_like(U)
+        A.check(A.lib().gap_pair_split(self._h, _ptr(chi), _ptr(U), _ptr(e), U.numel(), self.stream()),
+                self._h, "gap_pair_split")
+        return e
+
     @property
     def steps_done(self) -> int:
         return A.lib().gap_steps_done(self._h)

@@ -78,3 +78,58 @@ def test_quantum_emission_matches_oracle(precision, rtol):
     rel = np.abs(xa[big] / xb[big] - 1.0)
     assert rel.max() <= rtol, rel.max()
     gpu.close()
+
+
+def test_pair_split_matches_oracle():
+    """The electron's share of a conversion: the table against the oracle's
+    exact inverse.  Its emulation bounds the smaller share's relative error
+    by 1.5e-4 for u = min(U, 1 - U) >= 1e-3 and 3.2e-3 down to u = 1e-6
+    (chi <= 1e4); below chi = 1e-3 the Gaussian limit holds to O(chi)."""
+    g = _gap("fp64")
+    cases = [(chi, U) for chi in (2e-3, 0.05, 1.0, 77.0, 1e3, 5e3)
+             for U in (1e-6, 1e-5, 1e-4, 1e-3, 0.01, 0.2, 0.45, 0.5, 0.7, 0.999, 1 - 1e-5)]
+    chi = np.array([c for c, _ in cases])
+    U = np.array([u for _, u in cases])
+    e = g.pair_split(torch.tensor(chi), torch.tensor(U)).cpu().numpy()
+    ref = np.array([O.bw_split(c, u) for c, u in cases])
+    u = np.minimum(U, 1 - U)
+    small_gpu, small_ref = np.minimum(e, 1 - e), np.minimum(ref, 1 - ref)
+    rel = np.abs(small_gpu / small_ref - 1.0)
+    assert np.all((e < 0.5) == (U < 0.5) | (U == 0.5))
+    assert rel[u >= 1e-3].max() <= 3e-4, rel[u >= 1e-3].max()
+    assert rel.max() <= 5e-3, rel.max()
+    # Gaussian limit below the table
+    for c in (2e-4, 5e-4):
+        eg = g.pair_split(torch.tensor([c] * 3), torch.tensor([0.1, 0.3, 0.9])).cpu().numpy()
+        er = np.array([O.bw_split(c, x) for x in (0.1, 0.3, 0.9)])
+        assert np.all(np.abs(eg - er) <= 5e-3 * np.abs(er - 0.5))
+    g.close()
+
+
+def test_quantum_pair_creation_matches_oracle():
+    """Photons converting in a gap with qed_quantum: the same pairs at the same
+    steps, the shares from the same draws (table tolerance), energy x split
+    exactly between the two."""
+    cfg = dict(nx=512, boundary=O.BC_SURFACE, qed=1, qed_quantum=1, b=0.1, lambda_hat=1e-4, rho_hat=20.0,
+               rate_mult=10.0, dx=0.1, dt=0.045, gap_length=51.2, ppc=1, density=1e-6)
+    g, o = P.make_pair(cfg, "fp64", tile=64)
+    N = 200
+    ids = np.arange(1, N + 1, dtype=np.uint64)
+    ts = np.array([-math.log(O.uniform(5, int(i), 0, O.CH_BW_TAU, 0)) for i in ids])
+    x = 30.0 + np.arange(N) % 50
+    X = 1.0 + (np.arange(N) % 7) * 0.3
+    dirs = np.where(np.arange(N) % 3 == 0, -1, 1)
+    w = np.full(N, 1e-7)
+    g.add_particles(2, ids, X, x, w, ts, n0=np.zeros(N, np.int64), direction=dirs)
+    for i in range(N):
+        o.add_photon(int(ids[i]), X[i], x[i], w[i], int(dirs[i]), 0, ts[i])
+    g.step(60)
+    o.step(60)
+    cg, co = g.diag(spectrum=False)["counters"], o.counters()
+    assert cg["pairs"] == co["pairs"] > 10
+    a, b = P.leptons_gpu(g), P.leptons_oracle(o)
+    assert np.array_equal(a["id"], b["id"])
+    ga, gb = np.sqrt(1 + a["u"] ** 2), np.sqrt(1 + b["u"] ** 2)
+    assert np.abs(ga / gb - 1.0).max() <= 5e-3
+    assert np.median(np.abs(ga / gb - 1.0)) <= 1e-4
+    g.close()

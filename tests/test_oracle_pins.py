@@ -631,7 +631,7 @@ def test_bw_split_integrates_to_paper_tbw():
     """(1/(pi sqrt3 chi)) int_0^1 p de is T_BW of eq. tau_bw: the paper's
     asymptotes 0.23 e^(-8/(3 chi)) (chi << 1) and 0.38 chi^(-1/3) (chi >> 1),
     and its fit within the stated ~10 % in between."""
-    T = lambda chi: 2.0 * O.bw_half(chi, 0.0) / (math.pi * math.sqrt(3.0) * chi)
+    T = lambda chi: 2.0 * O.bw_tail(chi, 0.5) / (math.pi * math.sqrt(3.0) * chi)
     a, _ = _paper("tbw_small_coeff")
     b, _ = _paper("tbw_large_coeff")
     assert T(0.02) == pytest.approx(a * math.exp(-8.0 / (3.0 * 0.02)), rel=0.01)
@@ -650,9 +650,16 @@ def test_bw_split_gaussian_limit_and_symmetry():
         for U in (0.01, 0.3, 0.77):
             e = O.bw_split(chi, U)
             assert e + O.bw_split(chi, 1.0 - U) == pytest.approx(1.0, abs=1e-12)
-            F = 0.5 - O.bw_half(chi, e) / (2.0 * O.bw_half(chi, 0.0)) if e < 0.5 else \
-                0.5 + O.bw_half(chi, 1.0 - e) / (2.0 * O.bw_half(chi, 0.0))
+            F = O.bw_tail(chi, e) / (2.0 * O.bw_tail(chi, 0.5)) if e < 0.5 else \
+                1.0 - O.bw_tail(chi, 1.0 - e) / (2.0 * O.bw_tail(chi, 0.5))
             assert F == pytest.approx(U, abs=1e-12)
+    # the far tail against scipy's adaptive quadrature of the Bessel form
+    chi, e = 5e3, 3e-5
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        ref = integrate.quad(lambda x: _bw_ref(chi, x), 0, e, points=[1e-6, 1e-5], limit=400, epsrel=1e-10)[0]
+    assert O.bw_tail(chi, e) == pytest.approx(ref, rel=1e-8)
 
 
 def test_bw_split_pair_conserves_energy():
