@@ -95,7 +95,8 @@ def test_pair_split_matches_oracle():
     u = np.minimum(U, 1 - U)
     small_gpu, small_ref = np.minimum(e, 1 - e), np.minimum(ref, 1 - ref)
     rel = np.abs(small_gpu / small_ref - 1.0)
-    assert np.all((e < 0.5) == (U < 0.5) | (U == 0.5))
+    off = U != 0.5
+    assert np.all((e[off] < 0.5) == (U[off] < 0.5))
     assert rel[u >= 1e-3].max() <= 3e-4, rel[u >= 1e-3].max()
     assert rel.max() <= 5e-3, rel.max()
     # Gaussian limit below the table
@@ -123,10 +124,10 @@ def test_quantum_pair_creation_matches_oracle():
     g.add_particles(2, ids, X, x, w, ts, n0=np.zeros(N, np.int64), direction=dirs)
     for i in range(N):
         o.add_photon(int(ids[i]), X[i], x[i], w[i], int(dirs[i]), 0, ts[i])
-    g.step(60)
-    o.step(60)
+    g.step(120)
+    o.step(120)
     cg, co = g.diag(spectrum=False)["counters"], o.counters()
-    assert cg["pairs"] == co["pairs"] > 10
+    assert cg["pairs"] == co["pairs"] > 30
     a, b = P.leptons_gpu(g), P.leptons_oracle(o)
     assert np.array_equal(a["id"], b["id"])
     ga, gb = np.sqrt(1 + a["u"] ** 2), np.sqrt(1 + b["u"] ** 2)
