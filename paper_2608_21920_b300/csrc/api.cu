@@ -452,7 +452,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.qs_rows = kQsRows;
   v.qs_tab_d = C.take<double2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
   v.qs_tab_f = C.take<float2>(qs_any ? (size_t)kQsRows * kQsNodes : 0);
-  v.bw_tab = C.take<double2>(qs_any ? (size_t)kBwRows * kQsNodes : 0);
+  v.bw_tab = C.take<float2>(qs_any ? (size_t)kBwRows * kQsNodes : 0);
   v.max_nx = max_nx;
   v.max_P = max_P;
   v.dmom = C.take<double>(8 * (size_t)max_nx);
@@ -584,7 +584,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_c, qc.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.quad_a, qa.data(), sizeof(double) * v.quad_n, cudaMemcpyHostToDevice, st);
   std::vector<double2> qtab_d, bwtab;
-  std::vector<float2> qtab_f;
+  std::vector<float2> qtab_f, bwtab_f;
   if (qs_any) {  // the quantum spectrum table, only when a gap asks for it
     qtab_d.resize((size_t)kQsRows * kQsNodes);
     qtab_f.resize(qtab_d.size());
@@ -598,8 +598,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     bwtab.resize((size_t)kBwRows * kQsNodes);
     const BwHost bh(qh);
     for (int r = 0; r < kBwRows; ++r) bh.row(std::exp(kBwLchi0 + r * kQsDlchi), &bwtab[(size_t)r * kQsNodes]);
+    bwtab_f.resize(bwtab.size());  // (G, dG/d(1/2 - eta)) in float
+    for (size_t i = 0; i < bwtab.size(); ++i) bwtab_f[i] = make_float2((float)bwtab[i].x, (float)(-bwtab[i].y));
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(v.bw_tab, bwtab.data(), sizeof(double2) * bwtab.size(), cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(v.bw_tab, bwtab_f.data(), sizeof(float2) * bwtab_f.size(), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_check(h, e, "layout upload");

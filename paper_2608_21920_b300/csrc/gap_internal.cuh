@@ -49,6 +49,12 @@ __host__ __device__ __forceinline__ R bw_node(int k) {
   const R f = (R)k / (R)(kQsNodes - 1);
   return (R)0.5 * f * f * f * (f * ((R)6 * f - (R)15) + (R)10);
 }
+// The same nodes as the smaller share 1/2 - eta_k, without cancellation.
+template <class R = double>
+__host__ __device__ __forceinline__ R bw_node_small(int k) {
+  const R g = (R)(kQsNodes - 1 - k) / (R)(kQsNodes - 1);
+  return (R)0.5 * g * g * g * (g * ((R)6 * g - (R)15) + (R)10);
+}
 
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
@@ -111,7 +117,7 @@ struct View {
   int32_t qs_any, qs_rows;
   double2 *qs_tab_d;
   float2 *qs_tab_f;
-  double2 *bw_tab;  // pair energy split: per row of ln chi, (G, dG/deta) on kQsNodes nodes
+  float2 *bw_tab;  // pair energy split: per row of ln chi, (G, dG/d(1/2 - eta)) on kQsNodes nodes
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
   int32_t *ph_gap;       // photons alive per gap
@@ -407,9 +413,9 @@ struct QsNode {
   template <class R>
   __device__ static R at(int k) { return qs_node<R>(k); }
 };
-struct BwNode {
+struct BwNodeSmall {
   template <class R>
-  __device__ static R at(int k) { return bw_node<R>(k); }
+  __device__ static R at(int k) { return bw_node_small<R>(k); }
 };
 
 // Catmull-Rom blend of four row values over ln chi (t in [0, 1] between the
@@ -448,10 +454,12 @@ __device__ __noinline__ R qspec_inverse(const View &v, R chi, R U) {
 }
 
 // Pair energy split (qed_quantum): the electron's fraction e of the photon
-// energy for a conversion at chi and a draw U, e = 1/2 -+ eta (minus for
-// U < 1/2) with G(eta) = 2 min(U, 1 - U) inverted in four rows of the table
-// and ln eta blended over ln chi.  Below chi = 1e-3 the Gaussian limit
-// (variance 3 chi / 64) applies; above 1e4 the last row.
+// energy for a conversion at chi and a draw U: the smaller share
+// e_s = 1/2 - eta with G = 2 min(U, 1 - U), inverted in float in four rows
+// of the table (the table's precision; float keeps the FP64 units free for
+// the conversions of a discharge) and its logarithm blended over ln chi in
+// double; e = e_s for U < 1/2, else 1 - e_s.  Below chi = 1e-3 the Gaussian
+// limit (variance 3 chi / 64) applies; above 1e4 the last row.
 __device__ __noinline__ static double bw_split(const View &v, double chi, double U) {
   const double u = U < 0.5 ? U : 1.0 - U;
   double eta;
@@ -466,15 +474,17 @@ __device__ __noinline__ static double bw_split(const View &v, double chi, double
     if (i > kBwRows - 2) i = kBwRows - 2;
     const double t = rr - (double)i;
     int rows[4];
+    float ps[4];
     double p[4];
     for (int j = 0; j < 4; ++j) {
       const int r = i - 1 + j;
       rows[j] = r < 0 ? 0 : (r > kBwRows - 1 ? kBwRows - 1 : r);
     }
-    rows_invert<double, double2, BwNode>(v.bw_tab, rows, 2.0 * u, p);
-    for (int j = 0; j < 4; ++j) p[j] = p[j] > 0.0 ? log(p[j]) : -700.0;
-    eta = exp(catmull_rom<double>(p, t));
-    if (eta > 0.5) eta = 0.5;
+    rows_invert<float, float2, BwNodeSmall>(v.bw_tab, rows, (float)(2.0 * u), ps);
+    for (int j = 0; j < 4; ++j) p[j] = ps[j] > 0.0f ? log((double)ps[j]) : -700.0;
+    double small = exp(catmull_rom<double>(p, t));
+    if (small > 0.5) small = 0.5;
+    return U < 0.5 ? small : 1.0 - small;
   }
   return U < 0.5 ? 0.5 - eta : 0.5 + eta;
 }

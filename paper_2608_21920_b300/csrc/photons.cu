@@ -263,8 +263,11 @@ __device__ __forceinline__ void photon_scan_one(const View &v, int b, int64_t i,
   }
 }
 
+// Both photon-pass kernels keep five blocks of 256 threads per SM (at most
+// 51 registers): the scan is latency-bound and needs the warps; the rare
+// conversion with a quantum pair split spills instead.
 template <class R>
-__global__ void __launch_bounds__(256) k_photon_scan(View v) {
+__global__ void __launch_bounds__(256, 5) k_photon_scan(View v) {
   const int b = v.ctl->ph_cur;
   const int64_t n = photon_fill(v, b);
   const int64_t step = v.ctl->step;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(256) k_photon_scan(View v) {
 // Part 2: schedule the work list (one photon per thread, densely packed);
 // an imported photon may have its event in this very step.
 template <class R>
-__global__ void __launch_bounds__(256) k_photon_schedule(View v) {
+__global__ void __launch_bounds__(256, 5) k_photon_schedule(View v) {
   const int b = v.ctl->ph_cur;
   const int64_t n = v.ctl->ph_work_n;
   const int64_t step = v.ctl->step;

@@ -83,8 +83,9 @@ def test_quantum_emission_matches_oracle(precision, rtol):
 def test_pair_split_matches_oracle():
     """The electron's share of a conversion: the table against the oracle's
     exact inverse.  Its emulation bounds the smaller share's relative error
-    by 1.5e-4 for u = min(U, 1 - U) >= 1e-3 and 3.2e-3 down to u = 1e-6
-    (chi <= 1e4); below chi = 1e-3 the Gaussian limit holds to O(chi)."""
+    by 1.6e-5 for u = min(U, 1 - U) >= 1e-3 and 3.7e-3 down to u = 1e-6
+    (chi <= 1e4); the float inversion adds 1e-6; below chi = 1e-3 the
+    Gaussian limit holds to O(chi)."""
     g = _gap("fp64")
     cases = [(chi, U) for chi in (2e-3, 0.05, 1.0, 77.0, 1e3, 5e3)
              for U in (1e-6, 1e-5, 1e-4, 1e-3, 0.01, 0.2, 0.45, 0.5, 0.7, 0.999, 1 - 1e-5)]
@@ -97,8 +98,8 @@ def test_pair_split_matches_oracle():
     rel = np.abs(small_gpu / small_ref - 1.0)
     off = U != 0.5
     assert np.all((e[off] < 0.5) == (U[off] < 0.5))
-    assert rel[u >= 1e-3].max() <= 3e-4, rel[u >= 1e-3].max()
-    assert rel.max() <= 5e-3, rel.max()
+    assert rel[u >= 1e-3].max() <= 1e-4, rel[u >= 1e-3].max()
+    assert rel.max() <= 6e-3, rel.max()
     # Gaussian limit below the table
     for c in (2e-4, 5e-4):
         eg = g.pair_split(torch.tensor([c] * 3), torch.tensor([0.1, 0.3, 0.9])).cpu().numpy()
