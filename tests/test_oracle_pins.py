@@ -708,6 +708,27 @@ def test_pair_energy_and_charge_conservation():
     assert L["X"][0] == L["X"][1]
 
 
+def test_energy_ledger_closes_with_quantum_spectra():
+    """The ledger also closes when photon energies follow the quantum
+    spectrum (R26) and pairs the differential split (R27): 600 steps of the
+    small discharge, emissions and conversions included."""
+    s = _discharge_sim(qed_quantum=1)
+
+    def total():
+        L, P, c = s.leptons(), s.photons(), s.counters()
+        field = 0.5 * s.cfg["dx"] * np.sum(s.E() ** 2)
+        kin = np.sum(L["w"] * np.sqrt(1 + L["u"] ** 2))
+        ph = np.sum(P["w"] * P["x"])
+        return (field + kin + ph + c["e_radiated"] + c["e_absorbed"] + c["e_escaped"]
+                + c["e_photon_escaped"] - c["e_injected"] - c["work_jm"]), field + kin
+    L0, scale0 = total()
+    s.step(600)
+    L1, _ = total()
+    c = s.counters()
+    assert c["pairs"] > 0 and c["emit_events"] > 1000
+    assert abs(L1 - L0) < 0.02 * (abs(c["work_jm"]) + scale0)
+
+
 @pytest.mark.parametrize("inject_theta", [0.0, 0.3])
 def test_energy_ledger_closes(inject_theta):
     s = _discharge_sim(inject_theta=inject_theta)
