@@ -21,7 +21,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "gap_oracle.c")
 
 BC_SURFACE, BC_PERIODIC = 0, 1
-INIT_EMPTY, INIT_COLD, INIT_PAIR_THERMAL = 0, 1, 2
+INIT_EMPTY, INIT_COLD, INIT_PAIR_THERMAL, INIT_GAP_PROTONS = 0, 1, 2, 3
 ALPHA_EM = 7.2973525693e-3
 PHOTON_BIT = 1 << 63
 CH_INIT_U, CH_TAU0, CH_EMIT_X, CH_EMIT_TAU, CH_BW_TAU, CH_INJECT, CH_PAIR, CH_PHOTON, CH_MERGE = (
@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("gap_index", C.c_int32), ("qed", C.c_int32), ("boundary", C.c_int32),
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
+        ("protons", C.c_int32), ("m_ion", C.c_double),
     ]
 
 
@@ -104,6 +105,8 @@ def lib():
         L.orc_get_counters.argtypes = [vp, C.POINTER(Counters)]
         L.orc_get_leptons.argtypes = [vp] + [vp] * 6
         L.orc_get_photons.argtypes = [vp] + [vp] * 8
+        L.orc_get_lepton_heavy.argtypes = [vp, vp]
+        L.orc_add_proton.argtypes = [vp, u64, d, d, d]
         _lib = L
     return _lib
 
@@ -204,7 +207,7 @@ DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
                 init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0,
-                filter_passes=0, qed_quantum=0)
+                filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0)
 
 
 class Sim:
@@ -227,6 +230,9 @@ class Sim:
     # state ---------------------------------------------------------------
     def add_lepton(self, pid, q, X, u, w, tau=1e30):
         lib().orc_add_lepton(self.h, pid, q, X, u, w, tau)
+
+    def add_proton(self, pid, X, u, w):
+        lib().orc_add_proton(self.h, pid, X, u, w)
 
     def add_photon(self, pid, X, x, w, direction, n0, tau_star):
         lib().orc_add_photon(self.h, pid, X, x, w, direction, n0, tau_star)
@@ -276,6 +282,8 @@ class Sim:
         out = dict(id=np.empty(n, np.uint64), q=np.empty(n, np.int32), X=np.empty(n),
                    u=np.empty(n), w=np.empty(n), tau=np.empty(n))
         lib().orc_get_leptons(self.h, *(_p(out[k]) for k in ("id", "q", "X", "u", "w", "tau")))
+        out["heavy"] = np.empty(n, np.int32)
+        lib().orc_get_lepton_heavy(self.h, _p(out["heavy"]))
         return out
 
     def photons(self):

@@ -107,7 +107,7 @@ uint64_t orc_child_id(uint64_t parent, uint32_t step, uint32_t channel,
 enum {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
   CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_MERGE = 10,
-  CH_INJECT_U = 12, CH_PAIR_E = 13
+  CH_INJECT_U = 12, CH_PAIR_E = 13, CH_INJECT_P = 14
 };
 
 /* ------------------------------------------------------------------------- */
@@ -418,7 +418,7 @@ double orc_mj_sample(uint64_t seed, uint64_t id, double theta, int *ok) {
 /* PIC model                                                                  */
 /* ------------------------------------------------------------------------- */
 enum { ORC_BC_SURFACE = 0, ORC_BC_PERIODIC = 1 };
-enum { ORC_INIT_EMPTY = 0, ORC_INIT_COLD = 1, ORC_INIT_PAIR_THERMAL = 2 };
+enum { ORC_INIT_EMPTY = 0, ORC_INIT_COLD = 1, ORC_INIT_PAIR_THERMAL = 2, ORC_INIT_GAP_PROTONS = 3 };
 
 typedef struct {
   double alpha;      /* j_m / j_co (Sect. 2.2) */
@@ -444,9 +444,13 @@ typedef struct {
   double inject_theta; /* temperature of the injected atmosphere (m_e c^2); 0 = cold */
   int32_t filter_passes; /* binomial smoothing passes of the current per step; 0 = none */
   int32_t qed_quantum;   /* 1: quantum photon spectrum (orc_qspec_*); 0: classical */
+  int32_t protons;       /* 1: the surface also supplies protons (see the injection) */
+  double m_ion;          /* proton mass in m_e (0 -> 1836) */
 } orc_params;
 
-typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; } orc_lepton;
+/* heavy = 1 marks a proton (charge +1, mass m_ion; u is its momentum per
+ * m_ion c, so gamma = sqrt(1 + u^2) for every species). */
+typedef struct { uint64_t id; double X, u, w, tau; int32_t q; int32_t alive; int32_t heavy, pad; } orc_lepton;
 /* A photon moves at c along h from X_ref, where it was at the start of step
  * n_ref (its birth step n0 for photons born in the run); X is its current
  * position, kept for export. */
@@ -480,6 +484,9 @@ static double Fshape(double s) { /* fraction of the unit cloud right of a node *
   return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
 }
 static int64_t imod(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
+
+static double ion_mass(const orc_params *p) { return p->m_ion > 0.0 ? p->m_ion : 1836.0; }
+static double lepton_mass(const orc_params *p, const orc_lepton *L) { return L->heavy ? ion_mass(p) : 1.0; }
 
 static void push_lepton(orc_sim *s, orc_lepton L) {
   if (s->nlep == s->caplep) {
@@ -583,6 +590,22 @@ orc_sim *orc_create(const orc_params *pin) {
         L.tau = -log(orc_uniform(p->seed, L.id, 0, CH_TAU0, 0));
         push_lepton(s, L);
       }
+  } else if (p->init == ORC_INIT_GAP_PROTONS) {
+    /* Sect. 6.1 start: electrons at n_co everywhere and protons at the same
+     * positions below H_gap (eta = 0 there, eta_co above), all at rest; the
+     * Gauss solve then gives the linear ramp of E up to H_gap. */
+    const double Hc = p->gap_length / p->dx;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int64_t c = 0; c < p->nx; ++c)
+        for (int64_t j = 0; j < p->ppc; ++j) {
+          const double X = (double)c + ((double)j + 0.5) / (double)p->ppc;
+          if (sp == 1 && !(X < Hc)) continue;
+          orc_lepton L = {0};
+          L.id = load_id(p->gap_index, sp, c, p->ppc, j);
+          L.X = X; L.u = 0.0; L.w = s->w0; L.q = sp == 0 ? -1 : +1; L.heavy = sp; L.alive = 1;
+          L.tau = -log(orc_uniform(p->seed, L.id, 0, CH_TAU0, 0));
+          push_lepton(s, L);
+        }
   } else if (p->init == ORC_INIT_PAIR_THERMAL) {
     /* e- and e+ at density/2 each, 1D Maxwell-Juttner momenta; the electrons
      * are displaced by (A/k) sin(k X) with k = 2 pi / nx (cells): a Langmuir
@@ -629,6 +652,11 @@ void orc_add_lepton(orc_sim *s, uint64_t id, int32_t q, double X, double u,
                     double w, double tau) {
   orc_lepton L = {0};
   L.id = id; L.q = q; L.X = X; L.u = u; L.w = w; L.tau = tau; L.alive = 1;
+  push_lepton(s, L);
+}
+void orc_add_proton(orc_sim *s, uint64_t id, double X, double u, double w) {
+  orc_lepton L = {0};
+  L.id = id; L.q = +1; L.heavy = 1; L.X = X; L.u = u; L.w = w; L.tau = 1e30; L.alive = 1;
   push_lepton(s, L);
 }
 void orc_add_photon(orc_sim *s, uint64_t id, double X, double x, double w,
@@ -704,9 +732,10 @@ static double photon_pos(const orc_params *p, const orc_photon *P, int64_t m, do
  * is applied to E_k as a deposit, so Gauss's law holds.  level grows by one
  * per consecutive over-cap step (up to 7) and returns to 0 when the gap is
  * under the cap. */
-typedef struct { int32_t q, dir; int64_t k; int64_t bin; uint64_t id; int64_t idx; } mkey;
+typedef struct { int32_t q, dir; int64_t k; int64_t bin; uint64_t id; int64_t idx; int32_t heavy, pad; } mkey;
 static int mkey_cmp(const void *a, const void *b) {
   const mkey *x = (const mkey *)a, *y = (const mkey *)b;
+  if (x->heavy != y->heavy) return x->heavy < y->heavy ? -1 : 1;
   if (x->q != y->q) return x->q < y->q ? -1 : 1;
   if (x->k != y->k) return x->k < y->k ? -1 : 1;
   if (x->dir != y->dir) return x->dir < y->dir ? -1 : 1;
@@ -730,7 +759,7 @@ static void merge(orc_sim *s, uint32_t n) {
     int64_t k = (int64_t)floor(L->X + 0.5);
     if (p->boundary == ORC_BC_PERIODIC) k = imod(k, p->nx);
     key[i].q = L->q; key[i].dir = L->u >= 0.0 ? 1 : 0; key[i].k = k; key[i].bin = b;
-    key[i].id = L->id; key[i].idx = i;
+    key[i].id = L->id; key[i].idx = i; key[i].heavy = L->heavy;
   }
   qsort(key, (size_t)nl, sizeof(mkey), mkey_cmp);
   /* with smoothing, the re-centring flux is gathered per node, smoothed like
@@ -739,8 +768,8 @@ static void merge(orc_sim *s, uint32_t n) {
   int64_t a = 0;
   while (a < nl) {
     int64_t e = a + 1;
-    while (e < nl && key[e].q == key[a].q && key[e].k == key[a].k && key[e].dir == key[a].dir &&
-           key[e].bin == key[a].bin)
+    while (e < nl && key[e].heavy == key[a].heavy && key[e].q == key[a].q && key[e].k == key[a].k &&
+           key[e].dir == key[a].dir && key[e].bin == key[a].bin)
       ++e;
     if (e - a >= 3) {
       double W = 0.0, Sp = 0.0, Sm = 0.0, Sphi = 0.0;
@@ -784,7 +813,8 @@ static void merge(orc_sim *s, uint32_t n) {
       for (int c = 0; c < 2; ++c) {
         orc_lepton L = {0};
         L.id = orc_child_id(key[a].id, n, CH_MERGE, (uint32_t)c) & ~ORC_PHOTON_BIT;
-        L.q = key[a].q; L.X = X; L.u = c == 0 ? ua : ub; L.w = c == 0 ? wa : wb; L.alive = 1;
+        L.q = key[a].q; L.heavy = key[a].heavy; L.X = X; L.u = c == 0 ? ua : ub; L.w = c == 0 ? wa : wb;
+        L.alive = 1;
         L.tau = -log(orc_uniform(p->seed, L.id, n + 1, CH_TAU0, 0));
         push_lepton(s, L);
       }
@@ -813,7 +843,8 @@ static void merge(orc_sim *s, uint32_t n) {
  *     Sect. 6.1, convert into an e-e+ pair when it reaches its threshold;
  *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface (D
  *     smoothed by filter_passes binomial passes first, when asked);
- *  4. surface injection of electrons (Sect. 2.3 / 6.1 atmosphere);
+ *  4. surface injection of electrons, and with protons of protons
+ *     (Sect. 2.3 / 6.1 atmosphere);
  *  5. merge when leptons + photons exceed the cap (see merge()). */
 void orc_step(orc_sim *s) {
   const orc_params *p = &s->p;
@@ -828,11 +859,12 @@ void orc_step(orc_sim *s) {
     orc_lepton *L = &s->lep[ip];
     double X0 = L->X, u = L->u;
     /* a1-a2: gather and kick */
-    u += (double)L->q * gather(s, X0) * dt;
+    if (L->heavy) u += (double)L->q * gather(s, X0) * dt / ion_mass(p);
+    else u += (double)L->q * gather(s, X0) * dt;
     /* a3: emission sub-cycling within this step */
     orc_photon born[64];
     int nborn = 0;
-    if (p->qed && X0 < Hc) {
+    if (p->qed && X0 < Hc && !L->heavy) {
       double trem = dt, tau = L->tau;
       int k = 0;
       for (;;) {
@@ -883,9 +915,9 @@ void orc_step(orc_sim *s) {
     if (p->boundary == ORC_BC_PERIODIC) {
       X1 = wrap(p, X1);
     } else if (X1 < 0.0) {
-      L->alive = 0; s->cnt.absorbed++; s->cnt.e_absorbed += L->w * g;
+      L->alive = 0; s->cnt.absorbed++; s->cnt.e_absorbed += L->w * g * lepton_mass(p, L);
     } else if (X1 >= (double)p->nx) {
-      L->alive = 0; s->cnt.escaped++; s->cnt.e_escaped += L->w * g;
+      L->alive = 0; s->cnt.escaped++; s->cnt.e_escaped += L->w * g * lepton_mass(p, L);
     }
     L->X = X1;
     for (int b = 0; b < nborn; ++b) {
@@ -997,6 +1029,25 @@ void orc_step(orc_sim *s) {
       s->cnt.e_injected += s->w0 * sqrt(1.0 + L.u * L.u); /* total energy w gamma */
       ++j;
     }
+    /* with protons, an excess of negative charge is screened the other way:
+     * while it exceeds half a macro-particle charge a proton is added (its
+     * own channel; the temperature in its rest-mass units is theta/m_ion) */
+    for (int jp = 0; p->protons && deficit < -0.5 * s->w0; ++jp) {
+      if (jp >= p->kmax_inject) { s->cnt.inject_overflow++; break; }
+      orc_lepton L = {0};
+      L.id = orc_child_id(inject_root(p->gap_index), n, CH_INJECT_P, (uint32_t)jp) & ~ORC_PHOTON_BIT;
+      double o = 0.5 * orc_uniform(p->seed, L.id, n + 1, CH_INJECT_P, 0);
+      L.q = +1; L.heavy = 1; L.X = o; L.u = 0.0; L.w = s->w0; L.tau = 1e30; L.alive = 1;
+      if (p->inject_theta > 0.0) {
+        int ok = 1;
+        L.u = fabs(orc_mj_draw(p->seed, L.id, (uint32_t)(n + 1), CH_INJECT_U, p->inject_theta / ion_mass(p), &ok));
+        if (!ok) s->cnt.load_overflow++;
+      }
+      push_lepton(s, L);
+      deficit += s->w0 * (o + 0.5);
+      s->cnt.injected++;
+      s->cnt.e_injected += s->w0 * ion_mass(p) * sqrt(1.0 + L.u * L.u);
+    }
   }
   merge(s, n);
   s->step++;
@@ -1073,6 +1124,7 @@ void orc_moments(const orc_sim *s, double *dens, double *g3w, double *wsum, doub
   memset(charge, 0, (size_t)nx * sizeof(double));
   for (int64_t i = 0; i < s->nlep; ++i) {
     const orc_lepton *L = &s->lep[i];
+    if (L->heavy) continue;  /* the pair plasma's moments: protons are left out */
     double g = sqrt(1.0 + L->u * L->u);
     int sp = L->q < 0 ? 0 : 1, dr = L->u >= 0.0 ? 0 : 1;
     int64_t c0 = (int64_t)floor(L->X - 0.5);
@@ -1105,6 +1157,9 @@ void orc_get_leptons(const orc_sim *s, uint64_t *id, int32_t *q, double *X, doub
     id[i] = s->lep[i].id; q[i] = s->lep[i].q; X[i] = s->lep[i].X; u[i] = s->lep[i].u;
     w[i] = s->lep[i].w; tau[i] = s->lep[i].tau;
   }
+}
+void orc_get_lepton_heavy(const orc_sim *s, int32_t *heavy) {
+  for (int64_t i = 0; i < s->nlep; ++i) heavy[i] = s->lep[i].heavy;
 }
 void orc_get_photons(const orc_sim *s, uint64_t *id, double *X, double *x, double *w,
                      double *tau_star, double *tau_acc, int32_t *dir, int32_t *n0) {

@@ -471,6 +471,130 @@ def test_negative_alpha_field_grows_linearly():
     assert c["injected"] > 1000 and c["absorbed"] > 1000 and c["escaped"] == 0
 
 
+# ------------------------------------------------------------------ protons
+def test_proton_free_acceleration():
+    """A proton (charge +1, mass m_ion, u its momentum per m_ion c) in a
+    uniform field: leapfrog gives u = E t / m_ion exactly; an electron beside
+    it, u = -E t."""
+    s = O.Sim(nx=512, boundary=O.BC_PERIODIC, dx=0.1, dt=0.045, m_ion=1836.0)
+    E0 = 0.7
+    s.set_E(np.full(s.nnode, E0))
+    s.add_proton(1, 100.0, 0.0, 1e-30)
+    s.add_lepton(2, -1, 200.0, 0.0, 1e-30)
+    s.step(300)
+    L = s.leptons()
+    t = 300 * 0.045
+    up = L["u"][L["heavy"] == 1][0]
+    ue = L["u"][L["heavy"] == 0][0]
+    assert up == pytest.approx(E0 * t / 1836.0, rel=1e-12)
+    assert ue == pytest.approx(-E0 * t, rel=1e-12)
+
+
+def test_gap_protons_linear_ramp():
+    """Sect. 6.1's start: electrons everywhere, protons below H_gap (eta = 0
+    there, eta_co above); Gauss gives E rising linearly from 0 at the surface
+    to its co-rotation value at H_gap (E_i = i dx in these units) and flat
+    above."""
+    nx, dx = 100, 0.1
+    s = O.Sim(nx=nx, ppc=4, dx=dx, dt=0.045, boundary=O.BC_SURFACE, init=O.INIT_GAP_PROTONS,
+              gap_length=80 * dx, protons=1)
+    E = s.E()
+    i = np.arange(nx + 1)
+    ramp = np.where(i <= 80, i * dx, 80 * dx)
+    # exact away from the node at H_gap and the top node, where the unit
+    # clouds straddle the density step or leave the domain
+    far = (np.abs(i - 80) >= 1) & (i < nx)
+    assert np.allclose(E[far], ramp[far], rtol=0, atol=1e-12)
+    assert abs(E[80] - 80 * dx) <= dx / 4
+    L = s.leptons()
+    assert (L["heavy"] == 1).sum() == 80 * 4 and (L["heavy"] == 0).sum() == nx * 4
+    assert np.all(L["X"][L["heavy"] == 1] < 80)
+
+
+def _langmuir_two_species(m, nx=64, ppc=16, steps=1200):
+    dx, dt = 0.1, 0.045
+    s = O.Sim(nx=nx, boundary=O.BC_PERIODIC, dx=dx, dt=dt, m_ion=m if m else 1836.0)
+    w = dx / ppc
+    k = 2 * math.pi / nx
+    A = 0.001  # linear regime: at 0.01 light ions shift the frequency by 0.2 %
+    pid = 0
+    for c in range(nx):
+        for j in range(ppc):
+            X0 = c + (j + 0.5) / ppc
+            s.add_lepton(pid, -1, (X0 + A / k * math.sin(k * X0)) % nx, 0.0, w)
+            if m:
+                s.add_proton(pid + 1, X0, 0.0, w)
+            pid += 2
+    s.set_eta_bg(0.0 if m else -1.0)
+    s.solve_gauss()
+    node = nx // 4
+    tr = [s.E()[node]]
+    for _ in range(steps):
+        s.step(1)
+        tr.append(s.E()[node])
+    tr = np.array(tr)
+    zc = np.where(np.sign(tr[:-1]) != np.sign(tr[1:]))[0]
+    tz = zc + tr[zc] / (tr[zc] - tr[zc + 1])
+    return math.pi / (np.mean(np.diff(tz)) * dt), dt
+
+
+def test_two_species_langmuir_frequency():
+    """Cold electrons and ions of equal density oscillate at
+    omega^2 = omega_pe^2 (1 + m_e/m_i) (light ions, m_i = 4, make the shift
+    large), against electrons over a fixed background at the same mode (the
+    shape factors cancel); leapfrog omega = (2/dt) asin(Omega dt / 2)."""
+    m = 4.0
+    w_e, dt = _langmuir_two_species(0)
+    w_2, _ = _langmuir_two_species(m)
+    Om_e = 2 / dt * math.sin(w_e * dt / 2)
+    Om_2 = 2 / dt * math.sin(w_2 * dt / 2)
+    assert Om_2 / Om_e == pytest.approx(math.sqrt(1.0 + 1.0 / m), rel=1e-4)
+
+
+def test_proton_injection_screens_negative_excess():
+    """With protons the surface supply screens both ways: electrons piled
+    into cell 0 beyond eta_co dx draw protons from the surface until cell 0
+    is within half a macro-particle charge of it."""
+    dx, ppc = 0.1, 4
+    w0 = dx / ppc
+    s = O.Sim(nx=64, ppc=ppc, dx=dx, dt=0.045, boundary=O.BC_SURFACE, init=O.INIT_EMPTY, protons=1)
+    for i in range(10):
+        s.add_lepton(i + 1, -1, 0.25, 0.0, w0)
+    s.solve_gauss()
+    s.step(1)
+    L = s.leptons()
+    c = s.counters()
+    assert (L["heavy"] == 1).sum() >= 3 and c["injected"] == (L["heavy"] == 1).sum()
+    assert np.all((L["X"][L["heavy"] == 1] > 0) & (L["X"][L["heavy"] == 1] <= 0.5))
+    assert abs(s.cell_charge(0) + dx) <= 0.5 * w0 + 1e-15
+    # without the option the excess stays
+    s2 = O.Sim(nx=64, ppc=ppc, dx=dx, dt=0.045, boundary=O.BC_SURFACE, init=O.INIT_EMPTY)
+    for i in range(10):
+        s2.add_lepton(i + 1, -1, 0.25, 0.0, w0)
+    s2.solve_gauss()
+    s2.step(1)
+    assert s2.counters()["injected"] == 0
+
+
+def test_energy_ledger_closes_with_protons():
+    """alpha = -2 from the Sect. 6.1 start with protons: kinetic energy
+    w m gamma for every species; the ledger closes over 600 steps."""
+    s = _discharge_sim(alpha=-2.0, qed=0, init=O.INIT_GAP_PROTONS, protons=1, inject_theta=0.3)
+
+    def total():
+        L, c = s.leptons(), s.counters()
+        field = 0.5 * s.cfg["dx"] * np.sum(s.E() ** 2)
+        m = np.where(L["heavy"] == 1, 1836.0, 1.0)
+        kin = np.sum(L["w"] * m * np.sqrt(1 + L["u"] ** 2))
+        return (field + kin + c["e_absorbed"] + c["e_escaped"] - c["e_injected"] - c["work_jm"]), field + kin
+    L0, scale0 = total()
+    s.step(600)
+    L1, _ = total()
+    c = s.counters()
+    assert c["injected"] > 0
+    assert abs(L1 - L0) < 0.02 * (abs(c["work_jm"]) + scale0)
+
+
 def test_boundaries_absorb_and_escape():
     s = O.Sim(nx=16, boundary=O.BC_SURFACE, dx=0.1, dt=0.045)
     s.add_lepton(1, -1, 0.2, -5.0, 1e-30)   # falls back onto the star
