@@ -1,9 +1,12 @@
 // step.cu -- kernels of one time step of the 1D radiative PIC model
 // (paper Sect. 6.1 cycle reduced to the field-aligned direction):
 //   k_push      gather, kick, curvature emission, drift, deposit, boundaries,
-//               Ampere update of E (one block per tile, fused)
+//   k_push_lean Ampere update of E fused per tile (gaps with a current filter
+//   k_push_tma  leave it to filter.cu); k_push takes work items from a
+//               persistent grid, the lean and bulk-copy pushes one tile per block
 //   (photon propagation and pair creation: photons.cu)
-//   k_inject    cold-electron surface injection (atmosphere, Sect. 2.3 / 6.1)
+//   k_inject    surface injection of electrons, cold or at the atmosphere's
+//               temperature (Sect. 2.3 / 6.1)
 //   k_house     per-step bookkeeping of the tile segments and buffers
 //   k_rebin_*   compaction of the particle store into the other buffer
 #include "gap_internal.cuh"
