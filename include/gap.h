@@ -57,11 +57,16 @@ extern "C" {
 #define GAP_INIT_COLD 1         /* cold electrons at rest, `density`, ppc per cell */
 #define GAP_INIT_PAIR_THERMAL 2 /* e- and e+ at density/2 each, 1D Maxwell-Juttner(theta),
                                    electrons displaced by a Langmuir seed of amplitude seed_amp */
+#define GAP_INIT_GAP_PROTONS 3  /* Sect. 6.1 start: cold electrons at `density` everywhere and
+                                   protons at the same positions below H_gap (eta = 0 there,
+                                   eta_co above): E rises linearly to H_gap.  Needs protons = 1
+                                   and a surface gap */
 
 /* particle kinds for gap_get_particles / gap_add_particles */
 #define GAP_ELECTRON 0
 #define GAP_POSITRON 1
 #define GAP_PHOTON 2
+#define GAP_PROTON 3 /* export only (gap_get_particles / gap_sample_particles) */
 
 /* Parameters of one gap.  The problem statement of the paper (Sect. 2.2 and
  * 6.1): twist alpha = j_m/j_co, field b = B/B_Q, field-line curvature radius
@@ -123,6 +128,15 @@ typedef struct gap_params {
                             below chi = 1e-3), the positron the rest;
                             0: the classical shape and x/2 each.  0 or 1,
                             else GAP_EINVAL */
+  int32_t protons;       /* 1: protons (charge +1, mass m_ion, u their momentum per
+                            m_ion c; no QED): the GAP_INIT_GAP_PROTONS start, and
+                            the surface also draws protons while cell 0 holds more
+                            negative charge than eta_co dx by over half a macro-
+                            particle charge (thermal at inject_theta / m_ion).  The
+                            gap's Ampere step runs after the push (as with a current
+                            filter).  Needs the FP64 state and cap = 0, else
+                            GAP_EINVAL */
+  double m_ion;          /* proton mass in m_e (0 -> 1836) */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */

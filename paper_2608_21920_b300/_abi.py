@@ -10,8 +10,8 @@ SO_PATH = os.path.join(HERE, "libgap.so")
 GAP_OK, GAP_EINVAL, GAP_ENOSPACE, GAP_ECAP, GAP_ETIMEOUT, GAP_ECUDA, GAP_ECHECK, GAP_ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 GAP_FP64_PLAIN, GAP_FP32_STATE = 0, 1
 GAP_BC_SURFACE, GAP_BC_PERIODIC = 0, 1
-GAP_INIT_EMPTY, GAP_INIT_COLD, GAP_INIT_PAIR_THERMAL = 0, 1, 2
-GAP_ELECTRON, GAP_POSITRON, GAP_PHOTON = 0, 1, 2
+GAP_INIT_EMPTY, GAP_INIT_COLD, GAP_INIT_PAIR_THERMAL, GAP_INIT_GAP_PROTONS = 0, 1, 2, 3
+GAP_ELECTRON, GAP_POSITRON, GAP_PHOTON, GAP_PROTON = 0, 1, 2, 3
 
 
 class GapParams(C.Structure):
@@ -24,6 +24,7 @@ class GapParams(C.Structure):
         ("qed", C.c_int32), ("boundary", C.c_int32), ("init", C.c_int32),
         ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32), ("gap_index", C.c_int32),
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
+        ("protons", C.c_int32), ("m_ion", C.c_double),
     ]
 
 

@@ -19,6 +19,7 @@ struct gap_handle {
   std::vector<GapDev> gaps_h;
   std::vector<TileDev> tiles_h;
   std::vector<LoadSpec> loads;
+  std::vector<int32_t> proton_loads;  // gaps that start with protons below H_gap
   int64_t total_nodes = 0, steps_done = 0;
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -91,7 +92,7 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.nx < 8 || q.nx > (1ll << 28)) { msg = "nx out of range"; return GAP_EINVAL; }
     if (!(q.dx > 0) || !(q.dt > 0) || q.dt / q.dx >= 0.5) { msg = "need dx, dt > 0 and c dt/dx < 1/2"; return GAP_EINVAL; }
     if (q.boundary != GAP_BC_SURFACE && q.boundary != GAP_BC_PERIODIC) { msg = "boundary"; return GAP_EINVAL; }
-    if (q.init < GAP_INIT_EMPTY || q.init > GAP_INIT_PAIR_THERMAL) { msg = "init"; return GAP_EINVAL; }
+    if (q.init < GAP_INIT_EMPTY || q.init > GAP_INIT_GAP_PROTONS) { msg = "init"; return GAP_EINVAL; }
     if (q.init != GAP_INIT_EMPTY && q.ppc <= 0) { msg = "ppc must be > 0 for a load"; return GAP_EINVAL; }
     if (q.kmax_emit < 0 || q.kmax_emit > kMaxEmit) { msg = "kmax_emit must be <= 16"; return GAP_EINVAL; }
     if (q.qed && (!(q.lambda_hat > 0) || !(q.rho_hat > 0) || q.rate_mult < 0)) { msg = "QED scales"; return GAP_EINVAL; }
@@ -100,6 +101,12 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.filter_passes < 0 || q.filter_passes > 16) { msg = "filter_passes must be in [0, 16]"; return GAP_EINVAL; }
     if (q.filter_passes > 0 && q.nx < 2 * (int64_t)q.filter_passes + 2) { msg = "filter_passes needs nx >= 2 passes + 2"; return GAP_EINVAL; }
     if (q.qed_quantum != 0 && q.qed_quantum != 1) { msg = "qed_quantum must be 0 or 1"; return GAP_EINVAL; }
+    if (q.protons != 0 && q.protons != 1) { msg = "protons must be 0 or 1"; return GAP_EINVAL; }
+    if (q.protons && cfg.precision != GAP_FP64_PLAIN) { msg = "protons need the FP64 state"; return GAP_EINVAL; }
+    if (q.protons && q.cap > 0) { msg = "protons with a macro-particle cap are not supported"; return GAP_EINVAL; }
+    if (q.init == GAP_INIT_GAP_PROTONS && (!q.protons || q.boundary != GAP_BC_SURFACE))
+      { msg = "the proton start needs protons and a surface gap"; return GAP_EINVAL; }
+    if (q.m_ion < 0.0) { msg = "m_ion must be >= 0"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -298,7 +305,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<LoadSpec> loads;
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
-  bool qed_any = false, surface_any = false, merge_any = false, filter_any = false, qs_any = false;
+  bool qed_any = false, surface_any = false, merge_any = false, filter_any = false, qs_any = false, pr_any = false;
+  int64_t pr_need = 0;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
     GapDev &g = gaps[i];
@@ -337,7 +345,12 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.cap = q.cap > 0 ? q.cap : 0;
     g.inject_theta = q.inject_theta;
     g.filter_passes = q.filter_passes;
-    filter_any |= q.filter_passes > 0;
+    g.protons = q.protons;
+    g.m_ion = q.m_ion > 0.0 ? q.m_ion : 1836.0;
+    g.defer = q.filter_passes > 0 || q.protons ? 1 : 0;
+    filter_any |= g.defer != 0;
+    pr_any |= q.protons != 0;
+    if (q.protons) pr_need += 2 * q.nx * std::max<int64_t>(q.ppc, 1) + 65536;
     g.qed_quantum = q.qed && q.qed_quantum ? 1 : 0;
     qs_any |= g.qed_quantum != 0;
     merge_any |= q.cap > 0;
@@ -351,7 +364,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     if (rem < 4 && nt > 1) nt -= 1;
     g.tile_begin = (int32_t)tiles.size();
     g.n_tiles = (int32_t)nt;
-    const int64_t species = q.init == GAP_INIT_PAIR_THERMAL ? 2 : (q.init == GAP_INIT_COLD ? 1 : 0);
+    const int64_t species =
+        q.init == GAP_INIT_PAIR_THERMAL ? 2 : (q.init == GAP_INIT_COLD || q.init == GAP_INIT_GAP_PROTONS ? 1 : 0);
     for (int64_t t = 0; t < nt; ++t) {
       TileDev td{};
       td.gap = i;
@@ -379,7 +393,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     if (q.init != GAP_INIT_EMPTY) {
       LoadSpec ls{};
       ls.gap = i;
-      ls.init = q.init;
+      ls.init = q.init == GAP_INIT_GAP_PROTONS ? GAP_INIT_COLD : q.init;  // the electrons of that start
       ls.species_count = (int32_t)species;
       ls.ppc = q.ppc;
       ls.n_per_species = load;
@@ -409,6 +423,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.has_w = (qed_any || merge_any) ? 1 : 0;  // merging makes weights unequal
   v.merge_any = merge_any ? 1 : 0;
   v.filter_any = filter_any ? 1 : 0;
+  v.pr_any = pr_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
   v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
@@ -492,6 +507,13 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     v.ptan[b] = C.take<double>(ph_cap);
   }
   v.ph_work = C.take<int64_t>(ph_cap);
+  v.pr_cap = pr_need;
+  v.pr_X = C.take<double>(pr_need);
+  v.pr_u = C.take<double>(pr_need);
+  v.pr_w = C.take<double>(pr_need);
+  v.pr_id = C.take<uint64_t>(pr_need);
+  v.pr_gap = C.take<int32_t>(pr_need);
+  v.pr_alive = C.take<int32_t>(pr_need);
   v.ph_capacity = ph_cap;
   char *bb[2];
   size_t bbytes = 0;
@@ -522,6 +544,9 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   h->gaps_h = gaps;
   h->tiles_h = tiles;
   h->loads = loads;
+  h->proton_loads.clear();
+  for (int i = 0; i < n; ++i)
+    if (p[i].init == GAP_INIT_GAP_PROTONS) h->proton_loads.push_back(i);
   h->total_nodes = total_nodes;
   h->buf_base[0] = bb[0];
   h->buf_base[1] = bb[1];
@@ -615,6 +640,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (c->error & 16) return fail(h, GAP_ETIMEOUT, "a bulk-copy stage of the push kernel never completed");
   if (c->error & 32) return fail(h, GAP_ECHECK, "a lepton outside its tile's nodes reached the merge");
   if (c->error & 64) return fail(h, GAP_ECHECK, "a photon event was not taken at its step");
+  if (c->error & 128) return fail(h, GAP_ECAP, "proton storage exhausted");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));
@@ -652,6 +678,7 @@ int gap_init(const gap_params *params, int32_t n_gaps, const gap_config *cfg, vo
   if (r) { *out = h; return r; }
   cudaStream_t st = (cudaStream_t)stream;
   launch_load(h->v, h->loads.data(), (int)h->loads.size(), 0, st);
+  for (int32_t gi : h->proton_loads) launch_load_protons(h->v, gi, h->gaps_h[gi].nx * h->params[gi].ppc, st);
   launch_sync_used(h->v, st);
   launch_force_rebin(h->v, st);
   launch_rebin(h->v, h->slack, st);
@@ -802,7 +829,7 @@ static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t st
                             uint64_t *host_id, double *host_X, double *host_u, double *host_w,
                             double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
                             void *stream) {
-  if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > 2 || !n_out) return GAP_EINVAL;
+  if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > GAP_PROTON || !n_out) return GAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Ctl c;
   int r = read_ctl(h, &c, st);
@@ -810,7 +837,10 @@ static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t st
   const int64_t scap = (int64_t)(h->buf_bytes / (8 * 7));
   double *stage = reinterpret_cast<double *>(h->buf_base[c.lep_cur ^ 1]);
   cudaError_t e = cudaMemsetAsync(h->export_count, 0, sizeof(unsigned long long), st);
-  launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st, stride);
+  if (kind == GAP_PROTON)
+    launch_export_protons(h->v, gap, stage, scap, h->export_count, stride, st);
+  else
+    launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st, stride);
   if (e == cudaSuccess) e = cudaGetLastError();
   unsigned long long cnt = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, h->export_count, sizeof(cnt), cudaMemcpyDeviceToHost, st);

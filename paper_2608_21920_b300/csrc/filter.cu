@@ -14,9 +14,9 @@
 // mirrors evenly about nodes 0 and nx.  The cell charge of the Gauss solve
 // and residual is mirrored oddly about the same nodes (init.cu), the pairing
 // under which smoothing commutes with the node-to-cell difference, so Gauss's
-// law holds for the smoothed charge.  Both kernels touch only gaps with
-// filter_passes > 0, and the tiles of a gap cover its nodes k0 .. k0 + nk - 1
-// without overlap.
+// law holds for the smoothed charge.  Both kernels touch only gaps that defer
+// Ampere (filter_passes > 0, or protons: zero passes, the update alone), and
+// the tiles of a gap cover its nodes k0 .. k0 + nk - 1 without overlap.
 #include <algorithm>
 
 #include "gap_internal.cuh"
@@ -48,7 +48,7 @@ template <class R>
 __global__ void k_flux_take(View v) {
   const TileDev ti = v.tiles[blockIdx.x];
   const GapDev &g = v.gaps[ti.gap];
-  if (g.filter_passes <= 0) return;
+  if (!g.defer) return;
   unsigned long long *out = reinterpret_cast<unsigned long long *>(v.Dflt);
   for (int i = threadIdx.x; i < ti.nk; i += blockDim.x) {
     const int64_t gn = g.node_off + ti.k0 + i;
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) k_filter_apply(View v, int mode) {
   for (int t = t0; t < t1; ++t) {
     const TileDev ti = v.tiles[t];
     const GapDev &g = v.gaps[ti.gap];
-    const int P = g.filter_passes;
-    if (P <= 0) continue;
+    if (!g.defer) continue;
+    const int P = g.filter_passes;  // 0: Ampere alone (a gap with protons)
     if (mode == 0 && ti.gap != work_gap) {  // block-uniform
       if (work_gap >= 0) {
         const GapDev &gw = v.gaps[work_gap];

@@ -59,7 +59,8 @@ __host__ __device__ __forceinline__ R bw_node_small(int k) {
 // Draw channels of the counter-based generator (interface values).
 enum Channel : uint32_t {
   CH_INIT_U = 1, CH_TAU0 = 3, CH_EMIT_X = 4, CH_EMIT_TAU = 5,
-  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_INJECT_U = 12, CH_PAIR_E = 13
+  CH_BW_TAU = 6, CH_INJECT = 7, CH_PAIR = 8, CH_PHOTON = 9, CH_INJECT_U = 12, CH_PAIR_E = 13,
+  CH_INJECT_P = 14
 };
 
 enum Counter {
@@ -79,6 +80,9 @@ struct GapDev {
   double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold
   int32_t filter_passes;  // binomial current-smoothing passes per step; 0 = none
   int32_t qed_quantum;    // 1: quantum photon spectrum (table below); 0: classical
+  int32_t protons;        // 1: a proton store and proton supply (FP64 state)
+  int32_t defer;          // Ampere left to filter.cu (a current filter, or protons)
+  double m_ion;           // proton mass in m_e
 };
 
 struct TileDev {
@@ -95,6 +99,7 @@ struct Ctl {
   int64_t ph_work_n;  // photons on the scheduling work list this step
   int64_t last_rebin_step;
   int64_t ph_dead;  // photons dead since the last photon compaction
+  int64_t pr_count;  // protons stored (alive or not)
   int32_t need_ph_compact;
   int32_t hold_copies;  // test hook: bulk-copy pushes leave their first stage unissued
   int32_t push_items, push_next;  // the push work list of this step and its counter
@@ -109,7 +114,11 @@ struct View {
   int32_t n_gaps, n_tiles, tile, precision;
   int32_t qed_any, surface_any, has_w, rebin_every;
   int32_t variant, merge_any;
-  int32_t filter_any, pad_f;  // some gap smooths its current
+  int32_t filter_any, pr_any;  // some gap defers Ampere (current filter or protons); some has protons
+  int64_t pr_cap;             // proton store (unsorted, FP64): position, momentum per m_ion c, weight
+  double *pr_X, *pr_u, *pr_w;
+  uint64_t *pr_id;
+  int32_t *pr_gap, *pr_alive;
   double *Dflt;               // [2 x dcharge_len] smoothing scratch (node flux; two cell buffers)
   // quantum photon spectrum (some gap with qed_quantum): per row of ln chi,
   // the normalised survival S(s)/S(0) and its s-derivative on kQsNodes nodes

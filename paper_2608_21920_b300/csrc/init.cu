@@ -64,6 +64,82 @@ __global__ void k_load(View v, LoadSpec sp) {
   }
 }
 
+// Protons of the Sect. 6.1 start: the quiet-start positions of the electrons
+// below H_gap, at rest, weight w0 (FP64 state), ids with species bit 1.
+__global__ void k_load_protons(View v, int gap, int64_t n) {
+  const GapDev &g = v.gaps[gap];
+  const int64_t ppc = n / g.nx;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = p / ppc, j = p % ppc;
+    const double X = (double)cell + ((double)j + 0.5) / (double)ppc;
+    if (!(X < g.Hc)) continue;
+    const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->pr_count), 1ull);
+    if (i >= v.pr_cap) {
+      atomicOr(&v.ctl->error, 128);  // proton storage exhausted
+      continue;
+    }
+    v.pr_X[i] = X;
+    v.pr_u[i] = 0.0;
+    v.pr_w[i] = g.w0;
+    v.pr_id[i] = ((uint64_t)g.gap_index << 40) | (1ull << 39) | (uint64_t)(cell * ppc + j);
+    v.pr_gap[i] = gap;
+    v.pr_alive[i] = 1;
+  }
+}
+
+void launch_load_protons(const View &v, int gap, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  if (n > 0) k_load_protons<<<blocks, 256, 0, st>>>(v, gap, n);
+}
+
+// Charge of the protons per cell (cloud in cell) into Q: all gaps at their
+// node offsets (gap < 0, the Gauss solve), or one gap from 0 (the diagnostics).
+__global__ void k_proton_charge(View v, int gap, unsigned long long *Q) {
+  const int64_t n = v.ctl->pr_count < v.pr_cap ? v.ctl->pr_count : v.pr_cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!v.pr_alive[i]) continue;
+    const int gi = v.pr_gap[i];
+    if (gap >= 0 && gi != gap) continue;
+    const GapDev &g = v.gaps[gi];
+    const int64_t off = gap >= 0 ? 0 : g.node_off;
+    const double X = v.pr_X[i];
+    const int64_t c0 = (int64_t)floor(X - 0.5);
+    for (int64_t c = c0; c <= c0 + 1; ++c) {
+      const double a = X - (double)c, b = X - (double)c - 1.0;
+      const double fa = a + 0.5 < 0.0 ? 0.0 : (a + 0.5 > 1.0 ? 1.0 : a + 0.5);
+      const double fb = b + 0.5 < 0.0 ? 0.0 : (b + 0.5 > 1.0 ? 1.0 : b + 0.5);
+      const double fr = fa - fb;
+      if (fr == 0.0) continue;
+      int64_t cc = c;
+      if (g.periodic) cc = (c % g.nx + g.nx) % g.nx;
+      else if (c < 0 || c >= g.nx) continue;
+      atomicAdd(reinterpret_cast<double *>(&Q[off + cc]), v.pr_w[i] * fr);
+    }
+  }
+}
+
+// Export of one gap's live protons (every stride-th by id), lepton layout.
+__global__ void k_export_protons(View v, int gap, double *stage, int64_t cap, unsigned long long *count,
+                                 int64_t stride) {
+  const int64_t n = v.ctl->pr_count < v.pr_cap ? v.ctl->pr_count : v.pr_cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!v.pr_alive[i] || v.pr_gap[i] != gap) continue;
+    if (stride > 1 && (v.pr_id[i] % (uint64_t)stride) != 0) continue;
+    const unsigned long long o = atomicAdd(count, 1ull);
+    if ((int64_t)o >= cap) continue;
+    reinterpret_cast<uint64_t *>(stage)[o] = v.pr_id[i];
+    stage[cap + o] = v.pr_X[i];
+    stage[2 * cap + o] = v.pr_u[i];
+    stage[3 * cap + o] = v.pr_w[i];
+    stage[4 * cap + o] = 1e30;  // no optical depth: protons do not radiate
+  }
+}
+
+void launch_export_protons(const View &v, int gap, double *stage, int64_t cap, unsigned long long *count,
+                           int64_t stride, cudaStream_t st) {
+  k_export_protons<<<148, 256, 0, st>>>(v, gap, stage, cap, count, stride);
+}
+
 void launch_load(const View &v, const LoadSpec *spec, int n_specs, int64_t max_n, cudaStream_t st) {
   (void)max_n;
   for (int i = 0; i < n_specs; ++i) {
@@ -247,6 +323,7 @@ void launch_gauss(const View &v, int set_background, cudaStream_t st) {
   cudaMemsetAsync(v.dcharge, 0, sizeof(unsigned long long) * (size_t)v.dcharge_len, st);
   if (v.precision == GAP_FP32_STATE) k_cell_charge<float><<<v.n_tiles, 256, 0, st>>>(v, -1, v.dcharge);
   else k_cell_charge<double><<<v.n_tiles, 256, 0, st>>>(v, -1, v.dcharge);
+  if (v.pr_any) k_proton_charge<<<148 * 4, 256, 0, st>>>(v, -1, v.dcharge);
   k_gauss_scan<<<v.n_gaps, 1024, 0, st>>>(v, set_background);
 }
 
@@ -479,6 +556,7 @@ void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st)
   if (v.precision == GAP_FP32_STATE) k_moments<float><<<gh.n_tiles, 256, 0, st>>>(v, gap);
   else k_moments<double><<<gh.n_tiles, 256, 0, st>>>(v, gap);
   launch_photon_moments(v, gap, st);
+  if (v.pr_any) k_proton_charge<<<148 * 4, 256, 0, st>>>(v, gap, v.dcharge);  // for the Gauss residual
   k_reduce<<<1, 1024, 0, st>>>(v, gap);
   if (P >= 2) {
     double2 *a = reinterpret_cast<double2 *>(v.fft[0]);

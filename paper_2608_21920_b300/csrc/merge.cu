@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       // filter collects it for smoothing (k_filter_apply, mode 1)
       int64_t node_g = kn;
       if (g.periodic) node_g %= g.nx;
-      if (flux != 0.0 && g.filter_passes > 0) {
+      if (flux != 0.0 && g.defer) {
         if (sizeof(R) == 4) acc_add_global(&v.Dg[g.node_off + node_g], flux_units);
         else acc_add_global(&v.Dg[g.node_off + node_g], flux);
       } else if (flux != 0.0 && (g.periodic || node_g > 0)) {

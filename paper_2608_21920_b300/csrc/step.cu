@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   bool finish = true;  // this block completes the tile
-  if (g.filter_passes > 0) {
+  if (g.defer) {
     for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
       const Acc qi = node_charge(i);
       if (qi == (Acc)0) continue;
@@ -1115,6 +1115,70 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
 }
 
 // ---------------------------------------------------------------------------
+// k_push_heavy: the protons (FP64 state; charge +1, mass m_ion, u their
+// momentum per m_ion c; no QED), one thread each, from the unsorted store.
+// Gather of E^n, kick u += E dt / m_ion, drift, the flux through the nodes
+// crossed into the global accumulators (their gaps defer Ampere to
+// filter.cu), cell 0's charge for the injection, and the boundaries.
+__global__ void __launch_bounds__(256) k_push_heavy(View v) {
+  const int64_t n = v.ctl->pr_count < v.pr_cap ? v.ctl->pr_count : v.pr_cap;
+  const int ecur = v.ctl->e_cur;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!v.pr_alive[i]) continue;
+    const int gi = v.pr_gap[i];
+    const GapDev &g = v.gaps[gi];
+    const double *E = v.E[ecur] + g.node_off;
+    const bool periodic = g.periodic != 0;
+    const double X0 = v.pr_X[i], w = v.pr_w[i];
+    // linear gather between nodes floor(X) and floor(X) + 1
+    const double cf = floor(X0);
+    int64_t c = (int64_t)cf, c1 = c + 1;
+    const double o = X0 - cf;
+    if (periodic) {
+      c = (c % g.nx + g.nx) % g.nx;
+      c1 = (c1 % g.nx + g.nx) % g.nx;
+    }
+    const double Eg = (1.0 - o) * E[c] + o * E[c1];
+    const double u = v.pr_u[i] + Eg * g.dt / g.m_ion;
+    const double gm = sqrt(1.0 + u * u);
+    const double X1 = X0 + u / gm * g.cdx;
+    // flux q w [F(X1 - k) - F(X0 - k)], F(s) = clamp(s + 1/2, 0, 1)
+    const double lo = X0 < X1 ? X0 : X1, hi = X0 < X1 ? X1 : X0;
+    const int64_t k0 = (int64_t)floor(lo - 0.5), k1 = (int64_t)floor(hi + 0.5);
+    for (int64_t k = k0; k <= k1; ++k) {
+      const double a1 = X1 - (double)k + 0.5, a0 = X0 - (double)k + 0.5;
+      const double f1 = a1 < 0.0 ? 0.0 : (a1 > 1.0 ? 1.0 : a1), f0 = a0 < 0.0 ? 0.0 : (a0 > 1.0 ? 1.0 : a0);
+      const double dF = f1 - f0;
+      if (dF == 0.0) continue;
+      int64_t node = k;
+      if (periodic) node = (k % g.nx + g.nx) % g.nx;
+      else if (k < 0 || k > g.nx) continue;
+      atomicAdd(reinterpret_cast<double *>(&v.Dg[g.node_off + node]), w * dF);
+    }
+    v.pr_u[i] = u;
+    double Xn = X1;
+    if (periodic) {
+      Xn = fmod(X1, (double)g.nx);
+      if (Xn < 0.0) Xn += (double)g.nx;
+      if (Xn >= (double)g.nx) Xn -= (double)g.nx;
+    } else if (X1 < 0.0) {
+      v.pr_alive[i] = 0;
+      atomicAdd(&v.counters[gi * C_NCNT + C_ABSORBED], 1ull);
+      atomicAdd(&v.ledger[gi * L_NLED + L_ABS], w * gm * g.m_ion);
+    } else if (X1 >= (double)g.nx) {
+      v.pr_alive[i] = 0;
+      atomicAdd(&v.counters[gi * C_NCNT + C_ESCAPED], 1ull);
+      atomicAdd(&v.ledger[gi * L_NLED + L_ESC], w * gm * g.m_ion);
+    }
+    v.pr_X[i] = Xn;
+    if (!periodic && v.pr_alive[i]) {  // cell 0's share of the cloud, for the injection
+      const double a = Xn + 0.5, b = Xn - 0.5;
+      const double fr = (a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a)) - (b < 0.0 ? 0.0 : (b > 1.0 ? 1.0 : b));
+      if (fr != 0.0) atomicAdd(reinterpret_cast<double *>(&v.q0[gi]), w * fr);
+    }
+  }
+}
+
 // k_inject: one warp per gap with a surface.  Cell 0 must hold the
 // co-rotation charge eta_co dx = -dx; while its deficit exceeds half a
 // macro-particle charge an electron is added at X = U/2 in (0, 1/2], at rest
@@ -1187,6 +1251,38 @@ __global__ void k_inject(View v) {
     if (injected) {
       atomicAdd(&C[C_INJECTED], (unsigned long long)injected);
       atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0 * e_inj);
+    }
+    // with protons an excess of negative charge is screened the other way:
+    // while it exceeds half a macro-particle charge a proton is added at
+    // X = U/2 (its own channel; thermal at inject_theta / m_ion in its
+    // rest-mass units), appended to the proton store
+    for (int jp = 0; g.protons && deficit < -0.5 * g.w0; ++jp) {
+      if (jp >= g.kmax_inject) {
+        atomicAdd(&C[C_INJ_OVF], 1ull);
+        break;
+      }
+      const uint64_t id = child_id(g.inj_root, (uint32_t)step, CH_INJECT_P, (uint32_t)jp) & ~kPhotonBit;
+      const double o = 0.5 * uniform53(g.seed, id, (uint32_t)(step + 1), CH_INJECT_P, 0);
+      double u = 0.0;
+      if (g.inject_theta > 0.0) {
+        bool ok = true;
+        u = fabs(mj_draw(g.seed, id, (uint32_t)(step + 1), CH_INJECT_U, g.inject_theta / g.m_ion, ok));
+        if (!ok) atomicAdd(&C[C_LOAD_OVF], 1ull);
+      }
+      const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->pr_count), 1ull);
+      if (i < v.pr_cap) {
+        v.pr_X[i] = o;
+        v.pr_u[i] = u;
+        v.pr_w[i] = g.w0;
+        v.pr_id[i] = id;
+        v.pr_gap[i] = gi;
+        v.pr_alive[i] = 1;
+      } else {
+        atomicOr(&v.ctl->error, 128);  // proton storage exhausted
+      }
+      deficit = __dadd_rn(deficit, __dmul_rn(g.w0, o + 0.5));  // a separate product and sum
+      atomicAdd(&C[C_INJECTED], 1ull);
+      atomicAdd(&v.ledger[gi * L_NLED + L_INJ], g.w0 * g.m_ion * sqrt(1.0 + u * u));
     }
   }
 }
@@ -1603,7 +1699,8 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     else
       k_push<R, false, false><<<grid, threads, smem, st>>>(v);
   }
-  launch_filter(v, 0, st);  // Ampere of the gaps with a current filter
+  if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons (FP64 state)
+  launch_filter(v, 0, st);  // Ampere of the gaps that defer it (current filter, protons)
 }
 
 template <class R>
@@ -1644,7 +1741,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
   return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
-         (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0);
+         (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0) + (v.pr_any ? 1 : 0);
 }
 
 void launch_sync_used(const View &v, cudaStream_t st) {

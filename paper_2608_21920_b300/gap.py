@@ -18,7 +18,7 @@ PARAM_DEFAULTS = dict(
     alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0, gap_length=0.0,
     density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0, nx=64, ppc=0, cap=0, seed=0,
     qed=0, boundary=A.GAP_BC_SURFACE, init=A.GAP_INIT_EMPTY, kmax_emit=16, kmax_inject=64,
-    gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0)
+    gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0)
 
 PRECISION = {"fp64": A.GAP_FP64_PLAIN, "fp32": A.GAP_FP32_STATE}
 

@@ -1,0 +1,78 @@
+"""Protons on the CUDA path (FP64 state) against the FP64 oracle: the Sect.
+6.1 start (electrons everywhere, protons below H_gap, the linear ramp of E),
+the proton push (kick by 1/m_ion, flux into the deferred Ampere step), and
+the surface supply in both signs."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import _pair as P
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-10
+START = dict(nx=128, ppc=4, dx=0.1, dt=0.045, alpha=2.0, b=0.1, qed=1, lambda_hat=2e-4, rho_hat=10.0,
+             rate_mult=5.0, init=O.INIT_GAP_PROTONS, boundary=O.BC_SURFACE, seed=3, protons=1)
+
+
+def _protons_gpu(g, gap=0):
+    p = g.particles(3, gap)
+    order = np.argsort(p["id"], kind="stable")
+    return {k: v[order] for k, v in p.items()}
+
+
+def _split_oracle(o):
+    L = o.leptons()
+    order = np.argsort(L["id"], kind="stable")
+    L = {k: v[order] for k, v in L.items()}
+    e = {k: v[L["heavy"] == 0] for k, v in L.items()}
+    p = {k: v[L["heavy"] == 1] for k, v in L.items()}
+    return e, p
+
+
+def _parity(cfg, checkpoints):
+    g, o = P.make_pair(cfg, "fp64", tile=32)
+    P.compare_field(g.field(), o.E(), RTOL64, "initial E (the ramp)")
+    n_prev = 0
+    for n in checkpoints:
+        g.step(n - n_prev)
+        o.step(n - n_prev)
+        n_prev = n
+        d = g.diag(spectrum=False)
+        P.compare_counters(d["counters"], o.counters(), f"step {n}")
+        P.compare_field(g.field(), o.E(), RTOL64, f"step {n}")
+        e_o, p_o = _split_oracle(o)
+        P.compare_leptons(P.leptons_gpu(g), e_o, RTOL64, f"leptons step {n}")
+        pg = _protons_gpu(g)
+        pg["q"] = np.ones(pg["id"].size, np.int32)
+        P.compare_leptons(pg, p_o, RTOL64, f"protons step {n}")
+        assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    return g, o
+
+
+def test_proton_start_parity():
+    """The Sect. 6.1 start with QED: the ramp, then electrons, protons, E and
+    counters at 1e-10 over 400 steps."""
+    g, o = _parity(START, [1, 100, 400])
+    _, p_o = _split_oracle(o)
+    assert p_o["id"].size > 300 and np.abs(p_o["u"]).max() > 0
+    g.close()
+
+
+def test_negative_alpha_with_protons_parity():
+    """alpha = -2 with a T = 0.3 atmosphere and protons: the surface draws
+    electrons and protons; parity at 1e-10 over 600 steps."""
+    cfg = dict(START, alpha=-2.0, qed=0, inject_theta=0.3)
+    g, o = _parity(cfg, [50, 300, 600])
+    c = o.counters()
+    assert c["injected"] > 0 and c["absorbed"] > 0
+    g.close()
+
+
+def test_protons_need_fp64_and_no_cap():
+    from paper_2608_21920_b300 import Gap
+    from paper_2608_21920_b300._abi import GapError
+    with pytest.raises(GapError):
+        Gap(P.gpu_params(START), precision="fp32")
+    with pytest.raises(GapError):
+        Gap(P.gpu_params(dict(START, cap=1000)), precision="fp64")
