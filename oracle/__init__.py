@@ -48,6 +48,8 @@ class Params(C.Structure):
         ("init", C.c_int32), ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32),
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
         ("protons", C.c_int32), ("m_ion", C.c_double),
+        ("em", C.c_int32), ("pml_cells", C.c_int32), ("beta_y", C.c_double), ("beta_z", C.c_double),
+        ("pml_sigma", C.c_double),
     ]
 
 
@@ -107,6 +109,8 @@ def lib():
         L.orc_get_photons.argtypes = [vp] + [vp] * 8
         L.orc_get_lepton_heavy.argtypes = [vp, vp]
         L.orc_add_proton.argtypes = [vp, u64, d, d, d]
+        L.orc_set_em.argtypes = [vp, pd, pd, pd, pd]
+        L.orc_get_em.argtypes = [vp, pd, pd, pd, pd]
         _lib = L
     return _lib
 
@@ -207,7 +211,8 @@ DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 gap_length=0.0, density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
                 init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0,
-                filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0)
+                filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0,
+                em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0)
 
 
 class Sim:
@@ -247,6 +252,21 @@ class Sim:
 
     def solve_gauss(self):
         lib().orc_solve_gauss(self.h)
+
+    def set_em(self, Ey, Ez, By, Bz):
+        """Transverse fields (em = 1): E_y, E_z on the nx cells (half steps),
+        B_y, B_z on the nodes."""
+        nx = self.cfg["nx"]
+        a = [np.ascontiguousarray(f, dtype=np.float64) for f in (Ey, Ez, By, Bz)]
+        assert a[0].size == a[1].size == nx and a[2].size == a[3].size == self.nnode
+        lib().orc_set_em(self.h, *[_pd(f) for f in a])
+
+    def em(self):
+        """(E_y, E_z, B_y, B_z) of an em = 1 gap."""
+        nx = self.cfg["nx"]
+        out = [np.empty(nx), np.empty(nx), np.empty(self.nnode), np.empty(self.nnode)]
+        lib().orc_get_em(self.h, *[_pd(f) for f in out])
+        return tuple(out)
 
     def step(self, n=1):
         lib().orc_run(self.h, int(n))

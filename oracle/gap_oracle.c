@@ -446,6 +446,10 @@ typedef struct {
   int32_t qed_quantum;   /* 1: quantum photon spectrum (orc_qspec_*); 0: classical */
   int32_t protons;       /* 1: the surface also supplies protons (see the injection) */
   double m_ion;          /* proton mass in m_e (0 -> 1836) */
+  int32_t em;            /* 1: transverse fields E_y, E_z, B_y, B_z (see em_advance) */
+  int32_t pml_cells;     /* absorbing layer below the top of a surface gap; 0 = none */
+  double beta_y, beta_z; /* velocity of the co-rotating frame (App. A), across h */
+  double pml_sigma;      /* peak conductivity of the layer (omega_p); 0 -> a 1e-6 reflection */
 } orc_params;
 
 /* heavy = 1 marks a proton (charge +1, mass m_ion; u is its momentum per
@@ -470,6 +474,9 @@ typedef struct {
   orc_params p;
   int64_t nnode;       /* nodes holding E: nx+1 (surface) or nx (periodic) */
   double *E, *D;       /* E on nodes; D = sum q w dF, the charge through each node */
+  double *Ey, *Ez;     /* em: transverse E on cells (centres c + 1/2), at half steps */
+  double *By, *Bz;     /* em: transverse B on nodes, at whole steps */
+  double *Jv;          /* em: dt j_vir,h on nodes for this step's Ampere */
   double eta_bg;       /* Gauss background: eta_co = -1 (surface), mean load charge (periodic) */
   double w0;           /* weight of a loaded / injected macro-particle */
   orc_lepton *lep; int64_t nlep, caplep;
@@ -577,6 +584,13 @@ orc_sim *orc_create(const orc_params *pin) {
   s->nnode = p->boundary == ORC_BC_PERIODIC ? p->nx : p->nx + 1;
   s->E = (double *)calloc((size_t)s->nnode, sizeof(double));
   s->D = (double *)calloc((size_t)s->nnode, sizeof(double));
+  if (p->em) {
+    s->Ey = (double *)calloc((size_t)p->nx, sizeof(double));
+    s->Ez = (double *)calloc((size_t)p->nx, sizeof(double));
+    s->By = (double *)calloc((size_t)s->nnode, sizeof(double));
+    s->Bz = (double *)calloc((size_t)s->nnode, sizeof(double));
+    s->Jv = (double *)calloc((size_t)s->nnode, sizeof(double));
+  }
   s->w0 = p->ppc > 0 ? p->density * p->dx / (double)p->ppc : 0.0;
   s->eta_bg = -1.0;
   if (p->init == ORC_INIT_COLD) {
@@ -644,6 +658,7 @@ orc_sim *orc_create(const orc_params *pin) {
 
 void orc_destroy(orc_sim *s) {
   if (!s) return;
+  free(s->Ey); free(s->Ez); free(s->By); free(s->Bz); free(s->Jv);
   free(s->E); free(s->D); free(s->lep); free(s->ph); free(s);
 }
 
@@ -670,6 +685,19 @@ void orc_add_photon(orc_sim *s, uint64_t id, double X, double x, double w,
 void orc_set_eta_bg(orc_sim *s, double eta) { s->eta_bg = eta; }
 void orc_binomial_smooth(double *a, int64_t n, int32_t passes, int32_t ext) { binomial_smooth(a, n, passes, ext); }
 void orc_set_E(orc_sim *s, const double *E) { memcpy(s->E, E, (size_t)s->nnode * sizeof(double)); }
+/* transverse fields (em = 1): E_y, E_z have nx entries, B_y, B_z nnode */
+void orc_set_em(orc_sim *s, const double *Ey, const double *Ez, const double *By, const double *Bz) {
+  memcpy(s->Ey, Ey, (size_t)s->p.nx * sizeof(double));
+  memcpy(s->Ez, Ez, (size_t)s->p.nx * sizeof(double));
+  memcpy(s->By, By, (size_t)s->nnode * sizeof(double));
+  memcpy(s->Bz, Bz, (size_t)s->nnode * sizeof(double));
+}
+void orc_get_em(const orc_sim *s, double *Ey, double *Ez, double *By, double *Bz) {
+  memcpy(Ey, s->Ey, (size_t)s->p.nx * sizeof(double));
+  memcpy(Ez, s->Ez, (size_t)s->p.nx * sizeof(double));
+  memcpy(By, s->By, (size_t)s->nnode * sizeof(double));
+  memcpy(Bz, s->Bz, (size_t)s->nnode * sizeof(double));
+}
 
 /* Deposit of one move X0 -> X1 (unwrapped): the charge through node i is
  * q w [F(X1 - i) - F(X0 - i)], the change of the cloud fraction right of i
@@ -834,6 +862,90 @@ static void merge(orc_sim *s, uint32_t n) {
   s->nlep = m;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Transverse fields in the co-rotating frame (App. A), in the 1D reduction:  */
+/* every quantity depends on h alone, B = B_* h-hat + B_perp, and the frame   */
+/* moves at beta = (0, beta_y, beta_z) across h.  In code units (c = 1, 4 pi  */
+/* absorbed) App. A's Maxwell equations give, with d = d/dh,                  */
+/*   dB_y/dt =  d E_z,            dB_z/dt = -d E_y,                           */
+/*   dE_y/dt = -d B_z + jv_y,     dE_z/dt =  d B_y + jv_z,                    */
+/*   dE_h/dt = (Ampere of Sect. 2.2) + jv_h,                                  */
+/* and the virtual current jv = -{curl(beta x E) + beta x curl E              */
+/*   - curl[beta x (beta x B)]} at r = R reads, with P = beta (beta.B)        */
+/*   - beta^2 B_perp,                                                         */
+/*   jv_h = -(beta_y d E_y + beta_z d E_z),                                   */
+/*   jv_y = -beta_y d E_h - d P_z,  jv_z = -beta_z d E_h + d P_y.             */
+/* The virtual charge eta_vir = eta_co + beta . curl B = eta_co               */
+/*   - beta_y d B_z + beta_z d B_y enters Gauss's law (see the residual).     */
+/* Particles move along B_* (the strong-field limit), so they carry no        */
+/* transverse current: the transverse fields are driven by jv alone.          */
+/*                                                                           */
+/* Grid (Yee, second order): E_y, E_z at cell centres and half steps, B_y,    */
+/* B_z at nodes and whole steps; d E_h lives on cells, d E_perp on nodes.     */
+/* Called after the particle push, before Ampere: E_h is still E^n, the cells */
+/* go from n - 1/2 to n + 1/2 with B^n and E_h^n, then the nodes from n to    */
+/* n + 1 with E_perp^{n+1/2}, and Jv = dt jv_h^{n+1/2} is left for Ampere.    */
+/* Surface gap: the star (node 0) is a conductor, E_perp = 0 there (cell -1   */
+/* mirrors cell 0 with a sign change); so is the top (node nx), behind an     */
+/* absorbing layer of pml_cells cells (Sect. 6.1: escaping fields are damped  */
+/* to vacuum).  The layer is a matched electric and magnetic conductivity     */
+/* sigma(X) = sigma_max ((X - X_p)/pml_cells)^3 above X_p = nx - pml_cells    */
+/* (Berenger's layer in 1D, where matching needs no field splitting), each    */
+/* field advanced by the lossy-medium update F <- a F + b (rhs) with          */
+/* a = (1 - sigma dt/2)/(1 + sigma dt/2), b = dt/(1 + sigma dt/2); the        */
+/* default sigma_max = 4 ln(1e6)/(2 pml_cells dx) gives a continuum normal-   */
+/* incidence reflection of 1e-6.  Periodic gap: both grids wrap.              */
+/* ------------------------------------------------------------------------- */
+static double pml_sigma_max(const orc_params *p) {
+  if (p->pml_sigma > 0.0) return p->pml_sigma;
+  return 4.0 * log(1e6) / (2.0 * (double)p->pml_cells * p->dx);
+}
+static double pml_sigma_at(const orc_params *p, double X) {
+  if (p->boundary == ORC_BC_PERIODIC || p->pml_cells <= 0) return 0.0;
+  const double Xp = (double)(p->nx - p->pml_cells);
+  if (!(X > Xp)) return 0.0;
+  const double f = (X - Xp) / (double)p->pml_cells;
+  return pml_sigma_max(p) * f * f * f;
+}
+/* transverse E of cell c, with the conductor images of a surface gap */
+static double cell_field(const orc_sim *s, const double *F, int64_t c) {
+  const int64_t nx = s->p.nx;
+  if (s->p.boundary == ORC_BC_PERIODIC) return F[imod(c, nx)];
+  if (c < 0) return -F[-1 - c];
+  if (c >= nx) return -F[2 * nx - 1 - c];
+  return F[c];
+}
+static void em_advance(orc_sim *s) {
+  const orc_params *p = &s->p;
+  const double dt = p->dt, dx = p->dx, by = p->beta_y, bz = p->beta_z;
+  const double b2 = by * by + bz * bz;
+  const int64_t nx = p->nx;
+  for (int64_t c = 0; c < nx; ++c) {
+    const int64_t i0 = c, i1 = p->boundary == ORC_BC_PERIODIC ? imod(c + 1, nx) : c + 1;
+    const double dEh = (s->E[i1] - s->E[i0]) / dx;
+    const double bB0 = by * s->By[i0] + bz * s->Bz[i0], bB1 = by * s->By[i1] + bz * s->Bz[i1];
+    const double Py0 = by * bB0 - b2 * s->By[i0], Py1 = by * bB1 - b2 * s->By[i1];
+    const double Pz0 = bz * bB0 - b2 * s->Bz[i0], Pz1 = bz * bB1 - b2 * s->Bz[i1];
+    const double jvy = -by * dEh - (Pz1 - Pz0) / dx;
+    const double jvz = -bz * dEh + (Py1 - Py0) / dx;
+    const double ry = -(s->Bz[i1] - s->Bz[i0]) / dx + jvy;
+    const double rz = (s->By[i1] - s->By[i0]) / dx + jvz;
+    const double sg = pml_sigma_at(p, (double)c + 0.5);
+    const double a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt), b = dt / (1.0 + 0.5 * sg * dt);
+    s->Ey[c] = a * s->Ey[c] + b * ry;
+    s->Ez[c] = a * s->Ez[c] + b * rz;
+  }
+  for (int64_t i = 0; i < s->nnode; ++i) {
+    const double dEy = (cell_field(s, s->Ey, i) - cell_field(s, s->Ey, i - 1)) / dx;
+    const double dEz = (cell_field(s, s->Ez, i) - cell_field(s, s->Ez, i - 1)) / dx;
+    const double sg = pml_sigma_at(p, (double)i);
+    const double a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt), b = dt / (1.0 + 0.5 * sg * dt);
+    s->Bz[i] = a * s->Bz[i] - b * dEy;
+    s->By[i] = a * s->By[i] + b * dEz;
+    s->Jv[i] = -dt * (by * dEy + bz * dEz);
+  }
+}
+
 /* One time step n -> n+1.  Order (Sect. 6.1 PIC cycle, reduced to 1D along B):
  *  1. every lepton: gather E^n, kick (Sect. 4: du/dt = (q/m) E), curvature
  *     emission by optical-depth sub-cycling (eq. tau_syn, Sect. 6.1 MC
@@ -841,7 +953,8 @@ static void merge(orc_sim *s, uint32_t n) {
  *  2. every photon alive at step start: propagate at c, accumulate the
  *     Breit-Wheeler optical depth (eq. tau_bw) at the accumulated angle of
  *     Sect. 6.1, convert into an e-e+ pair when it reaches its threshold;
- *  3. Ampere (Sect. 2.2): E_i += dt j_m - D_i, E_0 = 0 at the surface (D
+ *  3. with em, the transverse fields (em_advance); Ampere (Sect. 2.2):
+ *     E_i += dt j_m - D_i (+ dt jv_h with em), E_0 = 0 at the surface (D
  *     smoothed by filter_passes binomial passes first, when asked);
  *  4. surface injection of electrons, and with protons of protons
  *     (Sect. 2.3 / 6.1 atmosphere);
@@ -989,11 +1102,13 @@ void orc_step(orc_sim *s) {
   if (p->filter_passes > 0)
     binomial_smooth(s->D, s->nnode, p->filter_passes,
                     p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_NODE_EVEN);
+  if (p->em) em_advance(s);
   int64_t i0 = p->boundary == ORC_BC_PERIODIC ? 0 : 1;
   double work = 0.0;
   for (int64_t i = i0; i < s->nnode; ++i) {
     double En = s->E[i];
     s->E[i] = En + (dt * jm - s->D[i]);
+    if (p->em) s->E[i] += s->Jv[i];
     work += 0.5 * (En + s->E[i]);
   }
   if (p->boundary != ORC_BC_PERIODIC) s->E[0] = 0.0;
@@ -1100,9 +1215,14 @@ double orc_gauss_residual(const orc_sim *s, double *max_abs_E) {
   if (P > 0) binomial_smooth(Q, p->nx, P, p->boundary == ORC_BC_PERIODIC ? ORC_EXT_PERIODIC : ORC_EXT_CELL_ODD);
   int64_t c_lo = p->boundary == ORC_BC_PERIODIC ? 0 : 1 + P;
   int64_t c_hi = p->boundary == ORC_BC_PERIODIC ? p->nx - 1 : p->nx - 2 - P;
+  /* with transverse fields: the virtual charge -beta_y dB_z + beta_z dB_y
+   * joins eta_co; the layer's damping of B breaks that balance inside it */
+  if (p->em && p->boundary != ORC_BC_PERIODIC && p->pml_cells > 0 && c_hi > p->nx - p->pml_cells - 1)
+    c_hi = p->nx - p->pml_cells - 1;
   for (int64_t c = c_lo; c <= c_hi; ++c) {
     int64_t c1 = p->boundary == ORC_BC_PERIODIC ? imod(c + 1, p->nx) : c + 1;
     double res = (s->E[c1] - s->E[c]) - Q[c];
+    if (p->em) res -= p->beta_y * (s->Bz[c1] - s->Bz[c]) - p->beta_z * (s->By[c1] - s->By[c]);
     if (fabs(res) > r) r = fabs(res);
   }
   for (int64_t i = 0; i < s->nnode; ++i) if (fabs(s->E[i]) > em) em = fabs(s->E[i]);
