@@ -137,6 +137,26 @@ typedef struct gap_params {
                             filter).  Needs the FP64 state and cap = 0, else
                             GAP_EINVAL */
   double m_ion;          /* proton mass in m_e (0 -> 1836) */
+  int32_t em;            /* 1: transverse fields E_y, E_z (cells, half steps) and B_y,
+                            B_z (nodes, whole steps) of App. A's co-rotating frame in
+                            the 1D reduction: a Yee leapfrog driven by the virtual
+                            current jv = -{curl(beta x E) + beta x curl E
+                            - curl[beta x (beta x B)]} (particles move along B_* and
+                            carry no transverse current); jv_h joins the Ampere step
+                            of E_h and the virtual charge -beta_y dB_z/dh +
+                            beta_z dB_y/dh joins Gauss's law.  The star is a
+                            conductor.  The gap's Ampere step runs after the push.
+                            0 or 1, else GAP_EINVAL */
+  int32_t pml_cells;     /* em on a surface gap: an absorbing layer of this many cells
+                            below the top (a conductor behind it): matched electric
+                            and magnetic conductivity sigma_max ((X - X_p)/pml_cells)^3
+                            above X_p = nx - pml_cells (Sect. 6.1: escaping fields are
+                            damped).  0 = none (the top is a bare conductor);
+                            0 <= pml_cells <= nx/2, else GAP_EINVAL */
+  double beta_y, beta_z; /* velocity of the co-rotating frame across h (App. A; the
+                            paper's 3e-6); |beta| < 1, zero unless em */
+  double pml_sigma;      /* sigma_max in omega_p; 0 -> 4 ln(1e6) / (2 pml_cells dx), a
+                            continuum reflection of 1e-6 */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */
@@ -218,6 +238,19 @@ int gap_diag(gap_handle *h, int32_t gap, gap_diag_out *out, double *host_spectru
 /* Copy E of gap `gap` (nnode = nx+1 surface, nx periodic values). */
 int gap_get_field(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream);
 int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, void *stream);
+
+/* Transverse fields of a gap with em = 1 (App. A): component GAP_EM_EY or
+   GAP_EM_EZ (nx cell values, at step - 1/2 after `step` steps), GAP_EM_BY or
+   GAP_EM_BZ (nnode node values, at the step).  `n` must be at least the
+   component's length; a gap without em, a bad component or a short buffer
+   returns GAP_EINVAL.  Synchronises the stream.  Setting writes the values the
+   next step starts from. */
+#define GAP_EM_EY 0
+#define GAP_EM_EZ 1
+#define GAP_EM_BY 2
+#define GAP_EM_BZ 3
+int gap_get_em(gap_handle *h, int32_t gap, int32_t component, double *host_dst, int64_t n, void *stream);
+int gap_set_em(gap_handle *h, int32_t gap, int32_t component, const double *host_src, int64_t n, void *stream);
 
 /* Export the particles of one kind of one gap, in arbitrary order, as FP64:
  * X is the absolute position in cells, u = gamma beta (photons: x, the

@@ -12,6 +12,7 @@ GAP_FP64_PLAIN, GAP_FP32_STATE = 0, 1
 GAP_BC_SURFACE, GAP_BC_PERIODIC = 0, 1
 GAP_INIT_EMPTY, GAP_INIT_COLD, GAP_INIT_PAIR_THERMAL, GAP_INIT_GAP_PROTONS = 0, 1, 2, 3
 GAP_ELECTRON, GAP_POSITRON, GAP_PHOTON, GAP_PROTON = 0, 1, 2, 3
+GAP_EM_EY, GAP_EM_EZ, GAP_EM_BY, GAP_EM_BZ = 0, 1, 2, 3
 
 
 class GapParams(C.Structure):
@@ -25,6 +26,8 @@ class GapParams(C.Structure):
         ("kmax_emit", C.c_int32), ("kmax_inject", C.c_int32), ("gap_index", C.c_int32),
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
         ("protons", C.c_int32), ("m_ion", C.c_double),
+        ("em", C.c_int32), ("pml_cells", C.c_int32), ("beta_y", C.c_double), ("beta_z", C.c_double),
+        ("pml_sigma", C.c_double),
     ]
 
 
@@ -78,6 +81,8 @@ def lib():
     L.gap_diag.argtypes = [vp, i32, C.POINTER(GapDiagOut), vp, i64, vp, vp]
     L.gap_get_field.argtypes = [vp, i32, vp, i64, vp]
     L.gap_set_field.argtypes = [vp, i32, vp, i64, vp]
+    L.gap_get_em.argtypes = [vp, i32, i32, vp, i64, vp]
+    L.gap_set_em.argtypes = [vp, i32, i32, vp, i64, vp]
     L.gap_get_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_sample_particles.argtypes = [vp, i32, i32, i64, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_add_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
@@ -109,7 +114,7 @@ def lib():
 
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
-            "gap_get_field", "gap_set_field", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
+            "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
             "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 

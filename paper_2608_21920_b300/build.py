@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libgap.so")
-SOURCES = ["api.cu", "step.cu", "init.cu", "merge.cu", "filter.cu", "photons.cu", "ode.cu", "spectrum_noalloc.cu"]
+SOURCES = ["api.cu", "step.cu", "init.cu", "merge.cu", "filter.cu", "em.cu", "photons.cu", "ode.cu", "spectrum_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -107,6 +107,14 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.init == GAP_INIT_GAP_PROTONS && (!q.protons || q.boundary != GAP_BC_SURFACE))
       { msg = "the proton start needs protons and a surface gap"; return GAP_EINVAL; }
     if (q.m_ion < 0.0) { msg = "m_ion must be >= 0"; return GAP_EINVAL; }
+    if (q.em != 0 && q.em != 1) { msg = "em must be 0 or 1"; return GAP_EINVAL; }
+    if (!std::isfinite(q.beta_y) || !std::isfinite(q.beta_z) || !(q.beta_y * q.beta_y + q.beta_z * q.beta_z < 1.0))
+      { msg = "beta must be finite with |beta| < 1"; return GAP_EINVAL; }
+    if (!q.em && (q.beta_y != 0.0 || q.beta_z != 0.0 || q.pml_cells != 0))
+      { msg = "beta and pml_cells need em = 1"; return GAP_EINVAL; }
+    if (q.pml_cells < 0 || (q.pml_cells > 0 && (q.boundary != GAP_BC_SURFACE || 2 * (int64_t)q.pml_cells > q.nx)))
+      { msg = "pml_cells must be in [0, nx/2], on a surface gap"; return GAP_EINVAL; }
+    if (!(q.pml_sigma >= 0.0) || !std::isfinite(q.pml_sigma)) { msg = "pml_sigma must be >= 0"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -306,6 +314,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
   bool qed_any = false, surface_any = false, merge_any = false, filter_any = false, qs_any = false, pr_any = false;
+  bool em_any = false;
   int64_t pr_need = 0;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
@@ -347,7 +356,14 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.filter_passes = q.filter_passes;
     g.protons = q.protons;
     g.m_ion = q.m_ion > 0.0 ? q.m_ion : 1836.0;
-    g.defer = q.filter_passes > 0 || q.protons ? 1 : 0;
+    g.em = q.em;
+    g.pml_cells = q.em ? q.pml_cells : 0;
+    g.beta_y = q.beta_y;
+    g.beta_z = q.beta_z;
+    g.pml_smax = g.pml_cells <= 0 ? 0.0
+                 : (q.pml_sigma > 0.0 ? q.pml_sigma : 4.0 * std::log(1e6) / (2.0 * (double)g.pml_cells * q.dx));
+    em_any |= q.em != 0;
+    g.defer = q.filter_passes > 0 || q.protons || q.em ? 1 : 0;
     filter_any |= g.defer != 0;
     pr_any |= q.protons != 0;
     if (q.protons) pr_need += 2 * q.nx * std::max<int64_t>(q.ppc, 1) + 65536;
@@ -424,6 +440,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.merge_any = merge_any ? 1 : 0;
   v.filter_any = filter_any ? 1 : 0;
   v.pr_any = pr_any ? 1 : 0;
+  v.em_any = em_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
   v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
@@ -474,6 +491,14 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.dcharge = C.take<unsigned long long>(dchg);
   v.dcharge_len = dchg;
   v.Dflt = C.take<double>(filter_any ? 2 * (size_t)dchg : 0);
+  {  // transverse fields: zero at start (part of the cleared metadata)
+    const size_t ne = em_any ? (size_t)total_nodes : 0;
+    v.em_Ey = C.take<double>(ne);
+    v.em_Ez = C.take<double>(ne);
+    v.em_By = C.take<double>(ne);
+    v.em_Bz = C.take<double>(ne);
+    v.em_Jv = C.take<double>(ne);
+  }
   v.fft[0] = C.take<double>(2 * (size_t)max_P);
   v.fft[1] = C.take<double>(2 * (size_t)max_P);
   v.dred = C.take<double>(32);
@@ -781,6 +806,41 @@ int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, v
     e = cudaMemcpyAsync(h->v.E[b] + g.node_off, host_E, sizeof(double) * g.nnode, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_check(h, e, "set field");
+}
+
+static int em_component(gap_handle *h, int32_t gap, int32_t component, int64_t n, double **dev, int64_t *len) {
+  if (!h || gap < 0 || gap >= h->n_gaps || component < GAP_EM_EY || component > GAP_EM_BZ) return GAP_EINVAL;
+  const GapDev &g = h->gaps_h[gap];
+  if (!g.em) return GAP_EINVAL;
+  *len = component <= GAP_EM_EZ ? g.nx : g.nnode;
+  if (n < *len) return GAP_EINVAL;
+  double *base[4] = {h->v.em_Ey, h->v.em_Ez, h->v.em_By, h->v.em_Bz};
+  *dev = base[component] + g.node_off;
+  return GAP_OK;
+}
+
+int gap_get_em(gap_handle *h, int32_t gap, int32_t component, double *host_dst, int64_t n, void *stream) {
+  double *dev = nullptr;
+  int64_t len = 0;
+  if (!host_dst) return GAP_EINVAL;
+  int r = em_component(h, gap, component, n, &dev, &len);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host_dst, dev, sizeof(double) * (size_t)len, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "get em");
+}
+
+int gap_set_em(gap_handle *h, int32_t gap, int32_t component, const double *host_src, int64_t n, void *stream) {
+  double *dev = nullptr;
+  int64_t len = 0;
+  if (!host_src) return GAP_EINVAL;
+  int r = em_component(h, gap, component, n, &dev, &len);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dev, host_src, sizeof(double) * (size_t)len, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "set em");
 }
 
 int gap_solve_gauss(gap_handle *h, int32_t set_background, void *stream) {

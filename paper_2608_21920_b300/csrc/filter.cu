@@ -15,7 +15,8 @@
 // and residual is mirrored oddly about the same nodes (init.cu), the pairing
 // under which smoothing commutes with the node-to-cell difference, so Gauss's
 // law holds for the smoothed charge.  Both kernels touch only gaps that defer
-// Ampere (filter_passes > 0, or protons: zero passes, the update alone), and
+// Ampere (filter_passes > 0, or protons or transverse fields: zero passes,
+// the update alone, plus dt jv_h of the transverse fields), and
 // the tiles of a gap cover its nodes k0 .. k0 + nk - 1 without overlap.
 #include <algorithm>
 
@@ -175,7 +176,8 @@ __global__ void __launch_bounds__(256) k_filter_apply(View v, int mode) {
         const double sd = sm.value(P + i, P, coef, scale);
         if (mode == 0) {
           const double eo = Eo[node];
-          const double en = (!periodic && node == 0) ? 0.0 : eo + (djm - sd);
+          double en = (!periodic && node == 0) ? 0.0 : eo + (djm - sd);
+          if (g.em && (periodic || node > 0)) en += v.em_Jv[g.node_off + node];  // dt jv_h (em.cu)
           En[node] = en;
           work += eo + en;
         } else if (periodic || node > 0) {

@@ -83,6 +83,10 @@ struct GapDev {
   int32_t protons;        // 1: a proton store and proton supply (FP64 state)
   int32_t defer;          // Ampere left to filter.cu (a current filter, or protons)
   double m_ion;           // proton mass in m_e
+  int32_t em;             // 1: transverse fields of the co-rotating frame (em.cu)
+  int32_t pml_cells;      // absorbing layer below the top of a surface gap; 0 = none
+  double beta_y, beta_z;  // velocity of the co-rotating frame across h
+  double pml_smax;        // peak conductivity of the layer (omega_p)
 };
 
 struct TileDev {
@@ -119,6 +123,10 @@ struct View {
   double *pr_X, *pr_u, *pr_w;
   uint64_t *pr_id;
   int32_t *pr_gap, *pr_alive;
+  // transverse fields (some gap with em), indexed like the nodes (node_off):
+  // E_y, E_z on cells c < nx, B_y, B_z on nodes; Jv = dt jv_h of this step
+  int32_t em_any, em_pad;
+  double *em_Ey, *em_Ez, *em_By, *em_Bz, *em_Jv;
   double *Dflt;               // [2 x dcharge_len] smoothing scratch (node flux; two cell buffers)
   // quantum photon spectrum (some gap with qed_quantum): per row of ln chi,
   // the normalised survival S(s)/S(0) and its s-derivative on kQsNodes nodes

@@ -453,11 +453,16 @@ __global__ void __launch_bounds__(1024) k_reduce(View v, int gap) {
     Qs = filter_cells_block(A, B, nx, P, g.periodic != 0);
   }
   double gr = 0.0;
-  const int64_t clo = g.periodic ? 0 : 1 + P, chi = g.periodic ? nx - 1 : nx - 2 - P;
+  int64_t clo = g.periodic ? 0 : 1 + P, chi = g.periodic ? nx - 1 : nx - 2 - P;
+  // transverse fields: the virtual charge -beta_y dB_z + beta_z dB_y joins
+  // eta_co; the absorbing layer's damping of B breaks that balance inside it
+  if (g.em && !g.periodic && g.pml_cells > 0 && chi > nx - g.pml_cells - 1) chi = nx - g.pml_cells - 1;
+  const double *By = v.em_By + g.node_off, *Bz = v.em_Bz + g.node_off;
   for (int64_t c = clo + threadIdx.x; c <= chi; c += blockDim.x) {
     const int64_t c1 = g.periodic ? (c + 1) % nx : c + 1;
     const double q = Qs ? Qs[c] : charge_value(v, g, v.dcharge[c]) - g.eta_bg * g.dx;
-    const double r = (E[c1] - E[c]) - q;
+    double r = (E[c1] - E[c]) - q;
+    if (g.em) r -= g.beta_y * (Bz[c1] - Bz[c]) - g.beta_z * (By[c1] - By[c]);
     gr = fmax(gr, fabs(r));
   }
   sv[threadIdx.x] = emin;

@@ -19,6 +19,7 @@ int launches_per_step(const View &v);
 void launch_rebin(const View &v, double slack, cudaStream_t st);
 void launch_merge(const View &v, cudaStream_t st);
 void launch_filter(const View &v, int mode, cudaStream_t st);
+void launch_em(const View &v, cudaStream_t st);
 void launch_load_protons(const View &v, int gap, int64_t n, cudaStream_t st);
 void launch_export_protons(const View &v, int gap, double *stage, int64_t cap, unsigned long long *count,
                            int64_t stride, cudaStream_t st);

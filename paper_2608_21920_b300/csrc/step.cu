@@ -707,9 +707,10 @@ __global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.filter_passes > 0) {
-    // a gap with a current filter: every node's flux goes to the global
-    // accumulators (k_push units) and k_filter_apply finishes E
+  if (g.defer) {
+    // a gap that defers Ampere (current filter, transverse fields): every
+    // node's flux goes to the global accumulators (k_push units) and
+    // k_filter_apply finishes E
     for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
       const long long c = node_sum(i);
       if (c == 0) continue;
@@ -1055,9 +1056,10 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.filter_passes > 0) {
-    // a gap with a current filter: every node's flux goes to the global
-    // accumulators (k_push units) and k_filter_apply finishes E
+  if (g.defer) {
+    // a gap that defers Ampere (current filter, transverse fields): every
+    // node's flux goes to the global accumulators (k_push units) and
+    // k_filter_apply finishes E
     for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
       const long long c = node_sum(i);
       if (c == 0) continue;
@@ -1682,7 +1684,8 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       }
       default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
     }
-    launch_filter(v, 0, st);  // Ampere of the gaps with a current filter
+    launch_em(v, st);         // transverse fields, before E_h moves on
+    launch_filter(v, 0, st);  // Ampere of the gaps that defer it
     return;
   }
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
@@ -1700,6 +1703,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       k_push<R, false, false><<<grid, threads, smem, st>>>(v);
   }
   if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons (FP64 state)
+  launch_em(v, st);  // transverse fields, before E_h moves on
   launch_filter(v, 0, st);  // Ampere of the gaps that defer it (current filter, protons)
 }
 
@@ -1741,7 +1745,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
   return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
-         (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0) + (v.pr_any ? 1 : 0);
+         (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0) + (v.pr_any ? 1 : 0) + (v.em_any ? 2 : 0);
 }
 
 void launch_sync_used(const View &v, cudaStream_t st) {

@@ -18,7 +18,8 @@ PARAM_DEFAULTS = dict(
     alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0, gap_length=0.0,
     density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0, nx=64, ppc=0, cap=0, seed=0,
     qed=0, boundary=A.GAP_BC_SURFACE, init=A.GAP_INIT_EMPTY, kmax_emit=16, kmax_inject=64,
-    gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0)
+    gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0,
+    em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0)
 
 PRECISION = {"fp64": A.GAP_FP64_PLAIN, "fp32": A.GAP_FP32_STATE}
 
@@ -168,6 +169,23 @@ class Gap:
     def set_field(self, E, gap: int = 0):
         E = np.ascontiguousarray(E, dtype=np.float64)
         A.check(A.lib().gap_set_field(self._h, gap, _ptr(E), E.size, self.stream()), self._h, "gap_set_field")
+
+    def em(self, gap: int = 0):
+        """Transverse fields of an em = 1 gap: (E_y, E_z) on the nx cells at
+        the half step before the current one, (B_y, B_z) on the nodes."""
+        nx = int(self.param_dicts[gap]["nx"])
+        out = []
+        for comp, n in ((A.GAP_EM_EY, nx), (A.GAP_EM_EZ, nx), (A.GAP_EM_BY, self.nnode(gap)),
+                        (A.GAP_EM_BZ, self.nnode(gap))):
+            a = np.empty(n)
+            A.check(A.lib().gap_get_em(self._h, gap, comp, _ptr(a), n, self.stream()), self._h, "gap_get_em")
+            out.append(a)
+        return tuple(out)
+
+    def set_em(self, Ey, Ez, By, Bz, gap: int = 0):
+        for comp, f in ((A.GAP_EM_EY, Ey), (A.GAP_EM_EZ, Ez), (A.GAP_EM_BY, By), (A.GAP_EM_BZ, Bz)):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            A.check(A.lib().gap_set_em(self._h, gap, comp, _ptr(f), f.size, self.stream()), self._h, "gap_set_em")
 
     def solve_gauss(self, set_background: bool = True):
         A.check(A.lib().gap_solve_gauss(self._h, int(set_background), self.stream()), self._h, "gap_solve_gauss")
