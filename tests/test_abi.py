@@ -52,3 +52,36 @@ def test_product_path_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("CPU oracle", ""), f
+
+
+def test_option_checks_and_em_layout_without_gpu():
+    """Host-side validation of the transverse-field and proton options, and
+    the five FP64 node arrays (E_y, E_z, B_y, B_z, dt jv_h) the fields add."""
+    from paper_2608_21920_b300 import _abi as A
+    from paper_2608_21920_b300.gap import make_params
+    L = A.lib()
+    n = C.c_size_t(0)
+    f64 = A.GapConfig(precision=A.GAP_FP64_PLAIN, tile=64)
+    f32 = A.GapConfig(precision=A.GAP_FP32_STATE, tile=64)
+
+    def code(cfg=f64, **kw):
+        p = make_params(**dict(dict(nx=512, ppc=4, init=A.GAP_INIT_COLD), **kw))
+        return L.gap_workspace_bytes(C.byref(p), 1, C.byref(cfg), C.byref(n))
+
+    good = [dict(em=1), dict(em=1, beta_y=3e-6), dict(em=1, beta_y=0.6, beta_z=0.7), dict(em=1, pml_cells=16),
+            dict(em=1, pml_cells=256, pml_sigma=5.0), dict(protons=1), dict(protons=1, init=A.GAP_INIT_GAP_PROTONS)]
+    bad = [dict(beta_y=1e-3), dict(pml_cells=4), dict(em=1, beta_y=0.8, beta_z=0.6), dict(em=1, beta_z=float("inf")),
+           dict(em=1, pml_cells=257), dict(em=1, pml_cells=-1), dict(em=3), dict(em=1, pml_cells=8, pml_sigma=-2.0),
+           dict(em=1, pml_cells=8, boundary=A.GAP_BC_PERIODIC, init=A.GAP_INIT_EMPTY, ppc=0),
+           dict(protons=2), dict(protons=1, cap=1000), dict(init=A.GAP_INIT_GAP_PROTONS),
+           dict(protons=1, init=A.GAP_INIT_GAP_PROTONS, boundary=A.GAP_BC_PERIODIC), dict(protons=1, m_ion=-1.0)]
+    for kw in good:
+        assert code(**kw) == A.GAP_OK, kw
+    for kw in bad:
+        assert code(**kw) == A.GAP_EINVAL, kw
+    assert code(f32, em=1, beta_y=0.1) == A.GAP_OK
+    assert code(f32, protons=1) == A.GAP_EINVAL  # protons need the FP64 state
+    assert code(nx=512) == A.GAP_OK
+    plain = n.value
+    assert code(nx=512, em=1) == A.GAP_OK
+    assert n.value - plain >= 5 * 8 * 513
