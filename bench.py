@@ -47,15 +47,24 @@ def set_size(nx):
     N_PARTICLES = 2 * NX * PPC
 WORKLOAD_NAME = ("cfg2 push+deposit roofline: Nx=2^20 periodic, 4.19e8 e+- (200+200 per cell, "
                  "0.5 n_co each), Maxwell-Juttner theta=0.1, 1e-3 Langmuir seed, QED off")
-SETUP = {"filter_passes": 0, "inject_theta": 0.0, "qed_quantum": 0}  # options (off for the headline)
+SETUP = {"filter_passes": 0, "inject_theta": 0.0, "qed_quantum": 0, "em": 0, "beta_y": 0.0}  # off for the headline
+BETA_ROT = 3e-6  # the co-rotating frame's velocity in Sect. 6.1
+PML_CELLS = 16   # absorbing layer below the top of the batch's surface gaps
 
 
-def set_setup(filter_passes, inject_theta, qed_quantum=0):
-    """Sect. 6.1's binomial current filter and hot atmosphere, and the quantum
-    photon spectrum, applied to the workloads (the atmosphere and the
-    spectrum only matter for the QED surface gaps of the batch)."""
+def set_setup(filter_passes, inject_theta, qed_quantum=0, em=0):
+    """Sect. 6.1's binomial current filter and hot atmosphere, the quantum
+    photon spectrum, and the transverse fields of the co-rotating frame
+    (App. A), applied to the workloads (the atmosphere and the spectrum only
+    matter for the QED surface gaps of the batch; the absorbing layer only
+    for surface gaps)."""
     global WORKLOAD_NAME, BATCH_NAME
-    SETUP.update(filter_passes=filter_passes, inject_theta=inject_theta, qed_quantum=qed_quantum)
+    SETUP.update(filter_passes=filter_passes, inject_theta=inject_theta, qed_quantum=qed_quantum,
+                 em=1 if em else 0, beta_y=BETA_ROT if em else 0.0)
+    if em:
+        WORKLOAD.update(em=1, beta_y=BETA_ROT)
+        WORKLOAD_NAME += f", transverse fields of the co-rotating frame (beta={BETA_ROT:g})"
+        BATCH_NAME += f", transverse fields (beta={BETA_ROT:g}, {PML_CELLS}-cell absorbing layer)"
     if qed_quantum:
         BATCH_NAME += ", quantum photon spectrum"
     if filter_passes:
@@ -265,6 +274,7 @@ def run_ours(args):
     bpp = BYTES_PER_PARTICLE["fp32"]
     achieved = bpp * N_PARTICLES / (r32["push_ms"] / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
+    deferred = bool(SETUP["filter_passes"] or SETUP["em"])  # the push hands Ampere to k_filter_apply
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": r32["K"],
         "warmup": args.warmup, "ms_per_step": r32["ms"] / r32["K"], "higher_is_better": True,
@@ -275,10 +285,11 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "kernel": ("k_push_lean (FP32, no QED, uniform weights)" if not SETUP["filter_passes"] else
-                                "k_push (FP32 generic, no QED) + k_flux_take + k_filter_apply"),
+                     "kernel": ("k_push_lean (FP32, no QED, uniform weights)" if not deferred else
+                                "k_push_lean (FP32, Ampere deferred) + k_flux_take + k_filter_apply"
+                                + (" + k_em_cells + k_em_nodes" if SETUP["em"] else "")),
                      "bytes_per_particle": bpp, "push_ms_per_launch": r32["push_ms"],
-                     "traffic": traffic_record("k_push", "fp32") if not SETUP["filter_passes"] else None},
+                     "traffic": traffic_record("k_push", "fp32") if not deferred else None},
         "gpu_launches": int(r32["launches"]),
         "clocks": r32["clocks"],
         "gauss_residual": r32["gauss"], "E_abs_max": r32["E_abs_max"],
@@ -312,7 +323,7 @@ def _oracle_sample(nx, steps, warmup):
     import oracle as O
     s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
               init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0,
-              filter_passes=SETUP["filter_passes"])
+              filter_passes=SETUP["filter_passes"], em=SETUP["em"], beta_y=SETUP["beta_y"])
     if warmup:
         s.step(warmup)
     t0 = time.perf_counter()
@@ -356,7 +367,7 @@ def run_reference(args):
     import oracle as O
     s = O.Sim(nx=nx, ppc=PPC, dx=0.1, dt=0.045, theta=0.1, seed_amp=1e-3, density=1.0,
               init=O.INIT_PAIR_THERMAL, boundary=O.BC_PERIODIC, seed=0,
-              filter_passes=SETUP["filter_passes"])
+              filter_passes=SETUP["filter_passes"], em=SETUP["em"], beta_y=SETUP["beta_y"])
     s.step(args.warmup)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -395,6 +406,10 @@ def run_batch(args):
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
     params = [dict(p, **SETUP) for p in workloads.batch(args.gaps)]
+    if SETUP["em"]:
+        for p in params:
+            if p.get("boundary", 0) == 0:  # surface gap
+                p["pml_cells"] = PML_CELLS
     peaks, peak_kind = measured_peaks()
     tuned = None
     tile, threads, rebin = args.tile if args.tile != 256 else 128, args.threads, args.rebin_every or 64
@@ -492,12 +507,15 @@ def main():
                     help="binomial current-filter passes per step (Sect. 6.1 uses 8; 0: off)")
     ap.add_argument("--inject-theta", type=float, default=0.0,
                     help="batch: temperature of the surface atmosphere (Sect. 6.1 uses 0.3; 0: cold)")
+    ap.add_argument("--em", action="store_true",
+                    help="transverse fields of the co-rotating frame (App. A) at beta 3e-6; surface gaps "
+                         "get a 16-cell absorbing layer (default: off)")
     ap.add_argument("--qed-quantum", action="store_true",
                     help="batch: photon energies from the quantum spectrum (default: classical shape)")
     args = ap.parse_args()
     if args.nx:
         set_size(args.nx)
-    set_setup(args.filter_passes, args.inject_theta, 1 if args.qed_quantum else 0)
+    set_setup(args.filter_passes, args.inject_theta, 1 if args.qed_quantum else 0, 1 if args.em else 0)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
