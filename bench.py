@@ -398,18 +398,26 @@ def _total_leptons(g):
     return n
 
 
-def run_batch(args):
-    """The batched parameter sweep: all gaps advance together, one launch per
-    kernel per step, replayed from CUDA graphs of `--graph-chunk` steps."""
-    import torch
-    from paper_2608_21920_b300 import Gap, autotune, workloads
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
-    params = [dict(p, **SETUP) for p in workloads.batch(args.gaps)]
+def batch_params(n_gaps):
+    """The batch workload's gap parameters with the options of SETUP (the
+    absorbing layer only on surface gaps)."""
+    from paper_2608_21920_b300 import workloads
+    params = [dict(p, **SETUP) for p in workloads.batch(n_gaps)]
     if SETUP["em"]:
         for p in params:
             if p.get("boundary", 0) == 0:  # surface gap
                 p["pml_cells"] = PML_CELLS
+    return params
+
+
+def run_batch(args):
+    """The batched parameter sweep: all gaps advance together, one launch per
+    kernel per step, replayed from CUDA graphs of `--graph-chunk` steps."""
+    import torch
+    from paper_2608_21920_b300 import Gap, autotune
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    params = batch_params(args.gaps)
     peaks, peak_kind = measured_peaks()
     tuned = None
     tile, threads, rebin = args.tile if args.tile != 256 else 128, args.threads, args.rebin_every or 64
