@@ -131,8 +131,9 @@ def test_rotation_about_h_rotates_the_transverse_fields():
 
 def test_gauss_law_with_the_virtual_charge():
     """d E_h = eta - eta_co - beta_y d B_z + beta_z d B_y holds to round-off
-    while jv_h visibly moves E_h (beta = 0.3), and in a filtered QED
-    discharge at a surface with an absorbing layer (outside the layer)."""
+    while jv_h visibly moves E_h (beta = 0.3), in a filtered QED discharge
+    at a surface with an absorbing layer (outside the layer), and through the
+    merges of a capped one."""
     a = _pair_plasma(beta_y=0.2, beta_z=0.2)
     c = _pair_plasma()
     a.step(150)
@@ -148,6 +149,11 @@ def test_gauss_law_with_the_virtual_charge():
     r, emax = s.gauss_residual()
     assert r < 1e-13 * max(1.0, emax)
     assert np.abs(s.em()[0]).max() > 1e-4
+    # through merges under a cap (their re-centring flux reaches E_h), oblique beta
+    s = O.Sim(**dict(cfg, filter_passes=0, inject_theta=0.0, beta_y=0.05, beta_z=0.03, cap=450))
+    s.step(900)
+    r, emax = s.gauss_residual()
+    assert s.counters()["merged"] > 0 and r < 1e-13 * max(1.0, emax)
 
 
 def _pml_run(nx, pml, n):
