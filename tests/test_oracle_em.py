@@ -216,3 +216,25 @@ def test_discharge_field_spectrum_and_transverse_level():
     assert -2.7 < slope < -1.7, slope
     assert 1e-7 < np.median(ratios) < 1e-5, np.median(ratios)
     assert 1e-3 < max(osc) < 1e-1, max(osc)
+
+
+def test_the_papers_full_setup_keeps_gauss_law():
+    """Every option of Sect. 6.1 at once: the start with protons (the linear
+    ramp), QED, the 8-pass current filter, the T = 0.3 atmosphere, the
+    co-rotating frame at beta = 3e-6 with an absorbing layer.  Gauss's law
+    (smoothed charge with protons, virtual charge) holds to round-off over a
+    discharge, and E_y stays of order beta E_h."""
+    cfg = dict(nx=256, ppc=4, dx=0.1, dt=0.045, alpha=2.0, b=0.1, qed=1, lambda_hat=2e-4, rho_hat=10.0,
+               rate_mult=5.0, init=O.INIT_GAP_PROTONS, boundary=O.BC_SURFACE, seed=3, protons=1, filter_passes=8,
+               inject_theta=0.3, em=1, beta_y=3e-6, pml_cells=32)
+    s = O.Sim(**cfg)
+    r, emax = s.gauss_residual()
+    assert r < 1e-13 * max(1.0, emax)
+    s.step(1500)
+    c = s.counters()
+    assert c["pairs"] > 1000 and c["injected"] > 0
+    assert (s.leptons()["heavy"] == 1).sum() > 100
+    r, emax = s.gauss_residual()
+    assert r < 1e-12 * max(1.0, emax)
+    ratio = np.abs(s.em()[0]).max() / emax
+    assert 1e-7 < ratio < 1e-4, ratio
