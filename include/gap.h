@@ -284,7 +284,9 @@ int gap_add_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t n, const
 
 /* Recompute E of every gap from Gauss's law (Sect. 2.2): E_0 = 0 at the
  * surface, zero mean for periodic gaps; the periodic background eta_bg is
- * set to the mean charge density when set_background is nonzero. */
+ * set to the mean charge density when set_background is nonzero.  The
+ * virtual charge of a gap with em (its B_y, B_z term) is not included: it is
+ * zero while the transverse B is, as at the start. */
 int gap_solve_gauss(gap_handle *h, int32_t set_background, void *stream);
 
 /* Override the Gauss background eta_bg of a gap (default: -1 at a surface). */
