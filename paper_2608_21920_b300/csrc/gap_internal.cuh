@@ -240,15 +240,35 @@ __device__ __forceinline__ double mj_bmax(double theta) {
   return us * exp(-(gs - 1.0) / (2.0 * theta));
 }
 
-// The draw with bmax given (a loader forms it once).  The bounds
-// 1 - 1/a <= ln a <= a - 1 settle about 70 % of the rounds without the
-// logarithm; only where a bound lies within a relative 1e-12 of the
-// threshold is ln a taken, so every decision is the one the logarithm gives.
+// The draw with bmax given (a loader forms it once).  Each round's test
+// 2 ln a <= -(gamma - 1)/theta is first evaluated in float (u = v/a,
+// gamma - 1 = u^2/(sqrt(1 + u^2) + 1), logf): it decides only when its two
+// sides differ by more than 4e-6 (|lhs| + |rhs|) + 1e-6, about four times
+// their float rounding (a few ulp each, the ulp of logf and the rounding of
+// a to float included), so every decision it takes is the FP64 one; it
+// settles all but about 1e-5 of the rounds, and FP64 is left with the
+// accepted round's u = v/a.  The rest go to the FP64 test: the bounds
+// 1 - 1/a <= ln a <= a - 1, and ln a itself only where a bound lies within
+// a relative 1e-12 of the threshold, so every decision is the one the
+// logarithm gives.
 __device__ __noinline__ static double mj_draw_b(uint64_t seed, uint64_t id, uint32_t step, uint32_t channel,
                                                 double theta, double bmax, bool &ok) {
+  const float inv_theta_f = 1.0f / (float)theta;
   for (uint32_t r = 0; r < 64; ++r) {
     const double a = uniform53(seed, id, step, channel, 2 * r);
     const double vv = bmax * (2.0 * uniform53(seed, id, step, channel, 2 * r + 1) - 1.0);
+    {
+      const float af = (float)a, uf = (float)vv / af;
+      const float u2 = uf * uf;
+      const float rf = -(u2 / (sqrtf(1.0f + u2) + 1.0f)) * inv_theta_f;
+      const float lf = 2.0f * logf(af);
+      const float m = 4e-6f * (fabsf(rf) + fabsf(lf)) + 1e-6f;
+      if (lf <= rf - m) {
+        ok = true;
+        return vv / a;
+      }
+      if (lf > rf + m) continue;
+    }
     const double u = vv / a;
     const double gm1 = u * u / (sqrt(1.0 + u * u) + 1.0);
     const double rhs = -gm1 / theta;
