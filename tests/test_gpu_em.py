@@ -226,3 +226,33 @@ def test_em_full_setup_parity():
         P.compare_leptons(pg, p_o, RTOL64, f"protons step {n}")
         assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_em_discharge_statements_of_sect_6_6(precision):
+    """The three Sect. 6.6 statements the oracle checks on config 1 at
+    beta = 3e-6, measured on the CUDA path's own fields: oscillations
+    delta E_h / E_rot ~ 1e-2, |E_h(k)|^2 ~ k^-2, E_y ~ 1e-6 E_h."""
+    from paper_2608_21920_b300 import Gap
+    cfg = dict(P.CONFIG1, em=1, beta_y=3e-6, pml_cells=32)
+    g = Gap(P.gpu_params(cfg), precision=precision, tile=64)
+    Hc = int(0.8 * cfg["nx"])
+    E_rot = 0.8 * cfg["nx"] * cfg["dx"]
+    ratios, spec, osc = [], [], []
+    w = np.hanning(Hc)
+    for blk in range(40):
+        g.step(100)
+        E, Ey = g.field()[:Hc], g.em()[0][:Hc]
+        ratios.append(np.abs(Ey).max() / np.abs(E).max())
+        osc.append(np.abs((E - np.convolve(E, np.ones(16) / 16, mode="same"))[16:-16]).max() / E_rot)
+        if blk >= 20:
+            spec.append(np.abs(np.fft.rfft((E - E.mean()) * w)) ** 2)
+    assert g.diag(spectrum=False)["counters"]["pairs"] > 1000
+    S = np.mean(spec, axis=0)
+    k = np.arange(S.size)
+    band = (k >= 8) & (k <= 150)
+    slope = np.polyfit(np.log(k[band]), np.log(S[band]), 1)[0]
+    assert -2.7 < slope < -1.7, slope
+    assert 1e-7 < np.median(ratios) < 1e-5, np.median(ratios)
+    assert 1e-3 < max(osc) < 1e-1, max(osc)
+    g.close()
