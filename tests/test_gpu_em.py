@@ -163,3 +163,96 @@ def test_em_options_are_checked():
     with pytest.raises(GapError):
         g.em()
     g.close()
+
+
+def test_em_batch_mixed_with_plain_gaps_parity():
+    """A batch of four gaps: with and without the transverse fields, periodic
+    and surface; each gap against its own oracle at 1e-10."""
+    from paper_2608_21920_b300 import Gap
+    cfgs = [dict(PAIRS_EM, gap_index=0), dict(P.THERMAL_PAIRS, gap_index=1, seed=1),
+            dict(DISCHARGE_EM, gap_index=2, filter_passes=0), dict(DISCHARGE_EM, gap_index=3, em=0, beta_y=0.0,
+                                                                   pml_cells=0)]
+    batch = Gap([P.gpu_params(c) for c in cfgs], precision="fp64", tile=32)
+    oracles = [O.Sim(**{k: v for k, v in c.items() if k in O.DEFAULTS}) for c in cfgs]
+    batch.step(300)
+    for i, (c, o) in enumerate(zip(cfgs, oracles)):
+        o.step(300)
+        P.compare_field(batch.field(i), o.E(), RTOL64, f"gap {i}")
+        period = c["nx"] if c["boundary"] == O.BC_PERIODIC else None
+        P.compare_leptons(P.leptons_gpu(batch, i), P.leptons_oracle(o), RTOL64, f"gap {i}", period)
+        if c.get("em"):
+            for name, a, b in zip(("E_y", "E_z", "B_y", "B_z"), batch.em(i), o.em()):
+                if np.abs(b).max() > 0:
+                    P.compare_field(a, b, RTOL64, f"gap {i} {name}")
+    batch.close()
+
+
+def test_em_under_a_cap_parity():
+    """Merging under a macro-particle cap with the transverse fields (oblique
+    beta): fields, particles and counters at 1e-10 over 900 steps."""
+    cfg = dict(DISCHARGE_EM, filter_passes=0, inject_theta=0.0, beta_y=0.05, beta_z=0.03, cap=450)
+    g, o = _parity(cfg, [300, 900], tile=32)
+    assert o.counters()["merged"] > 0
+    g.close()
+
+
+def test_em_full_setup_parity():
+    """The paper's full set-up (start with protons, QED, 8-pass filter,
+    T = 0.3 atmosphere, beta = 3e-6 with a 32-cell layer), FP64: e+-,
+    protons, all fields and counters at 1e-10."""
+    cfg = dict(nx=256, ppc=4, dx=0.1, dt=0.045, alpha=2.0, b=0.1, qed=1, lambda_hat=2e-4, rho_hat=10.0,
+               rate_mult=5.0, init=O.INIT_GAP_PROTONS, boundary=O.BC_SURFACE, seed=3, protons=1, filter_passes=8,
+               inject_theta=0.3, em=1, beta_y=3e-6, pml_cells=32)
+    g, o = P.make_pair(cfg, "fp64", tile=32)
+    prev = 0
+    for n in (1, 400, 1000):
+        g.step(n - prev)
+        o.step(n - prev)
+        prev = n
+        d = g.diag(spectrum=False)
+        P.compare_counters(d["counters"], o.counters(), f"step {n}")
+        P.compare_field(g.field(), o.E(), RTOL64, f"E_h step {n}")
+        _compare_em(g, o, RTOL64, f"step {n}")
+        L = o.leptons()
+        order = np.argsort(L["id"], kind="stable")
+        L = {k: v[order] for k, v in L.items()}
+        e_o = {k: v[L["heavy"] == 0] for k, v in L.items()}
+        p_o = {k: v[L["heavy"] == 1] for k, v in L.items()}
+        P.compare_leptons(P.leptons_gpu(g), e_o, RTOL64, f"e+- step {n}")
+        pg = g.particles(3)
+        order = np.argsort(pg["id"], kind="stable")
+        pg = {k: v[order] for k, v in pg.items()}
+        pg["q"] = np.ones(pg["id"].size, np.int32)
+        P.compare_leptons(pg, p_o, RTOL64, f"protons step {n}")
+        assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_em_discharge_statements_of_sect_6_6(precision):
+    """The three Sect. 6.6 statements the oracle checks on config 1 at
+    beta = 3e-6, measured on the CUDA path's own fields: oscillations
+    delta E_h / E_rot ~ 1e-2, |E_h(k)|^2 ~ k^-2, E_y ~ 1e-6 E_h."""
+    from paper_2608_21920_b300 import Gap
+    cfg = dict(P.CONFIG1, em=1, beta_y=3e-6, pml_cells=32)
+    g = Gap(P.gpu_params(cfg), precision=precision, tile=64)
+    Hc = int(0.8 * cfg["nx"])
+    E_rot = 0.8 * cfg["nx"] * cfg["dx"]
+    ratios, spec, osc = [], [], []
+    w = np.hanning(Hc)
+    for blk in range(40):
+        g.step(100)
+        E, Ey = g.field()[:Hc], g.em()[0][:Hc]
+        ratios.append(np.abs(Ey).max() / np.abs(E).max())
+        osc.append(np.abs((E - np.convolve(E, np.ones(16) / 16, mode="same"))[16:-16]).max() / E_rot)
+        if blk >= 20:
+            spec.append(np.abs(np.fft.rfft((E - E.mean()) * w)) ** 2)
+    assert g.diag(spectrum=False)["counters"]["pairs"] > 1000
+    S = np.mean(spec, axis=0)
+    k = np.arange(S.size)
+    band = (k >= 8) & (k <= 150)
+    slope = np.polyfit(np.log(k[band]), np.log(S[band]), 1)[0]
+    assert -2.7 < slope < -1.7, slope
+    assert 1e-7 < np.median(ratios) < 1e-5, np.median(ratios)
+    assert 1e-3 < max(osc) < 1e-1, max(osc)
+    g.close()
