@@ -198,7 +198,10 @@ typedef struct gap_diag_out {
   double g3_peak;     /* <gamma^-3> at the peak cell */
   double M_split[4];  /* at the peak cell: e- up, e- down, e+ up, e+ down */
   double E_min, E_max;/* over gap nodes */
-  double gauss_residual; /* max |(E_{c+1}-E_c) - (Q_c - eta_bg dx)| over interior cells */
+  double gauss_residual; /* max |(E_{c+1}-E_c) - (Q_c - eta_bg dx)| over interior cells;
+                            Q smoothed like the current with a filter, the virtual
+                            charge included with em, cells in the absorbing layer left
+                            out */
   double E_abs_max;
   double field_energy, lepton_energy, photon_energy;
   int64_t spectrum_len; /* P/2 + 1 entries written to host_spectrum when given */

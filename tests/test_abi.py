@@ -86,3 +86,34 @@ def test_option_checks_and_em_layout_without_gpu():
     plain = n.value
     assert code(nx=512, em=1) == A.GAP_OK
     assert n.value - plain >= 5 * 8 * 513
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """gap.h compiles as strict C99, and the binding's ctypes structures have
+    the header's size and field offsets (a field out of order on either side
+    would shift every later field)."""
+    import shutil
+    import subprocess
+    from paper_2608_21920_b300 import _abi as A
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    STRUCTS = (("gap_params", A.GapParams), ("gap_config", A.GapConfig), ("gap_counters", A.GapCounters),
+               ("gap_diag_out", A.GapDiagOut))
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gap.h"', "int main(void) {"]
+    for ctype, st in STRUCTS:
+        lines.append(f'  printf("{ctype} size %zu\\n", sizeof({ctype}));')
+        for name, _ in st._fields_:
+            lines.append(f'  printf("{ctype} {name} %zu\\n", offsetof({ctype}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(t, n): int(v) for t, n, v in (l.split() for l in out if l)}
+    for ctype, st in STRUCTS:
+        assert got[(ctype, "size")] == C.sizeof(st), ctype
+        for name, _ in st._fields_:
+            assert got[(ctype, name)] == getattr(st, name).offset, (ctype, name)

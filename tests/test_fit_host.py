@@ -1,0 +1,89 @@
+"""fit.py's host logic on the CPU: the fit's integrator (the GPU kernels of
+ode.py) is replaced, inside this test only, by the oracle's torch RK4, so
+that the parameter mapping, the loss, the gradient path and the re-seeding
+of overflowed sets can be checked without a GPU.  Traces are made by the
+same model at known parameters."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ode as oracle_ode
+
+TRUTH = dict(alpha=2.0, t_x=5e-3, t_pm=4e-3, t_acc=5e-8, g3=5e-7)
+ES = 3.0          # the field scale of the traces
+EVERY, S = 10, 41  # ODE steps per sample, samples
+SAMPLE_DT = 5e-3   # in t_esc
+
+
+@pytest.fixture
+def fit(monkeypatch):
+    from paper_2608_21920_b300 import fit as F
+    from paper_2608_21920_b300 import ode as O
+
+    def forward(p, y0, dt, nsteps, every=1, ckpt_every=0, delta=0.0):
+        return oracle_ode.rk4(y0, p, dt[:, None], nsteps, delta=delta or None, record_every=every), None
+
+    def integrate(p, y0, dt, nsteps, every=1, ckpt_every=None, delta=0.0):
+        return oracle_ode.rk4(y0, p, dt[:, None], nsteps, delta=delta or None, record_every=every)
+
+    monkeypatch.setattr(O, "forward", forward)
+    monkeypatch.setattr(O, "integrate", integrate)
+    return F
+
+
+def _traces(fit):
+    p = oracle_ode.as_tensor([TRUTH, dict(TRUTH, alpha=3.0)])
+    y0 = torch.tensor([[1.0, 0.0, 1.2, 0.0]] * 2, dtype=torch.float64)
+    dt = torch.full((2,), SAMPLE_DT / EVERY, dtype=torch.float64)
+    out = oracle_ode.rk4(y0, p, dt[:, None], (S - 1) * EVERY, delta=fit.DELTA, record_every=EVERY)
+    M = out[:, :, 0].numpy()
+    E = (out[:, :, 2].abs() * ES).numpy()
+    return dict(M=M, E=E, alpha=np.array([2.0, 3.0]), t_esc=np.ones(2), sample_dt=np.full(2, SAMPLE_DT))
+
+
+def _truth_theta(prob):
+    th = torch.tensor([math.log(TRUTH[k]) for k in ("t_x", "t_pm", "t_acc", "g3")] + [math.log(ES)],
+                      dtype=torch.float64)
+    return th.repeat(prob.B, 1)
+
+
+def test_loss_vanishes_at_the_generating_parameters(fit):
+    tr = _traces(fit)
+    assert tr["M"][-1].min() > 10 * tr["M"][0].max()  # the traces contain a discharge
+    prob = fit.Problem(tr, starts=3, every=EVERY, device="cpu")
+    L = prob.loss_per_set(_truth_theta(prob))
+    assert L.max() < 1e-20
+    L0 = prob.loss_per_set(prob.theta.detach())
+    ok = prob.finite(prob.theta)
+    assert ok.any() and L0[ok].min() > 1e-6  # random starts are not already at the answer
+    assert torch.all(L0[~ok] == 0.0)  # an overflowing start contributes nothing (it is re-seeded)
+
+
+def test_gradient_matches_central_differences(fit):
+    prob = fit.Problem(_traces(fit), starts=3, every=EVERY, device="cpu")
+    with torch.no_grad():
+        prob.theta.copy_(_truth_theta(prob) + 0.05 * torch.randn(prob.B, 5, dtype=torch.float64,
+                                                                   generator=torch.Generator().manual_seed(3)))
+    ok = prob.finite(prob.theta)
+    assert bool(ok.all())
+    mx, med = fit.fd_check(prob, ok, n=4, h=1e-6)
+    assert med < 1e-5 and mx < 1e-3
+
+
+def test_reseed_replaces_only_the_flagged_sets(fit):
+    prob = fit.Problem(_traces(fit), starts=3, every=EVERY, device="cpu")
+    before = prob.theta.detach().clone()
+    ok = torch.tensor([True, False, True, True, True, False])
+    n = prob.reseed(ok)
+    after = prob.theta.detach()
+    assert n == 2
+    assert torch.equal(after[ok], before[ok])
+    assert not torch.equal(after[~ok], before[~ok])
+    # a flagged set starts from its own gap's best finite start, perturbed
+    L = prob.loss_per_set(before).view(2, 3)
+    for bad, gap in ((1, 0), (5, 1)):
+        cand = [i for i in range(3 * gap, 3 * gap + 3) if ok[i]]
+        best = min(cand, key=lambda i: float(L.view(-1)[i]))
+        assert float((after[bad] - before[best]).abs().max()) < 2.0
