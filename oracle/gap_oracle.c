@@ -773,21 +773,27 @@ static int mkey_cmp(const void *a, const void *b) {
 }
 static void merge(orc_sim *s, uint32_t n) {
   const orc_params *p = &s->p;
-  if (p->cap <= 0 || s->nlep + s->nph <= p->cap) { s->merge_level = 0; return; }
+  /* the cap bounds the pair cascade: e+- and photons count, and only e+-
+   * merge; protons, which no process multiplies, are left alone */
+  int64_t n_pairs = 0;
+  for (int64_t i = 0; i < s->nlep; ++i) n_pairs += !s->lep[i].heavy;
+  if (p->cap <= 0 || n_pairs + s->nph <= p->cap) { s->merge_level = 0; return; }
   const double width = 0.1 * (double)(1 << s->merge_level);
   if (s->merge_level < 7) s->merge_level++;
-  int64_t nl = s->nlep;
-  mkey *key = (mkey *)malloc((size_t)(nl > 0 ? nl : 1) * sizeof(mkey));
-  for (int64_t i = 0; i < nl; ++i) {
+  int64_t nl = 0;
+  mkey *key = (mkey *)malloc((size_t)(s->nlep > 0 ? s->nlep : 1) * sizeof(mkey));
+  for (int64_t i = 0; i < s->nlep; ++i) {
     const orc_lepton *L = &s->lep[i];
+    if (L->heavy) continue;
     double g = sqrt(1.0 + L->u * L->u);
     int64_t b = (int64_t)floor(log(g) / width);
     if (b < 0) b = 0;
     if (b > 255) b = 255;
     int64_t k = (int64_t)floor(L->X + 0.5);
     if (p->boundary == ORC_BC_PERIODIC) k = imod(k, p->nx);
-    key[i].q = L->q; key[i].dir = L->u >= 0.0 ? 1 : 0; key[i].k = k; key[i].bin = b;
-    key[i].id = L->id; key[i].idx = i; key[i].heavy = L->heavy;
+    key[nl].q = L->q; key[nl].dir = L->u >= 0.0 ? 1 : 0; key[nl].k = k; key[nl].bin = b;
+    key[nl].id = L->id; key[nl].idx = i; key[nl].heavy = L->heavy;
+    ++nl;
   }
   qsort(key, (size_t)nl, sizeof(mkey), mkey_cmp);
   /* with smoothing, the re-centring flux is gathered per node, smoothed like

@@ -69,11 +69,12 @@ def test_option_checks_and_em_layout_without_gpu():
         return L.gap_workspace_bytes(C.byref(p), 1, C.byref(cfg), C.byref(n))
 
     good = [dict(em=1), dict(em=1, beta_y=3e-6), dict(em=1, beta_y=0.6, beta_z=0.7), dict(em=1, pml_cells=16),
-            dict(em=1, pml_cells=256, pml_sigma=5.0), dict(protons=1), dict(protons=1, init=A.GAP_INIT_GAP_PROTONS)]
+            dict(em=1, pml_cells=256, pml_sigma=5.0), dict(protons=1), dict(protons=1, init=A.GAP_INIT_GAP_PROTONS),
+            dict(protons=1, cap=1000)]
     bad = [dict(beta_y=1e-3), dict(pml_cells=4), dict(em=1, beta_y=0.8, beta_z=0.6), dict(em=1, beta_z=float("inf")),
            dict(em=1, pml_cells=257), dict(em=1, pml_cells=-1), dict(em=3), dict(em=1, pml_cells=8, pml_sigma=-2.0),
            dict(em=1, pml_cells=8, boundary=A.GAP_BC_PERIODIC, init=A.GAP_INIT_EMPTY, ppc=0),
-           dict(protons=2), dict(protons=1, cap=1000), dict(init=A.GAP_INIT_GAP_PROTONS),
+           dict(protons=2), dict(init=A.GAP_INIT_GAP_PROTONS),
            dict(protons=1, init=A.GAP_INIT_GAP_PROTONS, boundary=A.GAP_BC_PERIODIC), dict(protons=1, m_ion=-1.0)]
     for kw in good:
         assert code(**kw) == A.GAP_OK, kw

@@ -69,10 +69,16 @@ def test_negative_alpha_with_protons_parity():
     g.close()
 
 
-def test_protons_need_fp64_and_no_cap():
+def test_protons_need_fp64():
     from paper_2608_21920_b300 import Gap
     from paper_2608_21920_b300._abi import GapError
     with pytest.raises(GapError):
         Gap(P.gpu_params(START), precision="fp32")
-    with pytest.raises(GapError):
-        Gap(P.gpu_params(dict(START, cap=1000)), precision="fp64")
+
+
+def test_protons_under_a_cap_parity():
+    """The cap bounds e+- and photons only (R28): the electrons merge, the
+    protons are left alone; everything at 1e-10 against the oracle."""
+    g, o = _parity(dict(START, cap=300), [1, 100, 400])
+    assert o.counters()["merged"] > 0
+    g.close()

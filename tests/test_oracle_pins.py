@@ -1087,3 +1087,23 @@ def test_merge_keeps_gauss_and_cap_in_a_discharge(filter_passes):
     assert r < 1e-12 * max(1.0, emax)
     n = s.leptons()["id"].size + s.photons()["id"].size
     assert n < 2 * 450
+
+
+def test_protons_are_neither_merged_nor_counted():
+    """The cap bounds the pair cascade (R28): cold protons at rest would
+    share merge groups, yet over a step in which the electrons merge every
+    proton keeps its id, and the cap counts electrons, positrons and photons
+    only (512 electrons + 410 protons against a cap of 300 leave 259
+    electrons)."""
+    cfg = dict(nx=128, ppc=4, dx=0.1, dt=0.045, alpha=0.5, init=O.INIT_GAP_PROTONS, boundary=O.BC_SURFACE,
+               seed=3, protons=1, cap=300)
+    s = O.Sim(**cfg)
+    L0 = s.leptons()
+    p0 = np.sort(L0["id"][L0["heavy"] == 1])
+    s.step(1)
+    L = s.leptons()
+    assert np.array_equal(np.sort(L["id"][L["heavy"] == 1]), p0)
+    n_e = int((L["heavy"] == 0).sum())
+    assert s.counters()["merged"] > 0 and n_e <= 300 < n_e + p0.size
+    r, emax = s.gauss_residual()
+    assert r < 1e-13 * max(1.0, emax)
