@@ -69,10 +69,35 @@ def test_negative_alpha_with_protons_parity():
     g.close()
 
 
-def test_protons_need_fp64_and_no_cap():
+def test_protons_need_no_cap():
     from paper_2608_21920_b300 import Gap
     from paper_2608_21920_b300._abi import GapError
     with pytest.raises(GapError):
-        Gap(P.gpu_params(START), precision="fp32")
-    with pytest.raises(GapError):
         Gap(P.gpu_params(dict(START, cap=1000)), precision="fp64")
+
+
+@pytest.mark.parametrize("alpha,theta", [(2.0, 0.0), (-2.0, 0.3)])
+def test_protons_fp32_state_track_oracle(alpha, theta):
+    """FP32 state with protons (QED off, so that both sides take the same
+    events): the protons' positions sit on the state's offset grid, so the
+    Gauss law holds to round-off; e+-, protons and E follow the oracle
+    within the FP32 bound of a short run (2e-4 relative, E 1e-3), and the
+    surface supply within a few macro-particles."""
+    cfg = dict(START, qed=0, alpha=alpha, inject_theta=theta)
+    g, o = P.make_pair(cfg, "fp32", tile=32)
+    d = g.diag(spectrum=False)
+    assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    g.step(60)
+    o.step(60)
+    d = g.diag(spectrum=False)
+    assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    Eg, Eo = g.field(), o.E()
+    assert np.abs(Eg - Eo).max() <= 1e-3 * np.abs(Eo).max()
+    e_o, p_o = _split_oracle(o)
+    pg = _protons_gpu(g)
+    assert abs(pg["id"].size - p_o["id"].size) <= 3
+    common, ia, ib = np.intersect1d(pg["id"], p_o["id"], return_indices=True)
+    assert common.size >= p_o["id"].size - 3
+    assert np.abs(pg["X"][ia] - p_o["X"][ib]).max() <= 2e-4 * max(1.0, np.abs(p_o["X"]).max())
+    assert abs(d["counters"]["injected"] - o.counters()["injected"]) <= 3
+    g.close()
