@@ -135,7 +135,9 @@ typedef struct gap_params {
                             particle charge (thermal at inject_theta / m_ion).  The
                             gap's Ampere step runs after the push (as with a current
                             filter).  Protons are neither merged nor counted toward
-                            the cap.  Needs the FP64 state, else GAP_EINVAL */
+                            the cap.  With the FP32 state the protons keep FP64
+                            positions on the state's offset grid (X + 1/2 a multiple
+                            of 2^-23), so their charge is exact too */
   double m_ion;          /* proton mass in m_e (0 -> 1836) */
   int32_t em;            /* 1: transverse fields E_y, E_z (cells, half steps) and B_y,
                             B_z (nodes, whole steps) of App. A's co-rotating frame in

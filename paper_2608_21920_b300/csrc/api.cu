@@ -102,7 +102,6 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.filter_passes > 0 && q.nx < 2 * (int64_t)q.filter_passes + 2) { msg = "filter_passes needs nx >= 2 passes + 2"; return GAP_EINVAL; }
     if (q.qed_quantum != 0 && q.qed_quantum != 1) { msg = "qed_quantum must be 0 or 1"; return GAP_EINVAL; }
     if (q.protons != 0 && q.protons != 1) { msg = "protons must be 0 or 1"; return GAP_EINVAL; }
-    if (q.protons && cfg.precision != GAP_FP64_PLAIN) { msg = "protons need the FP64 state"; return GAP_EINVAL; }
     if (q.init == GAP_INIT_GAP_PROTONS && (!q.protons || q.boundary != GAP_BC_SURFACE))
       { msg = "the proton start needs protons and a surface gap"; return GAP_EINVAL; }
     if (q.m_ion < 0.0) { msg = "m_ion must be >= 0"; return GAP_EINVAL; }

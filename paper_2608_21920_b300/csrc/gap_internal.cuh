@@ -21,6 +21,13 @@ constexpr uint64_t kPhotonBit = 0x8000000000000000ull;
 constexpr int kPhiBits = 23;                   // FP32 offset grid 2^-23
 constexpr double kPhiUnit = 1.0 / 8388608.0;   // 2^-23
 constexpr int kWeightShift = 8;                // FP32 weight unit = w0 / 2^8
+
+// Protons with the FP32 state keep FP64 positions on the leptons' offset
+// grid: X + 1/2 a multiple of 2^-23 (exact in double up to 2^29 cells), so
+// that every cloud fraction and flux of a proton is a whole number of the
+// state's charge units (grid_units times 2^kWeightShift for weight w0).
+__device__ __forceinline__ double grid_position(double X) { return rint((X + 0.5) * 8388608.0) * kPhiUnit - 0.5; }
+__device__ __forceinline__ long long grid_units(double f) { return llrint(f * 8388608.0); }
 constexpr int kMaxEmit = 16;                   // emission events per lepton-step (upper bound)
 constexpr int kPushChunk = 4096;  // leptons per push work item (multiple of 32)
 static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 contributions per node");

@@ -78,7 +78,7 @@ __global__ void k_load_protons(View v, int gap, int64_t n) {
       atomicOr(&v.ctl->error, 128);  // proton storage exhausted
       continue;
     }
-    v.pr_X[i] = X;
+    v.pr_X[i] = v.precision == GAP_FP32_STATE ? grid_position(X) : X;
     v.pr_u[i] = 0.0;
     v.pr_w[i] = g.w0;
     v.pr_id[i] = ((uint64_t)g.gap_index << 40) | (1ull << 39) | (uint64_t)(cell * ppc + j);
@@ -113,7 +113,10 @@ __global__ void k_proton_charge(View v, int gap, unsigned long long *Q) {
       int64_t cc = c;
       if (g.periodic) cc = (c % g.nx + g.nx) % g.nx;
       else if (c < 0 || c >= g.nx) continue;
-      atomicAdd(reinterpret_cast<double *>(&Q[off + cc]), v.pr_w[i] * fr);
+      if (v.precision == GAP_FP32_STATE)  // whole charge units (positions on the offset grid)
+        atomicAdd(&Q[off + cc], (unsigned long long)(grid_units(fr) * (1ll << kWeightShift)));
+      else
+        atomicAdd(reinterpret_cast<double *>(&Q[off + cc]), v.pr_w[i] * fr);
     }
   }
 }

@@ -1125,6 +1125,8 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
 __global__ void __launch_bounds__(256) k_push_heavy(View v) {
   const int64_t n = v.ctl->pr_count < v.pr_cap ? v.ctl->pr_count : v.pr_cap;
   const int ecur = v.ctl->e_cur;
+  const bool f32 = v.precision == GAP_FP32_STATE;  // integer flux, positions on the offset grid
+  const long long wu = 1ll << kWeightShift;        // weight w0 in the FP32 state's units
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (!v.pr_alive[i]) continue;
     const int gi = v.pr_gap[i];
@@ -1143,7 +1145,8 @@ __global__ void __launch_bounds__(256) k_push_heavy(View v) {
     const double Eg = (1.0 - o) * E[c] + o * E[c1];
     const double u = v.pr_u[i] + Eg * g.dt / g.m_ion;
     const double gm = sqrt(1.0 + u * u);
-    const double X1 = X0 + u / gm * g.cdx;
+    double X1 = X0 + u / gm * g.cdx;
+    if (f32) X1 = grid_position(X1);  // the FP32 state's grid (exact integer charge)
     // flux q w [F(X1 - k) - F(X0 - k)], F(s) = clamp(s + 1/2, 0, 1)
     const double lo = X0 < X1 ? X0 : X1, hi = X0 < X1 ? X1 : X0;
     const int64_t k0 = (int64_t)floor(lo - 0.5), k1 = (int64_t)floor(hi + 0.5);
@@ -1155,7 +1158,8 @@ __global__ void __launch_bounds__(256) k_push_heavy(View v) {
       int64_t node = k;
       if (periodic) node = (k % g.nx + g.nx) % g.nx;
       else if (k < 0 || k > g.nx) continue;
-      atomicAdd(reinterpret_cast<double *>(&v.Dg[g.node_off + node]), w * dF);
+      if (f32) atomicAdd(&v.Dg[g.node_off + node], (unsigned long long)(grid_units(dF) * wu));
+      else atomicAdd(reinterpret_cast<double *>(&v.Dg[g.node_off + node]), w * dF);
     }
     v.pr_u[i] = u;
     double Xn = X1;
@@ -1176,7 +1180,10 @@ __global__ void __launch_bounds__(256) k_push_heavy(View v) {
     if (!periodic && v.pr_alive[i]) {  // cell 0's share of the cloud, for the injection
       const double a = Xn + 0.5, b = Xn - 0.5;
       const double fr = (a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a)) - (b < 0.0 ? 0.0 : (b > 1.0 ? 1.0 : b));
-      if (fr != 0.0) atomicAdd(reinterpret_cast<double *>(&v.q0[gi]), w * fr);
+      if (fr != 0.0) {
+        if (f32) atomicAdd(&v.q0[gi], (unsigned long long)(grid_units(fr) * wu));
+        else atomicAdd(reinterpret_cast<double *>(&v.q0[gi]), w * fr);
+      }
     }
   }
 }
@@ -1273,7 +1280,7 @@ __global__ void k_inject(View v) {
       }
       const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->pr_count), 1ull);
       if (i < v.pr_cap) {
-        v.pr_X[i] = o;
+        v.pr_X[i] = sizeof(R) == 4 ? grid_position(o) : o;
         v.pr_u[i] = u;
         v.pr_w[i] = g.w0;
         v.pr_id[i] = id;
@@ -1684,6 +1691,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       }
       default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
     }
+    if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons
     launch_em(v, st);         // transverse fields, before E_h moves on
     launch_filter(v, 0, st);  // Ampere of the gaps that defer it
     return;

@@ -81,7 +81,7 @@ def test_option_checks_and_em_layout_without_gpu():
     for kw in bad:
         assert code(**kw) == A.GAP_EINVAL, kw
     assert code(f32, em=1, beta_y=0.1) == A.GAP_OK
-    assert code(f32, protons=1) == A.GAP_EINVAL  # protons need the FP64 state
+    assert code(f32, protons=1) == A.GAP_OK
     assert code(nx=512) == A.GAP_OK
     plain = n.value
     assert code(nx=512, em=1) == A.GAP_OK

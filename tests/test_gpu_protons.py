@@ -69,16 +69,36 @@ def test_negative_alpha_with_protons_parity():
     g.close()
 
 
-def test_protons_need_fp64():
-    from paper_2608_21920_b300 import Gap
-    from paper_2608_21920_b300._abi import GapError
-    with pytest.raises(GapError):
-        Gap(P.gpu_params(START), precision="fp32")
-
-
 def test_protons_under_a_cap_parity():
     """The cap bounds e+- and photons only (R28): the electrons merge, the
     protons are left alone; everything at 1e-10 against the oracle."""
     g, o = _parity(dict(START, cap=300), [1, 100, 400])
     assert o.counters()["merged"] > 0
+    g.close()
+
+
+@pytest.mark.parametrize("alpha,theta", [(2.0, 0.0), (-2.0, 0.3)])
+def test_protons_fp32_state_track_oracle(alpha, theta):
+    """FP32 state with protons (QED off, so that both sides take the same
+    events): the protons' positions sit on the state's offset grid, so the
+    Gauss law holds to round-off; e+-, protons and E follow the oracle
+    within the FP32 bound of a short run (2e-4 relative, E 1e-3), and the
+    surface supply within a few macro-particles."""
+    cfg = dict(START, qed=0, alpha=alpha, inject_theta=theta)
+    g, o = P.make_pair(cfg, "fp32", tile=32)
+    d = g.diag(spectrum=False)
+    assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    g.step(60)
+    o.step(60)
+    d = g.diag(spectrum=False)
+    assert d["gauss_residual"] <= 1e-12 * max(1.0, d["E_abs_max"])
+    Eg, Eo = g.field(), o.E()
+    assert np.abs(Eg - Eo).max() <= 1e-3 * np.abs(Eo).max()
+    e_o, p_o = _split_oracle(o)
+    pg = _protons_gpu(g)
+    assert abs(pg["id"].size - p_o["id"].size) <= 3
+    common, ia, ib = np.intersect1d(pg["id"], p_o["id"], return_indices=True)
+    assert common.size >= p_o["id"].size - 3
+    assert np.abs(pg["X"][ia] - p_o["X"][ib]).max() <= 2e-4 * max(1.0, np.abs(p_o["X"]).max())
+    assert abs(d["counters"]["injected"] - o.counters()["injected"]) <= 3
     g.close()
