@@ -44,7 +44,7 @@ extern "C" {
 #define GAP_ECHECK (-6)   /* a device-side consistency check failed */
 #define GAP_ETOOBIG (-7)  /* input larger than a fixed-size internal buffer */
 
-/* precision of the particle state (Sect. 6.1 pushes; BASELINE precision pattern) */
+/* precision of the particle state (Sect. 6.1 pushes) */
 #define GAP_FP64_PLAIN 0 /* FP64 offsets, momenta, weights; FP64 charge deposit */
 #define GAP_FP32_STATE 1 /* FP32 offsets and momenta; exact integer charge deposit; FP64 field */
 
@@ -78,7 +78,12 @@ typedef struct gap_params {
   double alpha;      /* j_m / j_co */
   double b;          /* B / B_Q */
   double lambda_hat; /* reduced Compton wavelength / skin depth */
-  double rho_hat;    /* field-line curvature radius / skin depth */
+  double rho_hat;    /* field-line curvature radius / skin depth.  The caller converts
+                        the paper's rho_c (cm) to it: rho_c / d_e with the skin depth
+                        d_e of Sect. 2.2, or, for boxes too small for the physical
+                        value to give pairs, a rescaled value in the spirit of Sect.
+                        6.1's rescaling of the QED scales (the workload recipes use
+                        rho_hat = 20 rho_c / 1e7 cm) */
   double rate_mult;  /* multiplier of both QED rates (>= 0) */
   double gap_length; /* H_gap in skin depths; QED inhibited above it.  0 -> 0.8 nx dx */
   double density;    /* initial lepton density, units of n_co */
@@ -93,9 +98,12 @@ typedef struct gap_params {
                         dual cell, direction and ln(gamma) bin (width
                         0.1 * 2^level, level = consecutive over-cap steps, at
                         most 7) are merged in groups of >= 3 into two, keeping
-                        weight, momentum, energy and Gauss's law.  The paper
-                        describes no merging scheme; this one is the
-                        library's own.  Photons are not merged. */
+                        weight, momentum, energy and Gauss's law (with the
+                        FP32 state a group whose weight exceeds 2^33 - 2
+                        units of w0/256 stays unmerged: its children would
+                        overflow their 32-bit weights).  The paper describes
+                        no merging scheme; this one is the library's own.
+                        Photons are not merged. */
   uint64_t seed;     /* Philox4x32-10 key of this gap */
   int32_t qed;       /* 0/1: curvature emission and one-photon pair creation */
   int32_t boundary;  /* GAP_BC_* */
@@ -321,7 +329,11 @@ int gap_spectrum_inverse(gap_handle *h, const double *dev_U, double *dev_xi, int
  *  - The working array (1 MiB) is a file-scope device array that every GPU
  *    loading the library holds until the process exits.  The first call on a
  *    device looks its address up (cudaGetSymbolAddress) with that device
- *    current; make that first call before any stream capture.
+ *    current; make that first call before any stream capture.  The address
+ *    is kept for the life of the process: after cudaDeviceReset (or anything
+ *    else that destroys the device's context) the module may load elsewhere,
+ *    so do not call this entry point on that device again in the same
+ *    process.
  *  - All calls share the array: calls that overlap on the GPU (for example on
  *    two streams) race; serialise them.  Each call rewrites every entry it
  *    reads, so no state carries over between calls.

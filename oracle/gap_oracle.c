@@ -1077,13 +1077,16 @@ void orc_step(orc_sim *s) {
         const double lmid = ((double)n - (double)P->n0 + 0.5) * dt;
         const double chi = P->x * p->b * fabs(sin(lmid / p->rho_hat));
         double e = orc_bw_split(chi, orc_uniform(p->seed, P->id, n, CH_PAIR_E, 0));
-        if (e * P->x < 1.0) e = 1.0 / P->x;
-        if ((1.0 - e) * P->x < 1.0) e = 1.0 - 1.0 / P->x;
+        /* a share below one rest mass is raised to it, on the energies
+         * themselves: (1/x) x can round to just below 1 */
         ge = e * P->x;
+        if (ge < 1.0) ge = 1.0;
+        if (P->x - ge < 1.0) ge = P->x - 1.0;
       }
       for (int k = 0; k < 2; ++k) {
         const double gk = k == 0 ? ge : P->x - ge;
-        const double up = (double)P->dir * sqrt((gk - 1.0) * (gk + 1.0));
+        const double pk = (gk - 1.0) * (gk + 1.0);
+        const double up = (double)P->dir * sqrt(pk > 0.0 ? pk : 0.0);
         orc_lepton L = {0};
         L.id = orc_child_id(P->id, n, CH_PAIR, (uint32_t)k) & ~ORC_PHOTON_BIT;
         L.q = k == 0 ? -1 : +1;

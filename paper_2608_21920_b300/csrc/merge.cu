@@ -187,6 +187,14 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     if (b > kMergeBins - 1) b = kMergeBins - 1;
     return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
   };
+  // a group merges when it has three or more members; in the FP32 state
+  // its children carry 32-bit weights, so a group whose summed weight would
+  // not split into two of them is left unmerged
+  auto merges = [&](int key) -> bool {
+    if (cnt[key] < 3) return false;
+    if (sizeof(R) == 4 && (unsigned long long)sw[key] > 2ull * 0xffffffffull) return false;
+    return true;
+  };
   auto weight_of = [&](int64_t src) -> double {
     const W wq = as<W>(v.lw[nxt][s])[src];
     return sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     // M^2 - W^2 = D (2W + D) carry no cancellation for nearly cold groups
     for (int j = lane; j < nt; j += 32) {
       const int key = touched[j];
-      if (cnt[key] < 3) continue;
+      if (!merges(key)) continue;
       sp[key] = 0.5 * log(sp[key] / sm[key]);
       sm[key] = 0.0;
     }
@@ -237,23 +245,23 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
-      if (cnt[key] < 3) continue;
+      if (!merges(key)) continue;
       const double u = (double)as<R>(v.lu[nxt][s])[src];
       const double h = sinh(0.5 * (asinh(u) - sp[key]));
       atomicAdd(&sm[key], weight_of(src) * 2.0 * h * h);
     }
     __syncwarp();
-    // leptons of small groups are copied through
+    // leptons of groups that do not merge are copied through
     for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
-      if (cnt[key_of(src)] < 3) copy_out(src);
+      if (!merges(key_of(src))) copy_out(src);
     }
     // groups of three or more become two
     const int32_t kn = k0 + node;
     for (int j = lane; j < nt; j += 32) {
       const int key = touched[j];
       const int n = cnt[key];
-      if (n < 3) continue;
+      if (!merges(key)) continue;
       double Wt, flux;
       long long flux_units = 0;  // FP32 state: the moved charge in integer units
       W wa, wb;

@@ -213,10 +213,12 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     if (g.qed_quantum) {
       const double lmid = ((double)step - (double)v.pn0[b][i] + 0.5) * g.dt;
       const double chi = x * g.b * fabs(sin(lmid / g.rho_hat));
-      double e = bw_split(v, chi, uniform53(g.seed, id, (uint32_t)step, CH_PAIR_E, 0));
-      if (e * x < 1.0) e = 1.0 / x;
-      if ((1.0 - e) * x < 1.0) e = 1.0 - 1.0 / x;
+      const double e = bw_split(v, chi, uniform53(g.seed, id, (uint32_t)step, CH_PAIR_E, 0));
+      // each share at least one rest mass, clamped on the energies (a
+      // clamp on e would leave (1/x) x just below 1 for some x)
       ge = e * x;
+      if (ge < 1.0) ge = 1.0;
+      if (x - ge < 1.0) ge = x - 1.0;
     }
     int32_t k;
     R phi;
@@ -227,7 +229,8 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     else wq = (W)w;
     for (int s = 0; s < 2; ++s) {
       const double gs = s == 0 ? ge : x - ge;
-      const double up = (double)dir * sqrt((gs - 1.0) * (gs + 1.0));
+      const double ps = (gs - 1.0) * (gs + 1.0);
+      const double up = (double)dir * sqrt(ps > 0.0 ? ps : 0.0);
       const uint64_t lid = child_id(id, (uint32_t)step, CH_PAIR, (uint32_t)s) & ~kPhotonBit;
       const R tau = (R)(-log(uniform53(g.seed, lid, (uint32_t)(step + 1), CH_TAU0, 0)));
       append_lepton<R>(v, s, tn, k, phi, (R)up, wq, tau, lid);

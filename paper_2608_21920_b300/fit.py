@@ -39,7 +39,11 @@ def load_traces(path: str) -> dict:
     z = np.load(path)
     nx, dx, dt = z["param_nx"], z["param_dx"], z["param_dt"]
     steps = z["step"]
-    return dict(M=z["M_avg"], E=z["E_abs_max"], alpha=z["param_alpha"], t_esc=0.8 * nx * dx,
+    # the model's time unit is the escape time over the gap, H_gap / c
+    # (Sect. 5.2); a gap saved with H_gap = 0 had the default 0.8 nx dx
+    H = z["param_gap_length"] if "param_gap_length" in z.files else np.zeros_like(nx)
+    t_esc = np.where(H > 0, H, 0.8 * nx * dx)
+    return dict(M=z["M_avg"], E=z["E_abs_max"], alpha=z["param_alpha"], t_esc=t_esc,
                 sample_dt=(steps[1] - steps[0]) * dt)
 
 

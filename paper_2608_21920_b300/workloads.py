@@ -137,7 +137,7 @@ def run_traces(params, steps: int, every: int, precision: str = "fp32", graph_ch
     out["t_init_s"] = np.array(t_init)
     if spectra:
         out["spectrum"] = np.array(spectra)
-    for k in ("alpha", "b", "rho_hat", "nx", "ppc", "dx", "dt", "cap"):
+    for k in ("alpha", "b", "rho_hat", "nx", "ppc", "dx", "dt", "cap", "gap_length"):
         out["param_" + k] = np.array([p.get(k, 0) for p in plist], dtype=float)
     g.close()
     return out

@@ -87,3 +87,16 @@ def test_reseed_replaces_only_the_flagged_sets(fit):
         cand = [i for i in range(3 * gap, 3 * gap + 3) if ok[i]]
         best = min(cand, key=lambda i: float(L.view(-1)[i]))
         assert float((after[bad] - before[best]).abs().max()) < 2.0
+
+
+def test_load_traces_takes_t_esc_from_the_gap_length(tmp_path):
+    """The model's time unit is H_gap / c (Sect. 5.2): a trace saved with an
+    explicit gap length uses it, one saved with 0 falls back to 0.8 nx dx."""
+    from paper_2608_21920_b300 import fit
+    p = tmp_path / "tr.npz"
+    np.savez(p, M_avg=np.ones((3, 2)), E_abs_max=np.ones((3, 2)), step=np.array([0, 10, 20]),
+             param_nx=np.array([100.0, 200.0]), param_dx=np.array([0.1, 0.1]), param_dt=np.array([0.045, 0.045]),
+             param_alpha=np.array([1.0, 2.0]), param_gap_length=np.array([5.0, 0.0]))
+    tr = fit.load_traces(str(p))
+    assert np.allclose(tr["t_esc"], [5.0, 16.0])
+    assert np.allclose(tr["sample_dt"], 0.45)

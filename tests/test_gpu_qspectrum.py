@@ -135,3 +135,33 @@ def test_quantum_pair_creation_matches_oracle():
     assert np.abs(ga / gb - 1.0).max() <= 5e-3
     assert np.median(np.abs(ga / gb - 1.0)) <= 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("x0,b,n0", [(2.0 + 1e-9, 0.1, 0), (49.0, 1.0, -698)])
+def test_pair_split_clamp_gives_finite_momenta(precision, x0, b, n0):
+    """The clamp of a share below one rest mass (R27) acts on the energies:
+    near the threshold x = 2, and at x = 49 where (1/49) 49 rounds below 1,
+    400 conversions give finite momenta, clamped shares exactly at rest, the
+    oracle's pair count, and energies summing to x."""
+    cfg = dict(nx=512, boundary=O.BC_SURFACE, qed=1, qed_quantum=1, b=b, lambda_hat=1e-4, rho_hat=20.0,
+               rate_mult=10.0, dx=0.1, dt=0.045, gap_length=51.2, ppc=1, density=1e-6)
+    g, o = P.make_pair(cfg, precision, tile=64)
+    N = 400
+    ids = np.arange(1000, 1000 + N, dtype=np.uint64)
+    X = 5.0 + 0.01 * np.arange(N)
+    g.add_particles(2, ids, X, np.full(N, x0), np.full(N, 1e-3), np.zeros(N), n0=np.full(N, n0, np.int64),
+                    direction=np.ones(N))
+    for i in range(N):
+        o.add_photon(int(ids[i]), X[i], x0, 1e-3, 1, n0, 0.0)
+    g.step(1)
+    o.step(1)
+    assert g.diag(spectrum=False)["counters"]["pairs"] == o.counters()["pairs"] == N
+    a = P.leptons_gpu(g)
+    born = np.isin(a["id"], P.leptons_oracle(o)["id"])
+    u = a["u"][born]
+    assert u.size == 2 * N and np.all(np.isfinite(u)) and np.all(u >= 0)
+    assert np.count_nonzero(u == 0.0) > 0
+    gam = np.sqrt(1 + u.astype(np.float64) ** 2)
+    assert gam.sum() == pytest.approx(N * x0, rel=1e-9 if precision == "fp64" else 1e-5)
+    g.close()

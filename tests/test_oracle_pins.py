@@ -798,6 +798,27 @@ def test_bw_split_pair_conserves_energy():
     assert abs(g[0] - 40.0) > 1e-6  # split off the half
 
 
+@pytest.mark.parametrize("x0,b,n0", [(2.0 + 1e-9, 0.1, 0), (2.01, 0.1, 0), (49.0, 1.0, -698)])
+def test_bw_split_clamp_leaves_finite_momenta(x0, b, n0):
+    """R27's clamp of a share below one rest mass.  Near the pair threshold
+    x = 2 about half the draws fall below it; at x = 49 (born 698 steps
+    earlier, so sin(l / rho_hat) ~ 1 and chi ~ 49) a few per cent do, and
+    (1/49) 49 rounds to just below 1, so the clamp must act on the energies.
+    Every lepton of 400 conversions has a finite momentum (a clamped share is
+    exactly at rest) and each pair's energies sum to x."""
+    s = O.Sim(nx=512, boundary=O.BC_SURFACE, qed=1, qed_quantum=1, b=b, lambda_hat=1e-4, rho_hat=20.0,
+              rate_mult=10.0, dx=0.1, dt=0.045, gap_length=51.2)
+    n = 400
+    for k in range(n):
+        s.add_photon(1000 + k, 5.0 + 0.01 * k, x0, 1e-3, 1, n0, 0.0)
+    s.step(1)
+    L = s.leptons()
+    assert L["id"].size == 2 * n and np.all(np.isfinite(L["u"])) and np.all(L["u"] >= 0)
+    assert np.count_nonzero(L["u"] == 0.0) > 0  # the clamp acted
+    g = np.sqrt(1 + L["u"] ** 2)
+    assert g.sum() == pytest.approx(n * x0, rel=1e-9)
+
+
 def test_pair_conversion_length_distribution():
     """Photons accumulate tau_BW (eq. tau_bw) at the angle sin psi = |sin(l/R)|
     (Sect. 6.1) and convert at tau = -ln U: P(converted by l) = 1 - exp(-tau(l))."""
