@@ -429,7 +429,8 @@ def run_batch(args):
         init = sum(p["nx"] * p["ppc"] for p in params)
         cap_kw = dict(lepton_capacity=int(args.capacity_factor * init),
                       photon_capacity=int(4 * args.capacity_factor * init // 3))
-    g = Gap(params, precision="fp32", tile=tile, threads=threads, rebin_every=rebin, **cap_kw)
+    g = Gap(params, precision="fp32", tile=tile, threads=threads, rebin_every=rebin, variant=args.variant,
+            **cap_kw)
     s = torch.cuda.Stream()
     chunk = args.graph_chunk
     with torch.cuda.stream(s):

@@ -463,6 +463,12 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     v.gross[s] = C.take<int32_t>(NT);
   }
   v.item_start = C.take<int32_t>((size_t)NT + 1);
+  // items per tile: max(1, chunks of each species), each species' chunks at
+  // most used / kPushChunk + 1, and the used slots of all tiles at most the
+  // store's capacity
+  const int64_t item_cap = 2 * (lep_cap / kPushChunk) + 2 * (int64_t)NT + 2;
+  v.item_tile = C.take<int32_t>((size_t)item_cap);
+  v.item_cap = (int32_t)std::min<int64_t>(item_cap, INT32_MAX);
   v.tile_done = C.take<int32_t>(NT);
   v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);
   v.ledger = C.take<double>((size_t)n * L_NLED);
@@ -664,6 +670,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (c->error & 32) return fail(h, GAP_ECHECK, "a lepton outside its tile's nodes reached the merge");
   if (c->error & 64) return fail(h, GAP_ECHECK, "a photon event was not taken at its step");
   if (c->error & 128) return fail(h, GAP_ECAP, "proton storage exhausted");
+  if (c->error & 256) return fail(h, GAP_ECHECK, "more push work items than the item table holds");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));

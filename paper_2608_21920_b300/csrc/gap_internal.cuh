@@ -158,6 +158,8 @@ struct View {
   int32_t *last_cnt[2];  // per tile: alive count after the last re-bin
   int32_t *gross[2];     // per tile: appends since the last re-bin
   int32_t *item_start;   // [n_tiles + 1] first push item of each tile
+  int32_t *item_tile;    // [item_cap] tile of each push item
+  int32_t item_cap;      // bound on the push items of a step
   int32_t *tile_done;    // [n_tiles] items of the tile finished this step
   // lepton stores [buffer][species]
   int32_t *lk[2][2];

@@ -59,8 +59,10 @@ __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t 
 // last of its items to finish does the update.  The four edge nodes shared
 // with the neighbouring tiles are finished by whichever of the two tiles
 // arrives second (atomic arrival count, no waiting).
-template <class R, bool QED, bool HAS_W>
-__global__ void __launch_bounds__(256, 3) k_push(View v) {
+constexpr int kDeferQueue = 32 + 32 * 4;  // queue of a warp: < 32 left + one group of 32 lanes x 4
+
+template <class R, bool QED, bool HAS_W, bool DEFER = false, int MINB = 3>
+__global__ void __launch_bounds__(256, MINB) k_push(View v) {
   using W = typename Prec<R>::W;
   using Acc = typename Prec<R>::Acc;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
   __shared__ double sLed[4];
   __shared__ int sDead[2];
   __shared__ int s_item, s_last;
+  __shared__ int s_queue[DEFER ? 8 * kDeferQueue : 1];  // deferred leptons, per warp (<= 256 threads)
 
   for (;;) {
   __syncthreads();  // the previous item is done with shared memory
@@ -78,16 +81,7 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
   __syncthreads();
   const int item = s_item;
   if (item >= v.ctl->push_items) return;
-  int t;
-  {
-    int lo = 0, hi = v.n_tiles;  // item_start[t] <= item < item_start[t + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (v.item_start[mid] <= item) lo = mid;
-      else hi = mid;
-    }
-    t = lo;
-  }
+  const int t = v.item_tile[item];  // item_start[t] <= item < item_start[t + 1]
   const int nitems = v.item_start[t + 1] - v.item_start[t];
   int s_only, r0, r1;
   {
@@ -188,62 +182,13 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
     uint64_t *Ip = v.lid[cur][s];
     int dead = 0;
 
-    // One lepton: gather, kick, emission, drift, deposit, boundaries.  k is
-    // set to -1 when the lepton leaves the tile (migrated or removed).
-    auto push_one = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot) {
-      const int lk = k - (k0 - 1);
-      // a1-a2: linear gather of node E at X = k + phi - 3/2, kick
-      const R sph = phi - (R)1.5;
-      const int j = sph >= (R)0 ? lk : lk - 1;
-      const R tt = sph >= (R)0 ? sph : sph + (R)1;
-      const R Ep = sE[j] + tt * (sE[j + 1] - sE[j]);
-      u += (R)q * Ep * dt;
-      // a3: curvature emission by optical-depth sub-cycling (eq. tau_syn)
-      R ph_x[QED ? kMaxEmit : 1];
-      int ph_k[QED ? kMaxEmit : 1];
-      int nph = 0;
-      bool have_id = false;
-      uint64_t id = 0;
-      if (QED && g.qed && phi < Hc15 - (R)k) {
-        R trem = dt;
-        int kk = 0;
-        for (;;) {
-          R gm = sqrt((R)1 + u * u);
-          R chi, r;
-          if (sizeof(R) == 4) {
-            chi = gm * gm * (R)chi_cf;
-            r = (R)rate_cf * gm * (R)tsyn_f((float)chi);
-          } else {
-            chi = gm * gm * (R)g.lambda_hat / (R)g.rho_hat;
-            r = (R)g.rate_mult * (R)kAlphaEm * gm * (R)tsyn_d((double)chi) / (R)g.rho_hat;
-          }
-          if (!(r > (R)0)) break;
-          if (tau > r * trem) {
-            tau -= r * trem;
-            break;
-          }
-          trem -= tau / r;
-          if (!have_id) {
-            id = Ip[slot];
-            have_id = true;
-          }
-          const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau,
-                                         g.qed_quantum != 0);
-          const R x = xs >= (R)0 ? xs : -xs;
-          ++c_emit;
-          if (x >= (R)2) {
-            ph_x[nph] = xs;  // the sign carries the direction
-            ph_k[nph] = kk;
-            ++nph;
-          } else {
-            l_rad += (double)w * wunit * (double)x;
-          }
-          if (++kk >= g.kmax_emit) {
-            ++c_ovf;
-            break;
-          }
-        }
-      }
+    // a4, a8, a7 of one lepton after its kick and emissions: drift, the
+    // charge through the nodes it crosses, boundaries, the photons it emitted
+    // (born at its new position), the cell-0 charge of a surface tile and
+    // the move to another tile.  k is set to -1 when the lepton leaves the
+    // tile (migrated or removed).
+    auto move_one = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot, const int lk,
+                        const int nph, const R *ph_x, const int *ph_k, const bool have_id, const uint64_t id) {
       // a4: drift
       R dX;
       if (sizeof(R) == 4) {
@@ -343,17 +288,184 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
         k = kn;
         phi = pn;
       } else {
-        if (!have_id) id = Ip[slot];
         const int tn = tile_of(v, g, kn);
-        append_lepton<R>(v, s, tn, kn, pn, u, w, tau, id);
+        append_lepton<R>(v, s, tn, kn, pn, u, w, tau, have_id ? id : Ip[slot]);
         k = -1;
         ++dead;
       }
     };
 
+    // One lepton: gather, kick, emission, then move_one.
+    auto push_one = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot) {
+      const int lk = k - (k0 - 1);
+      // a1-a2: linear gather of node E at X = k + phi - 3/2, kick
+      const R sph = phi - (R)1.5;
+      const int j = sph >= (R)0 ? lk : lk - 1;
+      const R tt = sph >= (R)0 ? sph : sph + (R)1;
+      const R Ep = sE[j] + tt * (sE[j + 1] - sE[j]);
+      u += (R)q * Ep * dt;
+      // a3: curvature emission by optical-depth sub-cycling (eq. tau_syn)
+      R ph_x[QED ? kMaxEmit : 1];
+      int ph_k[QED ? kMaxEmit : 1];
+      int nph = 0;
+      bool have_id = false;
+      uint64_t id = 0;
+      if (QED && g.qed && phi < Hc15 - (R)k) {
+        R trem = dt;
+        int kk = 0;
+        for (;;) {
+          R gm = sqrt((R)1 + u * u);
+          R chi, r;
+          if (sizeof(R) == 4) {
+            chi = gm * gm * (R)chi_cf;
+            r = (R)rate_cf * gm * (R)tsyn_f((float)chi);
+          } else {
+            chi = gm * gm * (R)g.lambda_hat / (R)g.rho_hat;
+            r = (R)g.rate_mult * (R)kAlphaEm * gm * (R)tsyn_d((double)chi) / (R)g.rho_hat;
+          }
+          if (!(r > (R)0)) break;
+          if (tau > r * trem) {
+            tau -= r * trem;
+            break;
+          }
+          trem -= tau / r;
+          if (!have_id) {
+            id = Ip[slot];
+            have_id = true;
+          }
+          const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau,
+                                         g.qed_quantum != 0);
+          const R x = xs >= (R)0 ? xs : -xs;
+          ++c_emit;
+          if (x >= (R)2) {
+            ph_x[nph] = xs;  // the sign carries the direction
+            ph_k[nph] = kk;
+            ++nph;
+          } else {
+            l_rad += (double)w * wunit * (double)x;
+          }
+          if (++kk >= g.kmax_emit) {
+            ++c_ovf;
+            break;
+          }
+        }
+      }
+      move_one(k, phi, u, w, tau, slot, lk, nph, ph_x, ph_k, have_id, id);
+    };
+
+    // The same lepton when its optical depth outlasts the step (no emission):
+    // returns false, changing nothing, when an emission falls within the
+    // step, so that the caller hands the lepton to push_one.  The arithmetic
+    // is push_one's for a lepton that does not emit.
+    auto push_quiet = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot) -> bool {
+      const int lk = k - (k0 - 1);
+      const R sph = phi - (R)1.5;
+      const int j = sph >= (R)0 ? lk : lk - 1;
+      const R tt = sph >= (R)0 ? sph : sph + (R)1;
+      const R Ep = sE[j] + tt * (sE[j + 1] - sE[j]);
+      const R un = u + (R)q * Ep * dt;
+      R tn = tau;
+      if (QED && g.qed && phi < Hc15 - (R)k) {
+        const R gm = sqrt((R)1 + un * un);
+        R chi, r;
+        if (sizeof(R) == 4) {
+          chi = gm * gm * (R)chi_cf;
+          r = (R)rate_cf * gm * (R)tsyn_f((float)chi);
+        } else {
+          chi = gm * gm * (R)g.lambda_hat / (R)g.rho_hat;
+          r = (R)g.rate_mult * (R)kAlphaEm * gm * (R)tsyn_d((double)chi) / (R)g.rho_hat;
+        }
+        if (r > (R)0) {
+          if (!(tn > r * dt)) return false;
+          tn -= r * dt;
+        }
+      }
+      u = un;
+      tau = tn;
+      move_one(k, phi, u, w, tau, slot, lk, 0, nullptr, nullptr, false, 0ull);
+      return true;
+    };
+
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    if constexpr (DEFER) {
+      // 16-byte vectors of VD leptons per lane through push_quiet; a lepton
+      // that emits this step is left unchanged and queued (its offset from
+      // `start`) in the warp's queue, and whenever 32 are queued the warp
+      // runs push_one on them, one per lane, so that the emission events of
+      // a warp run side by side instead of one lane at a time.
+      constexpr int VD = 4;
+      int *wq = s_queue + (threadIdx.x >> 5) * kDeferQueue;
+      int qn = 0;  // warp-uniform
+      auto drain = [&](const int n) {
+        if (lane < n) {
+          const int64_t slot = start + wq[qn - n + lane];
+          int32_t k = Kp[slot];
+          R phi = Pp[slot], u = Up[slot], tau = Tp[slot];
+          const W w = HAS_W ? Wp[slot] : w_def;
+          push_one(k, phi, u, w, tau, slot);
+          Kp[slot] = k;
+          Pp[slot] = phi;
+          Up[slot] = u;
+          Tp[slot] = tau;
+        }
+        qn -= n;
+        __syncwarp();
+      };
+      const int ngroups = (used + VD - 1) / VD;
+      for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
+        const int gi = g0 + lane;
+        const int base = gi * VD;
+        const int64_t slot0 = start + base;
+        const int nvalid = gi >= ngroups ? 0 : (used - base < VD ? used - base : VD);
+        Vec<int32_t, VD> kv;
+        Vec<R, VD> pv, uv, tv;
+        Vec<W, VD> wv;
+        unsigned later = 0;
+        if (nvalid > 0) {
+          kv = *reinterpret_cast<const Vec<int32_t, VD> *>(Kp + slot0);
+          pv = *reinterpret_cast<const Vec<R, VD> *>(Pp + slot0);
+          uv = *reinterpret_cast<const Vec<R, VD> *>(Up + slot0);
+          if (HAS_W) wv = *reinterpret_cast<const Vec<W, VD> *>(Wp + slot0);
+          tv = *reinterpret_cast<const Vec<R, VD> *>(Tp + slot0);
+#pragma unroll
+          for (int jj = 0; jj < VD; ++jj) {
+            if (jj < nvalid && kv.a[jj] >= 0 &&
+                !push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj))
+              later |= 1u << jj;
+          }
+          if (nvalid == VD) {
+            *reinterpret_cast<Vec<int32_t, VD> *>(Kp + slot0) = kv;
+            *reinterpret_cast<Vec<R, VD> *>(Pp + slot0) = pv;
+            *reinterpret_cast<Vec<R, VD> *>(Up + slot0) = uv;
+            *reinterpret_cast<Vec<R, VD> *>(Tp + slot0) = tv;
+          } else {
+            for (int jj = 0; jj < nvalid; ++jj) {
+              Kp[slot0 + jj] = kv.a[jj];
+              Pp[slot0 + jj] = pv.a[jj];
+              Up[slot0 + jj] = uv.a[jj];
+              Tp[slot0 + jj] = tv.a[jj];
+            }
+          }
+        }
+        // queue the deferred leptons in lane order (at most 32 VD more)
+        const int nd = __popc(later);
+        int incl = nd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = qn + incl - nd;
+        for (unsigned b = later; b; b &= b - 1u) wq[pos++] = base + __ffs(b) - 1;
+        qn += total;
+        __syncwarp();
+        while (qn >= 32) drain(32);
+      }
+      if (qn > 0) drain(qn);
+    } else {
     const int ngroups = (used + VEC - 1) / VEC;
     // warp-uniform trip count (lanes past the end load nothing)
-    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
       const int gi = g0 + lane;
       const int base = gi * VEC;
@@ -391,6 +503,7 @@ __global__ void __launch_bounds__(256, 3) k_push(View v) {
           if (QED) Tp[slot0 + jj] = tv.a[jj];
         }
       }
+    }
     }
     // one atomic per warp for the dead / migrated count
     for (int o = 16; o > 0; o >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, o);
@@ -1660,14 +1773,18 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
     }
     __syncthreads();
     const int before = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + x - c;
-    if (t < n) v.item_start[t] = before;
+    if (t < n) {
+      v.item_start[t] = before;
+      for (int i = before; i < before + c && i < v.item_cap; ++i) v.item_tile[i] = t;
+    }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) carry = before + c;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     v.item_start[n] = carry;
-    v.ctl->push_items = carry;
+    if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
+    v.ctl->push_items = carry < v.item_cap ? carry : v.item_cap;
     v.ctl->push_next = 0;
   }
 }
@@ -1700,7 +1817,14 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
   k_push_items<<<1, 1024, 0, st>>>(v);
   const int grid = 148 * 4;  // persistent: blocks take items until the list is empty
   if (v.qed_any) {
-    if (v.has_w)
+    // FP32 state: emitters deferred to converged warp passes (variant 0: at
+    // most 64 registers, 4 blocks per SM; 1: 80 registers, 3 blocks per SM),
+    // or every lepton pushed in place (variant 2)
+    if (sizeof(R) == 4 && v.has_w && v.variant == 0)
+      k_push<float, true, true, true, 4><<<grid, threads, smem, st>>>(v);
+    else if (sizeof(R) == 4 && v.has_w && v.variant == 1)
+      k_push<float, true, true, true, 3><<<grid, threads, smem, st>>>(v);
+    else if (v.has_w)
       k_push<R, true, true><<<grid, threads, smem, st>>>(v);
     else
       k_push<R, true, false><<<grid, threads, smem, st>>>(v);
