@@ -427,11 +427,22 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           uv = *reinterpret_cast<const Vec<R, VD> *>(Up + slot0);
           if (HAS_W) wv = *reinterpret_cast<const Vec<W, VD> *>(Wp + slot0);
           tv = *reinterpret_cast<const Vec<R, VD> *>(Tp + slot0);
-#pragma unroll
+          // the vectors rotate through element 0, so that push_quiet is
+          // inlined once: a quarter of the instruction footprint, which the
+          // warps of a block otherwise wait on (instruction fetch)
+#pragma unroll 1
           for (int jj = 0; jj < VD; ++jj) {
-            if (jj < nvalid && kv.a[jj] >= 0 &&
-                !push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj))
-              later |= 1u << jj;
+            int32_t k = kv.a[0];
+            R ph = pv.a[0], uu = uv.a[0], ta = tv.a[0];
+            const W ww = HAS_W ? wv.a[0] : w_def;
+            if (jj < nvalid && k >= 0 && !push_quiet(k, ph, uu, ww, ta, slot0 + jj)) later |= 1u << jj;
+#pragma unroll
+            for (int r = 0; r < VD - 1; ++r) {
+              kv.a[r] = kv.a[r + 1]; pv.a[r] = pv.a[r + 1]; uv.a[r] = uv.a[r + 1]; tv.a[r] = tv.a[r + 1];
+              if (HAS_W) wv.a[r] = wv.a[r + 1];
+            }
+            kv.a[VD - 1] = k; pv.a[VD - 1] = ph; uv.a[VD - 1] = uu; tv.a[VD - 1] = ta;
+            if (HAS_W) wv.a[VD - 1] = ww;
           }
           if (nvalid == VD) {
             *reinterpret_cast<Vec<int32_t, VD> *>(Kp + slot0) = kv;
