@@ -231,6 +231,23 @@ def run_ours(args):
         r = dict(ms=ms, K=K, push_ms=push_ms / max(push_n, 1), push_n=push_n, launches=lps * K,
                  gauss=d["gauss_residual"], E_abs_max=d["E_abs_max"],
                  n=d["n_electrons"] + d["n_positrons"], clocks=clk)
+        if precision == "fp32" and args.steady_steps > 0:
+            # after the timed window: enough steps that compactions and the
+            # drifted store order are inside (the store is compacted every
+            # rebin_every steps)
+            g.profile(True)
+            barrier()
+            e0.record(s)
+            g.step(args.steady_steps)
+            e1.record(s)
+            barrier()
+            sms = rank_max(e0.elapsed_time(e1))
+            sp_ms, sp_n, _ = g.profile(False)
+            r["steady"] = dict(steps=args.steady_steps, ms_per_step=sms / args.steady_steps,
+                               push_ms_per_launch=sp_ms / max(sp_n, 1),
+                               value=job_throughput(N_PARTICLES, args.steady_steps, sms, world))
+        if precision == "fp32" and world == 1 and not args.no_cpu and not (SETUP["filter_passes"] or SETUP["em"]):
+            r["error_vs_oracle"] = oracle_window_error(g, args.tile or 256)
         results[precision] = r
         if precision == "fp32" and not args.no_e2e:
             # end to end through the public API: init from host parameters,
@@ -265,6 +282,11 @@ def run_ours(args):
                             d2h_bytes_per_step=int(NX * 8 + 64))
         del g
         torch.cuda.empty_cache()
+    qr = None
+    if not args.no_qed:  # the QED leg: the batch of surface gaps in discharge, every rank its own replica
+        qa = argparse.Namespace(**vars(args))
+        qa.steps, qa.tile, qa.variant = 50, 128, 0
+        qr = batch_measure(qa, world, local)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -295,6 +317,15 @@ def run_ours(args):
         "gauss_residual": r32["gauss"], "E_abs_max": r32["E_abs_max"],
         "particles_alive": r32["n"],
     }
+    if "steady" in r32:
+        st = r32["steady"]
+        a_st = bpp * N_PARTICLES / (st["push_ms_per_launch"] / 1e3) / 1e9
+        line["steady_state"] = {"steps": st["steps"], "value": st["value"], "unit": UNIT,
+                                "ms_per_step": st["ms_per_step"], "push_ms_per_launch": st["push_ms_per_launch"],
+                                "achieved": a_st, "frac": a_st / peak,
+                                "window": f"the {st['steps']} steps after the timed ones, compactions included"}
+    if "error_vs_oracle" in r32:
+        line["error_vs_oracle"] = r32["error_vs_oracle"]
     if tuned:
         line["config"]["autotune_ms_per_push"] = tuned
         line["config"]["threads"] = args.threads
@@ -312,11 +343,57 @@ def run_ours(args):
         line["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": r64["K"], "ms_per_step": r64["ms"] / r64["K"],
                               "achieved_gbs": a64, "frac": a64 / peak, "gauss_residual": r64["gauss"],
                               "fp32_over_fp64": value / v64}
+    if qr is not None:
+        line["qed"] = {"metric": METRIC, "value": qr["value"], "unit": UNIT, "steps": qr["steps"],
+                       "ms_per_step": qr["ms_per_step"], "roofline": qr["roofline"], "clocks": qr["clocks"],
+                       "gpu_launches": qr["gpu_launches"], "config": qr["config"],
+                       "phases_ms_per_step": qr["phases_ms_per_step"],
+                       "counts": {k: qr[k] for k in ("pairs", "merged", "photons_merged", "emit_events")}}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def oracle_window_error(g, tile, t_lo=1000, n_tiles=4):
+    """Error of one FP32 step against the FP64 oracle at full size (outside
+    the timed region; part of the baseline leg, the one place that runs the
+    oracle): the leptons of n_tiles tiles and one tile of halo on each side
+    are exported, pushed one step by the oracle from the GPU's state and E^n,
+    and the oracle's E^{n+1} on the window's nodes and the leptons' new
+    positions and momenta are compared with the GPU's step."""
+    import numpy as np
+    import oracle as O
+    t_hi = t_lo + n_tiles
+    E0 = g.field()
+    lep = [g.tile_particles(kind, t_lo - 1, t_hi + 1) for kind in (0, 1)]
+    g.step(1)
+    E1 = g.field()
+    after = [g.tile_particles(kind, t_lo - 2, t_hi + 2) for kind in (0, 1)]
+    o = O.Sim(nx=NX, boundary=O.BC_PERIODIC, dx=WORKLOAD["dx"], dt=WORKLOAD["dt"], init=O.INIT_EMPTY,
+              filter_passes=SETUP["filter_passes"], em=SETUP["em"], beta_y=SETUP["beta_y"])
+    o.set_E(E0)
+    for kind, q in ((0, -1), (1, 1)):
+        L = lep[kind]
+        for i in range(L["id"].size):
+            o.add_lepton(int(L["id"][i]), q, float(L["X"][i]), float(L["u"][i]), float(L["w"][i]))
+    o.step(1)
+    Eo = o.E()
+    nodes = np.arange(t_lo * tile, t_hi * tile + 1)
+    dE = np.abs(Eo[nodes] - E0[nodes])
+    err = np.abs(E1[nodes] - Eo[nodes])
+    Lo = o.leptons()
+    got = {k: np.concatenate([a[k] for a in after]) for k in ("id", "X", "u")}
+    common, ia, ib = np.intersect1d(got["id"], Lo["id"], return_indices=True)
+    dX = got["X"][ia] - Lo["X"][ib]
+    dX -= NX * np.round(dX / NX)
+    du = np.abs(got["u"][ia] - Lo["u"][ib]) / np.maximum(np.abs(Lo["u"][ib]), 1.0)
+    return {"E_max_abs": float(err.max()), "E_max_rel_to_step_change": float(err.max() / np.median(dE)),
+            "E_max_rel": float(err.max() / np.abs(Eo[nodes]).max()), "nodes": int(nodes.size),
+            "X_max_abs_cells": float(np.abs(dX).max()), "u_max_rel": float(du.max()), "leptons": int(common.size),
+            "method": f"one FP32 step from the GPU state against the FP64 oracle on tiles {t_lo}-{t_hi - 1} "
+                      f"(+1 tile halo) of the full-size workload, after the timed steps"}
 
 
 def _oracle_sample(nx, steps, warmup):
@@ -346,6 +423,26 @@ def host_cpu():
     return {"cpu_model": model, "host_cores": os.cpu_count()}
 
 
+def _oracle_replica(a):
+    nx, steps = a
+    rate, dt = _oracle_sample(nx, steps, 1)
+    return 2 * nx * PPC * steps, dt
+
+
+def cpu_baseline_parallel(nx, steps, procs):
+    """The same oracle on `procs` host cores at once: independent replicas of
+    the sample in separate processes (the oracle itself is single-threaded;
+    the workload's gaps and samples are independent), aggregate
+    macroparticle-steps over the slowest replica's time."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")  # this process already holds a CUDA context
+    with ctx.Pool(procs) as pool:
+        out = pool.map(_oracle_replica, [(nx, steps)] * procs)
+    work = sum(o[0] for o in out)
+    t = max(o[1] for o in out)
+    return work / t, t
+
+
 def cpu_baseline(seconds):
     """The FP64 oracle as it stands, single-threaded on the host, on a bounded
     sample of the workload (same density, temperature and seed; fewer cells)."""
@@ -353,9 +450,17 @@ def cpu_baseline(seconds):
     rate, dt = _oracle_sample(nx, 2, 0)
     steps = max(2, int(seconds * rate / (2 * nx * PPC)))
     rate, dt = _oracle_sample(nx, steps, 1)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Nx=2^14 periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), {steps} steps, {dt:.1f} s",
-            **host_cpu()}
+    rec = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"Nx=2^14 periodic, {2 * nx * PPC:.3g} e+- (200+200/cell), {steps} steps, {dt:.1f} s",
+           **host_cpu()}
+    procs = min(os.cpu_count() or 1, 16)
+    if procs > 1:
+        psteps = max(2, steps // 2)
+        prate, pt = cpu_baseline_parallel(nx, psteps, procs)
+        rec["parallel"] = {"value": prate, "unit": UNIT, "cores": procs, "kind": "oracle replicas",
+                           "sample": f"{procs} processes, each the sample above for {psteps} steps, "
+                                     f"slowest {pt:.1f} s"}
+    return rec
 
 
 def run_reference(args):
@@ -410,13 +515,13 @@ def batch_params(n_gaps):
     return params
 
 
-def run_batch(args):
+def batch_measure(args, world=1, local=0):
     """The batched parameter sweep: all gaps advance together, one launch per
-    kernel per step, replayed from CUDA graphs of `--graph-chunk` steps."""
+    kernel per step, replayed from CUDA graphs of `--graph-chunk` steps; the
+    QED push (FP32 state, emission, stored weights) timed on its own."""
     import torch
     from paper_2608_21920_b300 import Gap, autotune
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
+    rank = rank_info()[0]
     params = batch_params(args.gaps)
     peaks, peak_kind = measured_peaks()
     tuned = None
@@ -448,7 +553,8 @@ def run_batch(args):
         g.step(K, graph_chunk=chunk)
         e1.record(s)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    import torch.distributed as dist
+    ms = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, "cuda")
     clk = clocks.stop()
     n1 = _total_leptons(g)
     # the push kernel alone, eagerly launched between CUDA events
@@ -464,10 +570,11 @@ def run_batch(args):
     achieved = bpp * 0.5 * (n1 + n2) / (push_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
     c = [g.diag(i, spectrum=False)["counters"] for i in range(g.n_gaps)]
-    line = {
-        "metric": METRIC, "value": world * nmean * K / (ms / 1e3), "unit": UNIT, "n_gpus": world,
-        "steps": K, "warmup": args.warmup * chunk, "ms_per_step": ms / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    res = {
+        "value": world * nmean * K / (ms / 1e3), "steps": K, "warmup": args.warmup * chunk, "ms_per_step": ms / K,
         "config": {"workload": BATCH_NAME.format(n=args.gaps, last=args.gaps - 1), "gaps": args.gaps,
                    "capacity_factor": args.capacity_factor or None, "graph_chunk": chunk, "tile": tile,
                    "threads": threads, "rebin_every": rebin, "advanced_before_timing": args.batch_advance,
@@ -478,10 +585,24 @@ def run_batch(args):
         "gpu_launches": int(lps * K),
         "clocks": clk,
         "pairs": int(sum(x["pairs"] for x in c)), "merged": int(sum(x["merged"] for x in c)),
+        "photons_merged": int(sum(x["photons_merged"] for x in c)),
+        "emit_events": int(sum(x["emit_events"] for x in c)),
         "phases_ms_per_step": {k: v / max(nph, 1) for k, v in phases.items()},
     }
     if tuned:
-        line["config"]["autotune_ms_per_step"] = tuned
+        res["config"]["autotune_ms_per_step"] = tuned
+    return res
+
+
+def run_batch(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    r = batch_measure(args, world, local)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    line.update({k: v for k, v in r.items() if k not in line})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -497,11 +618,14 @@ def main():
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--rebin-every", type=int, default=0, help="steps between sorted compactions (0: library default)")
     ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--steady-steps", type=int, default=192,
+                    help="steps timed after the headline window, compactions included (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-qed", action="store_true", help="leave out the QED batch sub-record")
     ap.add_argument("--autotune", action="store_true", help="pick tile and threads by timing the push kernel")
     ap.add_argument("--nx", type=int, default=0, help="smaller workload for profiling captures only")
     ap.add_argument("--workload", choices=["roofline", "batch"], default="roofline",

@@ -101,9 +101,13 @@ typedef struct gap_params {
                         weight, momentum, energy and Gauss's law (with the
                         FP32 state a group whose weight exceeds 2^33 - 2
                         units of w0/256 stays unmerged: its children would
-                        overflow their 32-bit weights).  The paper describes
-                        no merging scheme; this one is the library's own.
-                        Photons are not merged. */
+                        overflow their 32-bit weights).  The photons born in
+                        an over-cap step merge too: those of the same cell,
+                        direction and ln(x) bin (the leptons' width) become
+                        one photon of the group's weight, energy sum w x and
+                        mean position, with a fresh threshold depth.  The
+                        paper describes no merging scheme; this one is the
+                        library's own. */
   uint64_t seed;     /* Philox4x32-10 key of this gap */
   int32_t qed;       /* 0/1: curvature emission and one-photon pair creation */
   int32_t boundary;  /* GAP_BC_* */
@@ -198,7 +202,7 @@ typedef struct gap_handle gap_handle;
 typedef struct gap_counters {
   int64_t emit_events, photons, pairs, injected, absorbed, escaped, photons_escaped,
       emit_overflow, inject_overflow, load_overflow, spilled, photon_overflow, merged,
-      reserved0, reserved1, reserved2;
+      photons_merged, reserved1, reserved2;
   double e_radiated, e_absorbed, e_escaped, e_photon_escaped, e_injected, work_jm,
       reserved3, reserved4;
 } gap_counters;
@@ -289,6 +293,20 @@ int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uin
 int gap_sample_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
                          uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
                          int64_t *n_out, void *stream);
+
+/* Export the leptons of one species (kind 0 electrons, 1 positrons) stored
+ * in tiles [tile_lo, tile_hi) of gap `gap` (tile i holds the leptons whose
+ * dual cell k = floor(X + 1/2) lies in [i tile, (i + 1) tile), tile the
+ * configuration's tile size), as gap_get_particles does: a window of a large
+ * gap, complete, with which the charge-conserving deposit and the Ampere
+ * step of Sect. 6.1 (Sect. 2.2, dE/dt = j_m - J) can be recomputed on the
+ * window's nodes.  Leptons spilled since the last compaction (counter
+ * `spilled`) are not in their tiles' segments and are left out.
+ * GAP_EINVAL for photons, protons or an empty or out-of-range tile range;
+ * GAP_ECAP if cap is too small (*n_out is the count).  Synchronises `stream`. */
+int gap_tile_particles(gap_handle *h, int32_t gap, int32_t kind, int32_t tile_lo, int32_t tile_hi, int64_t cap,
+                       uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
+                       int64_t *n_out, void *stream);
 
 /* Append n particles of one kind to gap `gap` (tests build hand-checkable
  * states).  Photons: host_u is x, host_tau is tau_star, host_aux2 packs

@@ -56,7 +56,8 @@ class Params(C.Structure):
 class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "emit_events", "photons", "pairs", "injected", "absorbed", "escaped",
-        "photons_escaped", "emit_overflow", "inject_overflow", "load_overflow", "merged")] + [
+        "photons_escaped", "emit_overflow", "inject_overflow", "load_overflow", "merged",
+        "photons_merged")] + [
         (n, C.c_double) for n in (
             "e_radiated", "e_absorbed", "e_escaped", "e_photon_escaped", "e_injected",
             "work_jm")]

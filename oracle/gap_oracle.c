@@ -466,7 +466,7 @@ typedef struct { uint64_t id; double X, x, w, tau_star, tau_acc, X_ref; int32_t 
  * (x -> 2 (x/2)) and injection (rest energy w) are exact ledger moves. */
 typedef struct {
   int64_t emit_events, photons, pairs, injected, absorbed, escaped,
-      photons_escaped, emit_overflow, inject_overflow, load_overflow, merged;
+      photons_escaped, emit_overflow, inject_overflow, load_overflow, merged, photons_merged;
   double e_radiated, e_absorbed, e_escaped, e_photon_escaped, e_injected, work_jm;
 } orc_counters;
 
@@ -771,6 +771,72 @@ static int mkey_cmp(const void *a, const void *b) {
   if (x->id != y->id) return x->id < y->id ? -1 : 1;
   return 0;
 }
+/* Photons under the cap (the survey's N -> 1 conserving w and w x), merged
+ * at birth: while the gap is over its cap, the photons born in this step's
+ * push (n0 = n + 1) of each (cell floor(X), direction, bin of ln x of the
+ * leptons' width) group with at least two members become one photon of
+ * weight W = sum w and energy x = sum w x / W at the weighted mean position
+ * sum w X / W, so that the number of real photons, their energy and their
+ * momentum are kept.  Members share their birth step, hence their angle to
+ * the field at every later step (R10), and none has accumulated any depth
+ * yet, so the new photon is a newborn photon in every respect: it draws its
+ * threshold depth like one (channel BW_TAU at step n + 1) and starts its
+ * accumulation at step n + 1.  Its id is the child (channel MERGE) of the
+ * group's smallest id.  Older photons are left alone. */
+typedef struct { int64_t k; int32_t dir, pad; int64_t bin; uint64_t id; int64_t idx; } pkey;
+static int pkey_cmp(const void *a, const void *b) {
+  const pkey *x = (const pkey *)a, *y = (const pkey *)b;
+  if (x->k != y->k) return x->k < y->k ? -1 : 1;
+  if (x->dir != y->dir) return x->dir < y->dir ? -1 : 1;
+  if (x->bin != y->bin) return x->bin < y->bin ? -1 : 1;
+  if (x->id != y->id) return x->id < y->id ? -1 : 1;
+  return 0;
+}
+static void merge_photons(orc_sim *s, uint32_t n, double width) {
+  const orc_params *p = &s->p;
+  const int64_t np = s->nph;
+  pkey *key = (pkey *)malloc((size_t)(np > 0 ? np : 1) * sizeof(pkey));
+  int64_t nk = 0;
+  for (int64_t i = 0; i < np; ++i) {
+    const orc_photon *P = &s->ph[i];
+    if (P->n0 != (int32_t)n + 1) continue;
+    int64_t b = (int64_t)floor(log(P->x) / width);
+    if (b < 0) b = 0;
+    if (b > 255) b = 255;
+    int64_t k = (int64_t)floor(P->X);
+    if (p->boundary == ORC_BC_PERIODIC) k = imod(k, p->nx);
+    key[nk].k = k; key[nk].dir = P->dir; key[nk].pad = 0; key[nk].bin = b; key[nk].id = P->id; key[nk].idx = i;
+    ++nk;
+  }
+  qsort(key, (size_t)nk, sizeof(pkey), pkey_cmp);
+  int64_t a = 0;
+  while (a < nk) {
+    int64_t e = a + 1;
+    while (e < nk && key[e].k == key[a].k && key[e].dir == key[a].dir && key[e].bin == key[a].bin) ++e;
+    if (e - a >= 2) {
+      double W = 0.0, Wx = 0.0, WX = 0.0;
+      for (int64_t j = a; j < e; ++j) {
+        orc_photon *P = &s->ph[key[j].idx];
+        W += P->w; Wx += P->w * P->x; WX += P->w * P->X;
+        P->alive = 0;
+      }
+      orc_photon Q = {0};
+      Q.id = orc_child_id(key[a].id, n, CH_MERGE, 0) | ORC_PHOTON_BIT;
+      Q.X = WX / W; Q.X_ref = Q.X; Q.n_ref = (int32_t)n + 1;
+      Q.x = Wx / W; Q.w = W; Q.dir = key[a].dir; Q.n0 = (int32_t)n + 1;
+      Q.tau_star = -log(orc_uniform(p->seed, Q.id, n + 1, CH_BW_TAU, 0));
+      Q.tau_acc = 0.0; Q.alive = 1;
+      push_photon(s, Q);
+      s->cnt.photons_merged += (e - a) - 1;
+    }
+    a = e;
+  }
+  free(key);
+  int64_t m = 0;
+  for (int64_t i = 0; i < s->nph; ++i) if (s->ph[i].alive) s->ph[m++] = s->ph[i];
+  s->nph = m;
+}
+
 static void merge(orc_sim *s, uint32_t n) {
   const orc_params *p = &s->p;
   /* the cap bounds the pair cascade: e+- and photons count, and only e+-
@@ -866,6 +932,7 @@ static void merge(orc_sim *s, uint32_t n) {
   int64_t m = 0;
   for (int64_t i = 0; i < s->nlep; ++i) if (s->lep[i].alive) s->lep[m++] = s->lep[i];
   s->nlep = m;
+  merge_photons(s, n, width);
 }
 
 /* ------------------------------------------------------------------------- */

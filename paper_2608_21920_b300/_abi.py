@@ -44,7 +44,7 @@ class GapCounters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "emit_events", "photons", "pairs", "injected", "absorbed", "escaped", "photons_escaped",
         "emit_overflow", "inject_overflow", "load_overflow", "spilled", "photon_overflow", "merged",
-        "reserved0", "reserved1", "reserved2")] + [(n, C.c_double) for n in (
+        "photons_merged", "reserved1", "reserved2")] + [(n, C.c_double) for n in (
             "e_radiated", "e_absorbed", "e_escaped", "e_photon_escaped", "e_injected", "work_jm",
             "reserved3", "reserved4")]
 
@@ -85,6 +85,7 @@ def lib():
     L.gap_set_em.argtypes = [vp, i32, i32, vp, i64, vp]
     L.gap_get_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_sample_particles.argtypes = [vp, i32, i32, i64, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
+    L.gap_tile_particles.argtypes = [vp, i32, i32, i32, i32, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_add_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
     L.gap_solve_gauss.argtypes = [vp, i32, vp]
     L.gap_set_background.argtypes = [vp, i32, d]
@@ -114,7 +115,7 @@ def lib():
 
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
-            "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_add_particles",
+            "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_tile_particles", "gap_add_particles",
             "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 

@@ -403,7 +403,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
       }
       lep_need[s] += need;
     }
-    if (q.qed) ph_need += q.cap > 0 ? q.cap : 16 * std::max<int64_t>(load, 1024);
+    // photons: the cap bounds the pair cascade only on average (photons merge
+    // at birth, older ones wait to convert or escape), so a capped gap keeps
+    // at least the uncapped default
+    if (q.qed) ph_need += std::max<int64_t>(q.cap, 16 * std::max<int64_t>(load, 1024));
     if (q.init != GAP_INIT_EMPTY) {
       LoadSpec ls{};
       ls.gap = i;
@@ -476,6 +479,20 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.merge_state = C.take<int32_t>(4 * (size_t)n);
   v.merge_width = C.take<double>(n);
   v.ph_gap = C.take<int32_t>(n);
+  {  // photon merge table: twice the photon store (newborns are at most all of it), 2^10 .. 2^22 entries
+    int64_t H = 0;
+    if (merge_any && qed_any) {
+      H = 1024;
+      while (H < 2 * ph_cap && H < (int64_t(1) << 22)) H <<= 1;
+    }
+    v.phm_size = H;
+    v.phm_key = C.take<unsigned long long>((size_t)H);
+    v.phm_nid = C.take<unsigned long long>((size_t)H);
+    v.phm_W = C.take<double>((size_t)H);
+    v.phm_Wx = C.take<double>((size_t)H);
+    v.phm_WX = C.take<double>((size_t)H);
+    v.phm_cnt = C.take<unsigned>((size_t)H);
+  }
   const int spec_n = 1024;
   v.spec_n = spec_n;
   v.spec_tab = C.take<float2>(spec_n);
@@ -869,11 +886,21 @@ int gap_set_background(gap_handle *h, int32_t gap, double eta_bg) {
   return cuda_check(h, e, "set background");
 }
 
-// Shared by gap_get_particles (stride 1) and gap_sample_particles.
+// Shared by gap_get_particles (stride 1), gap_sample_particles and
+// gap_tile_particles (tiles [tile_lo, tile_hi) of the gap; -1: all).
 static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
                             uint64_t *host_id, double *host_X, double *host_u, double *host_w,
                             double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
-                            void *stream);
+                            void *stream, int32_t tile_lo = -1, int32_t tile_hi = -1);
+
+int gap_tile_particles(gap_handle *h, int32_t gap, int32_t kind, int32_t tile_lo, int32_t tile_hi, int64_t cap,
+                       uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
+                       int64_t *n_out, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || kind == GAP_PHOTON || kind == GAP_PROTON) return GAP_EINVAL;
+  if (tile_lo < 0 || tile_hi <= tile_lo || tile_hi > h->gaps_h[gap].n_tiles) return GAP_EINVAL;
+  return export_particles(h, gap, kind, 1, cap, host_id, host_X, host_u, host_w, host_tau, nullptr, nullptr, n_out,
+                          stream, tile_lo, tile_hi);
+}
 
 int gap_get_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t cap, uint64_t *host_id,
                       double *host_X, double *host_u, double *host_w, double *host_tau, double *host_aux,
@@ -893,7 +920,7 @@ int gap_sample_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t strid
 static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t stride, int64_t cap,
                             uint64_t *host_id, double *host_X, double *host_u, double *host_w,
                             double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
-                            void *stream) {
+                            void *stream, int32_t tile_lo, int32_t tile_hi) {
   if (!h || gap < 0 || gap >= h->n_gaps || kind < 0 || kind > GAP_PROTON || !n_out) return GAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Ctl c;
@@ -905,7 +932,9 @@ static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t st
   if (kind == GAP_PROTON)
     launch_export_protons(h->v, gap, stage, scap, h->export_count, stride, st);
   else
-    launch_export_impl(h->v, gap, kind, stage, scap, h->export_count, h->gaps_h[gap].n_tiles, st, stride);
+    launch_export_impl(h->v, gap, kind, stage, scap, h->export_count,
+                       tile_lo >= 0 ? tile_hi - tile_lo : h->gaps_h[gap].n_tiles, st, stride,
+                       tile_lo >= 0 ? tile_lo : 0);
   if (e == cudaSuccess) e = cudaGetLastError();
   unsigned long long cnt = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, h->export_count, sizeof(cnt), cudaMemcpyDeviceToHost, st);

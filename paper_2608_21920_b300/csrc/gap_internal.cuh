@@ -72,7 +72,7 @@ enum Channel : uint32_t {
 
 enum Counter {
   C_EMIT = 0, C_PHOTONS, C_PAIRS, C_INJECTED, C_ABSORBED, C_ESCAPED, C_PH_ESCAPED,
-  C_EMIT_OVF, C_INJ_OVF, C_LOAD_OVF, C_SPILL, C_PH_OVF, C_MERGED, C_R0, C_R1, C_R2, C_NCNT
+  C_EMIT_OVF, C_INJ_OVF, C_LOAD_OVF, C_SPILL, C_PH_OVF, C_MERGED, C_PH_MERGED, C_R1, C_R2, C_NCNT
 };
 enum Ledger { L_RAD = 0, L_ABS, L_ESC, L_PH_ESC, L_INJ, L_WORK, L_R3, L_R4, L_NLED };
 
@@ -116,6 +116,8 @@ struct Ctl {
   int32_t push_items, push_next;  // the push work list of this step and its counter
   int64_t spill_n[2];
   int64_t new_total[2];
+  int64_t ph_nb_start;  // photon store fill before this step's push (0 after a photon compaction)
+  int64_t phm_end;      // photon store fill when the photon merge began
 };
 
 // Everything a kernel needs, passed by value.
@@ -144,6 +146,12 @@ struct View {
   float2 *bw_tab;  // pair energy split: per row of ln chi, (G, dG/d(1/2 - eta)) on kQsNodes nodes
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
+  // photon merge at birth: open-addressing table of phm_size (a power of
+  // two) keys with the sums of each group; zero between merges
+  int64_t phm_size;
+  unsigned long long *phm_key, *phm_nid;  // key (0 = empty); max of ~id over the group
+  double *phm_W, *phm_Wx, *phm_WX;        // sum w, sum w x, sum w X
+  unsigned *phm_cnt;
   int32_t *ph_gap;       // photons alive per gap
   Ctl *ctl;
   double *E[2];

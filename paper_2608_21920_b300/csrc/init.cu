@@ -593,10 +593,10 @@ void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st)
 // Photon stage: id | X | x | w | tau_acc | tau_star | aux2.
 template <class R>
 __global__ void k_export_leptons(View v, int gap, int s, double *stage, int64_t cap,
-                                 unsigned long long *count, int64_t stride) {
+                                 unsigned long long *count, int64_t stride, int tile_first) {
   using W = typename Prec<R>::W;
   const GapDev &g = v.gaps[gap];
-  const int t = g.tile_begin + blockIdx.x;
+  const int t = g.tile_begin + tile_first + blockIdx.x;
   const int cur = v.ctl->lep_cur;
   const int64_t start = v.seg_start[s][t];
   const int used = v.seg_used[s][t];
@@ -689,13 +689,14 @@ void launch_import(const View &v, int gap, int kind, int64_t n, const double *st
 }
 
 void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
-                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride) {
+                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride,
+                        int tile_first) {
   if (kind == GAP_PHOTON) {
     launch_export_photons(v, gap, stage, cap, count, st);
   } else if (v.precision == GAP_FP32_STATE) {
-    k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride);
+    k_export_leptons<float><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride, tile_first);
   } else {
-    k_export_leptons<double><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride);
+    k_export_leptons<double><<<n_tiles_gap, 256, 0, st>>>(v, gap, kind, stage, cap, count, stride, tile_first);
   }
 }
 

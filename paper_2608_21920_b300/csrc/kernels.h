@@ -41,7 +41,8 @@ void launch_qspec_inverse(const View &v, const double *chi, const double *U, dou
                           cudaStream_t st);
 void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st);
 void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t cap,
-                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride = 1);
+                        unsigned long long *count, int n_tiles_gap, cudaStream_t st, int64_t stride = 1,
+                        int tile_first = 0);
 void launch_import(const View &v, int gap, int kind, int64_t n, const double *stage,
                    cudaStream_t st);
 

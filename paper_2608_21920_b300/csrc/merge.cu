@@ -1,4 +1,5 @@
-// merge.cu -- weight-conserving merge of leptons under the macro-particle cap.
+// merge.cu -- weight-conserving merge of leptons under the macro-particle cap,
+// and of the photons born in a step (at the end of the file).
 //
 // When a gap holds more leptons + photons than its cap after a step, the
 // leptons of every (species, dual cell k, direction, bin of ln gamma of width
@@ -338,6 +339,127 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Photons merged at birth.  While a gap is over its cap, the photons born in
+// this step's push (n0 = the step now beginning) of each (cell, direction,
+// bin of ln x of the leptons' width) group with at least two members become
+// one photon: weight W = sum w, energy sum w x / W, position sum w X / W,
+// the group's birth step, a fresh threshold depth (channel BW_TAU) and no
+// accumulated depth, scheduled by the next photon pass; its id is the child
+// (channel MERGE) of the group's smallest id.  Groups are gathered in an
+// open-addressing table keyed by (gap + 1, cell, direction, bin): one pass
+// adds every newborn photon's weight and moments to its key's entry, a
+// second retires the members of groups of two or more and lets the member
+// with the smallest id append the merged photon, a third clears the table.
+// A photon whose key finds no free entry within kPhmProbe probes (the table
+// holds twice the photon store, so only a store larger than 2^21 photons can
+// fill it that far) stays unmerged.
+constexpr int kPhmProbe = 64;
+
+__device__ __forceinline__ uint64_t phm_photon_key(const View &v, int b, int64_t i, int64_t step, double &X) {
+  if (v.pev[b][i] == kPhDead || v.pn0[b][i] != (int32_t)step) return 0ull;
+  const int gap = v.pgap[b][i];
+  if (!v.merge_state[4 * gap]) return 0ull;
+  const GapDev &g = v.gaps[gap];
+  const int32_t dir = v.pdir[b][i];
+  X = photon_pos(g, v.pXr[b][i], v.pnr[b][i], dir, step);
+  int64_t cell = (int64_t)floor(X);
+  if (g.periodic) {
+    cell %= g.nx;
+    if (cell < 0) cell += g.nx;
+  }
+  int64_t bin = (int64_t)floor(log(v.px[b][i]) / v.merge_width[gap]);
+  if (bin < 0) bin = 0;
+  if (bin > kMergeBins - 1) bin = kMergeBins - 1;
+  return ((uint64_t)(gap + 1) << 40) | ((uint64_t)cell << 9) | ((uint64_t)(dir > 0) << 8) | (uint64_t)bin;
+}
+
+// Entry of `key`: inserted when `insert`, else looked up; -1 if not found.
+__device__ __forceinline__ int64_t phm_slot(const View &v, uint64_t key, bool insert) {
+  const uint64_t mask = (uint64_t)v.phm_size - 1;
+  uint64_t h = mix64(key) & mask;
+  for (int p = 0; p < kPhmProbe; ++p, h = (h + 1) & mask) {
+    if (insert) {
+      const unsigned long long old = atomicCAS(&v.phm_key[h], 0ull, (unsigned long long)key);
+      if (old == 0ull || old == key) return (int64_t)h;
+    } else {
+      const unsigned long long k = v.phm_key[h];
+      if (k == key) return (int64_t)h;
+      if (k == 0ull) return -1;
+    }
+  }
+  return -1;
+}
+
+__global__ void k_phm_insert(View v) {
+  if (!(v.ctl->flags & 1)) return;
+  const int b = v.ctl->ph_cur;
+  const int64_t step = v.ctl->step;
+  const int64_t n = photon_fill(v, b);
+  const int64_t i0 = v.ctl->ph_nb_start < n ? v.ctl->ph_nb_start : n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.ctl->phm_end = n;  // appends of the next pass lie beyond
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double X = 0.0;
+    const uint64_t key = phm_photon_key(v, b, i, step, X);
+    if (!key) continue;
+    const int64_t h = phm_slot(v, key, true);
+    if (h < 0) continue;
+    const double w = v.pw[b][i], x = v.px[b][i];
+    atomicAdd(&v.phm_cnt[h], 1u);
+    atomicAdd(&v.phm_W[h], w);
+    atomicAdd(&v.phm_Wx[h], w * x);
+    atomicAdd(&v.phm_WX[h], w * X);
+    atomicMax(&v.phm_nid[h], ~(unsigned long long)v.pid[b][i]);
+  }
+}
+
+__global__ void k_phm_emit(View v) {
+  if (!(v.ctl->flags & 1)) return;
+  const int b = v.ctl->ph_cur;
+  const int64_t step = v.ctl->step;
+  const int64_t n = v.ctl->phm_end;
+  const int64_t i0 = v.ctl->ph_nb_start < n ? v.ctl->ph_nb_start : n;
+  unsigned long long killed = 0;
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double X = 0.0;
+    const uint64_t key = phm_photon_key(v, b, i, step, X);
+    if (!key) continue;
+    const int64_t h = phm_slot(v, key, false);
+    if (h < 0) continue;
+    const unsigned c = v.phm_cnt[h];
+    if (c < 2) continue;
+    const int gap = v.pgap[b][i];
+    const uint64_t id = v.pid[b][i];
+    v.pev[b][i] = kPhDead;
+    atomicSub(&v.ph_gap[gap], 1);
+    ++killed;
+    if (~id == v.phm_nid[h]) {  // the group's smallest id appends the merged photon
+      const GapDev &g = v.gaps[gap];
+      const double W = v.phm_W[h];
+      const uint64_t nid = child_id(id, (uint32_t)(step - 1), CH_MERGE, 0u) | kPhotonBit;
+      const double ts = -log(uniform53(g.seed, nid, (uint32_t)step, CH_BW_TAU, 0));
+      if (photon_append(v, b, gap, v.phm_WX[h] / W, (int32_t)step, v.phm_Wx[h] / W, W, ts, 0.0, nid, (int32_t)step,
+                        v.pdir[b][i], (int32_t)step))
+        atomicAdd(&v.ph_gap[gap], 1);
+      atomicAdd(&v.counters[gap * C_NCNT + C_PH_MERGED], (unsigned long long)(c - 1));
+    }
+  }
+  if (killed) atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->ph_dead), killed);
+}
+
+__global__ void k_phm_clear(View v) {
+  if (!(v.ctl->flags & 1)) return;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < v.phm_size; h += (int64_t)gridDim.x * blockDim.x) {
+    if (v.phm_key[h] == 0ull) continue;
+    v.phm_key[h] = 0ull;
+    v.phm_nid[h] = 0ull;
+    v.phm_W[h] = 0.0;
+    v.phm_Wx[h] = 0.0;
+    v.phm_WX[h] = 0.0;
+    v.phm_cnt[h] = 0u;
+  }
+}
+
 __global__ void k_merge_done(View v) { v.ctl->flags &= ~1; }
 
 void launch_merge(const View &v, cudaStream_t st) {
@@ -353,6 +475,11 @@ void launch_merge(const View &v, cudaStream_t st) {
   }
   if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
   else k_merge<double><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
+  if (v.phm_size > 0) {
+    k_phm_insert<<<2 * 148, 256, 0, st>>>(v);
+    k_phm_emit<<<2 * 148, 256, 0, st>>>(v);
+    k_phm_clear<<<2 * 148, 256, 0, st>>>(v);
+  }
   k_merge_done<<<1, 1, 0, st>>>(v);
   launch_filter(v, 1, st);  // smoothed re-centring correction of filter gaps
 }

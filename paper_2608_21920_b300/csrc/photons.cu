@@ -348,6 +348,7 @@ __global__ void k_photon_flip(View v) {
   c->ph_cur = b ^ 1;
   c->ph_dead = 0;
   c->need_ph_compact = 0;
+  c->ph_nb_start = 0;  // survivors in any order: the photon merge scans them all
 }
 
 void launch_photon_step(const View &v, cudaStream_t st) {

@@ -1796,6 +1796,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
     v.item_start[n] = carry;
     if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
     v.ctl->push_items = carry < v.item_cap ? carry : v.item_cap;
+    v.ctl->ph_nb_start = v.ctl->ph_count[v.ctl->ph_cur];  // photons born in this push lie beyond
     v.ctl->push_next = 0;
   }
 }
@@ -1887,7 +1888,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
-  return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? 3 : 0) + 5 +
+  return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
          (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0) + (v.pr_any ? 1 : 0) + (v.em_any ? 2 : 0);
 }
 

@@ -244,6 +244,20 @@ class Gap:
                                        self.stream()), self._h, "gap_sample_particles")
         return {k: v[:n.value] for k, v in out.items()}
 
+    def tile_particles(self, kind: int, tile_lo: int, tile_hi: int, gap: int = 0) -> dict:
+        """Leptons of one species stored in tiles [tile_lo, tile_hi) of a gap."""
+        L = A.lib()
+        n = C.c_int64(0)
+        L.gap_tile_particles(self._h, gap, kind, int(tile_lo), int(tile_hi), 0, None, None, None, None, None,
+                             C.byref(n), self.stream())
+        cap = n.value
+        out = dict(id=np.empty(cap, np.uint64), X=np.empty(cap), u=np.empty(cap), w=np.empty(cap),
+                   tau=np.empty(cap))
+        A.check(L.gap_tile_particles(self._h, gap, kind, int(tile_lo), int(tile_hi), cap, _ptr(out["id"]),
+                                     _ptr(out["X"]), _ptr(out["u"]), _ptr(out["w"]), _ptr(out["tau"]),
+                                     C.byref(n), self.stream()), self._h, "gap_tile_particles")
+        return {k: v[:n.value] for k, v in out.items()}
+
     def add_particles(self, kind: int, id, X, u, w, tau, n0=None, direction=None, gap: int = 0):
         id = np.ascontiguousarray(id, dtype=np.uint64)
         X, u, w, tau = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, u, w, tau))

@@ -76,7 +76,7 @@ def compare_field(Eg, Eo, rtol, what=""):
 
 
 COUNTER_KEYS = ("emit_events", "photons", "pairs", "injected", "absorbed", "escaped",
-                "photons_escaped", "emit_overflow", "inject_overflow", "merged")
+                "photons_escaped", "emit_overflow", "inject_overflow", "merged", "photons_merged")
 
 
 def compare_counters(cg, co, what=""):

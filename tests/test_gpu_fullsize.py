@@ -56,3 +56,46 @@ def test_config2_full_size_sampled_push_and_gauss():
     moved = np.abs((L["X"][oi] - np.concatenate([b["X"] for b in before])[np.argsort(
         np.concatenate([b["id"] for b in before]))]))
     assert np.median(np.minimum(moved, nx - moved)) > 1e-3  # the leptons did move
+
+
+def test_config2_full_size_window_field_parity():
+    """E^{n+1} at full size, node by node: the leptons of four tiles (1024
+    nodes) and of one tile of halo on each side are exported from the GPU
+    (gap_tile_particles), pushed one step by the oracle from the GPU's own
+    state and E^n, and the oracle's E^{n+1} = E^n + dt (j_m - J) on every
+    node of the four tiles must match the GPU's.  The difference comes only
+    from FP32 positions: each lepton's new offset lies within 2^-23 (grid) +
+    2^-23 (rounding of the FP32 drift) of the FP64 one, and at most the ~400
+    leptons whose clouds straddle a node move its charge, so per node
+    |dE| <= 400 w0 2^-22 (w0 = 2.5e-4); the step's own change of E is ~1e-3."""
+    from paper_2608_21920_b300 import Gap
+    cfg = dict(bench.WORKLOAD, nx=1 << 20, seed=0, gap_index=0)
+    nx, tile = cfg["nx"], 256
+    t_lo, t_hi = 1000, 1004
+    g = Gap(cfg, precision="fp32", tile=tile, threads=256, variant=0)
+    try:
+        g.step(3)
+        E0 = g.field()
+        lep = [g.tile_particles(kind, t_lo - 1, t_hi + 1) for kind in (0, 1)]
+        c = g.diag(spectrum=False)["counters"]
+        g.step(1)
+        E1 = g.field()
+    finally:
+        g.close()
+    assert c["spilled"] == 0
+    o = O.Sim(nx=nx, boundary=O.BC_PERIODIC, dx=cfg["dx"], dt=cfg["dt"], init=O.INIT_EMPTY)
+    o.set_E(E0)
+    w0 = cfg["density"] * cfg["dx"] / cfg["ppc"] / 2
+    for kind, q in ((0, -1), (1, 1)):
+        L = lep[kind]
+        assert L["id"].size > 6 * tile * cfg["ppc"] * 0.9
+        assert np.allclose(L["w"], w0, rtol=1e-12)
+        for i in range(L["id"].size):
+            o.add_lepton(int(L["id"][i]), q, float(L["X"][i]), float(L["u"][i]), float(L["w"][i]))
+    o.step(1)
+    Eo = o.E()
+    nodes = np.arange(t_lo * tile, t_hi * tile + 1)
+    err = np.abs(E1[nodes] - Eo[nodes])
+    dE = np.abs(Eo[nodes] - E0[nodes])
+    assert err.max() <= 400 * w0 * 2.0 ** -22, err.max()
+    assert np.median(dE) > 1e3 * 400 * w0 * 2.0 ** -22  # the step moved E far more than the bound

@@ -120,3 +120,70 @@ def test_merge_graph_replay_matches_eager():
         assert ca[k] == cb[k], k
     # shared-memory FP64 sums in the merge add in a run-dependent order
     assert np.abs(a.field() - b.field()).max() <= 1e-12 * np.abs(a.field()).max()
+
+
+def _emitting_pair(precision, cap, n=400, cells=(5, 6, 20, 40), seed=3):
+    """Leptons at gamma ~ 1000 that emit about two photons each per step,
+    crowded into a few cells, the same on both sides (ids, optical depths)."""
+    cfg = dict(nx=64, boundary=O.BC_PERIODIC, qed=1, b=0.1, lambda_hat=1e-5, rho_hat=20.0, rate_mult=100.0,
+               dx=0.1, dt=0.045, gap_length=6.4, cap=cap, seed=7, ppc=1, density=1.0)
+    g, o = P.make_pair(cfg, precision, tile=16)
+    rng = np.random.default_rng(seed)
+    rows = {0: [], 1: []}
+    for i in range(n):
+        X = cells[i % len(cells)] + 0.1 + 0.8 * rng.random()
+        u = (1 if i % 3 else -1) * 1000.0 * (1 + 0.1 * rng.random())
+        q = -1 if i % 2 else 1
+        w = 0.1 * (1 + np.floor(8 * rng.random()) / 8)  # whole FP32 weight units
+        tau = -np.log(rng.random())
+        o.add_lepton(i + 1, q, X, u, w, tau)
+        rows[0 if q < 0 else 1].append((i + 1, X, u, w, tau))
+    for kind, r in rows.items():
+        a = np.array(r)
+        g.add_particles(kind, a[:, 0].astype(np.uint64), a[:, 1], a[:, 2], a[:, 3], a[:, 4])
+    return g, o
+
+
+def _photons_by_id(p):
+    order = np.argsort(p["id"])
+    return {k: v[order] for k, v in p.items()}
+
+
+def test_photon_merge_at_birth_matches_oracle_fp64():
+    """Photons born in an over-cap step merge by (cell, direction, ln x bin):
+    the GPU's merged photons (ids, positions, energies, weights, threshold
+    depths, birth steps) equal the oracle's within 1e-10 over three steps,
+    with the same counts of merged photons and leptons."""
+    g, o = _emitting_pair("fp64", cap=50)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        cg, co = g.diag(spectrum=False)["counters"], o.counters()
+        P.compare_counters(cg, co, f"step {o.stepno}")
+        a, b = _photons_by_id(g.particles(2)), _photons_by_id(o.photons())
+        assert np.array_equal(a["id"], b["id"])
+        for k in ("X", "x", "w", "tau_star"):
+            d = np.abs(a[k] - b[k]) / np.maximum(np.abs(b[k]), 1.0)
+            assert d.max(initial=0.0) <= RTOL64, (k, d.max())
+        assert np.array_equal(a["n0"], b["n0"]) and np.array_equal(a["dir"], b["dir"])
+        P.compare_leptons(P.leptons_gpu(g), P.leptons_oracle(o), RTOL64, f"leptons step {o.stepno}", period=64)
+    assert co["photons_merged"] > 100
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_photon_merge_conserves_against_an_uncapped_twin(precision):
+    """The photons of a capped run after one step carry exactly the weight,
+    energy and momentum of an uncapped twin's photons (the same emissions
+    before the merge), in fewer photons."""
+    a, _ = _emitting_pair(precision, cap=0)
+    b, _ = _emitting_pair(precision, cap=50)
+    a.step(1)
+    b.step(1)
+    pa, pb = a.particles(2), b.particles(2)
+    assert pb["id"].size < pa["id"].size
+    assert b.diag(spectrum=False)["counters"]["photons_merged"] == pa["id"].size - pb["id"].size
+    for f in (lambda p: p["w"], lambda p: p["w"] * p["x"], lambda p: p["w"] * p["x"] * p["dir"]):
+        assert f(pb).sum() == pytest.approx(f(pa).sum(), rel=1e-12)
+    a.close()
+    b.close()

@@ -1128,3 +1128,83 @@ def test_protons_are_neither_merged_nor_counted():
     assert s.counters()["merged"] > 0 and n_e <= 300 < n_e + p0.size
     r, emax = s.gauss_residual()
     assert r < 1e-13 * max(1.0, emax)
+
+
+# ------------------------------------------------------------------ photon merge
+def _emitting_leptons(cap, n=400, cells=(5, 6, 20, 40), seed=3):
+    """Leptons at gamma ~ 1000 (chi ~ 0.5) that emit about two photons each
+    per step, crowded into a few cells and moving both ways."""
+    s = O.Sim(nx=64, boundary=O.BC_PERIODIC, qed=1, b=0.1, lambda_hat=1e-5, rho_hat=20.0, rate_mult=100.0,
+              dx=0.1, dt=0.045, gap_length=6.4, cap=cap, seed=7)
+    rng = np.random.default_rng(seed)
+    for i in range(n):
+        X = cells[i % len(cells)] + 0.1 + 0.8 * rng.random()
+        u = (1 if i % 3 else -1) * 1000.0 * (1 + 0.1 * rng.random())
+        s.add_lepton(i + 1, -1 if i % 2 else 1, X, u, 1.0 + rng.random(), -math.log(rng.random()))
+    return s
+
+
+def _photon_key(X, d, x, width=0.1):
+    return (int(np.floor(X)) % 64, int(d), min(max(int(np.floor(np.log(x) / width)), 0), 255))
+
+
+def test_photon_merge_conserves_weight_energy_and_momentum_per_group():
+    """Photons merged at birth under the cap (N -> 1): the photons born in a
+    step of each (cell, direction, ln x bin of width 0.1 at the first
+    over-cap step) group become one photon with the group's weight, energy
+    sum w x, momentum sum w x dir and weighted mean position; a lone photon
+    keeps its record.  Against a twin run without a cap, whose photons after
+    the same step are exactly the unmerged set."""
+    a, b = _emitting_leptons(0), _emitting_leptons(50)
+    a.step(1)
+    b.step(1)
+    pa, pb = a.photons(), b.photons()
+    assert np.all(pa["n0"] == 1) and pa["id"].size > 400
+    groups = {}
+    for j in range(pa["id"].size):
+        groups.setdefault(_photon_key(pa["X"][j], pa["dir"][j], pa["x"][j]), []).append(j)
+    assert pb["id"].size == len(groups) < pa["id"].size
+    assert b.counters()["photons_merged"] == pa["id"].size - len(groups)
+    got = {_photon_key(pb["X"][j], pb["dir"][j], pb["x"][j]): j for j in range(pb["id"].size)}
+    assert len(got) == len(groups)
+    for k, m in groups.items():
+        j = got[k]
+        W = pa["w"][m].sum()
+        assert pb["w"][j] == pytest.approx(W, rel=1e-14)
+        assert pb["w"][j] * pb["x"][j] == pytest.approx((pa["w"][m] * pa["x"][m]).sum(), rel=1e-14)
+        assert pb["X"][j] == pytest.approx((pa["w"][m] * pa["X"][m]).sum() / W, rel=1e-14)
+        assert pb["n0"][j] == 1 and pb["tau_acc"][j] == 0.0
+        if len(m) == 1:
+            assert pb["id"][j] == pa["id"][m[0]] and pb["tau_star"][j] == pa["tau_star"][m[0]]
+        else:
+            assert pb["id"][j] == O.child_id(int(pa["id"][m].min()), 0, O.CH_MERGE, 0) | O.PHOTON_BIT
+    for f in (lambda p: p["w"], lambda p: p["w"] * p["x"], lambda p: p["w"] * p["x"] * p["dir"]):
+        assert f(pb).sum() == pytest.approx(f(pa).sum(), rel=1e-13)
+
+
+def test_merged_photons_convert_by_the_law_with_their_energy():
+    """A merged photon is a newborn photon of energy sum w x / W: it converts
+    by P(converted by step m) = 1 - exp(-tau_m(x)), tau the depth of eq.
+    tau_bw accumulated step by step at the angle of Sect. 6.1, and its pair
+    carries its whole weight.  About 1500 merged photons followed over 40
+    steps: the surviving weight against its expectation within 5 sigma."""
+    s = _emitting_leptons(50, n=4000, cells=tuple(range(2, 62)), seed=4)
+    s.step(1)
+    ph = s.photons()
+    m = (ph["w"] > 2.5) & (ph["n0"] == 1)  # merged: two or more members of weight >= 1
+    ids, x, W = ph["id"][m], ph["x"][m], ph["w"][m]
+    assert ids.size > 800
+    cfg = s.cfg
+    dt, rho, b = cfg["dt"], cfg["rho_hat"], cfg["b"]
+    k = cfg["rate_mult"] * O.ALPHA_EM / cfg["lambda_hat"] * b
+    tau = np.zeros(ids.size)
+    for step in range(1, 41):
+        sp = abs(math.sin((step - 1 + 0.5) * dt / rho))
+        tau += dt * k * sp * np.array([O.tbw(xi * b * sp) for xi in x])
+        s.step(1)
+        if step % 10 == 0:
+            alive = np.isin(ids, s.photons()["id"])
+            p = np.exp(-tau)
+            expect, sd = (W * p).sum(), math.sqrt((W ** 2 * p * (1 - p)).sum())
+            assert abs(W[alive].sum() - expect) <= 5 * sd + 1e-9 * W.sum(), (step, W[alive].sum(), expect, sd)
+    assert np.exp(-tau).mean() < 0.7  # a good part converted
