@@ -294,6 +294,29 @@ int gap_sample_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t strid
                          uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,
                          int64_t *n_out, void *stream);
 
+/* Spectra of gap `gap` (Sect. 6.4, Fig. 6: the momentum distribution of the
+ * pair plasma over h in [0, H_gap] and the photon energy spectrum): the total
+ * weight (real particles per unit area, n_co d_e units) of the electrons
+ * (host_leptons[0 .. nbins)), the positrons (host_leptons[nbins .. 2 nbins))
+ * and the photons (host_photons[0 .. nbins)) with position below H_gap, per
+ * bin of ln p (p = |u| = gamma beta) or ln x (photons): nbins uniform bins
+ * over [lo, hi), values below lo (p = 0 included) counted in the first bin,
+ * values at or above hi in the last.  Leptons spilled since the last
+ * compaction (counter `spilled`) are left out.  1 <= nbins <= 1024 and
+ * hi > lo, else GAP_EINVAL.  Either output may be NULL.  Synchronises
+ * `stream`. */
+int gap_spectra(gap_handle *h, int32_t gap, int32_t nbins, double lo, double hi, double *host_leptons,
+                double *host_photons, void *stream);
+
+/* Return flux of gap `gap` (Sect. 6.5, Fig. 7: the pairs that fall back onto
+ * the star and heat its atmosphere): the total weight of the electrons and
+ * positrons absorbed at h < 0 since gap_init, per bin of ln gamma at
+ * absorption: host_out[i] holds 10^(i/8) <= gamma < 10^((i+1)/8) for
+ * i < GAP_RETURN_BINS - 1, the last bin every gamma above.  Protons are not
+ * tallied.  Synchronises `stream`. */
+#define GAP_RETURN_BINS 64
+int gap_return_spectrum(gap_handle *h, int32_t gap, double *host_out, void *stream);
+
 /* Export the leptons of one species (kind 0 electrons, 1 positrons) stored
  * in tiles [tile_lo, tile_hi) of gap `gap` (tile i holds the leptons whose
  * dual cell k = floor(X + 1/2) lies in [i tile, (i + 1) tile), tile the

@@ -100,6 +100,8 @@ def lib():
         L.orc_cell_charge.argtypes = [vp, i64]; L.orc_cell_charge.restype = d
         L.orc_gauss_residual.argtypes = [vp, pd]; L.orc_gauss_residual.restype = d
         L.orc_moments.argtypes = [vp, pd, pd, pd, pd]
+        L.orc_return_spectrum.argtypes = [vp, pd]
+        L.orc_spectra.argtypes = [vp, i32, d, d, pd, pd]
         for f in ("orc_nlep", "orc_nph", "orc_nnode", "orc_stepno"):
             getattr(L, f).argtypes = [vp]; getattr(L, f).restype = i64
         for f in ("orc_w0", "orc_eta_bg"):
@@ -330,6 +332,20 @@ class Sim:
         g3w, wsum, charge = np.empty(nx), np.empty(nx), np.empty(nx)
         lib().orc_moments(self.h, _pd(dens), _pd(g3w), _pd(wsum), _pd(charge))
         return dict(dens=dens.reshape(2, 2, nx), g3w=g3w, wsum=wsum, charge=charge)
+
+    def return_spectrum(self):
+        """Weight of the e+- absorbed at h < 0 so far per bin of ln gamma
+        (bin i: 10^(i/8) <= gamma < 10^((i+1)/8), the last open)."""
+        out = np.empty(64)
+        lib().orc_return_spectrum(self.h, _pd(out))
+        return out
+
+    def spectra(self, nbins, lo, hi):
+        """Weight per bin of ln p (electrons, positrons) and ln x (photons) in
+        the gap, nbins uniform bins over [lo, hi), clamped at both ends."""
+        lep, ph = np.empty(2 * nbins), np.empty(nbins)
+        lib().orc_spectra(self.h, int(nbins), float(lo), float(hi), _pd(lep), _pd(ph))
+        return lep.reshape(2, nbins), ph
 
     def diag(self):
         """Gap diagnostics of Sect. 6.2 / Fig. 5 from the per-cell moments."""

@@ -483,6 +483,8 @@ typedef struct {
   orc_photon *ph;  int64_t nph, capph;
   int64_t step;
   int32_t merge_level; /* consecutive over-cap steps (bin width 0.1 * 2^level) */
+  double ret_hist[64]; /* return flux (Sect. 6.5, Fig. 7): weight of e+- absorbed at
+                          h < 0 per bin of ln gamma, eight bins per decade from gamma = 1 */
   orc_counters cnt;
 } orc_sim;
 
@@ -502,6 +504,21 @@ static void push_lepton(orc_sim *s, orc_lepton L) {
   }
   s->lep[s->nlep++] = L;
 }
+/* bin of the return-flux tally: eight per decade of gamma from gamma = 1 */
+static int return_bin(double g) {
+  double b = floor(log(g) / (log(10.0) / 8.0));
+  if (!(b >= 0.0)) b = 0.0;
+  if (b > 63.0) b = 63.0;
+  return (int)b;
+}
+/* bin of a spectrum over [lo, hi) in nbins uniform bins, clamped */
+static int spectrum_bin(double z, int32_t nbins, double lo, double hi) {
+  double b = floor((z - lo) / (hi - lo) * (double)nbins);
+  if (!(b >= 0.0)) b = 0.0;
+  if (b > (double)(nbins - 1)) b = (double)(nbins - 1);
+  return (int)b;
+}
+
 static void push_photon(orc_sim *s, orc_photon P) {
   if (s->nph == s->capph) {
     s->capph = s->capph ? 2 * s->capph : 1024;
@@ -1102,6 +1119,7 @@ void orc_step(orc_sim *s) {
       X1 = wrap(p, X1);
     } else if (X1 < 0.0) {
       L->alive = 0; s->cnt.absorbed++; s->cnt.e_absorbed += L->w * g * lepton_mass(p, L);
+      if (!L->heavy) s->ret_hist[return_bin(g)] += L->w;
     } else if (X1 >= (double)p->nx) {
       L->alive = 0; s->cnt.escaped++; s->cnt.e_escaped += L->w * g * lepton_mass(p, L);
     }
@@ -1311,6 +1329,37 @@ double orc_gauss_residual(const orc_sim *s, double *max_abs_E) {
  * density of each species split by direction (u >= 0 up, u < 0 down), the
  * weighted sums of gamma^-3 and of the weight (for <gamma^-3>), and the
  * charge.  Arrays have nx entries; dens is [2 species][2 dirs][nx]. */
+/* Return flux (Sect. 6.5): the e+- absorbed at h < 0 since the start, as
+ * weight per bin of ln gamma: bin i holds 10^(i/8) <= gamma < 10^((i+1)/8),
+ * the last bin everything above. */
+void orc_return_spectrum(const orc_sim *s, double *out) {
+  for (int i = 0; i < 64; ++i) out[i] = s->ret_hist[i];
+}
+
+/* Spectra of the gap (Sect. 6.4, Fig. 6: the pair plasma's momentum
+ * distribution over h in [0, H_gap] and the photon energy spectrum): the
+ * weight of the electrons (lep[0..nbins)), the positrons (lep[nbins..2 nbins))
+ * and the photons (ph) in the gap, per bin of ln p (p = |u| = gamma beta) or
+ * ln x, nbins uniform bins over [lo, hi); values below lo (p = 0 included)
+ * count in the first bin, values at or above hi in the last. */
+void orc_spectra(const orc_sim *s, int32_t nbins, double lo, double hi, double *lep, double *ph) {
+  const orc_params *p = &s->p;
+  const double Hc = p->gap_length / p->dx;
+  for (int i = 0; i < 2 * nbins; ++i) lep[i] = 0.0;
+  for (int i = 0; i < nbins; ++i) ph[i] = 0.0;
+  for (int64_t i = 0; i < s->nlep; ++i) {
+    const orc_lepton *L = &s->lep[i];
+    if (L->heavy || !(L->X < Hc)) continue;
+    const int sp = L->q < 0 ? 0 : 1;
+    lep[sp * nbins + spectrum_bin(log(fabs(L->u)), nbins, lo, hi)] += L->w;
+  }
+  for (int64_t i = 0; i < s->nph; ++i) {
+    const orc_photon *P = &s->ph[i];
+    if (!(P->X < Hc)) continue;
+    ph[spectrum_bin(log(P->x), nbins, lo, hi)] += P->w;
+  }
+}
+
 void orc_moments(const orc_sim *s, double *dens, double *g3w, double *wsum, double *charge) {
   const orc_params *p = &s->p;
   int64_t nx = p->nx;

@@ -13,6 +13,7 @@ GAP_BC_SURFACE, GAP_BC_PERIODIC = 0, 1
 GAP_INIT_EMPTY, GAP_INIT_COLD, GAP_INIT_PAIR_THERMAL, GAP_INIT_GAP_PROTONS = 0, 1, 2, 3
 GAP_ELECTRON, GAP_POSITRON, GAP_PHOTON, GAP_PROTON = 0, 1, 2, 3
 GAP_EM_EY, GAP_EM_EZ, GAP_EM_BY, GAP_EM_BZ = 0, 1, 2, 3
+GAP_RETURN_BINS = 64
 
 
 class GapParams(C.Structure):
@@ -86,6 +87,8 @@ def lib():
     L.gap_get_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_sample_particles.argtypes = [vp, i32, i32, i64, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
     L.gap_tile_particles.argtypes = [vp, i32, i32, i32, i32, i64, vp, vp, vp, vp, vp, C.POINTER(i64), vp]
+    L.gap_spectra.argtypes = [vp, i32, i32, d, d, vp, vp, vp]
+    L.gap_return_spectrum.argtypes = [vp, i32, vp, vp]
     L.gap_add_particles.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
     L.gap_solve_gauss.argtypes = [vp, i32, vp]
     L.gap_set_background.argtypes = [vp, i32, d]
@@ -115,7 +118,7 @@ def lib():
 
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
-            "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_tile_particles", "gap_add_particles",
+            "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_tile_particles", "gap_spectra", "gap_return_spectrum", "gap_add_particles",
             "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint"]
 

@@ -523,6 +523,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.fft[0] = C.take<double>(2 * (size_t)max_P);
   v.fft[1] = C.take<double>(2 * (size_t)max_P);
   v.dred = C.take<double>(32);
+  v.ret_hist = C.take<double>((size_t)n * kRetBins);
+  v.spec_buf = C.take<double>(3 * (size_t)kSpecMaxBins);
   unsigned long long *export_count = C.take<unsigned long long>(4);
   size_t meta_end = C.off;
   for (int s = 0; s < 2; ++s) {
@@ -892,6 +894,39 @@ static int export_particles(gap_handle *h, int32_t gap, int32_t kind, int64_t st
                             uint64_t *host_id, double *host_X, double *host_u, double *host_w,
                             double *host_tau, double *host_aux, int64_t *host_aux2, int64_t *n_out,
                             void *stream, int32_t tile_lo = -1, int32_t tile_hi = -1);
+
+int gap_return_spectrum(gap_handle *h, int32_t gap, double *host_out, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || !host_out) return GAP_EINVAL;
+  if (h->status) return h->status;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host_out, h->v.ret_hist + (size_t)gap * kRetBins, sizeof(double) * kRetBins,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "return spectrum");
+}
+
+int gap_spectra(gap_handle *h, int32_t gap, int32_t nbins, double lo, double hi, double *host_leptons,
+                double *host_photons, void *stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || nbins < 1 || nbins > kSpecMaxBins || !(hi > lo)) return GAP_EINVAL;
+  if (h->status) return h->status;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(h->v.spec_buf, 0, sizeof(double) * 3 * kSpecMaxBins, st);
+  if (e == cudaSuccess) {
+    launch_spectra(h->v, gap, h->gaps_h[gap].n_tiles, nbins, lo, hi, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && host_leptons) {
+    e = cudaMemcpyAsync(host_leptons, h->v.spec_buf, sizeof(double) * nbins, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host_leptons + nbins, h->v.spec_buf + kSpecMaxBins, sizeof(double) * nbins,
+                          cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && host_photons)
+    e = cudaMemcpyAsync(host_photons, h->v.spec_buf + 2 * kSpecMaxBins, sizeof(double) * nbins,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_check(h, e, "spectra");
+}
 
 int gap_tile_particles(gap_handle *h, int32_t gap, int32_t kind, int32_t tile_lo, int32_t tile_hi, int64_t cap,
                        uint64_t *host_id, double *host_X, double *host_u, double *host_w, double *host_tau,

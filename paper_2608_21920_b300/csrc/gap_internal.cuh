@@ -29,6 +29,10 @@ constexpr int kWeightShift = 8;                // FP32 weight unit = w0 / 2^8
 __device__ __forceinline__ double grid_position(double X) { return rint((X + 0.5) * 8388608.0) * kPhiUnit - 0.5; }
 __device__ __forceinline__ long long grid_units(double f) { return llrint(f * 8388608.0); }
 constexpr int kMaxEmit = 16;                   // emission events per lepton-step (upper bound)
+// Return-flux tally (Sect. 6.5): eight bins per decade of gamma from gamma = 1
+constexpr int kRetBins = 64;
+constexpr double kRetDln = 0.28782313662425574;  // ln 10 / 8
+constexpr int kSpecMaxBins = 1024;              // gap_spectra: bins per histogram at most
 constexpr int kPushChunk = 8192;  // leptons per push work item (multiple of 32; the limb bound below)
 static_assert(kPushChunk <= 8192, "the 19-bit charge limbs hold at most 8192 contributions per node");
 
@@ -208,6 +212,8 @@ struct View {
   double *fft[2];               // complex scratch [2][2*max_P]
   int64_t max_nx, max_P, dcharge_len;
   double *dred;                 // reduction outputs
+  double *ret_hist;             // [gap][kRetBins] return flux: weight of e+- absorbed at h < 0 per ln gamma bin
+  double *spec_buf;             // [3][kSpecMaxBins] scratch of gap_spectra
   // export / import staging (the inactive buffers are used as scratch)
 };
 
@@ -822,6 +828,15 @@ __device__ __forceinline__ float bw_step_depth_f(const GapDev &g, float x, int32
   const float sp = fabsf(sinf(lmid / g.f_rho));
   const float chi = x * (float)g.b * sp;
   return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * (float)g.b * sp * tbw_f(chi);
+}
+
+// Tally one e+- absorbed at h < 0 (the return flux of Sect. 6.5) with weight
+// w in the bin of ln gamma, gamma from its momentum in double precision.
+__device__ __forceinline__ void tally_return(const View &v, int gap, double u, double w) {
+  double b = floor(log(sqrt(1.0 + u * u)) / kRetDln);
+  if (!(b >= 0.0)) b = 0.0;
+  if (b > (double)(kRetBins - 1)) b = (double)(kRetBins - 1);
+  atomicAdd(&v.ret_hist[gap * kRetBins + (int)b], w);
 }
 
 }  // namespace gapk

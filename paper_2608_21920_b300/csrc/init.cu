@@ -700,4 +700,73 @@ void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Spectra of one gap (Sect. 6.4, Fig. 6): the weight of the e- and e+ in the
+// gap (X < H_gap) per bin of ln p, p = |u| = gamma beta, and of its photons
+// per bin of ln x, nbins uniform bins over [lo, hi) clamped at both ends, into
+// v.spec_buf [e- | e+ | photons], kSpecMaxBins each (cleared by the caller).
+__device__ __forceinline__ int spectrum_bin(double z, int nbins, double lo, double hi) {
+  double b = floor((z - lo) / (hi - lo) * (double)nbins);
+  if (!(b >= 0.0)) b = 0.0;
+  if (b > (double)(nbins - 1)) b = (double)(nbins - 1);
+  return (int)b;
+}
+
+template <class R>
+__global__ void k_spectra_leptons(View v, int gap, int nbins, double lo, double hi) {
+  using W = typename Prec<R>::W;
+  extern __shared__ double sh[];  // [2][nbins]
+  for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x) sh[i] = 0.0;
+  __syncthreads();
+  const GapDev &g = v.gaps[gap];
+  const int t = g.tile_begin + blockIdx.x;
+  const int cur = v.ctl->lep_cur;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t start = v.seg_start[s][t];
+    const int used = v.seg_used[s][t];
+    for (int i = threadIdx.x; i < used; i += blockDim.x) {
+      const int64_t slot = start + i;
+      const int32_t k = v.lk[cur][s][slot];
+      if (k < 0) continue;
+      const double X = (double)k + ((double)as<R>(v.lphi[cur][s])[slot] - 1.5);
+      if (!(X < g.Hc)) continue;
+      const double u = (double)as<R>(v.lu[cur][s])[slot];
+      const double w = v.has_w ? (sizeof(R) == 4 ? (double)as<W>(v.lw[cur][s])[slot] * g.w_unit
+                                                 : (double)as<W>(v.lw[cur][s])[slot])
+                               : g.w0;
+      atomicAdd(&sh[s * nbins + spectrum_bin(log(fabs(u)), nbins, lo, hi)], w);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x)  // species s at spec_buf[s kSpecMaxBins + bin]
+    if (sh[i] != 0.0) atomicAdd(&v.spec_buf[(i / nbins) * kSpecMaxBins + i % nbins], sh[i]);
+}
+
+__global__ void k_spectra_photons(View v, int gap, int nbins, double lo, double hi) {
+  const int b = v.ctl->ph_cur;
+  const int64_t n = photon_fill(v, b);
+  const int64_t step = v.ctl->step;
+  const GapDev &g = v.gaps[gap];
+  double *out = v.spec_buf + 2 * kSpecMaxBins;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (v.pev[b][i] == kPhDead || v.pgap[b][i] != gap) continue;
+    const double X = photon_pos(g, v.pXr[b][i], v.pnr[b][i], v.pdir[b][i], step);
+    if (!(X < g.Hc)) continue;
+    atomicAdd(&out[spectrum_bin(log(v.px[b][i]), nbins, lo, hi)], v.pw[b][i]);
+  }
+}
+
+void launch_spectra(const View &v, int gap, int n_tiles_gap, int nbins, double lo, double hi, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)nbins * sizeof(double);
+  static bool attr = false;
+  if (!attr) {  // up to 2 x 1024 doubles of shared memory
+    cudaFuncSetAttribute(k_spectra_leptons<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSpecMaxBins * 8);
+    cudaFuncSetAttribute(k_spectra_leptons<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSpecMaxBins * 8);
+    attr = true;
+  }
+  if (v.precision == GAP_FP32_STATE) k_spectra_leptons<float><<<n_tiles_gap, 256, smem, st>>>(v, gap, nbins, lo, hi);
+  else k_spectra_leptons<double><<<n_tiles_gap, 256, smem, st>>>(v, gap, nbins, lo, hi);
+  if (v.qed_any) k_spectra_photons<<<148, 256, 0, st>>>(v, gap, nbins, lo, hi);
+}
+
 }  // namespace gapk

@@ -45,5 +45,6 @@ void launch_export_impl(const View &v, int gap, int kind, double *stage, int64_t
                         int tile_first = 0);
 void launch_import(const View &v, int gap, int kind, int64_t n, const double *stage,
                    cudaStream_t st);
+void launch_spectra(const View &v, int gap, int n_tiles_gap, int nbins, double lo, double hi, cudaStream_t st);
 
 }  // namespace gapk

@@ -244,6 +244,22 @@ class Gap:
                                        self.stream()), self._h, "gap_sample_particles")
         return {k: v[:n.value] for k, v in out.items()}
 
+    def spectra(self, nbins: int, lo: float, hi: float, gap: int = 0):
+        """Weight per bin of ln p (electrons, positrons: [2, nbins]) and of ln x
+        (photons: [nbins]) in the gap, nbins uniform bins over [lo, hi)."""
+        lep, ph = np.empty(2 * nbins), np.empty(nbins)
+        A.check(A.lib().gap_spectra(self._h, gap, int(nbins), float(lo), float(hi), _ptr(lep), _ptr(ph),
+                                    self.stream()), self._h, "gap_spectra")
+        return lep.reshape(2, nbins), ph
+
+    def return_spectrum(self, gap: int = 0) -> np.ndarray:
+        """Weight of the e+- absorbed at h < 0 per bin of ln gamma (eight per
+        decade from gamma = 1; the last bin open)."""
+        out = np.empty(A.GAP_RETURN_BINS)
+        A.check(A.lib().gap_return_spectrum(self._h, gap, _ptr(out), self.stream()), self._h,
+                "gap_return_spectrum")
+        return out
+
     def tile_particles(self, kind: int, tile_lo: int, tile_hi: int, gap: int = 0) -> dict:
         """Leptons of one species stored in tiles [tile_lo, tile_hi) of a gap."""
         L = A.lib()
