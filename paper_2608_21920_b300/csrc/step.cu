@@ -166,10 +166,11 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   // (coalesced scalar loads) with QED, whose lepton body is large and
   // instruction-bound, so that it is inlined once
   constexpr int VEC = QED ? 1 : 16 / (int)sizeof(R);
-  // per-thread event counts and energies, reduced per warp at the end (one
-  // shared atomic per warp instead of one per event)
-  unsigned c_emit = 0, c_ovf = 0, c_abs = 0, c_esc = 0, c_phesc = 0, c_ph = 0;
-  double l_rad = 0.0, l_abs = 0.0, l_esc = 0.0, l_phesc = 0.0;
+  // events (emission, absorption, escape) are rare per lepton-step: each is
+  // counted by a shared atomic where it happens, so that an item ends without
+  // a warp reduction of the counters and FP64 ledgers (FP64 is slow here)
+  auto count = [&](int i) { atomicAdd(&sCnt[i], 1ull); };
+  auto ledger = [&](int i, double x) { atomicAdd(&sLed[i], x); };
   for (int s = s_only; s == s_only; ++s) {
     const int q = s == 0 ? -1 : 1;
     const int64_t start = v.seg_start[s][t] + r0;  // multiples of 32 slots: 16-byte aligned
@@ -236,13 +237,13 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       if (!periodic) {
         if (kn < 0 || (kn == 0 && pn < (R)1.5)) {
           gone = true;
-          ++c_abs;
-          l_abs += (double)w * wunit * (double)sqrt((R)1 + u * u);
+          count(2);
+          ledger(1, (double)w * wunit * (double)sqrt((R)1 + u * u));
           tally_return(v, ti.gap, (double)u, (double)w * wunit);
         } else if ((int64_t)kn > nx || ((int64_t)kn == nx && pn >= (R)1.5)) {
           gone = true;
-          ++c_esc;
-          l_esc += (double)w * wunit * (double)sqrt((R)1 + u * u);
+          count(3);
+          ledger(2, (double)w * wunit * (double)sqrt((R)1 + u * u));
         }
       } else {
         if (kn < 0) kn += (int32_t)nx;
@@ -259,15 +260,15 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           int32_t dirb = xb >= 0.0 ? 1 : -1;
           xb = fabs(xb);
           if (!inside) {
-            ++c_phesc;
-            l_phesc += wd * xb;
+            count(4);
+            ledger(3, wd * xb);
             continue;
           }
           uint64_t pid = child_id(id, (uint32_t)step, CH_PHOTON, (uint32_t)ph_k[b]) | kPhotonBit;
           double tsb = -log(uniform53(g.seed, pid, (uint32_t)(step + 1), CH_BW_TAU, 0));
           photon_append(v, phbuf, ti.gap, Xn, (int32_t)(step + 1), xb, wd, tsb, 0.0, pid, (int32_t)(step + 1),
                         dirb, (int32_t)(step + 1));
-          ++c_ph;
+          count(6);
         }
       }
       if (gone) {
@@ -337,16 +338,16 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau,
                                          g.qed_quantum != 0);
           const R x = xs >= (R)0 ? xs : -xs;
-          ++c_emit;
+          count(0);
           if (x >= (R)2) {
             ph_x[nph] = xs;  // the sign carries the direction
             ph_k[nph] = kk;
             ++nph;
           } else {
-            l_rad += (double)w * wunit * (double)x;
+            ledger(0, (double)w * wunit * (double)x);
           }
           if (++kk >= g.kmax_emit) {
-            ++c_ovf;
+            count(1);
             break;
           }
         }
@@ -521,26 +522,6 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     for (int o = 16; o > 0; o >>= 1) dead += __shfl_down_sync(0xffffffffu, dead, o);
     if ((threadIdx.x & 31) == 0 && dead) atomicAdd(&sDead[s], dead);
   }
-  {
-    unsigned cc[6] = {c_emit, c_ovf, c_abs, c_esc, c_phesc, c_ph};
-    double ll[4] = {l_rad, l_abs, l_esc, l_phesc};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) cc[i] += __shfl_down_sync(0xffffffffu, cc[i], o);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) ll[i] += __shfl_down_sync(0xffffffffu, ll[i], o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      const int slot[6] = {0, 1, 2, 3, 4, 6};
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        if (cc[i]) atomicAdd(&sCnt[slot[i]], (unsigned long long)cc[i]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (ll[i] != 0.0) atomicAdd(&sLed[i], ll[i]);
-    }
-  }
   __syncthreads();
 
   // a9: Ampere on the tile's nodes (a gap with a current filter leaves it to
@@ -609,7 +590,8 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     }
     if (nitems > 1 && threadIdx.x == 0) v.tile_done[t] = 0;
   }
-  for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+  if (__any_sync(0xffffffffu, work != 0.0))  // only the warps that finished nodes
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
   if ((threadIdx.x & 31) == 0 && work != 0.0)
     atomicAdd(&v.ledger[ti.gap * L_NLED + L_WORK], 0.5 * work * g.dt * g.dx * g.jm);
   __syncthreads();
