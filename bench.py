@@ -342,6 +342,7 @@ def run_ours(args):
         a64 = BYTES_PER_PARTICLE["fp64"] * N_PARTICLES / (r64["push_ms"] / 1e3) / 1e9
         line["fp64_plain"] = {"value": v64, "unit": UNIT, "steps": r64["K"], "ms_per_step": r64["ms"] / r64["K"],
                               "achieved_gbs": a64, "frac": a64 / peak, "gauss_residual": r64["gauss"],
+                              "bound": "fp64 alu (the FP64 pipe ~85 % busy in the push; profiles/k_push_fp64_cfg2.md)",
                               "fp32_over_fp64": value / v64}
     if qr is not None:
         line["qed"] = {"metric": METRIC, "value": qr["value"], "unit": UNIT, "steps": qr["steps"],
