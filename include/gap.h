@@ -481,6 +481,38 @@ int ode_adjoint(const void *dev_p, const void *dev_dt, const void *dev_ckpt, con
                 int32_t B, int32_t nsteps, int32_t every, int32_t ckpt_every, double delta,
                 int32_t dtype, void *dev_gp, void *dev_gy0, void *dev_scratch, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Extended concurrency model: the plasma-inertia measure <gamma^-3> as a
+ * state (Sect. 5.2 says the paper solved such a moment expansion of the 1D
+ * Vlasov equation without giving it; this one is the library's reading, in
+ * the paper's approximations).  State y = (m_pm, m_x, eps, j, G) with
+ * G = m_pm <gamma^-3>; parameters p = (alpha, t_x, t_pm, t_acc, gamma_min,
+ * gamma_rad), units t_esc = 1:
+ *   dm_pm/dt, dm_x/dt, deps/dt as in eq. dis1-dis3,
+ *   dj/dt = -j + eps G / t_acc                                  (eq. dis4)
+ *   dG/dt = 2 gamma_min^-3 m_x / t_pm                  (pairs born at gamma_min,
+ *                                                      eq. gam_inj)
+ *         - G                                          (escape)
+ *         - 3 eps j (G/m_pm)^(4/3) / t_acc             (field work on cold
+ *                                                      streams: <gamma^-4 q beta>
+ *                                                      = <gamma^-3>^(4/3) j/m_pm)
+ *         + 3 m_pm / (gamma_rad^4 t_acc)               (curvature losses,
+ *                                                      eq. dgamma_curv, balanced
+ *                                                      at gamma_rad, eq. gam_rad)
+ * (G/m)^(4/3) of max(G, 0).  Layouts as for ode_forward / ode_adjoint with
+ * 5 state and 6 parameter entries per set: dev_p [B][6], dev_y0 [B][5],
+ * dev_out [T][B][5], dev_ckpt [nsteps/ckpt_every + 1][B][5], dev_gp [B][6],
+ * dev_gy0 [B][5], dev_scratch (ckpt_every+1)*B*5 values.  The term in
+ * (G/m)^(4/3) makes the system stiff where t_acc is small: the step must
+ * resolve 3 eps (j/m) (G/m)^(1/3) / t_acc.
+ * ------------------------------------------------------------------------ */
+int ode_ext_forward(const void *dev_p, const void *dev_y0, const void *dev_dt, int32_t B, int32_t nsteps,
+                    int32_t every, int32_t ckpt_every, double delta, int32_t dtype, void *dev_out,
+                    void *dev_ckpt, void *stream);
+int ode_ext_adjoint(const void *dev_p, const void *dev_dt, const void *dev_ckpt, const void *dev_gout,
+                    int32_t B, int32_t nsteps, int32_t every, int32_t ckpt_every, double delta,
+                    int32_t dtype, void *dev_gp, void *dev_gy0, void *dev_scratch, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

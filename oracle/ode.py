@@ -58,6 +58,58 @@ def rk4(y0, p, dt, nsteps, delta=None, record_every=1):
     return torch.stack(out, dim=0)
 
 
+# --------------------------------------------------------------------------
+# Extended model: the plasma-inertia measure as a state.  Sect. 5.2 says the
+# paper solved a model with <gamma^-3> obtained by a moment expansion of the
+# 1D Vlasov equation but does not give it; this is one such moment, in the
+# paper's own approximations, with each closure stated:
+#
+#  * the moment of <gamma^-3> over the pair plasma, G = m_pm <gamma^-3>,
+#    escapes like m_pm (c d/dh -> c/L, the rate 1/t_esc = 1);
+#  * acceleration by the field: du/dt = eps/t_acc per unit charge along the
+#    force (the t_acc of eq. dis4), so d<gamma^-3>/dt = -3 <gamma^-4 q beta>
+#    eps/t_acc; the cold-beam closure <gamma^-4 q beta> = <gamma^-3>^(4/3)
+#    j/m_pm (one Lorentz factor per stream, beta -> 1 with the sign of the
+#    current) gives dG/dt = -3 eps j (G/m_pm)^(4/3) / t_acc;
+#  * curvature losses (eq. dgamma_curv): dgamma/dt = -gamma^4/(gamma_rad^4
+#    t_acc), gamma_rad where they balance the acceleration at eps = 1
+#    (eq. gam_rad), so d<gamma^-3>/dt = +3/(gamma_rad^4 t_acc) per particle;
+#  * pairs are born at gamma_min (eq. gam_inj) at the rate 2 m_x/t_pm of
+#    eq. dis1, bringing 2 gamma_min^-3 m_x/t_pm to G;
+#  * eq. dis4 with m_pm <gamma^-3> = G: dj/dt = -j + eps G/t_acc.
+#
+# State y = (m_pm, m_x, eps, j, G); parameters p = (alpha, t_x, t_pm, t_acc,
+# gamma_min, gamma_rad).  (G/m)^(4/3) is taken of max(G, 0).
+
+def rhs_ext(y, p, delta=None):
+    """Right-hand side of the extended model for a batch: y [B,5], p [B,6]."""
+    m, mx, eps, j, G = y[:, 0], y[:, 1], y[:, 2], y[:, 3], y[:, 4]
+    alpha, tx, tpm, tacc, gmin, grad = (p[:, i] for i in range(6))
+    H = gate(torch.abs(eps) - 1.0, delta)
+    g3 = torch.clamp(G, min=0.0) / m
+    dm = 2.0 * mx / tpm - m
+    dmx = -mx / tpm + H * m / tx - mx
+    deps = alpha - j
+    dj = -j + eps * G / tacc
+    dG = (2.0 * mx / tpm) * gmin ** -3 - G - 3.0 * eps * j * g3 ** (4.0 / 3.0) / tacc + 3.0 * m / (grad ** 4 * tacc)
+    return torch.stack([dm, dmx, deps, dj, dG], dim=1)
+
+
+def rk4_ext(y0, p, dt, nsteps, delta=None, record_every=1):
+    """RK4 of the extended model; states at steps 0, record_every, ... [T, B, 5]."""
+    y = y0
+    out = [y]
+    for n in range(nsteps):
+        k1 = rhs_ext(y, p, delta)
+        k2 = rhs_ext(y + 0.5 * dt * k1, p, delta)
+        k3 = rhs_ext(y + 0.5 * dt * k2, p, delta)
+        k4 = rhs_ext(y + dt * k3, p, delta)
+        y = y + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if (n + 1) % record_every == 0:
+            out.append(y)
+    return torch.stack(out, dim=0)
+
+
 def fig2_params():
     """Fig. 2 (Sect. 5.5): alpha = 2, t_x = t_pm = 1e-3, t_acc = 4e-8, g3 = 8e-8."""
     return dict(alpha=2.0, t_x=1e-3, t_pm=1e-3, t_acc=4e-8, g3=8e-8)
