@@ -59,7 +59,7 @@ __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t 
 // last of its items to finish does the update.  The four edge nodes shared
 // with the neighbouring tiles are finished by whichever of the two tiles
 // arrives second (atomic arrival count, no waiting).
-constexpr int kDeferQueue = 32 + 32 * 4;  // queue of a warp: < 32 left + one group of 32 lanes x 4
+constexpr int kDeferQueue = 32 + 32 * 4;  // queue of a warp: < 32 left + one group of 32 lanes x VD (VD <= 4)
 
 template <class R, bool QED, bool HAS_W, bool DEFER = false, int MINB = 3>
 __global__ void __launch_bounds__(256, MINB) k_push(View v) {
@@ -390,12 +390,12 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
 
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     if constexpr (DEFER) {
-      // 16-byte vectors of VD leptons per lane through push_quiet; a lepton
+      // 8-byte vectors of VD leptons per lane through push_quiet; a lepton
       // that emits this step is left unchanged and queued (its offset from
       // `start`) in the warp's queue, and whenever 32 are queued the warp
       // runs push_one on them, one per lane, so that the emission events of
       // a warp run side by side instead of one lane at a time.
-      constexpr int VD = 4;
+      constexpr int VD = 2;
       int *wq = s_queue + (threadIdx.x >> 5) * kDeferQueue;
       int qn = 0;  // warp-uniform
       auto drain = [&](const int n) {
@@ -429,22 +429,14 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           uv = *reinterpret_cast<const Vec<R, VD> *>(Up + slot0);
           if (HAS_W) wv = *reinterpret_cast<const Vec<W, VD> *>(Wp + slot0);
           tv = *reinterpret_cast<const Vec<R, VD> *>(Tp + slot0);
-          // the vectors rotate through element 0, so that push_quiet is
-          // inlined once: a quarter of the instruction footprint, which the
-          // warps of a block otherwise wait on (instruction fetch)
-#pragma unroll 1
-          for (int jj = 0; jj < VD; ++jj) {
-            int32_t k = kv.a[0];
-            R ph = pv.a[0], uu = uv.a[0], ta = tv.a[0];
-            const W ww = HAS_W ? wv.a[0] : w_def;
-            if (jj < nvalid && k >= 0 && !push_quiet(k, ph, uu, ww, ta, slot0 + jj)) later |= 1u << jj;
+          // two leptons per lane: push_quiet inlined twice (four copies
+          // made the warps wait on instruction fetch; one copy with the
+          // vectors rotating through element 0 cost more in moves)
 #pragma unroll
-            for (int r = 0; r < VD - 1; ++r) {
-              kv.a[r] = kv.a[r + 1]; pv.a[r] = pv.a[r + 1]; uv.a[r] = uv.a[r + 1]; tv.a[r] = tv.a[r + 1];
-              if (HAS_W) wv.a[r] = wv.a[r + 1];
-            }
-            kv.a[VD - 1] = k; pv.a[VD - 1] = ph; uv.a[VD - 1] = uu; tv.a[VD - 1] = ta;
-            if (HAS_W) wv.a[VD - 1] = ww;
+          for (int jj = 0; jj < VD; ++jj) {
+            if (jj < nvalid && kv.a[jj] >= 0 &&
+                !push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj))
+              later |= 1u << jj;
           }
           if (nvalid == VD) {
             *reinterpret_cast<Vec<int32_t, VD> *>(Kp + slot0) = kv;
