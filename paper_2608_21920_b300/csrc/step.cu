@@ -423,6 +423,15 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
         Vec<R, VD> pv, uv, tv;
         Vec<W, VD> wv;
         unsigned later = 0;
+        // the warp's next groups pulled into L2 (-2 %)
+        if (gi + nwarp * 32 < ngroups) {
+          const int64_t nslot = slot0 + (int64_t)nwarp * 32 * VD;
+          asm volatile("prefetch.global.L2 [%0];" :: "l"(Kp + nslot));
+          asm volatile("prefetch.global.L2 [%0];" :: "l"(Pp + nslot));
+          asm volatile("prefetch.global.L2 [%0];" :: "l"(Up + nslot));
+          asm volatile("prefetch.global.L2 [%0];" :: "l"(Wp + nslot));
+          asm volatile("prefetch.global.L2 [%0];" :: "l"(Tp + nslot));
+        }
         if (nvalid > 0) {
           kv = *reinterpret_cast<const Vec<int32_t, VD> *>(Kp + slot0);
           pv = *reinterpret_cast<const Vec<R, VD> *>(Pp + slot0);
