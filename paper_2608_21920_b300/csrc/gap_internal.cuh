@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gap.h"
+#include "qed_exact.cuh"
 
 namespace gapk {
 
@@ -512,23 +513,31 @@ __device__ __noinline__ R qspec_inverse(const View &v, R chi, R U) {
     d = exp((R)3 * catmull_rom<R>(p, t));
   }
   const R w = (R)3 * chi * d;
-  return w / ((R)2 + w);
+  const R xi = w / ((R)2 + w);
+  // FP64: Newton steps on the exact survival from the table's estimate
+  if (sizeof(R) == 8) return (R)qs_refine((double)chi, (double)U, (double)xi);
+  return xi;
 }
 
 // Pair energy split (qed_quantum): the electron's fraction e of the photon
-// energy for a conversion at chi and a draw U: the smaller share
+// energy for a conversion at chi and a draw U (with `exact`, the FP64 state's
+// case, refined on the exact distribution: qed_exact.cuh): the smaller share
 // e_s = 1/2 - eta with G = 2 min(U, 1 - U), inverted in float in four rows
 // of the table (the table's precision; float keeps the FP64 units free for
 // the conversions of a discharge) and its logarithm blended over ln chi in
 // double; e = e_s for U < 1/2, else 1 - e_s.  Below chi = 1e-3 the Gaussian
 // limit (variance 3 chi / 64) applies; above 1e4 the last row.
-__device__ __noinline__ static double bw_split(const View &v, double chi, double U) {
+__device__ __noinline__ static double bw_split(const View &v, double chi, double U, bool exact) {
   const double u = U < 0.5 ? U : 1.0 - U;
   double eta;
   if (!(chi > 0.0)) {
     eta = 0.0;
   } else if (chi < 1e-3) {
     eta = sqrt(3.0 * chi / 64.0) * 1.4142135623730951 * erfinv(1.0 - 2.0 * u);
+    if (exact) {  // FP64: Newton steps on the exact distribution from the Gaussian estimate
+      const double small = bw_refine(chi, u, 0.5 - eta);
+      return U < 0.5 ? small : 1.0 - small;
+    }
   } else {
     double rr = (log(chi) - kBwLchi0) / kQsDlchi;
     if (rr > (double)(kBwRows - 1)) rr = (double)(kBwRows - 1);
@@ -546,6 +555,7 @@ __device__ __noinline__ static double bw_split(const View &v, double chi, double
     for (int j = 0; j < 4; ++j) p[j] = ps[j] > 0.0f ? log((double)ps[j]) : -700.0;
     double small = exp(catmull_rom<double>(p, t));
     if (small > 0.5) small = 0.5;
+    if (exact) small = bw_refine(chi, u, small);  // FP64: the exact distribution
     return U < 0.5 ? small : 1.0 - small;
   }
   return U < 0.5 ? 0.5 - eta : 0.5 + eta;

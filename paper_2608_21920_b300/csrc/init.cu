@@ -661,7 +661,7 @@ void launch_qspec_inverse(const View &v, const double *chi, const double *U, dou
 
 __global__ void k_pair_split(View v, const double *chi, const double *U, double *e, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    e[i] = bw_split(v, chi[i], U[i]);
+    e[i] = bw_split(v, chi[i], U[i], true);
 }
 
 void launch_pair_split(const View &v, const double *chi, const double *U, double *e, int64_t n, cudaStream_t st) {

@@ -213,7 +213,7 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     if (g.qed_quantum) {
       const double lmid = ((double)step - (double)v.pn0[b][i] + 0.5) * g.dt;
       const double chi = x * g.b * fabs(sin(lmid / g.rho_hat));
-      const double e = bw_split(v, chi, uniform53(g.seed, id, (uint32_t)step, CH_PAIR_E, 0));
+      const double e = bw_split(v, chi, uniform53(g.seed, id, (uint32_t)step, CH_PAIR_E, 0), sizeof(R) == 8);
       // each share at least one rest mass, clamped on the energies (a
       // clamp on e would leave (1/x) x just below 1 for some x)
       ge = e * x;

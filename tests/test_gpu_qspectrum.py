@@ -1,13 +1,17 @@
 """The quantum photon spectrum option (qed_quantum) on the CUDA path: the
-table inverse against the oracle's exact inverse, and one emission of each of
-800 leptons at chi = 2 against the oracle's emissions from the same draws.
+inverse against the oracle's exact inverse, one emission of each of 800
+leptons at chi = 2 and a discharge against the oracle's from the same draws.
 
-Tolerance: the table interpolates ln s = ln d / 3 over rows of ln chi (eight
-per decade, cubic) and the survival over 256 panels of s (cubic Hermite,
-panels crowded towards s = 0); its emulation against the exact inverse stays
-below 2e-5 relative in xi for chi in [1e-6, 1e5], so the FP64 bound is 1e-4.
-The FP32 evaluation adds float rounding of the survival (1e-7 absolute):
-relative 1e-3 for draws U <= 0.999."""
+Tolerances: the FP64 state refines the table's estimate by Newton steps on
+the exact survival (an exponential-integral reduction, qed_exact.cuh) and
+the pair split on the exact distribution (tanh-sinh), so it follows the
+oracle's exact inverses to rounding (1e-11 here, and the 1e-10 state parity
+of a discharge).  The FP32 state reads the table: it interpolates ln s =
+ln d / 3 over rows of ln chi (eight per decade, cubic) and the survival over
+256 panels of s (cubic Hermite, panels crowded towards s = 0), an emulation
+against the exact inverse below 2e-5 relative in xi for chi in [1e-6, 1e5],
+plus float rounding of the survival (1e-7 absolute): relative 1e-3 for draws
+U <= 0.999."""
 import math
 
 import numpy as np
@@ -28,7 +32,7 @@ def _gap(precision="fp64"):
     return Gap(P.gpu_params(QCFG), precision=precision, tile=16)
 
 
-@pytest.mark.parametrize("precision,rtol,umax", [("fp64", 1e-4, 1.0 - 1e-9), ("fp32", 1e-3, 0.999)])
+@pytest.mark.parametrize("precision,rtol,umax", [("fp64", 1e-11, 1.0 - 1e-9), ("fp32", 1e-3, 0.999)])
 def test_qspectrum_inverse_matches_oracle(precision, rtol, umax):
     g = _gap(precision)
     rng = np.random.default_rng(3)
@@ -40,7 +44,11 @@ def test_qspectrum_inverse_matches_oracle(precision, rtol, umax):
     ref = np.array([O.qspec_inverse(c, u) for c, u in zip(chi, U)])
     assert np.all((xi > 0) & (xi < 1))
     rel = np.abs(xi / ref - 1.0)
-    assert rel.max() <= rtol, (rel.max(), chi[rel.argmax()], U[rel.argmax()])
+    # near U = 1 both sides solve S(xi) = U S(0) with S(xi) and U S(0) equal to
+    # within (1 - U) S(0): the inverse is conditioned by 1/(1 - U), so rounding
+    # of S (1e-15) allows 1e-15/(1 - U) relative in xi
+    tol = np.maximum(rtol, 1e-14 / (1.0 - U)) if precision == "fp64" else rtol
+    assert np.all(rel <= tol), (rel.max(), chi[rel.argmax()], U[rel.argmax()])
     g.close()
 
 
@@ -53,7 +61,7 @@ def test_qspectrum_inverse_needs_a_quantum_gap():
     g.close()
 
 
-@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-4), ("fp32", 2e-3)])
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("fp32", 2e-3)])
 def test_quantum_emission_matches_oracle(precision, rtol):
     """tau = 0 makes every lepton emit once at the start of the step (a second
     event in the step is improbable: rate x dt ~ 3e-6); the recoil gives the
@@ -81,37 +89,30 @@ def test_quantum_emission_matches_oracle(precision, rtol):
 
 
 def test_pair_split_matches_oracle():
-    """The electron's share of a conversion: the table against the oracle's
-    exact inverse.  Its emulation bounds the smaller share's relative error
-    by 1.6e-5 for u = min(U, 1 - U) >= 1e-3 and 3.7e-3 down to u = 1e-6
-    (chi <= 1e4); the float inversion adds 1e-6; below chi = 1e-3 the
-    Gaussian limit holds to O(chi)."""
+    """The electron's share of a conversion (gap_pair_split, the FP64
+    evaluation): the table's estimate refined on the exact distribution
+    equals the oracle's exact inverse to 1e-11 of the smaller share, far
+    tail and Gaussian region (chi < 1e-3, where the estimate is the Gaussian
+    limit) included."""
     g = _gap("fp64")
-    cases = [(chi, U) for chi in (2e-3, 0.05, 1.0, 77.0, 1e3, 5e3)
+    cases = [(chi, U) for chi in (2e-4, 2e-3, 0.05, 1.0, 77.0, 1e3, 5e3)
              for U in (1e-6, 1e-5, 1e-4, 1e-3, 0.01, 0.2, 0.45, 0.5, 0.7, 0.999, 1 - 1e-5)]
     chi = np.array([c for c, _ in cases])
     U = np.array([u for _, u in cases])
     e = g.pair_split(torch.tensor(chi), torch.tensor(U)).cpu().numpy()
     ref = np.array([O.bw_split(c, u) for c, u in cases])
-    u = np.minimum(U, 1 - U)
     small_gpu, small_ref = np.minimum(e, 1 - e), np.minimum(ref, 1 - ref)
     rel = np.abs(small_gpu / small_ref - 1.0)
     off = U != 0.5
     assert np.all((e[off] < 0.5) == (U[off] < 0.5))
-    assert rel[u >= 1e-3].max() <= 1e-4, rel[u >= 1e-3].max()
-    assert rel.max() <= 6e-3, rel.max()
-    # Gaussian limit below the table
-    for c in (2e-4, 5e-4):
-        eg = g.pair_split(torch.tensor([c] * 3), torch.tensor([0.1, 0.3, 0.9])).cpu().numpy()
-        er = np.array([O.bw_split(c, x) for x in (0.1, 0.3, 0.9)])
-        assert np.all(np.abs(eg - er) <= 5e-3 * np.abs(er - 0.5))
+    assert rel.max() <= 1e-11, (rel.max(), chi[rel.argmax()], U[rel.argmax()])
     g.close()
 
 
 def test_quantum_pair_creation_matches_oracle():
-    """Photons converting in a gap with qed_quantum: the same pairs at the same
-    steps, the shares from the same draws (table tolerance), energy x split
-    exactly between the two."""
+    """Photons converting in a gap with qed_quantum (FP64 state): the same
+    pairs at the same steps, the shares from the same draws on the exact
+    distribution, and the pairs' states at 1e-10 of the oracle's."""
     cfg = dict(nx=512, boundary=O.BC_SURFACE, qed=1, qed_quantum=1, b=0.1, lambda_hat=1e-4, rho_hat=20.0,
                rate_mult=10.0, dx=0.1, dt=0.045, gap_length=51.2, ppc=1, density=1e-6)
     g, o = P.make_pair(cfg, "fp64", tile=64)
@@ -131,9 +132,24 @@ def test_quantum_pair_creation_matches_oracle():
     assert cg["pairs"] == co["pairs"] > 30
     a, b = P.leptons_gpu(g), P.leptons_oracle(o)
     assert np.array_equal(a["id"], b["id"])
-    ga, gb = np.sqrt(1 + a["u"] ** 2), np.sqrt(1 + b["u"] ** 2)
-    assert np.abs(ga / gb - 1.0).max() <= 5e-3
-    assert np.median(np.abs(ga / gb - 1.0)) <= 1e-4
+    P.compare_leptons(a, b, 1e-10, "pairs of the quantum split")
+    g.close()
+
+
+def test_config1_quantum_parity_first_200_steps():
+    """Config 1 with the quantum photon spectrum and pair split (FP64): E and
+    every lepton within 1e-10 of the oracle with identical event counters over
+    the first 200 steps (the survey's parity criterion), the emissions drawn
+    on the exact spectrum."""
+    cfg = dict(P.CONFIG1, qed_quantum=1)
+    g, o = P.make_pair(cfg, "fp64", tile=64)
+    for n in (100, 200):
+        g.step(n - o.stepno)
+        o.step(n - o.stepno)
+        P.compare_counters(g.diag(spectrum=False)["counters"], o.counters(), f"step {n}")
+        P.compare_field(g.field(), o.E(), 1e-10, f"E step {n}")
+        P.compare_leptons(P.leptons_gpu(g), P.leptons_oracle(o), 1e-10, f"leptons step {n}")
+    assert o.counters()["emit_events"] > 300
     g.close()
 
 

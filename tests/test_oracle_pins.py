@@ -1208,3 +1208,73 @@ def test_merged_photons_convert_by_the_law_with_their_energy():
             expect, sd = (W * p).sum(), math.sqrt((W ** 2 * p * (1 - p)).sum())
             assert abs(W[alive].sum() - expect) <= 5 * sd + 1e-9 * W.sum(), (step, W[alive].sum(), expect, sd)
     assert np.exp(-tau).mean() < 0.7  # a good part converted
+
+
+# ------------------------------------------------- exactness of the QED quadratures
+def _scaled_expn(n, x):
+    """e^x E_n(x): scipy's E_n below x = 600, its asymptotic series above
+    (error below 1e-20 there)."""
+    if x < 600:
+        return special.expn(n, x) * math.exp(x)
+    s, term = 0.0, 1.0 / x
+    for k in range(12):
+        s += term
+        term *= -(n + k) / x
+    return s
+
+
+def test_quantum_survival_against_the_exponential_integral_reduction():
+    """R26's survival S(xi) = int_xi^1 n, which the oracle integrates by
+    Gauss-Legendre panels in s = d^(1/3) of the Bessel integrands, against an
+    independent reduction: with w = 2 + 3 chi d each term of the t-integral
+    integrates over xi in closed form, int_d0^inf exp(-c d) w^-m dd =
+    exp(-c d0) w0^(1-m) e^x E_m(x) / (3 chi), x = c w0 / (3 chi), leaving
+    S = 2 int_0^inf exp(-c d0) [cosh(2t/3) (2 e^x E_3 / w0^2 + e^x E_1 / 2)
+    - cosh(t/3) e^x E_2 / (c w0)] dt (trapezoid, scipy's E_n)."""
+    def reduced(chi, xi):
+        d0 = 2 * xi / (3 * chi * (1 - xi)) if xi > 0 else 0.0
+        w0 = 2 + 3 * chi * d0
+        h, s, k = 0.125, 0.0, 0
+        while True:
+            t = k * h
+            c = math.cosh(t)
+            if c * d0 > 745:
+                break
+            x = c * w0 / (3 * chi)
+            f = math.exp(-c * d0) * (math.cosh(2 * t / 3) * (2 * _scaled_expn(3, x) / w0 ** 2 + 0.5 * _scaled_expn(1, x))
+                                     - math.cosh(t / 3) / c * _scaled_expn(2, x) / w0)
+            s += (0.5 if k == 0 else 1.0) * f
+            if k > 8 and abs(f) <= 1e-18 * abs(s):
+                break
+            k += 1
+        return 2 * h * s
+    for chi in (1e-3, 0.1, 2.0, 77.0, 1e3, 1e5):
+        for xi in (0.0, 1e-6, 1e-3, 0.1, 0.5, 0.9):
+            ref = reduced(chi, xi)
+            if ref < 1e-250:
+                continue
+            assert O.qspec_survival(chi, xi) == pytest.approx(ref, rel=1e-12), (chi, xi)
+
+
+def test_pair_split_tail_against_tanh_sinh():
+    """R27's distribution int_0^e0 p, which the oracle integrates by
+    Gauss-Legendre panels of a smoothstep map, against the tanh-sinh rule in
+    e with p from scipy's Bessel functions (K_2/3 and the integral of K_1/3 by
+    quad), to 1e-11 for chi in [1, 5e3]."""
+    def p(chi, e):
+        y = 2 / (3 * chi * e * (1 - e))
+        ik13 = integrate.quad(lambda s: special.kv(1 / 3, s), y, np.inf, epsabs=0, epsrel=2e-14, limit=200)[0]
+        return (e / (1 - e) + (1 - e) / e) * special.kv(2 / 3, y) + ik13
+
+    def tanh_sinh(chi, e0, h=1 / 32, tmax=3.2):
+        s = 0.0
+        for i in range(-int(tmax / h), int(tmax / h) + 1):
+            tau = i * h
+            u = 0.5 * math.pi * math.sinh(tau)
+            e = e0 / (1 + math.exp(-2 * u))
+            w = 0.5 * e0 * 0.5 * math.pi * math.cosh(tau) / math.cosh(u) ** 2
+            if e > 0 and 2 / (3 * chi * e * (1 - e)) < 700:
+                s += w * p(chi, e)
+        return h * s
+    for chi, e0 in ((1.0, 0.2), (1.0, 0.5), (77.0, 0.05), (77.0, 0.5), (5e3, 0.2), (5e3, 0.5)):
+        assert O.bw_tail(chi, e0) == pytest.approx(tanh_sinh(chi, e0), rel=1e-11), (chi, e0)
