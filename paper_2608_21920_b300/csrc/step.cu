@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   const GapDev &g = v.gaps[ti.gap];
   const int nk = ti.nk, k0 = ti.k0;
   const int64_t nx = g.nx;
+  const int32_t nx32 = (int32_t)nx;  // cells are int32
   const bool periodic = g.periodic != 0;
   // charge through the nodes: FP64 state, one double per node; FP32 state,
   // the exact integer in three 32-bit limbs per node (see limb_add)
@@ -161,6 +162,9 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   const float chi_cf = g.f_lam / g.f_rho;
   const float rate_cf = g.f_rate * (float)kAlphaEm / g.f_rho;
   const double wunit = sizeof(R) == 4 ? g.w_unit : 1.0;
+  // read once: the gap's record is in global memory, and the stores of the
+  // lepton loop would make the compiler reload it for every lepton
+  const bool qed_on = QED && g.qed != 0;
 
   // leptons per thread and group: 16-byte vectors without QED; one lepton
   // (coalesced scalar loads) with QED, whose lepton body is large and
@@ -240,14 +244,14 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           count(2);
           ledger(1, (double)w * wunit * (double)sqrt((R)1 + u * u));
           tally_return(v, ti.gap, (double)u, (double)w * wunit);
-        } else if ((int64_t)kn > nx || ((int64_t)kn == nx && pn >= (R)1.5)) {
+        } else if (kn > nx32 || (kn == nx32 && pn >= (R)1.5)) {
           gone = true;
           count(3);
           ledger(2, (double)w * wunit * (double)sqrt((R)1 + u * u));
         }
       } else {
-        if (kn < 0) kn += (int32_t)nx;
-        else if ((int64_t)kn >= nx) kn -= (int32_t)nx;
+        if (kn < 0) kn += nx32;
+        else if (kn >= nx32) kn -= nx32;
       }
       // photons born this step sit at the lepton's new position
       if (QED && nph > 0) {
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       int nph = 0;
       bool have_id = false;
       uint64_t id = 0;
-      if (QED && g.qed && phi < Hc15 - (R)k) {
+      if (qed_on && phi < Hc15 - (R)k) {
         R trem = dt;
         int kk = 0;
         for (;;) {
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       const R Ep = sE[j] + tt * (sE[j + 1] - sE[j]);
       const R un = u + (R)q * Ep * dt;
       R tn = tau;
-      if (QED && g.qed && phi < Hc15 - (R)k) {
+      if (qed_on && phi < Hc15 - (R)k) {
         const R gm = sqrt((R)1 + un * un);
         R chi, r;
         if (sizeof(R) == 4) {
@@ -461,20 +465,23 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
             }
           }
         }
-        // queue the deferred leptons in lane order (at most 32 VD more)
-        const int nd = __popc(later);
-        int incl = nd;
+        // queue the deferred leptons in lane order (at most 32 VD more): a
+        // lane's entries go after those of the lanes below it
+        const unsigned below = (1u << lane) - 1u;
+        int before = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
+        for (int jj = 0; jj < VD; ++jj) {
+          const unsigned bj = __ballot_sync(0xffffffffu, (later >> jj) & 1u);
+          before += __popc(bj & below);
+          total += __popc(bj);
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int pos = qn + incl - nd;
-        for (unsigned b = later; b; b &= b - 1u) wq[pos++] = base + __ffs(b) - 1;
-        qn += total;
-        __syncwarp();
-        while (qn >= 32) drain(32);
+        if (total > 0) {  // warp-uniform
+          int pos = qn + before;
+          for (unsigned b = later; b; b &= b - 1u) wq[pos++] = base + __ffs(b) - 1;
+          qn += total;
+          __syncwarp();
+          while (qn >= 32) drain(32);
+        }
       }
       if (qn > 0) drain(qn);
     } else {
