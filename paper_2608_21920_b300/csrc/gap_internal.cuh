@@ -34,8 +34,8 @@ constexpr int kMaxEmit = 16;                   // emission events per lepton-ste
 constexpr int kRetBins = 64;
 constexpr double kRetDln = 0.28782313662425574;  // ln 10 / 8
 constexpr int kSpecMaxBins = 1024;              // gap_spectra: bins per histogram at most
-constexpr int kPushChunk = 16384;  // leptons per push work item (multiple of 32; the limb bound below)
-static_assert(kPushChunk <= 16384, "the 18-bit charge limbs hold at most 16384 contributions per node");
+constexpr int kPushChunk = 32768;  // leptons per push work item (multiple of 32; the limb bound below)
+static_assert(kPushChunk <= 32768, "the 17-bit charge limbs hold at most 32768 contributions per node");
 
 // Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
 // ln 10 / 8 (89 rows to chi = 1e5); nodes s_k = 4 (k/256)^2, k < kQsNodes
@@ -616,22 +616,22 @@ __device__ __forceinline__ void red_shared_add_s32(int *p, int v) {
 
 // Exact 64-bit charge sums from 32-bit shared reductions: a contribution
 // c = q w F (|c| < 2^55: weight units w < 2^32, offset flux |F| <= 2^23) is
-// split as c = c2 2^36 + c1 2^18 + c0 with c0, c1 in [0, 2^18) and c2 =
-// floor(c / 2^36), each added to its own 32-bit counter.  A node receives at
+// split as c = c2 2^34 + c1 2^17 + c0 with c0, c1 in [0, 2^17) and c2 =
+// floor(c / 2^34), each added to its own 32-bit counter.  A node receives at
 // most one contribution per lepton of a push item (a move crosses a node at
-// most once), at most kPushChunk <= 16384, so the two unsigned limbs stay
-// below 16384 (2^18 - 1) < 2^32 and are exact.  The signed limb may wrap: the
-// node's sum c2sum 2^36 + c1sum 2^18 + c0sum is formed modulo 2^64, where
-// c2sum enters only through its value modulo 2^28, so the sum is exact
+// most once), at most kPushChunk <= 32768, so the two unsigned limbs stay
+// below 32768 (2^17 - 1) < 2^32 and are exact.  The signed limb may wrap: the
+// node's sum c2sum 2^34 + c1sum 2^17 + c0sum is formed modulo 2^64, where
+// c2sum enters only through its value modulo 2^30, so the sum is exact
 // whenever it fits in 64 bits (the bound of the global accumulators too).
 __device__ __forceinline__ void limb_add(unsigned *L0, unsigned *L1, int *L2, int i, long long c) {
   const unsigned long long u = (unsigned long long)c;
-  red_shared_add_u32(&L0[i], (unsigned)(u & 0x3FFFFull));
-  red_shared_add_u32(&L1[i], (unsigned)((u >> 18) & 0x3FFFFull));
-  red_shared_add_s32(&L2[i], (int)(c >> 36));
+  red_shared_add_u32(&L0[i], (unsigned)(u & 0x1FFFFull));
+  red_shared_add_u32(&L1[i], (unsigned)((u >> 17) & 0x1FFFFull));
+  red_shared_add_s32(&L2[i], (int)(c >> 34));
 }
 __device__ __forceinline__ long long limb_value(unsigned l0, unsigned l1, int l2) {
-  return (long long)(((unsigned long long)(long long)l2 << 36) + ((unsigned long long)l1 << 18) +
+  return (long long)(((unsigned long long)(long long)l2 << 34) + ((unsigned long long)l1 << 17) +
                      (unsigned long long)l0);
 }
 

@@ -451,7 +451,12 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
                 !push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj))
               later |= 1u << jj;
           }
-          if (nvalid == VD) {
+          if (nvalid == VD && sizeof(R) == 4 && VD == 2) {  // streaming stores: not read again this step
+            __stcs(reinterpret_cast<int2 *>(Kp + slot0), *reinterpret_cast<const int2 *>(&kv));
+            __stcs(reinterpret_cast<float2 *>(Pp + slot0), *reinterpret_cast<const float2 *>(&pv));
+            __stcs(reinterpret_cast<float2 *>(Up + slot0), *reinterpret_cast<const float2 *>(&uv));
+            __stcs(reinterpret_cast<float2 *>(Tp + slot0), *reinterpret_cast<const float2 *>(&tv));
+          } else if (nvalid == VD) {
             *reinterpret_cast<Vec<int32_t, VD> *>(Kp + slot0) = kv;
             *reinterpret_cast<Vec<R, VD> *>(Pp + slot0) = pv;
             *reinterpret_cast<Vec<R, VD> *>(Up + slot0) = uv;
