@@ -49,7 +49,7 @@ class Params(C.Structure):
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
         ("protons", C.c_int32), ("m_ion", C.c_double),
         ("em", C.c_int32), ("pml_cells", C.c_int32), ("beta_y", C.c_double), ("beta_z", C.c_double),
-        ("pml_sigma", C.c_double),
+        ("pml_sigma", C.c_double), ("jperp", C.c_int32), ("pad_jperp", C.c_int32),
     ]
 
 
@@ -114,6 +114,7 @@ def lib():
         L.orc_add_proton.argtypes = [vp, u64, d, d, d]
         L.orc_set_em.argtypes = [vp, pd, pd, pd, pd]
         L.orc_get_em.argtypes = [vp, pd, pd, pd, pd]
+        L.orc_get_jperp.argtypes = [vp, pd, pd]
         _lib = L
     return _lib
 
@@ -215,7 +216,7 @@ DEFAULTS = dict(alpha=0.0, b=0.1, lambda_hat=1e-5, rho_hat=100.0, rate_mult=1.0,
                 nx=64, ppc=0, cap=0, seed=0, gap_index=0, qed=0, boundary=BC_SURFACE,
                 init=INIT_EMPTY, kmax_emit=16, kmax_inject=64, inject_theta=0.0,
                 filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0,
-                em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0)
+                em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0, jperp=0)
 
 
 class Sim:
@@ -269,6 +270,14 @@ class Sim:
         nx = self.cfg["nx"]
         out = [np.empty(nx), np.empty(nx), np.empty(self.nnode), np.empty(self.nnode)]
         lib().orc_get_em(self.h, *[_pd(f) for f in out])
+        return tuple(out)
+
+    def jperp(self):
+        """(j_y, j_z) on the nx cells: the transverse particle current of the
+        last step (em = 1 with jperp = 1)."""
+        nx = self.cfg["nx"]
+        out = [np.empty(nx), np.empty(nx)]
+        lib().orc_get_jperp(self.h, *[_pd(f) for f in out])
         return tuple(out)
 
     def step(self, n=1):

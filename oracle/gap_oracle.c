@@ -451,6 +451,8 @@ typedef struct {
   int32_t pml_cells;     /* absorbing layer below the top of a surface gap; 0 = none */
   double beta_y, beta_z; /* velocity of the co-rotating frame (App. A), across h */
   double pml_sigma;      /* peak conductivity of the layer (omega_p); 0 -> a 1e-6 reflection */
+  int32_t jperp;         /* 1 (with em): transverse particle current (see jperp_deposit) */
+  int32_t pad_jperp;
 } orc_params;
 
 /* heavy = 1 marks a proton (charge +1, mass m_ion; u is its momentum per
@@ -478,6 +480,7 @@ typedef struct {
   double *Ey, *Ez;     /* em: transverse E on cells (centres c + 1/2), at half steps */
   double *By, *Bz;     /* em: transverse B on nodes, at whole steps */
   double *Jv;          /* em: dt j_vir,h on nodes for this step's Ampere */
+  double *Jy, *Jz;     /* em with jperp: transverse particle current of the step on cells */
   double eta_bg;       /* Gauss background: eta_co = -1 (surface), mean load charge (periodic) */
   double w0;           /* weight of a loaded / injected macro-particle */
   orc_lepton *lep; int64_t nlep, caplep;
@@ -608,6 +611,8 @@ orc_sim *orc_create(const orc_params *pin) {
     s->By = (double *)calloc((size_t)s->nnode, sizeof(double));
     s->Bz = (double *)calloc((size_t)s->nnode, sizeof(double));
     s->Jv = (double *)calloc((size_t)s->nnode, sizeof(double));
+    s->Jy = (double *)calloc((size_t)p->nx, sizeof(double));
+    s->Jz = (double *)calloc((size_t)p->nx, sizeof(double));
   }
   s->w0 = p->ppc > 0 ? p->density * p->dx / (double)p->ppc : 0.0;
   s->eta_bg = -1.0;
@@ -676,7 +681,7 @@ orc_sim *orc_create(const orc_params *pin) {
 
 void orc_destroy(orc_sim *s) {
   if (!s) return;
-  free(s->Ey); free(s->Ez); free(s->By); free(s->Bz); free(s->Jv);
+  free(s->Ey); free(s->Ez); free(s->By); free(s->Bz); free(s->Jv); free(s->Jy); free(s->Jz);
   free(s->E); free(s->D); free(s->lep); free(s->ph); free(s);
 }
 
@@ -715,6 +720,11 @@ void orc_get_em(const orc_sim *s, double *Ey, double *Ez, double *By, double *Bz
   memcpy(Ez, s->Ez, (size_t)s->p.nx * sizeof(double));
   memcpy(By, s->By, (size_t)s->nnode * sizeof(double));
   memcpy(Bz, s->Bz, (size_t)s->nnode * sizeof(double));
+}
+/* the transverse particle current of the last step (em with jperp), nx cells each */
+void orc_get_jperp(const orc_sim *s, double *Jy, double *Jz) {
+  memcpy(Jy, s->Jy, (size_t)s->p.nx * sizeof(double));
+  memcpy(Jz, s->Jz, (size_t)s->p.nx * sizeof(double));
 }
 
 /* Deposit of one move X0 -> X1 (unwrapped): the charge through node i is
@@ -968,8 +978,9 @@ static void merge(orc_sim *s, uint32_t n) {
 /*   jv_y = -beta_y d E_h - d P_z,  jv_z = -beta_z d E_h + d P_y.             */
 /* The virtual charge eta_vir = eta_co + beta . curl B = eta_co               */
 /*   - beta_y d B_z + beta_z d B_y enters Gauss's law (see the residual).     */
-/* Particles move along B_* (the strong-field limit), so they carry no        */
-/* transverse current: the transverse fields are driven by jv alone.          */
+/* Particles move along B_* (the strong-field limit); with jperp they also    */
+/* carry the guiding-centre transverse current of jperp_deposit, which joins  */
+/* the cells' update as dE_perp/dt = ... - j_perp.                           */
 /*                                                                           */
 /* Grid (Yee, second order): E_y, E_z at cell centres and half steps, B_y,    */
 /* B_z at nodes and whole steps; d E_h lives on cells, d E_perp on nodes.     */
@@ -1006,6 +1017,49 @@ static double cell_field(const orc_sim *s, const double *F, int64_t c) {
   if (c >= nx) return -F[2 * nx - 1 - c];
   return F[c];
 }
+/* Transverse particle current (App. A; Sect. 6.6, Fig. 8), in the guiding-   */
+/* centre limit of the strong field: with B = B_* h-hat + B_perp, B_* =       */
+/* b / lambda_hat in code units (omega_B / omega_p), a particle slides along  */
+/* its field line at beta_h and drifts at E x B / B^2, which to first order   */
+/* in B_perp / B_* and E_perp / B_* gives, for any mass,                      */
+/*   v_y = (beta_h B_y + E_z) / B_*,   v_z = (beta_h B_z - E_y) / B_*.        */
+/* The current of step n, which advances E_perp from n - 1/2 to n + 1/2, is   */
+/* deposited from the start-of-step position X^n with the step's velocity     */
+/* beta_h = u / gamma after the kick and emissions, E_perp^{n-1/2} taken      */
+/* linearly between cell centres (conductor images at a surface gap's ends)   */
+/* and B_perp^n linearly between nodes, both at X^n: j_perp(c) += q w v_perp  */
+/* S_c / dx, S_c the overlap of the unit top-hat cloud [X - 1/2, X + 1/2]     */
+/* with cell c.  A cloud's part outside a surface gap (below the star, above  */
+/* the top conductor) carries no current.  The particle state keeps u_h only: */
+/* the drift's energy, O((E_perp / B_*)^2), is not tracked.                   */
+static void jperp_deposit(orc_sim *s, double q, double w, double X, double u) {
+  const orc_params *p = &s->p;
+  const int64_t nx = p->nx;
+  const double Bs = p->b / p->lambda_hat;
+  const double bh = u / sqrt(1.0 + u * u);
+  /* cell centres c + 1/2: the cloud covers c0 = floor(X - 1/2) and c0 + 1 */
+  const double sc = X - 0.5;
+  const int64_t c0 = (int64_t)floor(sc);
+  const double tc = sc - (double)c0;
+  const double Ey = (1.0 - tc) * cell_field(s, s->Ey, c0) + tc * cell_field(s, s->Ey, c0 + 1);
+  const double Ez = (1.0 - tc) * cell_field(s, s->Ez, c0) + tc * cell_field(s, s->Ez, c0 + 1);
+  /* nodes i0 = floor(X) and i0 + 1 */
+  int64_t i0 = (int64_t)floor(X), i1 = i0 + 1;
+  const double tn = X - (double)i0;
+  if (p->boundary == ORC_BC_PERIODIC) { i0 = imod(i0, nx); i1 = imod(i1, nx); }
+  const double By = (1.0 - tn) * s->By[i0] + tn * s->By[i1];
+  const double Bz = (1.0 - tn) * s->Bz[i0] + tn * s->Bz[i1];
+  const double vy = (bh * By + Ez) / Bs, vz = (bh * Bz - Ey) / Bs;
+  const double S[2] = {1.0 - tc, tc};
+  for (int j = 0; j < 2; ++j) {
+    int64_t c = c0 + j;
+    if (p->boundary == ORC_BC_PERIODIC) c = imod(c, nx);
+    else if (c < 0 || c >= nx) continue;
+    s->Jy[c] += q * w * vy * S[j] / p->dx;
+    s->Jz[c] += q * w * vz * S[j] / p->dx;
+  }
+}
+
 static void em_advance(orc_sim *s) {
   const orc_params *p = &s->p;
   const double dt = p->dt, dx = p->dx, by = p->beta_y, bz = p->beta_z;
@@ -1019,8 +1073,12 @@ static void em_advance(orc_sim *s) {
     const double Pz0 = bz * bB0 - b2 * s->Bz[i0], Pz1 = bz * bB1 - b2 * s->Bz[i1];
     const double jvy = -by * dEh - (Pz1 - Pz0) / dx;
     const double jvz = -bz * dEh + (Py1 - Py0) / dx;
-    const double ry = -(s->Bz[i1] - s->Bz[i0]) / dx + jvy;
-    const double rz = (s->By[i1] - s->By[i0]) / dx + jvz;
+    double ry = -(s->Bz[i1] - s->Bz[i0]) / dx + jvy;
+    double rz = (s->By[i1] - s->By[i0]) / dx + jvz;
+    if (p->jperp) {
+      ry -= s->Jy[c];
+      rz -= s->Jz[c];
+    }
     const double sg = pml_sigma_at(p, (double)c + 0.5);
     const double a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt), b = dt / (1.0 + 0.5 * sg * dt);
     s->Ey[c] = a * s->Ey[c] + b * ry;
@@ -1057,6 +1115,10 @@ void orc_step(orc_sim *s) {
   const double jm = -p->alpha;            /* j_m = alpha j_co, j_co = -1 */
   const uint32_t n = (uint32_t)s->step;
   memset(s->D, 0, (size_t)s->nnode * sizeof(double));
+  if (p->em) {
+    memset(s->Jy, 0, (size_t)p->nx * sizeof(double));
+    memset(s->Jz, 0, (size_t)p->nx * sizeof(double));
+  }
   int64_t nph_old = s->nph;
 
   for (int64_t ip = 0; ip < s->nlep; ++ip) {
@@ -1110,6 +1172,8 @@ void orc_step(orc_sim *s) {
       }
       L->tau = tau;
     }
+    /* with em and jperp: the transverse current of the step at X^n */
+    if (p->em && p->jperp) jperp_deposit(s, (double)L->q, L->w, X0, u);
     /* a4: drift; a8: deposit of the move */
     double g = sqrt(1.0 + u * u);
     double X1 = X0 + u / g * cdx;
