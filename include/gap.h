@@ -155,8 +155,9 @@ typedef struct gap_params {
                             B_z (nodes, whole steps) of App. A's co-rotating frame in
                             the 1D reduction: a Yee leapfrog driven by the virtual
                             current jv = -{curl(beta x E) + beta x curl E
-                            - curl[beta x (beta x B)]} (particles move along B_* and
-                            carry no transverse current); jv_h joins the Ampere step
+                            - curl[beta x (beta x B)]} (particles move along B_*; with
+                            jperp they also carry the transverse current of their
+                            guiding centres); jv_h joins the Ampere step
                             of E_h and the virtual charge -beta_y dB_z/dh +
                             beta_z dB_y/dh joins Gauss's law.  The star is a
                             conductor.  The gap's Ampere step runs after the push.
@@ -171,6 +172,20 @@ typedef struct gap_params {
                             paper's 3e-6); |beta| < 1, zero unless em */
   double pml_sigma;      /* sigma_max in omega_p; 0 -> 4 ln(1e6) / (2 pml_cells dx), a
                             continuum reflection of 1e-6 */
+  int32_t jperp;         /* em: 1 adds the particles' transverse current in the
+                            guiding-centre limit of the strong field (App. A; Sect.
+                            6.6, Fig. 8).  With B_* = b / lambda_hat (omega_B /
+                            omega_p in code units) a particle slides along its field
+                            line at beta_h and drifts at E x B / B^2: v_y = (beta_h
+                            B_y + E_z) / B_*, v_z = (beta_h B_z - E_y) / B_*, with
+                            beta_h = u / gamma after the step's kick and emissions
+                            and E_perp^{n-1/2}, B_perp^n taken linearly at the start-
+                            of-step position, whose unit cloud deposits j_perp =
+                            q w v_perp / dx on the cells it covers (inside the gap);
+                            dE_perp/dt gains -j_perp.  The particle state keeps u_h
+                            alone.  Needs em, b > 0 and lambda_hat > 0; 0 or 1,
+                            else GAP_EINVAL */
+  int32_t pad0;          /* zero */
 } gap_params;
 
 /* Options shared by all gaps of one handle. */

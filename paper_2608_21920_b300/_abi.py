@@ -28,7 +28,7 @@ class GapParams(C.Structure):
         ("inject_theta", C.c_double), ("filter_passes", C.c_int32), ("qed_quantum", C.c_int32),
         ("protons", C.c_int32), ("m_ion", C.c_double),
         ("em", C.c_int32), ("pml_cells", C.c_int32), ("beta_y", C.c_double), ("beta_z", C.c_double),
-        ("pml_sigma", C.c_double),
+        ("pml_sigma", C.c_double), ("jperp", C.c_int32), ("pad0", C.c_int32),
     ]
 
 

@@ -113,6 +113,10 @@ int validate(const gap_params *p, int32_t n, const gap_config &cfg, std::string 
     if (q.pml_cells < 0 || (q.pml_cells > 0 && (q.boundary != GAP_BC_SURFACE || 2 * (int64_t)q.pml_cells > q.nx)))
       { msg = "pml_cells must be in [0, nx/2], on a surface gap"; return GAP_EINVAL; }
     if (!(q.pml_sigma >= 0.0) || !std::isfinite(q.pml_sigma)) { msg = "pml_sigma must be >= 0"; return GAP_EINVAL; }
+    if (q.jperp != 0 && q.jperp != 1) { msg = "jperp must be 0 or 1"; return GAP_EINVAL; }
+    if (q.jperp && (!q.em || !(q.b > 0.0) || !(q.lambda_hat > 0.0)))
+      { msg = "jperp needs em = 1, b > 0 and lambda_hat > 0"; return GAP_EINVAL; }
+    if (q.pad0 != 0) { msg = "pad0 must be zero"; return GAP_EINVAL; }
   }
   return GAP_OK;
 }
@@ -312,7 +316,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   std::vector<int64_t> cap0[2];
   int64_t total_nodes = 0, max_nx = 0, max_P = 2, lep_need[2] = {0, 0}, ph_need = 0;
   bool qed_any = false, surface_any = false, merge_any = false, filter_any = false, qs_any = false, pr_any = false;
-  bool em_any = false;
+  bool em_any = false, jperp_any = false;
   int64_t pr_need = 0;
   for (int i = 0; i < n; ++i) {
     const gap_params &q = p[i];
@@ -360,7 +364,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.beta_z = q.beta_z;
     g.pml_smax = g.pml_cells <= 0 ? 0.0
                  : (q.pml_sigma > 0.0 ? q.pml_sigma : 4.0 * std::log(1e6) / (2.0 * (double)g.pml_cells * q.dx));
+    g.jperp = q.em ? q.jperp : 0;
+    g.bstar_inv = g.jperp ? q.lambda_hat / q.b : 0.0;
     em_any |= q.em != 0;
+    jperp_any |= g.jperp != 0;
     g.defer = q.filter_passes > 0 || q.protons || q.em ? 1 : 0;
     filter_any |= g.defer != 0;
     pr_any |= q.protons != 0;
@@ -442,6 +449,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.filter_any = filter_any ? 1 : 0;
   v.pr_any = pr_any ? 1 : 0;
   v.em_any = em_any ? 1 : 0;
+  v.jperp_any = jperp_any ? 1 : 0;
   v.rebin_every = cfg.rebin_every;
   v.variant = cfg.variant;
   v.gaps = C.take<GapDev>(n);
@@ -519,6 +527,8 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     v.em_By = C.take<double>(ne);
     v.em_Bz = C.take<double>(ne);
     v.em_Jv = C.take<double>(ne);
+    v.em_jy = C.take<double>(jperp_any ? ne : 0);
+    v.em_jz = C.take<double>(jperp_any ? ne : 0);
   }
   v.fft[0] = C.take<double>(2 * (size_t)max_P);
   v.fft[1] = C.take<double>(2 * (size_t)max_P);

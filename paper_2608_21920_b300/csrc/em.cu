@@ -9,8 +9,10 @@
 // has the components
 //   jv_h = -(beta_y d E_y + beta_z d E_z),
 //   jv_y = -beta_y d E_h - d P_z,   jv_z = -beta_z d E_h + d P_y.
-// Particles move along B_* (the strong-field limit) and carry no transverse
-// current.
+// Particles move along B_* (the strong-field limit); with jperp their guiding
+// centres' transverse current j_perp (deposited by the push kernels in em_jy,
+// em_jz) joins the cells' update, dE_perp/dt = ... - j_perp, and is cleared
+// here for the next step.
 //
 // Yee grid, second order: E_y, E_z on cell centres at half steps; B_y, B_z
 // on nodes at whole steps.  Both kernels run after the push and before the
@@ -44,15 +46,6 @@ __device__ __forceinline__ double layer_sigma(const GapDev &g, double X) {
   return g.pml_smax * f * f * f;
 }
 
-// Cell c of a transverse E array, with the conductor images of a surface gap
-// (c in [-1, nx] here).
-__device__ __forceinline__ double cell_at(const double *F, int64_t c, const GapDev &g) {
-  if (g.periodic) return F[c < 0 ? c + g.nx : (c >= g.nx ? c - g.nx : c)];
-  if (c < 0) return -F[-1 - c];
-  if (c >= g.nx) return -F[2 * g.nx - 1 - c];
-  return F[c];
-}
-
 __global__ void __launch_bounds__(256) k_em_cells(View v) {
   const TileDev ti = v.tiles[blockIdx.x];
   const GapDev &g = v.gaps[ti.gap];
@@ -72,8 +65,15 @@ __global__ void __launch_bounds__(256) k_em_cells(View v) {
     const double Pz0 = bz * bB0 - b2 * Bz0, Pz1 = bz * bB1 - b2 * Bz1;
     const double jvy = -by * dEh - (Pz1 - Pz0) / dx;
     const double jvz = -bz * dEh + (Py1 - Py0) / dx;
-    const double ry = -(Bz1 - Bz0) / dx + jvy;
-    const double rz = (By1 - By0) / dx + jvz;
+    double ry = -(Bz1 - Bz0) / dx + jvy;
+    double rz = (By1 - By0) / dx + jvz;
+    if (g.jperp) {
+      double *jy = v.em_jy + g.node_off, *jz = v.em_jz + g.node_off;
+      ry -= jy[c];
+      rz -= jz[c];
+      jy[c] = 0.0;
+      jz[c] = 0.0;
+    }
     const double sg = layer_sigma(g, (double)c + 0.5);
     const double a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt), b = dt / (1.0 + 0.5 * sg * dt);
     Ey[c] = a * Ey[c] + b * ry;

@@ -99,6 +99,9 @@ struct GapDev {
   int32_t pml_cells;      // absorbing layer below the top of a surface gap; 0 = none
   double beta_y, beta_z;  // velocity of the co-rotating frame across h
   double pml_smax;        // peak conductivity of the layer (omega_p)
+  int32_t jperp;          // 1: the particles' transverse current (guiding centres)
+  int32_t jperp_pad;
+  double bstar_inv;       // 1 / B_* = lambda_hat / b (code units)
 };
 
 struct TileDev {
@@ -139,8 +142,9 @@ struct View {
   int32_t *pr_gap, *pr_alive;
   // transverse fields (some gap with em), indexed like the nodes (node_off):
   // E_y, E_z on cells c < nx, B_y, B_z on nodes; Jv = dt jv_h of this step
-  int32_t em_any, em_pad;
+  int32_t em_any, jperp_any;
   double *em_Ey, *em_Ez, *em_By, *em_Bz, *em_Jv;
+  double *em_jy, *em_jz;      // jperp: the particles' transverse current of the step (cells)
   double *Dflt;               // [2 x dcharge_len] smoothing scratch (node flux; two cell buffers)
   // quantum photon spectrum (some gap with qed_quantum): per row of ln chi,
   // the normalised survival S(s)/S(0) and its s-derivative on kQsNodes nodes
@@ -845,6 +849,15 @@ __device__ __forceinline__ float bw_step_depth_f(const GapDev &g, float x, int32
 
 // Tally one e+- absorbed at h < 0 (the return flux of Sect. 6.5) with weight
 // w in the bin of ln gamma, gamma from its momentum in double precision.
+// Cell c of a transverse E array, with the conductor images of a surface gap
+// (c in [-1, nx] here).
+__device__ __forceinline__ double cell_at(const double *F, int64_t c, const GapDev &g) {
+  if (g.periodic) return F[c < 0 ? c + g.nx : (c >= g.nx ? c - g.nx : c)];
+  if (c < 0) return -F[-1 - c];
+  if (c >= g.nx) return -F[2 * g.nx - 1 - c];
+  return F[c];
+}
+
 __device__ __forceinline__ void tally_return(const View &v, int gap, double u, double w) {
   double b = floor(log(sqrt(1.0 + u * u)) / kRetDln);
   if (!(b >= 0.0)) b = 0.0;

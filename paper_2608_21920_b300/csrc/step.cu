@@ -61,7 +61,7 @@ __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t 
 // arrives second (atomic arrival count, no waiting).
 constexpr int kDeferQueue = 32 + 32 * 4;  // queue of a warp: < 32 left + one group of 32 lanes x VD (VD <= 4)
 
-template <class R, bool QED, bool HAS_W, bool DEFER = false, int MINB = 3>
+template <class R, bool QED, bool HAS_W, bool DEFER = false, int MINB = 3, bool EM = false>
 __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   using W = typename Prec<R>::W;
   using Acc = typename Prec<R>::Acc;
@@ -115,6 +115,13 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     if (sizeof(R) == 4) return (Acc)limb_value(sL0[i], sL1[i], sL2[i]);
     return sD[i];
   };
+  // EM (gaps with the particles' transverse current): E_y, E_z on the cells
+  // k0-1 .. k0+nk-1 (index c - (k0-1)), B_y, B_z on the nodes like sE, and
+  // the current's sums on the cells
+  R *sEy = sE + (nk + 2), *sEz = sEy + (nk + 1);
+  R *sBy = sEz + (nk + 1), *sBz = sBy + (nk + 2);
+  R *sJy = sBz + (nk + 2), *sJz = sJy + (nk + 1);
+  const bool jp_on = EM && g.jperp != 0;
 
   const Ctl *ctl = v.ctl;
   const int ecur = ctl->e_cur;
@@ -140,6 +147,28 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       sL2[i] = 0;
     } else {
       sD[i] = (Acc)0;
+    }
+  }
+  if (jp_on) {
+    const double *Ey = v.em_Ey + g.node_off, *Ez = v.em_Ez + g.node_off;
+    const double *By = v.em_By + g.node_off, *Bz = v.em_Bz + g.node_off;
+    for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
+      int64_t node = (int64_t)k0 - 1 + i;
+      R by = (R)0, bz = (R)0;
+      if (periodic) node = (node + nx) % nx;
+      if (periodic || (node >= 0 && node <= nx)) {
+        by = (R)By[node];
+        bz = (R)Bz[node];
+      }
+      sBy[i] = by;
+      sBz[i] = bz;
+      if (i <= nk) {  // cell k0-1+i, with the conductor images of a surface gap
+        const int64_t c = (int64_t)k0 - 1 + i;
+        sEy[i] = (R)cell_at(Ey, c, g);
+        sEz[i] = (R)cell_at(Ez, c, g);
+        sJy[i] = (R)0;
+        sJz[i] = (R)0;
+      }
     }
   }
   if (threadIdx.x < 8) sCnt[threadIdx.x] = 0ull;
@@ -186,6 +215,32 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     R *Tp = as<R>(v.ltau[cur][s]);
     uint64_t *Ip = v.lid[cur][s];
     int dead = 0;
+
+    // The guiding centre's transverse current of the step (EM, jperp):
+    // v_y = (beta_h B_y + E_z)/B_*, v_z = (beta_h B_z - E_y)/B_*, with the
+    // fields at the start-of-step position X = k + phi - 3/2, whose unit
+    // cloud covers cells k-1 (share 2 - phi) and k (share phi - 1).
+    const R bsi = (R)g.bstar_inv;
+    const double jw = (double)q * wunit / g.dx;  // q w / dx per weight unit
+    auto jperp_dep = [&](const int lk, const R phi, const R u, const W w) {
+      const R s1 = phi - (R)1, s0 = (R)2 - phi;  // both exact for phi in [1, 2)
+      const R ey = s0 * sEy[lk - 1] + s1 * sEy[lk];
+      const R ez = s0 * sEz[lk - 1] + s1 * sEz[lk];
+      const R sph = phi - (R)1.5;
+      const int j = sph >= (R)0 ? lk : lk - 1;
+      const R tt = sph >= (R)0 ? sph : sph + (R)1;
+      const R by = sBy[j] + tt * (sBy[j + 1] - sBy[j]);
+      const R bz = sBz[j] + tt * (sBz[j + 1] - sBz[j]);
+      R bh;
+      if (sizeof(R) == 4) bh = u * (R)rsqrtf((float)((R)1 + u * u));
+      else bh = u / sqrt((R)1 + u * u);
+      const R a = (R)(jw * (double)w);
+      const R vy = (bh * by + ez) * bsi * a, vz = (bh * bz - ey) * bsi * a;
+      atomicAdd(&sJy[lk - 1], vy * s0);
+      atomicAdd(&sJy[lk], vy * s1);
+      atomicAdd(&sJz[lk - 1], vz * s0);
+      atomicAdd(&sJz[lk], vz * s1);
+    };
 
     // a4, a8, a7 of one lepton after its kick and emissions: drift, the
     // charge through the nodes it crosses, boundaries, the photons it emitted
@@ -356,6 +411,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           }
         }
       }
+      if (jp_on) jperp_dep(lk, phi, u, w);
       move_one(k, phi, u, w, tau, slot, lk, nph, ph_x, ph_k, have_id, id);
     };
 
@@ -388,6 +444,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       }
       u = un;
       tau = tn;
+      if (jp_on) jperp_dep(lk, phi, u, w);
       move_one(k, phi, u, w, tau, slot, lk, 0, nullptr, nullptr, false, 0ull);
       return true;
     };
@@ -536,6 +593,15 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     if ((threadIdx.x & 31) == 0 && dead) atomicAdd(&sDead[s], dead);
   }
   __syncthreads();
+  if (jp_on) {  // the item's transverse current to the gap's cells
+    for (int i = threadIdx.x; i <= nk; i += blockDim.x) {
+      int64_t c = (int64_t)k0 - 1 + i;
+      if (periodic) c = (c + nx) % nx;
+      else if (c < 0 || c >= nx) continue;  // outside the gap: no current
+      if (sJy[i] != (R)0) atomicAdd(&v.em_jy[g.node_off + c], (double)sJy[i]);
+      if (sJz[i] != (R)0) atomicAdd(&v.em_jz[g.node_off + c], (double)sJz[i]);
+    }
+  }
 
   // a9: Ampere on the tile's nodes (a gap with a current filter leaves it to
   // k_filter_apply: every node's flux goes to the global accumulators)
@@ -1299,6 +1365,25 @@ __global__ void __launch_bounds__(256) k_push_heavy(View v) {
       if (f32) atomicAdd(&v.Dg[g.node_off + node], (unsigned long long)(grid_units(dF) * wu));
       else atomicAdd(reinterpret_cast<double *>(&v.Dg[g.node_off + node]), w * dF);
     }
+    if (g.jperp) {  // the guiding centre's transverse current at X^n (as k_push)
+      const double sc = X0 - 0.5, cc = floor(sc), tc = sc - cc;
+      const int64_t c0 = (int64_t)cc;
+      const double *Ey = v.em_Ey + g.node_off, *Ez = v.em_Ez + g.node_off;
+      const double ey = (1.0 - tc) * cell_at(Ey, c0, g) + tc * cell_at(Ey, c0 + 1, g);
+      const double ez = (1.0 - tc) * cell_at(Ez, c0, g) + tc * cell_at(Ez, c0 + 1, g);
+      const double by = (1.0 - o) * v.em_By[g.node_off + c] + o * v.em_By[g.node_off + c1];
+      const double bz = (1.0 - o) * v.em_Bz[g.node_off + c] + o * v.em_Bz[g.node_off + c1];
+      const double bh = u / gm, a = w / g.dx;
+      const double vy = (bh * by + ez) * g.bstar_inv * a, vz = (bh * bz - ey) * g.bstar_inv * a;
+      for (int jc = 0; jc < 2; ++jc) {
+        int64_t cl = c0 + jc;
+        if (periodic) cl = (cl + g.nx) % g.nx;
+        else if (cl < 0 || cl >= g.nx) continue;
+        const double sh = jc == 0 ? 1.0 - tc : tc;
+        atomicAdd(&v.em_jy[g.node_off + cl], vy * sh);
+        atomicAdd(&v.em_jz[g.node_off + cl], vz * sh);
+      }
+    }
     v.pr_u[i] = u;
     double Xn = X1;
     if (periodic) {
@@ -1817,7 +1902,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
 
 template <class R>
 static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
-  if (sizeof(R) == 4 && !v.qed_any && !v.has_w) {
+  if (sizeof(R) == 4 && !v.qed_any && !v.has_w && !v.jperp_any) {
     const size_t smem_lean = (size_t)(v.tile + 8) * (2 * sizeof(unsigned) + sizeof(float2)) + 64;
     switch (v.variant) {
       case 1: k_push_lean<4, 6><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
@@ -1842,7 +1927,15 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
   k_push_items<<<1, 1024, 0, st>>>(v);
   const int grid = 148 * 4;  // persistent: blocks take items until the list is empty
-  if (v.qed_any) {
+  if (v.jperp_any) {
+    // the particles' transverse current: fields and current sums of the tile
+    // in shared memory as well, every lepton pushed in place
+    const size_t smem_em = smem + (size_t)(6 * v.tile + 16) * sizeof(R);
+    if (v.qed_any && v.has_w) k_push<R, true, true, false, 3, true><<<grid, threads, smem_em, st>>>(v);
+    else if (v.qed_any) k_push<R, true, false, false, 3, true><<<grid, threads, smem_em, st>>>(v);
+    else if (v.has_w) k_push<R, false, true, false, 3, true><<<grid, threads, smem_em, st>>>(v);
+    else k_push<R, false, false, false, 3, true><<<grid, threads, smem_em, st>>>(v);
+  } else if (v.qed_any) {
     // FP32 state: emitters deferred to converged warp passes (variant 0: at
     // most 64 registers, 4 blocks per SM; 1: 80 registers, 3 blocks per SM),
     // or every lepton pushed in place (variant 2)

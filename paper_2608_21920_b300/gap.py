@@ -19,7 +19,7 @@ PARAM_DEFAULTS = dict(
     density=1.0, dx=0.1, dt=0.045, theta=0.0, seed_amp=0.0, nx=64, ppc=0, cap=0, seed=0,
     qed=0, boundary=A.GAP_BC_SURFACE, init=A.GAP_INIT_EMPTY, kmax_emit=16, kmax_inject=64,
     gap_index=0, inject_theta=0.0, filter_passes=0, qed_quantum=0, protons=0, m_ion=1836.0,
-    em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0)
+    em=0, pml_cells=0, beta_y=0.0, beta_z=0.0, pml_sigma=0.0, jperp=0)
 
 PRECISION = {"fp64": A.GAP_FP64_PLAIN, "fp32": A.GAP_FP32_STATE}
 

@@ -7,7 +7,7 @@ import oracle as O
 GPU_KEYS = ("alpha", "b", "lambda_hat", "rho_hat", "rate_mult", "gap_length", "density", "dx",
             "dt", "theta", "seed_amp", "nx", "ppc", "cap", "seed", "qed", "boundary", "init",
             "kmax_emit", "kmax_inject", "gap_index", "inject_theta", "filter_passes", "qed_quantum", "protons", "m_ion",
-            "em", "pml_cells", "beta_y", "beta_z", "pml_sigma")
+            "em", "pml_cells", "beta_y", "beta_z", "pml_sigma", "jperp")
 
 # Config 1 of the workloads: cold electrons 16/cell at n_co, alpha = 1.5,
 # b = 0.1, QED scales raised so that pairs appear inside the 51 d_e box.
