@@ -475,9 +475,9 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   }
   v.item_start = C.take<int32_t>((size_t)NT + 1);
   // items per tile: max(1, chunks of each species), each species' chunks at
-  // most used / kPushChunk + 1, and the used slots of all tiles at most the
+  // most used / kPushChunkMin + 1, and the used slots of all tiles at most the
   // store's capacity
-  const int64_t item_cap = 2 * (lep_cap / kPushChunk) + 2 * (int64_t)NT + 2;
+  const int64_t item_cap = 2 * (lep_cap / kPushChunkMin) + 2 * (int64_t)NT + 2;
   v.item_tile = C.take<int32_t>((size_t)item_cap);
   v.item_cap = (int32_t)std::min<int64_t>(item_cap, INT32_MAX);
   v.tile_done = C.take<int32_t>(NT);

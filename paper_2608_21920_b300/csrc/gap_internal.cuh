@@ -34,7 +34,11 @@ constexpr int kMaxEmit = 16;                   // emission events per lepton-ste
 constexpr int kRetBins = 64;
 constexpr double kRetDln = 0.28782313662425574;  // ln 10 / 8
 constexpr int kSpecMaxBins = 1024;              // gap_spectra: bins per histogram at most
-constexpr int kPushChunk = 32768;  // leptons per push work item (multiple of 32; the limb bound below)
+// Leptons per push work item: a power of two from kPushChunkMin to kPushChunk,
+// chosen each step so that a large store is cut into at least ~2048 items
+// (long items cost less at their ends; enough of them keep every SM busy).
+constexpr int kPushChunk = 32768;  // the largest (multiple of 32; the limb bound below)
+constexpr int kPushChunkMin = 8192;
 static_assert(kPushChunk <= 32768, "the 17-bit charge limbs hold at most 32768 contributions per node");
 
 // Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
@@ -122,6 +126,7 @@ struct Ctl {
   int32_t need_ph_compact;
   int32_t hold_copies;  // test hook: bulk-copy pushes leave their first stage unissued
   int32_t push_items, push_next;  // the push work list of this step and its counter
+  int32_t push_chunk, push_pad;   // leptons per item this step (kPushChunkMin .. kPushChunk)
   int64_t spill_n[2];
   int64_t new_total[2];
   int64_t ph_nb_start;  // photon store fill before this step's push (0 after a photon compaction)

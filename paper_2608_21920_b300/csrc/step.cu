@@ -49,7 +49,7 @@ __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t 
 
 // ---------------------------------------------------------------------------
 // k_push: the work of a step is a list of items, each a chunk of at most
-// kPushChunk leptons of one species of one tile (every tile has at least one
+// push_chunk leptons of one species of one tile (every tile has at least one
 // item), taken by a persistent grid from an atomic counter so that the tiles
 // where a discharge concentrates its pairs are shared out over many blocks.
 // Shared memory holds E^n on the tile's nodes k0-1 .. k0+nk (in the precision
@@ -87,15 +87,16 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   {
     const int c = item - v.item_start[t];
     const int u0 = v.seg_used[0][t], u1 = v.seg_used[1][t];
-    const int n0c = (u0 + kPushChunk - 1) / kPushChunk;
+    const int chunk = v.ctl->push_chunk;
+    const int n0c = (u0 + chunk - 1) / chunk;
     if (c < n0c) {
       s_only = 0;
-      r0 = c * kPushChunk;
-      r1 = u0 < r0 + kPushChunk ? u0 : r0 + kPushChunk;
+      r0 = c * chunk;
+      r1 = u0 < r0 + chunk ? u0 : r0 + chunk;
     } else {
       s_only = 1;
-      r0 = (c - n0c) * kPushChunk;
-      r1 = u1 < r0 + kPushChunk ? u1 : r0 + kPushChunk;
+      r0 = (c - n0c) * chunk;
+      r1 = u1 < r0 + chunk ? u1 : r0 + chunk;
     }
   }
   const TileDev ti = v.tiles[t];
@@ -1854,15 +1855,28 @@ __global__ void k_rebin_finish(View v) {
 __global__ void __launch_bounds__(1024) k_push_items(View v) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
+  __shared__ unsigned long long s_total;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    s_total = 0ull;
+  }
   __syncthreads();
   const int n = v.n_tiles;
+  {  // the item length of this step from the store's fill
+    unsigned long long mine = 0ull;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) mine += (unsigned long long)(v.seg_used[0][t] + v.seg_used[1][t]);
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_total, mine);
+  }
+  __syncthreads();
+  int chunk = kPushChunkMin;
+  while (chunk < kPushChunk && s_total >= 2ull * 2048ull * (unsigned long long)chunk) chunk *= 2;
   for (int base = 0; base < n; base += blockDim.x) {
     const int t = base + threadIdx.x;
     int c = 0;
     if (t < n) {
       const int u0 = v.seg_used[0][t], u1 = v.seg_used[1][t];
-      c = (u0 + kPushChunk - 1) / kPushChunk + (u1 + kPushChunk - 1) / kPushChunk;
+      c = (u0 + chunk - 1) / chunk + (u1 + chunk - 1) / chunk;
       if (c < 1) c = 1;
     }
     int x = c;
@@ -1895,6 +1909,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
     v.item_start[n] = carry;
     if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
     v.ctl->push_items = carry < v.item_cap ? carry : v.item_cap;
+    v.ctl->push_chunk = chunk;
     v.ctl->ph_nb_start = v.ctl->ph_count[v.ctl->ph_cur];  // photons born in this push lie beyond
     v.ctl->push_next = 0;
   }
