@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     // the move to another tile.  k is set to -1 when the lepton leaves the
     // tile (migrated or removed).
     auto move_one = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot, const int lk,
-                        const int nph, const R *ph_x, const int *ph_k, const bool have_id, const uint64_t id) {
+                        const int nph, const R *ph_x, const int *ph_k, const bool have_id, const uint64_t id,
+                        const bool defer_move) -> bool {
       // a4: drift
       R dX;
       if (sizeof(R) == 4) {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       if (gone) {
         k = -1;
         ++dead;
-        return;
+        return false;
       }
       if (q0_tile && kn <= 1) {
         if (sizeof(R) == 4) {
@@ -349,12 +350,18 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       if (kn >= k0 && kn < k0 + nk) {
         k = kn;
         phi = pn;
+      } else if (defer_move) {  // moved on; the caller appends it to its new tile later
+        k = kn;
+        phi = pn;
+        ++dead;
+        return true;
       } else {
         const int tn = tile_of(v, g, kn);
         append_lepton<R>(v, s, tn, kn, pn, u, w, tau, have_id ? id : Ip[slot]);
         k = -1;
         ++dead;
       }
+      return false;
     };
 
     // One lepton: gather, kick, emission, then move_one.
@@ -413,14 +420,16 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
         }
       }
       if (jp_on) jperp_dep(lk, phi, u, w);
-      move_one(k, phi, u, w, tau, slot, lk, nph, ph_x, ph_k, have_id, id);
+      move_one(k, phi, u, w, tau, slot, lk, nph, ph_x, ph_k, have_id, id, false);
     };
 
     // The same lepton when its optical depth outlasts the step (no emission):
-    // returns false, changing nothing, when an emission falls within the
-    // step, so that the caller hands the lepton to push_one.  The arithmetic
-    // is push_one's for a lepton that does not emit.
-    auto push_quiet = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot) -> bool {
+    // returns 0, changing nothing, when an emission falls within the step,
+    // so that the caller hands the lepton to push_one; 1 when pushed; 2 when
+    // pushed into another tile, its new state left in place (k outside the
+    // tile) for the caller to append.  The arithmetic is push_one's for a
+    // lepton that does not emit.
+    auto push_quiet = [&](int32_t &k, R &phi, R &u, const W w, R &tau, const int64_t slot) -> int {
       const int lk = k - (k0 - 1);
       const R sph = phi - (R)1.5;
       const int j = sph >= (R)0 ? lk : lk - 1;
@@ -439,38 +448,45 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           r = (R)g.rate_mult * (R)kAlphaEm * gm * (R)tsyn_d((double)chi) / (R)g.rho_hat;
         }
         if (r > (R)0) {
-          if (!(tn > r * dt)) return false;
+          if (!(tn > r * dt)) return 0;
           tn -= r * dt;
         }
       }
       u = un;
       tau = tn;
       if (jp_on) jperp_dep(lk, phi, u, w);
-      move_one(k, phi, u, w, tau, slot, lk, 0, nullptr, nullptr, false, 0ull);
-      return true;
+      return move_one(k, phi, u, w, tau, slot, lk, 0, nullptr, nullptr, false, 0ull, DEFER) ? 2 : 1;
     };
 
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     if constexpr (DEFER) {
       // 8-byte vectors of VD leptons per lane through push_quiet; a lepton
       // that emits this step is left unchanged and queued (its offset from
-      // `start`) in the warp's queue, and whenever 32 are queued the warp
-      // runs push_one on them, one per lane, so that the emission events of
-      // a warp run side by side instead of one lane at a time.
+      // `start`) in the warp's queue, and so is one that moved into another
+      // tile (offset complemented), and whenever 32 are queued the warp
+      // runs push_one on the emitters and appends the movers, one per lane,
+      // so that these rare events of a warp run side by side instead of one
+      // lane at a time (an append waits on global atomics).
       constexpr int VD = 2;
       int *wq = s_queue + (threadIdx.x >> 5) * kDeferQueue;
       int qn = 0;  // warp-uniform
       auto drain = [&](const int n) {
         if (lane < n) {
-          const int64_t slot = start + wq[qn - n + lane];
+          const int e = wq[qn - n + lane];
+          const int64_t slot = start + (e >= 0 ? e : ~e);
           int32_t k = Kp[slot];
           R phi = Pp[slot], u = Up[slot], tau = Tp[slot];
           const W w = HAS_W ? Wp[slot] : w_def;
-          push_one(k, phi, u, w, tau, slot);
+          if (e >= 0) {
+            push_one(k, phi, u, w, tau, slot);
+            Pp[slot] = phi;
+            Up[slot] = u;
+            Tp[slot] = tau;
+          } else {  // pushed already: to its new tile
+            append_lepton<R>(v, s, tile_of(v, g, k), k, phi, u, w, tau, Ip[slot]);
+            k = -1;
+          }
           Kp[slot] = k;
-          Pp[slot] = phi;
-          Up[slot] = u;
-          Tp[slot] = tau;
         }
         qn -= n;
         __syncwarp();
@@ -484,7 +500,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
         Vec<int32_t, VD> kv;
         Vec<R, VD> pv, uv, tv;
         Vec<W, VD> wv;
-        unsigned later = 0;
+        unsigned later = 0, moved = 0;
         // the warp's next groups pulled into L2 (-2 %)
         if (gi + nwarp * 32 < ngroups) {
           const int64_t nslot = slot0 + (int64_t)nwarp * 32 * VD;
@@ -505,9 +521,11 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           // vectors rotating through element 0 cost more in moves)
 #pragma unroll
           for (int jj = 0; jj < VD; ++jj) {
-            if (jj < nvalid && kv.a[jj] >= 0 &&
-                !push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj))
-              later |= 1u << jj;
+            if (jj < nvalid && kv.a[jj] >= 0) {
+              const int r = push_quiet(kv.a[jj], pv.a[jj], uv.a[jj], HAS_W ? wv.a[jj] : w_def, tv.a[jj], slot0 + jj);
+              if (r != 1) later |= 1u << jj;
+              if (r == 2) moved |= 1u << jj;
+            }
           }
           if (nvalid == VD && sizeof(R) == 4 && VD == 2) {  // streaming stores: not read again this step
             __stcs(reinterpret_cast<int2 *>(Kp + slot0), *reinterpret_cast<const int2 *>(&kv));
@@ -540,7 +558,10 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
         }
         if (total > 0) {  // warp-uniform
           int pos = qn + before;
-          for (unsigned b = later; b; b &= b - 1u) wq[pos++] = base + __ffs(b) - 1;
+          for (unsigned b = later; b; b &= b - 1u) {
+            const int jb = __ffs(b) - 1;
+            wq[pos++] = (moved >> jb) & 1u ? ~(base + jb) : base + jb;
+          }
           qn += total;
           __syncwarp();
           while (qn >= 32) drain(32);
