@@ -479,6 +479,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   // store's capacity
   const int64_t item_cap = 2 * (lep_cap / kPushChunkMin) + 2 * (int64_t)NT + 2;
   v.item_tile = C.take<int32_t>((size_t)item_cap);
+  v.defer_list = C.take<int32_t>(cfg.precision == GAP_FP32_STATE && qed_any ? (size_t)kPushGrid * kDeferPerBlock : 0);
   v.item_cap = (int32_t)std::min<int64_t>(item_cap, INT32_MAX);
   v.tile_done = C.take<int32_t>(NT);
   v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);

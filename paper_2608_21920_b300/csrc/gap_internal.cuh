@@ -39,6 +39,11 @@ constexpr int kSpecMaxBins = 1024;              // gap_spectra: bins per histogr
 // (long items cost less at their ends; enough of them keep every SM busy).
 constexpr int kPushChunk = 32768;  // the largest (multiple of 32; the limb bound below)
 constexpr int kPushChunkMin = 8192;
+constexpr int kPushGrid = 148 * 4;  // blocks of the persistent push grid (4 per SM)
+// Leptons deferred by a block of the FP32 QED push in one item: a warp's
+// share of an item is at most push_chunk / warps + 32 VD leptons (VD = 2,
+// at most 32 warps), and each is deferred at most once.
+constexpr int kDeferPerBlock = kPushChunk + 2048;
 static_assert(kPushChunk <= 32768, "the 17-bit charge limbs hold at most 32768 contributions per node");
 
 // Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
@@ -181,6 +186,7 @@ struct View {
   int32_t *gross[2];     // per tile: appends since the last re-bin
   int32_t *item_start;   // [n_tiles + 1] first push item of each tile
   int32_t *item_tile;    // [item_cap] tile of each push item
+  int32_t *defer_list;   // [push grid x kDeferPerBlock] leptons deferred by the FP32 QED push
   int32_t item_cap;      // bound on the push items of a step
   int32_t *tile_done;    // [n_tiles] items of the tile finished this step
   // lepton stores [buffer][species]

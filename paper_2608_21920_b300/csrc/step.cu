@@ -59,7 +59,6 @@ __device__ __noinline__ R emission_event(const View &v, uint64_t seed, uint64_t 
 // last of its items to finish does the update.  The four edge nodes shared
 // with the neighbouring tiles are finished by whichever of the two tiles
 // arrives second (atomic arrival count, no waiting).
-constexpr int kDeferQueue = 32 + 32 * 4;  // queue of a warp: < 32 left + one group of 32 lanes x VD (VD <= 4)
 
 template <class R, bool QED, bool HAS_W, bool DEFER = false, int MINB = 3, bool EM = false>
 __global__ void __launch_bounds__(256, MINB) k_push(View v) {
@@ -73,7 +72,6 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   __shared__ double sLed[4];
   __shared__ int sDead[2];
   __shared__ int s_item, s_last;
-  __shared__ int s_queue[DEFER ? 8 * kDeferQueue : 1];  // deferred leptons, per warp (<= 256 threads)
 
   for (;;) {
   __syncthreads();  // the previous item is done with shared memory
@@ -468,11 +466,12 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
       // so that these rare events of a warp run side by side instead of one
       // lane at a time (an append waits on global atomics).
       constexpr int VD = 2;
-      int *wq = s_queue + (threadIdx.x >> 5) * kDeferQueue;
+      // the warp's list of deferred leptons (global scratch of the block)
+      int *wq = v.defer_list + (int64_t)blockIdx.x * kDeferPerBlock + (threadIdx.x >> 5) * (kDeferPerBlock / nwarp);
       int qn = 0;  // warp-uniform
-      auto drain = [&](const int n) {
+      auto drain_at = [&](const int i0, const int n) {
         if (lane < n) {
-          const int e = wq[qn - n + lane];
+          const int e = wq[i0 + lane];
           const int64_t slot = start + (e >= 0 ? e : ~e);
           int32_t k = Kp[slot];
           R phi = Pp[slot], u = Up[slot], tau = Tp[slot];
@@ -488,8 +487,6 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           }
           Kp[slot] = k;
         }
-        qn -= n;
-        __syncwarp();
       };
       const int ngroups = (used + VD - 1) / VD;
       for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
@@ -563,11 +560,11 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
             wq[pos++] = (moved >> jb) & 1u ? ~(base + jb) : base + jb;
           }
           qn += total;
-          __syncwarp();
-          while (qn >= 32) drain(32);
         }
       }
-      if (qn > 0) drain(qn);
+      // then the deferred leptons, 32 at a time
+      __syncwarp();
+      for (int i0 = 0; i0 < qn; i0 += 32) drain_at(i0, qn - i0 < 32 ? qn - i0 : 32);
     } else {
     const int ngroups = (used + VEC - 1) / VEC;
     // warp-uniform trip count (lanes past the end load nothing)
@@ -1962,7 +1959,7 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
   }
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
   k_push_items<<<1, 1024, 0, st>>>(v);
-  const int grid = 148 * 4;  // persistent: blocks take items until the list is empty
+  const int grid = kPushGrid;  // persistent: blocks take items until the list is empty
   if (v.jperp_any) {
     // the particles' transverse current: fields and current sums of the tile
     // in shared memory as well, every lepton pushed in place
