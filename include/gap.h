@@ -198,11 +198,13 @@ typedef struct gap_config {
                               0: 4 leptons/thread, >= 4 blocks/SM; 1: 4, >= 6;
                               2: 2, >= 8; 3: 4, >= 8; 4, 5: TMA bulk-copy
                               pipeline with 3 or 2 stages (the autotuner picks).
-                              FP32 path with QED: 0: leptons that emit within
-                              the step are deferred to converged warp passes,
-                              >= 4 blocks/SM; 1: the same, >= 3 blocks/SM;
-                              2-5: every lepton pushed in place.  All variants
-                              give the same results */
+                              FP32 path with QED: 0: two passes, the quiet
+                              leptons streamed at >= 5 blocks/SM and the
+                              leptons that emit within the step or move into
+                              another tile pushed by a second kernel from a
+                              list (Ampere then follows for every gap); 1: the
+                              same at >= 4 blocks/SM; 2-5: every lepton pushed
+                              in place.  All variants give the same results */
   int32_t reserved;
   double slack;            /* headroom of each tile segment (0 -> 0.125) */
   int64_t lepton_capacity; /* slots per species over all gaps (0 -> derived) */

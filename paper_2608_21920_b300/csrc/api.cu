@@ -437,6 +437,13 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   const int64_t dchg = std::max(total_nodes, max_nx);
 
   Carver C(base);
+  // the two-pass FP32 QED push leaves Ampere to k_filter_apply for every gap
+  // (its second pass deposits after the first has finished its tiles)
+  const bool two_pass = fp32 && qed_any && (cfg.variant == 0 || cfg.variant == 1);
+  for (auto &g : gaps) {
+    g.ampere_late = g.defer || two_pass ? 1 : 0;
+    filter_any |= g.ampere_late != 0;
+  }
   View v{};
   v.n_gaps = n;
   v.n_tiles = NT;
@@ -479,7 +486,14 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   // store's capacity
   const int64_t item_cap = 2 * (lep_cap / kPushChunkMin) + 2 * (int64_t)NT + 2;
   v.item_tile = C.take<int32_t>((size_t)item_cap);
-  v.defer_list = C.take<int32_t>(cfg.precision == GAP_FP32_STATE && qed_any ? (size_t)kPushGrid * kDeferPerBlock : 0);
+  {  // the two-pass FP32 QED push (variants 0 and 1): its deferred list,
+     // one entry for every lepton the two stores can hold (a lepton is
+     // deferred at most once a step)
+    const int64_t dcap = two_pass ? 2 * lep_cap : 0;
+    v.defer_slot = C.take<int64_t>((size_t)dcap);
+    v.defer_ts = C.take<uint32_t>((size_t)dcap);
+    v.defer_cap = dcap;
+  }
   v.item_cap = (int32_t)std::min<int64_t>(item_cap, INT32_MAX);
   v.tile_done = C.take<int32_t>(NT);
   v.counters = C.take<unsigned long long>((size_t)n * C_NCNT);
@@ -701,6 +715,7 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (c->error & 64) return fail(h, GAP_ECHECK, "a photon event was not taken at its step");
   if (c->error & 128) return fail(h, GAP_ECAP, "proton storage exhausted");
   if (c->error & 256) return fail(h, GAP_ECHECK, "more push work items than the item table holds");
+  if (c->error & 512) return fail(h, GAP_ECHECK, "more deferred leptons than the deferred list holds");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));

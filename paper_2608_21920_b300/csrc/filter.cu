@@ -16,7 +16,9 @@
 // under which smoothing commutes with the node-to-cell difference, so Gauss's
 // law holds for the smoothed charge.  Both kernels touch only gaps that defer
 // Ampere (filter_passes > 0, or protons or transverse fields: zero passes,
-// the update alone, plus dt jv_h of the transverse fields), and
+// the update alone, plus dt jv_h of the transverse fields; and every gap
+// under the two-pass FP32 QED push, zero passes, for the update), the merge's
+// correction (mode 1) only those with a filter or protons or fields, and
 // the tiles of a gap cover its nodes k0 .. k0 + nk - 1 without overlap.
 #include <algorithm>
 
@@ -46,10 +48,10 @@ __device__ __forceinline__ int64_t node_source(int64_t j, int64_t n, bool period
 // stores take and clear the accumulators.  FP32 state: the exact integer
 // flux is kept as is (the smoothing runs in integers); FP64 state: doubles.
 template <class R>
-__global__ void k_flux_take(View v) {
+__global__ void k_flux_take(View v, int mode) {
   const TileDev ti = v.tiles[blockIdx.x];
   const GapDev &g = v.gaps[ti.gap];
-  if (!g.defer) return;
+  if (!(mode == 0 ? g.ampere_late : g.defer)) return;
   unsigned long long *out = reinterpret_cast<unsigned long long *>(v.Dflt);
   for (int i = threadIdx.x; i < ti.nk; i += blockDim.x) {
     const int64_t gn = g.node_off + ti.k0 + i;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256) k_filter_apply(View v, int mode) {
   for (int t = t0; t < t1; ++t) {
     const TileDev ti = v.tiles[t];
     const GapDev &g = v.gaps[ti.gap];
-    if (!g.defer) continue;
+    if (!(mode == 0 ? g.ampere_late : g.defer)) continue;
     const int P = g.filter_passes;  // 0: Ampere alone (a gap with protons)
     if (mode == 0 && ti.gap != work_gap) {  // block-uniform
       if (work_gap >= 0) {
@@ -196,10 +198,10 @@ void launch_filter(const View &v, int mode, cudaStream_t st) {
   if (!v.filter_any) return;
   const int grid = std::min(v.n_tiles, 148 * 8);
   if (v.precision == GAP_FP32_STATE) {
-    k_flux_take<float><<<v.n_tiles, 256, 0, st>>>(v);
+    k_flux_take<float><<<v.n_tiles, 256, 0, st>>>(v, mode);
     k_filter_apply<float><<<grid, 256, 0, st>>>(v, mode);
   } else {
-    k_flux_take<double><<<v.n_tiles, 256, 0, st>>>(v);
+    k_flux_take<double><<<v.n_tiles, 256, 0, st>>>(v, mode);
     k_filter_apply<double><<<grid, 256, 0, st>>>(v, mode);
   }
 }

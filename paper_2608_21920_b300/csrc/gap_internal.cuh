@@ -40,10 +40,6 @@ constexpr int kSpecMaxBins = 1024;              // gap_spectra: bins per histogr
 constexpr int kPushChunk = 32768;  // the largest (multiple of 32; the limb bound below)
 constexpr int kPushChunkMin = 8192;
 constexpr int kPushGrid = 148 * 4;  // blocks of the persistent push grid (4 per SM)
-// Leptons deferred by a block of the FP32 QED push in one item: a warp's
-// share of an item is at most push_chunk / warps + 32 VD leptons (VD = 2,
-// at most 32 warps), and each is deferred at most once.
-constexpr int kDeferPerBlock = kPushChunk + 2048;
 static_assert(kPushChunk <= 32768, "the 17-bit charge limbs hold at most 32768 contributions per node");
 
 // Quantum photon spectrum table: rows of ln chi from ln 1e-6 in steps of
@@ -109,7 +105,7 @@ struct GapDev {
   double beta_y, beta_z;  // velocity of the co-rotating frame across h
   double pml_smax;        // peak conductivity of the layer (omega_p)
   int32_t jperp;          // 1: the particles' transverse current (guiding centres)
-  int32_t jperp_pad;
+  int32_t ampere_late;    // Ampere after the push kernels (filter.cu): defer, or the two-pass QED push
   double bstar_inv;       // 1 / B_* = lambda_hat / b (code units)
 };
 
@@ -132,6 +128,7 @@ struct Ctl {
   int32_t hold_copies;  // test hook: bulk-copy pushes leave their first stage unissued
   int32_t push_items, push_next;  // the push work list of this step and its counter
   int32_t push_chunk, push_pad;   // leptons per item this step (kPushChunkMin .. kPushChunk)
+  unsigned long long defer_n;     // entries of the deferred list this step (may exceed its capacity)
   int64_t spill_n[2];
   int64_t new_total[2];
   int64_t ph_nb_start;  // photon store fill before this step's push (0 after a photon compaction)
@@ -186,7 +183,12 @@ struct View {
   int32_t *gross[2];     // per tile: appends since the last re-bin
   int32_t *item_start;   // [n_tiles + 1] first push item of each tile
   int32_t *item_tile;    // [item_cap] tile of each push item
-  int32_t *defer_list;   // [push grid x kDeferPerBlock] leptons deferred by the FP32 QED push
+  // leptons the FP32 QED push defers to k_push_deferred (emitters, and
+  // leptons that moved into another tile): store slot, and tile | species
+  // << 30 | mover << 31
+  int64_t *defer_slot;
+  uint32_t *defer_ts;
+  int64_t defer_cap;
   int32_t item_cap;      // bound on the push items of a step
   int32_t *tile_done;    // [n_tiles] items of the tile finished this step
   // lepton stores [buffer][species]

@@ -459,35 +459,12 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     if constexpr (DEFER) {
       // 8-byte vectors of VD leptons per lane through push_quiet; a lepton
-      // that emits this step is left unchanged and queued (its offset from
-      // `start`) in the warp's queue, and so is one that moved into another
-      // tile (offset complemented), and whenever 32 are queued the warp
-      // runs push_one on the emitters and appends the movers, one per lane,
-      // so that these rare events of a warp run side by side instead of one
-      // lane at a time (an append waits on global atomics).
+      // that emits this step is left unchanged, and one that moved into
+      // another tile is left with its new state, and both go on the step's
+      // deferred list for k_push_deferred: their emission events and appends
+      // (which wait on global atomics) then run in full warps over the whole
+      // GPU, and this loop keeps the registers of the quiet lepton alone.
       constexpr int VD = 2;
-      // the warp's list of deferred leptons (global scratch of the block)
-      int *wq = v.defer_list + (int64_t)blockIdx.x * kDeferPerBlock + (threadIdx.x >> 5) * (kDeferPerBlock / nwarp);
-      int qn = 0;  // warp-uniform
-      auto drain_at = [&](const int i0, const int n) {
-        if (lane < n) {
-          const int e = wq[i0 + lane];
-          const int64_t slot = start + (e >= 0 ? e : ~e);
-          int32_t k = Kp[slot];
-          R phi = Pp[slot], u = Up[slot], tau = Tp[slot];
-          const W w = HAS_W ? Wp[slot] : w_def;
-          if (e >= 0) {
-            push_one(k, phi, u, w, tau, slot);
-            Pp[slot] = phi;
-            Up[slot] = u;
-            Tp[slot] = tau;
-          } else {  // pushed already: to its new tile
-            append_lepton<R>(v, s, tile_of(v, g, k), k, phi, u, w, tau, Ip[slot]);
-            k = -1;
-          }
-          Kp[slot] = k;
-        }
-      };
       const int ngroups = (used + VD - 1) / VD;
       for (int g0 = (threadIdx.x >> 5) * 32; g0 < ngroups; g0 += nwarp * 32) {
         const int gi = g0 + lane;
@@ -553,18 +530,26 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           before += __popc(bj & below);
           total += __popc(bj);
         }
-        if (total > 0) {  // warp-uniform
-          int pos = qn + before;
+        if (total > 0) {  // warp-uniform: reserve the warp's entries of the list
+          unsigned long long first = 0ull;
+          if (lane == 0) first = atomicAdd(&v.ctl->defer_n, (unsigned long long)total);
+          first = __shfl_sync(0xffffffffu, first, 0);
+          unsigned long long pos = first + (unsigned long long)before;
           for (unsigned b = later; b; b &= b - 1u) {
             const int jb = __ffs(b) - 1;
-            wq[pos++] = (moved >> jb) & 1u ? ~(base + jb) : base + jb;
+            const bool mover = (moved >> jb) & 1u;
+            if (pos < (unsigned long long)v.defer_cap) {
+              v.defer_slot[pos] = slot0 + jb;
+              v.defer_ts[pos] = (uint32_t)t | ((uint32_t)s << 30) | (mover ? 0x80000000u : 0u);
+            } else {  // never: the list holds every lepton of the store
+              atomicOr(&v.ctl->error, 512);
+              Kp[slot0 + jb] = -1;
+              if (!mover) ++dead;
+            }
+            ++pos;
           }
-          qn += total;
         }
       }
-      // then the deferred leptons, 32 at a time
-      __syncwarp();
-      for (int i0 = 0; i0 < qn; i0 += 32) drain_at(i0, qn - i0 < 32 ? qn - i0 : 32);
     } else {
     const int ngroups = (used + VEC - 1) / VEC;
     // warp-uniform trip count (lanes past the end load nothing)
@@ -628,7 +613,7 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   bool finish = true;  // this block completes the tile
-  if (g.defer) {
+  if (g.ampere_late) {
     for (int i = threadIdx.x; i < nk + 2; i += blockDim.x) {
       const Acc qi = node_charge(i);
       if (qi == (Acc)0) continue;
@@ -716,6 +701,196 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
     if (q0_tile && q0v != (Acc)0) acc_add_global(&v.q0[ti.gap], q0v);
   }
   }  // items
+}
+
+// ---------------------------------------------------------------------------
+// The second pass of the two-pass FP32 QED push: one deferred lepton of tile
+// t, species s, store slot `slot`.  A mover was pushed by the first pass and
+// only goes to its new tile; an emitter is pushed here from its start-of-step
+// state with the first pass's arithmetic (gather of E^n in the state's
+// precision, kick, emission sub-cycling, drift, exact charge through the
+// nodes, boundaries, photons born at the new position), its charge going to
+// the global node accumulators and its events to the global counters and
+// ledgers, since the first pass has left its tile.  Returns the leptons that
+// left the tile (an emitter removed or moved on; a mover was counted by the
+// first pass).
+template <class R>
+__device__ __noinline__ int push_deferred(const View &v, const int t, const int s, const int64_t slot,
+                                          const bool mover) {
+  using W = typename Prec<R>::W;
+  const TileDev ti = v.tiles[t];
+  const GapDev &g = v.gaps[ti.gap];
+  const int cur = v.ctl->lep_cur;
+  int32_t *Kp = v.lk[cur][s];
+  R *Pp = as<R>(v.lphi[cur][s]);
+  R *Up = as<R>(v.lu[cur][s]);
+  W *Wp = as<W>(v.lw[cur][s]);
+  R *Tp = as<R>(v.ltau[cur][s]);
+  const uint64_t id = v.lid[cur][s][slot];
+  int32_t k = Kp[slot];
+  R phi = Pp[slot], u = Up[slot], tau = Tp[slot];
+  const W w = Wp[slot];
+  if (mover) {
+    append_lepton<R>(v, s, tile_of(v, g, k), k, phi, u, w, tau, id);
+    Kp[slot] = -1;
+    return 0;
+  }
+  const int q = s == 0 ? -1 : 1;
+  const int64_t nx = g.nx;
+  const int32_t nx32 = (int32_t)nx;
+  const bool periodic = g.periodic != 0;
+  const int64_t step = v.ctl->step;
+  const double wunit = g.w_unit;
+  unsigned long long *C = v.counters + ti.gap * C_NCNT;
+  double *Lg = v.ledger + ti.gap * L_NLED;
+  const double *Eo = v.E[v.ctl->e_cur] + g.node_off;
+  auto e_at = [&](int64_t node) -> R {
+    if (periodic) return (R)Eo[(node + nx) % nx];
+    return (node >= 0 && node <= nx) ? (R)Eo[node] : (R)0;
+  };
+  // a1-a2: gather between nodes j and j + 1 (j = k or k - 1), kick
+  const R sph = phi - (R)1.5;
+  const int64_t j = sph >= (R)0 ? k : k - 1;
+  const R tt = sph >= (R)0 ? sph : sph + (R)1;
+  const R e0 = e_at(j), e1 = e_at(j + 1);
+  u += (R)q * (e0 + tt * (e1 - e0)) * (R)g.dt;
+  // a3: emission sub-cycling (the lepton is below H_gap and QED is on)
+  R ph_x[kMaxEmit];
+  int ph_k[kMaxEmit];
+  int nph = 0;
+  {
+    const float chi_cf = g.f_lam / g.f_rho;
+    const float rate_cf = g.f_rate * (float)kAlphaEm / g.f_rho;
+    R trem = (R)g.dt;
+    int kk = 0;
+    for (;;) {
+      R gm = sqrt((R)1 + u * u);
+      const R chi = gm * gm * (R)chi_cf;
+      const R r = (R)rate_cf * gm * (R)tsyn_f((float)chi);
+      if (!(r > (R)0)) break;
+      if (tau > r * trem) {
+        tau -= r * trem;
+        break;
+      }
+      trem -= tau / r;
+      const R xs = emission_event<R>(v, g.seed, id, (uint32_t)step, (uint32_t)kk, gm, chi, u, tau,
+                                     g.qed_quantum != 0);
+      const R x = xs >= (R)0 ? xs : -xs;
+      atomicAdd(&C[C_EMIT], 1ull);
+      if (x >= (R)2) {
+        ph_x[nph] = xs;
+        ph_k[nph] = kk;
+        ++nph;
+      } else {
+        atomicAdd(&Lg[L_RAD], (double)w * wunit * (double)x);
+      }
+      if (++kk >= g.kmax_emit) {
+        atomicAdd(&C[C_EMIT_OVF], 1ull);
+        break;
+      }
+    }
+  }
+  // a4: drift
+  const R dX = u * (R)rsqrtf((float)((R)1 + u * u)) * (R)g.cdx;
+  R pn = phi + dX;
+  int32_t kn = k;
+  if (pn >= (R)2) {
+    pn -= (R)1;
+    kn += 1;
+  } else if (pn < (R)1) {
+    pn += (R)1;
+    kn -= 1;
+    if (pn >= (R)2) {
+      pn -= (R)1;
+      kn += 1;
+    }
+  }
+  // a8: charge through nodes k and kn, exact integers into the accumulators
+  const int dk = kn - k;
+  {
+    const int Fo = __float2int_rn(((float)phi - 1.0f) * 8388608.0f);
+    const int Fn = __float2int_rn(((float)pn - 1.0f) * 8388608.0f);
+    const int f0 = dk == 0 ? Fn - Fo : (dk > 0 ? (1 << kPhiBits) - Fo : -Fo);
+    const long long qw = (long long)q * (long long)w;
+    auto add_node = [&](int64_t node, long long c) {
+      if (periodic) node = (node + nx) % nx;
+      else if (node < 0 || node > nx) return;
+      acc_add_global(&v.Dg[g.node_off + node], c);
+    };
+    add_node(k, qw * (long long)f0);
+    if (dk != 0) add_node(kn, qw * (long long)(dk > 0 ? Fn : Fn - (1 << kPhiBits)));
+  }
+  // a7: boundaries
+  bool gone = false;
+  if (!periodic) {
+    if (kn < 0 || (kn == 0 && pn < (R)1.5)) {
+      gone = true;
+      atomicAdd(&C[C_ABSORBED], 1ull);
+      atomicAdd(&Lg[L_ABS], (double)w * wunit * (double)sqrt((R)1 + u * u));
+      tally_return(v, ti.gap, (double)u, (double)w * wunit);
+    } else if (kn > nx32 || (kn == nx32 && pn >= (R)1.5)) {
+      gone = true;
+      atomicAdd(&C[C_ESCAPED], 1ull);
+      atomicAdd(&Lg[L_ESC], (double)w * wunit * (double)sqrt((R)1 + u * u));
+    }
+  } else {
+    if (kn < 0) kn += nx32;
+    else if (kn >= nx32) kn -= nx32;
+  }
+  // photons born this step sit at the lepton's new position
+  if (nph > 0) {
+    const double wd = (double)w * wunit;
+    double Xn = (double)kn + ((double)pn - 1.5);
+    if (periodic && Xn < 0.0) Xn += (double)nx;
+    const bool inside = periodic || (Xn >= 0.0 && Xn < (double)nx);
+    for (int b = 0; b < nph; ++b) {
+      double xb = (double)ph_x[b];
+      const int32_t dirb = xb >= 0.0 ? 1 : -1;
+      xb = fabs(xb);
+      if (!inside) {
+        atomicAdd(&C[C_PH_ESCAPED], 1ull);
+        atomicAdd(&Lg[L_PH_ESC], wd * xb);
+        continue;
+      }
+      const uint64_t pid = child_id(id, (uint32_t)step, CH_PHOTON, (uint32_t)ph_k[b]) | kPhotonBit;
+      const double tsb = -log(uniform53(g.seed, pid, (uint32_t)(step + 1), CH_BW_TAU, 0));
+      photon_append(v, v.ctl->ph_cur, ti.gap, Xn, (int32_t)(step + 1), xb, wd, tsb, 0.0, pid, (int32_t)(step + 1),
+                    dirb, (int32_t)(step + 1));
+      atomicAdd(&C[C_PHOTONS], 1ull);
+      atomicAdd(&v.ph_gap[ti.gap], 1);
+    }
+  }
+  Up[slot] = u;
+  Tp[slot] = tau;
+  if (gone) {
+    Kp[slot] = -1;
+    return 1;
+  }
+  if (!periodic && ti.k0 == 0 && kn <= 1) {  // cell 0's charge of a surface gap (the injection)
+    const int Fn = __float2int_rn(((float)pn - 1.0f) * 8388608.0f);
+    const long long frac = kn == 0 ? Fn : (1 << kPhiBits) - Fn;
+    acc_add_global(&v.q0[ti.gap], (long long)q * (long long)w * frac);
+  }
+  if (kn >= ti.k0 && kn < ti.k0 + ti.nk) {
+    Kp[slot] = kn;
+    Pp[slot] = pn;
+    return 0;
+  }
+  append_lepton<R>(v, s, tile_of(v, g, kn), kn, pn, u, w, tau, id);
+  Kp[slot] = -1;
+  return 1;
+}
+
+// The second pass over the step's deferred list.
+__global__ void __launch_bounds__(256) k_push_deferred(View v) {
+  const unsigned long long n0 = v.ctl->defer_n;
+  const int64_t n = n0 < (unsigned long long)v.defer_cap ? (int64_t)n0 : v.defer_cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t ts = v.defer_ts[i];
+    const int t = (int)(ts & 0x3FFFFFFFu), s = (int)((ts >> 30) & 1u);
+    const int dead = push_deferred<float>(v, t, s, v.defer_slot[i], (ts >> 31) != 0);
+    if (dead) atomicAdd(&v.seg_alive[s][t], -dead);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -925,7 +1100,7 @@ __global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.defer) {
+  if (g.ampere_late) {
     // a gap that defers Ampere (current filter, transverse fields): every
     // node's flux goes to the global accumulators (k_push units) and
     // k_filter_apply finishes E
@@ -1279,7 +1454,7 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.defer) {
+  if (g.ampere_late) {
     // a gap that defers Ampere (current filter, transverse fields): every
     // node's flux goes to the global accumulators (k_push units) and
     // k_filter_apply finishes E
@@ -1924,6 +2099,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    v.ctl->defer_n = 0ull;
     v.item_start[n] = carry;
     if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
     v.ctl->push_items = carry < v.item_cap ? carry : v.item_cap;
@@ -1969,13 +2145,17 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     else if (v.has_w) k_push<R, false, true, false, 3, true><<<grid, threads, smem_em, st>>>(v);
     else k_push<R, false, false, false, 3, true><<<grid, threads, smem_em, st>>>(v);
   } else if (v.qed_any) {
-    // FP32 state: emitters deferred to converged warp passes (variant 0: at
-    // most 64 registers, 4 blocks per SM; 1: 80 registers, 3 blocks per SM),
-    // or every lepton pushed in place (variant 2)
-    if (sizeof(R) == 4 && v.has_w && v.variant == 0)
+    // FP32 state: two passes, the quiet leptons streamed (variant 0: at most
+    // 48 registers, 5 blocks per SM; 1: 64 registers, 4 blocks per SM), then
+    // the deferred ones from the step's list; or every lepton pushed in
+    // place (variants 2-5)
+    if (sizeof(R) == 4 && v.has_w && v.variant == 0) {
+      k_push<float, true, true, true, 5><<<148 * 5, threads, smem, st>>>(v);
+      k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
+    } else if (sizeof(R) == 4 && v.has_w && v.variant == 1) {
       k_push<float, true, true, true, 4><<<grid, threads, smem, st>>>(v);
-    else if (sizeof(R) == 4 && v.has_w && v.variant == 1)
-      k_push<float, true, true, true, 3><<<grid, threads, smem, st>>>(v);
+      k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
+    }
     else if (v.has_w)
       k_push<R, true, true><<<grid, threads, smem, st>>>(v);
     else
