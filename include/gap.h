@@ -417,11 +417,15 @@ int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_
                 int64_t *launches_per_step);
 
 /* Phases of a profiled step (gap_profile_phases). */
-#define GAP_PHASE_PUSH 0   /* the fused push / emission / deposit / Ampere kernel */
+#define GAP_PHASE_PUSH 0   /* the streaming push kernel (with its item list): gather, kick,
+                              emission, drift, deposit, and Ampere where it is fused */
 #define GAP_PHASE_AFTER 1  /* photon propagation and conversion, injection, bookkeeping */
 #define GAP_PHASE_REBIN 2  /* store compaction (a no-op launch sequence between re-bins) */
 #define GAP_PHASE_MERGE 3  /* the over-cap check and merge */
-#define GAP_NPHASES 4
+#define GAP_PHASE_PUSH_TAIL 4 /* after the streaming push: the second pass of the two-pass
+                              QED push, protons, transverse fields, Ampere of the gaps
+                              that leave it to a separate kernel */
+#define GAP_NPHASES 5
 
 /* Durations (ms) of each phase summed over the steps profiled since the last
  * gap_profile call (which clears them), without clearing; ms_out holds

@@ -36,11 +36,11 @@ struct gap_handle {
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // kProfEvents per profiled step
   size_t ev_used = 0;
-  double phase_ms[GAP_NPHASES] = {0, 0, 0, 0};
+  double phase_ms[GAP_NPHASES] = {0, 0, 0, 0, 0};
   int64_t phase_steps = 0;
 };
 
-static constexpr size_t kProfEvents = 5;
+static constexpr size_t kProfEvents = 6;
 
 namespace {
 
@@ -771,8 +771,9 @@ int gap_step(gap_handle *h, int64_t nsteps, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   for (int64_t i = 0; i < nsteps; ++i) {
     if (h->profiling) {
-      // five events per step: before the push, after it, after the photon /
-      // injection / bookkeeping launches, after the re-bin, after the merge
+      // six events per step, in order: before the push, after its
+      // streaming kernel, after its tail, after the photon / injection /
+      // bookkeeping launches, after the re-bin, after the merge
       if (h->ev_used + kProfEvents > h->ev.size()) {
         for (int k = 0; k < 16 * kProfEvents; ++k) {
           cudaEvent_t e;
@@ -784,12 +785,14 @@ int gap_step(gap_handle *h, int64_t nsteps, void *stream) {
       cudaEventRecord(ev[0], st);
       launch_push(h->v, h->threads, st);
       cudaEventRecord(ev[1], st);
-      launch_after_push(h->v, st);
+      launch_push_tail(h->v, st);
       cudaEventRecord(ev[2], st);
-      launch_rebin(h->v, h->slack, st);
+      launch_after_push(h->v, st);
       cudaEventRecord(ev[3], st);
-      if (h->v.merge_any) launch_merge(h->v, st);
+      launch_rebin(h->v, h->slack, st);
       cudaEventRecord(ev[4], st);
+      if (h->v.merge_any) launch_merge(h->v, st);
+      cudaEventRecord(ev[5], st);
       h->ev_used += kProfEvents;
       continue;
     }
@@ -1215,10 +1218,14 @@ static int collect_phases(gap_handle *h) {
   if (!h->ev_used) return GAP_OK;
   cudaError_t e = cudaEventSynchronize(h->ev[h->ev_used - 1]);
   if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+  // the phase of each interval between consecutive events
+  static const int phase_of[GAP_NPHASES] = {GAP_PHASE_PUSH, GAP_PHASE_PUSH_TAIL, GAP_PHASE_AFTER, GAP_PHASE_REBIN,
+                                            GAP_PHASE_MERGE};
   for (size_t i = 0; i + kProfEvents <= h->ev_used; i += kProfEvents) {
-    for (int ph = 0; ph < GAP_NPHASES; ++ph) {
+    for (int k = 0; k < GAP_NPHASES; ++k) {
+      const int ph = phase_of[k];
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, h->ev[i + ph], h->ev[i + ph + 1]);
+      e = cudaEventElapsedTime(&ms, h->ev[i + k], h->ev[i + k + 1]);
       if (e != cudaSuccess) return cuda_check(h, e, "profile read");
       h->phase_ms[ph] += ms;
     }

@@ -2128,9 +2128,6 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
       }
       default: k_push_lean<4, 4><<<v.n_tiles, threads, smem_lean, st>>>(v); break;
     }
-    if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons
-    launch_em(v, st);         // transverse fields, before E_h moves on
-    launch_filter(v, 0, st);  // Ampere of the gaps that defer it
     return;
   }
   const size_t smem = (size_t)(v.tile + 8) * (sizeof(R) == 4 ? 16 : 16) + 64;
@@ -2149,13 +2146,10 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     // 48 registers, 5 blocks per SM; 1: 64 registers, 4 blocks per SM), then
     // the deferred ones from the step's list; or every lepton pushed in
     // place (variants 2-5)
-    if (sizeof(R) == 4 && v.has_w && v.variant == 0) {
+    if (sizeof(R) == 4 && v.has_w && v.variant == 0)
       k_push<float, true, true, true, 5><<<148 * 5, threads, smem, st>>>(v);
-      k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
-    } else if (sizeof(R) == 4 && v.has_w && v.variant == 1) {
+    else if (sizeof(R) == 4 && v.has_w && v.variant == 1)
       k_push<float, true, true, true, 4><<<grid, threads, smem, st>>>(v);
-      k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
-    }
     else if (v.has_w)
       k_push<R, true, true><<<grid, threads, smem, st>>>(v);
     else
@@ -2166,9 +2160,12 @@ static void launch_push_impl(const View &v, int threads, cudaStream_t st) {
     else
       k_push<R, false, false><<<grid, threads, smem, st>>>(v);
   }
-  if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons (FP64 state)
-  launch_em(v, st);  // transverse fields, before E_h moves on
-  launch_filter(v, 0, st);  // Ampere of the gaps that defer it (current filter, protons)
+}
+
+// The two-pass FP32 QED push (variants 0, 1; not with the transverse particle
+// current, whose push runs in place)
+static bool two_pass_push(const View &v) {
+  return v.precision == GAP_FP32_STATE && v.qed_any && v.has_w && !v.jperp_any && (v.variant == 0 || v.variant == 1);
 }
 
 template <class R>
@@ -2196,6 +2193,16 @@ void launch_push(const View &v, int threads, cudaStream_t st) {
   else launch_push_impl<double>(v, threads, st);
 }
 
+// After the streaming push: the second pass of the two-pass QED push, the
+// protons, the transverse fields (before E_h moves on) and Ampere of the
+// gaps that leave it to k_filter_apply.
+void launch_push_tail(const View &v, cudaStream_t st) {
+  if (two_pass_push(v)) k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
+  if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons
+  launch_em(v, st);
+  launch_filter(v, 0, st);
+}
+
 void launch_after_push(const View &v, cudaStream_t st) {
   if (v.precision == GAP_FP32_STATE) launch_after_push_impl<float>(v, st);
   else launch_after_push_impl<double>(v, st);
@@ -2203,12 +2210,13 @@ void launch_after_push(const View &v, cudaStream_t st) {
 
 void launch_step(const View &v, int threads, cudaStream_t st) {
   launch_push(v, threads, st);
+  launch_push_tail(v, st);
   launch_after_push(v, st);
 }
 
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
-  return (lean ? 1 : 2) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
+  return (lean ? 1 : 2) + (two_pass_push(v) ? 1 : 0) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
          (v.qed_any ? 2 : 0) + (v.filter_any ? (v.merge_any ? 4 : 2) : 0) + (v.pr_any ? 1 : 0) + (v.em_any ? 2 : 0);
 }
 

@@ -117,7 +117,7 @@ class Gap:
                 "gap_profile")
         return ms.value, n.value, lps.value
 
-    PHASES = ("push", "photons+inject+house", "rebin", "merge")
+    PHASES = ("push", "photons+inject+house", "rebin", "merge", "push_tail")
 
     def profile_phases(self) -> tuple[dict, int]:
         """Per-phase durations (ms, summed) of the steps profiled since the
