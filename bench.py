@@ -145,21 +145,32 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def traffic_record(kernel, precision):
-    """DRAM traffic per launch of the push kernel from a committed ncu summary,
-    valid only while the kernel's source text is unchanged."""
+# the source text of each recorded kernel: from the template line above its
+# signature to the next separator line
+TRAFFIC_KERNELS = {"k_push": "k_push_lean(View v)", "k_push_qed": "k_push(View v)"}
+
+
+def kernel_sha(kernel):
+    src = open(os.path.join(ROOT, "paper_2608_21920_b300", "csrc", "step.cu")).read()
+    i = src.index(TRAFFIC_KERNELS[kernel])
+    i = src.rfind("template", 0, i)
+    j = src.index("// -----------", i)
+    return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
+
+
+def traffic_record(kernel, precision, units=None):
+    """DRAM traffic per launch of a push kernel from a committed ncu summary,
+    valid only while the kernel's source text is unchanged; with `units`
+    (leptons per launch), the recorded bytes per lepton times the units."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[f"{kernel}:{precision}"]
     except Exception:
         return None
-    src = open(os.path.join(ROOT, "paper_2608_21920_b300", "csrc", "step.cu")).read()
-    i = src.index("k_push_lean(View v)")
-    i = src.rfind("template", 0, i)
-    j = src.index("// -----------", i)
-    sha = hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
-    if rec.get("step_cu_sha") != sha:
+    if rec.get("step_cu_sha") != kernel_sha(kernel):
         return None
+    if units is not None:
+        return rec.get("bytes_per_lepton") * units
     return rec.get("bytes_per_launch")
 
 
@@ -582,7 +593,8 @@ def batch_measure(args, world=1, local=0):
                    "leptons_mean": nmean, "l2": "inputs larger than L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"hbm_gbs of {peak_kind}", "kernel": "k_push (FP32, QED, stored weights)",
-                     "bytes_per_particle": bpp, "push_ms_per_launch": push_ms, "traffic": None},
+                     "bytes_per_particle": bpp, "push_ms_per_launch": push_ms,
+                     "traffic": traffic_record("k_push_qed", "fp32", units=0.5 * (n1 + n2))},
         "gpu_launches": int(lps * K),
         "clocks": clk,
         "pairs": int(sum(x["pairs"] for x in c)), "merged": int(sum(x["merged"] for x in c)),

@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(256, MINB) k_push_lean(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.ampere_late) {
+  if (g.defer) {
     // a gap that defers Ampere (current filter, transverse fields): every
     // node's flux goes to the global accumulators (k_push units) and
     // k_filter_apply finishes E
@@ -1454,7 +1454,7 @@ __global__ void __launch_bounds__(256, 4) k_push_tma(View v) {
   const double djm = g.dt * g.jm;
   double work = 0.0;
   auto node_sum = [&](int i) -> long long { return (long long)sHi[i] * 4096 + (long long)sLo[i]; };
-  if (g.ampere_late) {
+  if (g.defer) {
     // a gap that defers Ampere (current filter, transverse fields): every
     // node's flux goes to the global accumulators (k_push units) and
     // k_filter_apply finishes E
