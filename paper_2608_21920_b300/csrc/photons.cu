@@ -246,23 +246,17 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
     atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->ph_dead), (unsigned long long)__popc(mask));
 }
 
-// Photon pass of step n, part 1: a scan of the event steps.  Events of this
-// step are applied; photons waiting to be scheduled (new, imported, or at
-// their re-schedule step) go to a dense work list.
+// Photon pass of step n, part 1: a scan of the event steps.  Every photon
+// with something to do this step (new or imported and not yet scheduled, at
+// its re-schedule step, or at its event) goes to a dense work list, so that
+// the scan streams the event steps and the work runs in full warps.
 template <class R>
 __device__ __forceinline__ void photon_scan_one(const View &v, int b, int64_t i, int32_t ev, int64_t step) {
-  bool work = false;
-  if (ev == kPhPending) {
-    work = true;
-  } else if (ev == step) {
-    if (v.pkind[b][i] == PH_RESCHEDULE) work = true;
-    else photon_event<R>(v, b, i, step);
-  } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
-    atomicOr(&v.ctl->error, 64);
-  }
-  if (work) {
+  if (ev == kPhPending || ev == step) {
     const long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n));
     v.ph_work[slot] = (int64_t)i;
+  } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
+    atomicOr(&v.ctl->error, 64);
   }
 }
 
@@ -294,8 +288,9 @@ __global__ void __launch_bounds__(256, 5) k_photon_scan(View v) {
   }
 }
 
-// Part 2: schedule the work list (one photon per thread, densely packed);
-// an imported photon may have its event in this very step.
+// Part 2: the work list, one photon per thread: a photon to be scheduled
+// (new, imported, or at its re-schedule step) is scheduled, and may have its
+// event in this very step; a photon at its event converts or escapes.
 template <class R>
 __global__ void __launch_bounds__(256, 5) k_photon_schedule(View v) {
   const int b = v.ctl->ph_cur;
@@ -304,7 +299,7 @@ __global__ void __launch_bounds__(256, 5) k_photon_schedule(View v) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = v.ph_work[t];
-    schedule_photon<R>(v, b, i);
+    if (v.pev[b][i] == kPhPending || v.pkind[b][i] == PH_RESCHEDULE) schedule_photon<R>(v, b, i);
     if (v.pev[b][i] == step) photon_event<R>(v, b, i, step);
   }
 }
