@@ -180,12 +180,28 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
     v.lid[cur][s][d] = v.lid[nxt][s][src];
   };
+  // the bin floor(ln gamma / width) of the FP64 evaluation (FP64 runs at a
+  // small fraction of the FP32 rate here): taken from an FP32 evaluation t
+  // where that lies more than 1e-3 of a bin from a bin edge, else evaluated
+  // in FP64.  The FP32 t is within 1e-4 of a bin of the FP64 one: the
+  // rounding of u, 1 + u^2 and the square root moves ln gamma by ~2e-7,
+  // logf's ulp at ln gamma <= 21 is <= 2e-6, times 1/width <= 10, and the
+  // rounding of t <= 256 and of 1/width adds ~2e-5.
+  const float winv_f = (float)(1.0 / width);
   auto key_of = [&](int64_t src) -> int {
     const double u = (double)as<R>(v.lu[nxt][s])[src];
-    const double gm = sqrt(1.0 + u * u);
-    int64_t b = (int64_t)floor(log(gm) / width);
-    if (b < 0) b = 0;
-    if (b > kMergeBins - 1) b = kMergeBins - 1;
+    const float uf = (float)u;
+    const float tf = logf(sqrtf(1.0f + uf * uf)) * winv_f;
+    const float bf = floorf(tf);
+    int64_t b;
+    if (tf - bf > 1e-3f && bf + 1.0f - tf > 1e-3f && tf < (float)(kMergeBins - 1)) {
+      b = (int64_t)bf;
+    } else {
+      const double gm = sqrt(1.0 + u * u);
+      b = (int64_t)floor(log(gm) / width);
+      if (b < 0) b = 0;
+      if (b > kMergeBins - 1) b = kMergeBins - 1;
+    }
     return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
   };
   // a group merges when it has three or more members; in the FP32 state
