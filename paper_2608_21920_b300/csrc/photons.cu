@@ -249,46 +249,75 @@ __device__ void photon_event(const View &v, int b, int64_t i, int64_t step) {
 // Photon pass of step n, part 1: a scan of the event steps.  Every photon
 // with something to do this step (new or imported and not yet scheduled, at
 // its re-schedule step, or at its event) goes to a dense work list, so that
-// the scan streams the event steps and the work runs in full warps.
-template <class R>
-__device__ __forceinline__ void photon_scan_one(const View &v, int b, int64_t i, int32_t ev, int64_t step) {
-  if (ev == kPhPending || ev == step) {
-    const long long slot = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n));
-    v.ph_work[slot] = (int64_t)i;
-  } else if (ev != kPhDead && ev < step) {  // never: every event is taken at its step
-    atomicOr(&v.ctl->error, 64);
-  }
-}
+// the scan streams the event steps and the work runs in full warps.  Each
+// warp gathers its photons in shared memory and reserves their slots of the
+// list with one atomic per ~256 (one counter serves the whole GPU: reserving
+// a few at a time had the scan wait on it).
+constexpr int kScanBuf = 256;  // photons a warp gathers before it reserves
 
-// Both photon-pass kernels keep five blocks of 256 threads per SM (at most
-// 51 registers): the scan is latency-bound and needs the warps; the rare
-// conversion with a quantum pair split spills instead.
-template <class R>
 __global__ void __launch_bounds__(256, 5) k_photon_scan(View v) {
+  __shared__ long long sbuf[8][kScanBuf + 128];  // <= 8 warps; a warp adds at most 128 at a time
   const int b = v.ctl->ph_cur;
   const int64_t n = photon_fill(v, b);
   const int64_t step = v.ctl->step;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
-  // four event steps per 16-byte load; most photons are dead or not due
-  auto idle = [&](int32_t ev) { return ev == kPhDead || ev > step; };
-  const int4 *ev4 = reinterpret_cast<const int4 *>(v.pev[b]);
-  const int64_t n4 = n / 4;
-  for (int64_t q = tid; q < n4; q += stride) {
-    const int4 e = ev4[q];
-    if (idle(e.x) && idle(e.y) && idle(e.z) && idle(e.w)) continue;
-    const int64_t i = 4 * q;
-    if (!idle(e.x)) photon_scan_one<R>(v, b, i, e.x, step);
-    if (!idle(e.y)) photon_scan_one<R>(v, b, i + 1, e.y, step);
-    if (!idle(e.z)) photon_scan_one<R>(v, b, i + 2, e.z, step);
-    if (!idle(e.w)) photon_scan_one<R>(v, b, i + 3, e.w, step);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long *wb = sbuf[wid];
+  int wn = 0;  // warp-uniform
+  auto flush = [&]() {
+    unsigned long long base = 0ull;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->ph_work_n), (unsigned long long)wn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int j = lane; j < wn; j += 32) v.ph_work[base + j] = wb[j];
+    __syncwarp();
+    wn = 0;
+  };
+  auto due = [&](int32_t ev) { return ev == kPhPending || ev == step; };
+  const int32_t *ev1 = v.pev[b];
+  const int4 *ev4 = reinterpret_cast<const int4 *>(ev1);
+  const int64_t n4 = (n + 3) / 4;  // four event steps per 16-byte load; a ragged last vector as scalars
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count (lanes past the end hold dead photons)
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < n4; q0 += stride) {
+    const int64_t q = q0 + lane;
+    int32_t e[4] = {kPhDead, kPhDead, kPhDead, kPhDead};
+    if (4 * q + 3 < n) {
+      const int4 x = ev4[q];
+      e[0] = x.x;
+      e[1] = x.y;
+      e[2] = x.z;
+      e[3] = x.w;
+    } else if (q < n4) {
+      for (int j = 0; 4 * q + j < n; ++j) e[j] = ev1[4 * q + j];
+    }
+    unsigned mine = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (due(e[j])) mine |= 1u << j;
+      else if (e[j] != kPhDead && e[j] < step) atomicOr(&v.ctl->error, 64);  // never: events are taken at their step
+    }
+    // a lane's photons go after those of the lanes below it
+    const unsigned below = (1u << lane) - 1u;
+    int before = 0, total = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned bj = __ballot_sync(0xffffffffu, (mine >> j) & 1u);
+      before += __popc(bj & below);
+      total += __popc(bj);
+    }
+    if (total == 0) continue;  // warp-uniform
+    if (wn + total > kScanBuf) flush();
+    int pos = wn + before;
+    for (unsigned m = mine; m; m &= m - 1u) wb[pos++] = 4 * q + (__ffs(m) - 1);
+    wn += total;
+    __syncwarp();
   }
-  for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
-    const int32_t ev = v.pev[b][i];
-    if (!idle(ev)) photon_scan_one<R>(v, b, i, ev, step);
-  }
+  if (wn > 0) flush();
 }
 
-// Part 2: the work list, one photon per thread: a photon to be scheduled
+// Part 2 (five blocks of 256 threads per SM, at most 51 registers: the
+// kernel is latency-bound and needs the warps; the rare conversion with a
+// quantum pair split spills instead): the work list, one photon per thread:
+// a photon to be scheduled
 // (new, imported, or at its re-schedule step) is scheduled, and may have its
 // event in this very step; a photon at its event converts or escapes.
 template <class R>
@@ -349,10 +378,10 @@ __global__ void k_photon_flip(View v) {
 void launch_photon_step(const View &v, cudaStream_t st) {
   k_photon_work_reset<<<1, 1, 0, st>>>(v);
   if (v.precision == GAP_FP32_STATE) {
-    k_photon_scan<float><<<16 * 148, 256, 0, st>>>(v);  // many loads in flight: the scan is latency-bound
+    k_photon_scan<<<16 * 148, 256, 0, st>>>(v);  // many loads in flight
     k_photon_schedule<float><<<4 * 148, 256, 0, st>>>(v);
   } else {
-    k_photon_scan<double><<<16 * 148, 256, 0, st>>>(v);
+    k_photon_scan<<<16 * 148, 256, 0, st>>>(v);
     k_photon_schedule<double><<<4 * 148, 256, 0, st>>>(v);
   }
 }
