@@ -92,6 +92,7 @@ struct GapDev {
   int32_t tile_begin, n_tiles, gap_index, pad;
   double dx, dt, cdx, jm, Hc, lambda_hat, rho_hat, rate_mult, b, eta_bg, w0, w_unit;
   float f_dt, f_cdx, f_Hc, f_lam, f_rho, f_rate;
+  float f_b, f_pad;  // (float)b: FP64 -> FP32 conversions run on the FP64 units
   uint64_t seed, inj_root;
   int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
   double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold
@@ -856,8 +857,8 @@ __device__ __forceinline__ float tbw_f(float chi) {
 __device__ __forceinline__ float bw_step_depth_f(const GapDev &g, float x, int32_t n0, int64_t m) {
   const float lmid = ((float)(m - (int64_t)n0) + 0.5f) * g.f_dt;
   const float sp = fabsf(sinf(lmid / g.f_rho));
-  const float chi = x * (float)g.b * sp;
-  return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * (float)g.b * sp * tbw_f(chi);
+  const float chi = x * g.f_b * sp;
+  return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * g.f_b * sp * tbw_f(chi);
 }
 
 // Tally one e+- absorbed at h < 0 (the return flux of Sect. 6.5) with weight

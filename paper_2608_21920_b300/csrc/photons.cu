@@ -78,7 +78,7 @@ struct BwDepth<float> {
     return bw_step_depth_f(g, (float)x, n0, m);
   }
   static __device__ float bound(const GapDev &g, double x) {
-    return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * (float)g.b * tbw_f((float)(x * g.b));
+    return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * g.f_b * tbw_f((float)(x * g.b));
   }
   static __device__ float add(float a, float b) { return __fadd_rn(a, b); }
   static constexpr float margin = 2e-2f;  // covers FP32 rounding of sums of up to ~1e5 terms
