@@ -455,6 +455,11 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.has_w = (qed_any || merge_any) ? 1 : 0;  // merging makes weights unequal
   v.merge_any = merge_any ? 1 : 0;
   v.filter_any = filter_any ? 1 : 0;
+  {
+    bool da = false;
+    for (const auto &g : gaps) da |= g.defer != 0;
+    v.defer_any = da ? 1 : 0;
+  }
   v.pr_any = pr_any ? 1 : 0;
   v.em_any = em_any ? 1 : 0;
   v.jperp_any = jperp_any ? 1 : 0;

@@ -143,7 +143,8 @@ struct View {
   int32_t n_gaps, n_tiles, tile, precision;
   int32_t qed_any, surface_any, has_w, rebin_every;
   int32_t variant, merge_any;
-  int32_t filter_any, pr_any;  // some gap defers Ampere (current filter or protons); some has protons
+  int32_t filter_any, pr_any;  // some gap's Ampere runs in k_filter_apply; some gap has protons
+  int32_t defer_any, defer_pad;  // some gap defers Ampere for a filter, protons or transverse fields
   int64_t pr_cap;             // proton store (unsorted, FP64): position, momentum per m_ion c, weight
   double *pr_X, *pr_u, *pr_w;
   uint64_t *pr_id;

@@ -497,7 +497,7 @@ void launch_merge(const View &v, cudaStream_t st) {
     k_phm_clear<<<2 * 148, 256, 0, st>>>(v);
   }
   k_merge_done<<<1, 1, 0, st>>>(v);
-  launch_filter(v, 1, st);  // smoothed re-centring correction of filter gaps
+  if (v.defer_any) launch_filter(v, 1, st);  // smoothed re-centring correction of filter gaps
 }
 
 }  // namespace gapk
