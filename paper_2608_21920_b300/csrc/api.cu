@@ -353,6 +353,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
     g.f_rho = (float)g.rho_hat;
     g.f_rate = (float)g.rate_mult;
     g.f_b = (float)q.b;
+    g.inv_cdx = 1.0 / g.cdx;
     g.seed = q.seed;
     g.cap = q.cap > 0 ? q.cap : 0;
     g.inject_theta = q.inject_theta;

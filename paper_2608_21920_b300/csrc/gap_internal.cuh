@@ -93,6 +93,7 @@ struct GapDev {
   double dx, dt, cdx, jm, Hc, lambda_hat, rho_hat, rate_mult, b, eta_bg, w0, w_unit;
   float f_dt, f_cdx, f_Hc, f_lam, f_rho, f_rate;
   float f_b, f_pad;  // (float)b: FP64 -> FP32 conversions run on the FP64 units
+  double inv_cdx;     // 1 / cdx
   uint64_t seed, inj_root;
   int64_t cap;  // macro-particle cap (leptons + photons); 0 = none
   double inject_theta;  // temperature of the injected atmosphere (m_e c^2); 0 = cold

@@ -30,7 +30,9 @@ __device__ int64_t first_step(const GapDev &g, double Xr, int32_t nr, int32_t di
     return dir > 0 ? X >= T : X < T;
   };
   if (hit(j0)) return j0;
-  const double d = dir > 0 ? (T - Xr) / g.cdx : (Xr - T) / g.cdx;
+  // an estimate (the walk below finds the exact step): a product, not a
+  // division, which is long on the FP64 units
+  const double d = (dir > 0 ? T - Xr : Xr - T) * g.inv_cdx;
   // the exact motion puts the answer within rounding of the estimate: walk
   // the last steps; a long walk falls back to bisection
   {
@@ -74,8 +76,8 @@ struct BwDepth<double> {
 };
 template <>
 struct BwDepth<float> {
-  static __device__ float step(const GapDev &g, double x, int32_t n0, int64_t m) {
-    return bw_step_depth_f(g, (float)x, n0, m);
+  static __device__ float step(const GapDev &g, float x, int32_t n0, int64_t m) {
+    return bw_step_depth_f(g, x, n0, m);
   }
   static __device__ float bound(const GapDev &g, double x) {
     return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * g.f_b * tbw_f((float)(x * g.b));
@@ -90,7 +92,7 @@ template <class R>
 __device__ R photon_depth_at(const GapDev &g, double Xr, int32_t nr, int32_t dir, double x, int32_t n0,
                              int32_t m, R tau, int64_t n) {
   for (int64_t j = m; j < n; ++j)
-    if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
+    if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, (R)x, n0, j));
   return tau;
 }
 
@@ -100,6 +102,7 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
   const int gap = v.pgap[b][i];
   const GapDev &g = v.gaps[gap];
   const double Xr = v.pXr[b][i], x = v.px[b][i];
+  const R xs = (R)x;  // the energy in the state's precision, converted once
   const int32_t nr = v.pnr[b][i], dir = v.pdir[b][i], n0 = v.pn0[b][i];
   if (v.pkind[b][i] == PH_RESCHEDULE) {  // the walk so far becomes the checkpoint
     v.pm[b][i] = v.pmn[b][i];
@@ -120,7 +123,7 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
       int64_t j = m;
       kind = 0;
       for (int it = 0; it < kSchedIters; ++it, ++j) {
-        if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, x, n0, j));
+        if (photon_pos(g, Xr, nr, dir, j) < g.Hc) tau = BwDepth<R>::add(tau, BwDepth<R>::step(g, xs, n0, j));
         if (tau >= ts) {
           kind = PH_CONVERT;
           break;
@@ -169,7 +172,7 @@ __device__ void schedule_photon(const View &v, int b, int64_t i) {
         const int nb = hi - j < 4 ? (int)(hi - j) : 4;
         R r[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r[q] = q < nb ? BwDepth<R>::step(g, x, n0, j + q) : (R)0;
+        for (int q = 0; q < 4; ++q) r[q] = q < nb ? BwDepth<R>::step(g, xs, n0, j + q) : (R)0;
         bool conv = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
