@@ -243,8 +243,9 @@ def test_empty_gap_and_graph_replay():
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("threads", [256, 128])
 def test_fp32_qed_push_variants_are_bit_identical(variant, threads):
-    """The FP32 QED push with its emitters deferred to converged warp passes
-    (variants 0 and 1) and pushed in place (variant 2) performs the same
+    """The FP32 QED push in two passes (variants 0 and 1: the quiet leptons
+    streamed, the emitters and tile movers pushed by a second kernel from a
+    list, Ampere after both) and in place (variant 2) performs the same
     arithmetic: over a discharge with emissions, photons, pairs and a cap
     that merges, leptons, photons, E and every counter agree bit for bit."""
     from paper_2608_21920_b300 import Gap
