@@ -493,13 +493,14 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   // store's capacity
   const int64_t item_cap = 2 * (lep_cap / kPushChunkMin) + 2 * (int64_t)NT + 2;
   v.item_tile = C.take<int32_t>((size_t)item_cap);
-  {  // the two-pass FP32 QED push (variants 0 and 1): its deferred list,
-     // one entry for every lepton the two stores can hold (a lepton is
-     // deferred at most once a step)
-    const int64_t dcap = two_pass ? 2 * lep_cap : 0;
+  {  // the two-pass FP32 QED push (variants 0 and 1): its deferred list, an
+     // eighth of the lepton slots (the emitters and tile movers of a step are
+     // a few per cent; the rest, if ever, are found in the store)
+    const int64_t dcap = two_pass ? std::max<int64_t>(1 << 20, lep_cap / 8) : 0;
     v.defer_slot = C.take<int64_t>((size_t)dcap);
     v.defer_ts = C.take<uint32_t>((size_t)dcap);
     v.defer_cap = dcap;
+    v.defer_use = dcap;
   }
   v.item_cap = (int32_t)std::min<int64_t>(item_cap, INT32_MAX);
   v.tile_done = C.take<int32_t>(NT);
@@ -722,7 +723,6 @@ static int read_ctl(gap_handle *h, Ctl *c, cudaStream_t st) {
   if (c->error & 64) return fail(h, GAP_ECHECK, "a photon event was not taken at its step");
   if (c->error & 128) return fail(h, GAP_ECAP, "proton storage exhausted");
   if (c->error & 256) return fail(h, GAP_ECHECK, "more push work items than the item table holds");
-  if (c->error & 512) return fail(h, GAP_ECHECK, "more deferred leptons than the deferred list holds");
   if (c->error & 7)
     return fail(h, GAP_ECAP, c->error & 1 ? "lepton spill list exhausted"
                              : (c->error & 2 ? "photon storage exhausted" : "lepton storage exhausted"));
@@ -1255,6 +1255,12 @@ int gap_profile(gap_handle *h, int32_t on, double *push_ms_total, int64_t *push_
   if (push_ms_total) *push_ms_total = tot;
   if (push_launches) *push_launches = n;
   h->profiling = on != 0;
+  return GAP_OK;
+}
+
+int gap_defer_limit(gap_handle *h, int64_t n) {
+  if (!h || n < 0) return GAP_EINVAL;
+  h->v.defer_use = std::min<int64_t>(n, h->v.defer_cap);
   return GAP_OK;
 }
 

@@ -131,6 +131,7 @@ struct Ctl {
   int32_t push_items, push_next;  // the push work list of this step and its counter
   int32_t push_chunk, push_pad;   // leptons per item this step (kPushChunkMin .. kPushChunk)
   unsigned long long defer_n;     // entries of the deferred list this step (may exceed its capacity)
+  int32_t defer_over, defer_pad;  // some deferred lepton did not fit on the list this step
   int64_t spill_n[2];
   int64_t new_total[2];
   int64_t ph_nb_start;  // photon store fill before this step's push (0 after a photon compaction)
@@ -192,6 +193,7 @@ struct View {
   int64_t *defer_slot;
   uint32_t *defer_ts;
   int64_t defer_cap;
+  int64_t defer_use;     // its usable length: defer_cap (smaller in a test of the overflow)
   int32_t item_cap;      // bound on the push items of a step
   int32_t *tile_done;    // [n_tiles] items of the tile finished this step
   // lepton stores [buffer][species]

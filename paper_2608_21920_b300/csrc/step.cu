@@ -538,13 +538,14 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           for (unsigned b = later; b; b &= b - 1u) {
             const int jb = __ffs(b) - 1;
             const bool mover = (moved >> jb) & 1u;
-            if (pos < (unsigned long long)v.defer_cap) {
+            if (pos < (unsigned long long)v.defer_use) {
               v.defer_slot[pos] = slot0 + jb;
               v.defer_ts[pos] = (uint32_t)t | ((uint32_t)s << 30) | (mover ? 0x80000000u : 0u);
-            } else {  // never: the list holds every lepton of the store
-              atomicOr(&v.ctl->error, 512);
-              Kp[slot0 + jb] = -1;
-              if (!mover) ++dead;
+            } else {  // the list is full: k_push_overflow finds the lepton in the store
+              // (a mover by its node outside the tile, an emitter by its
+              // optical depth stored as -1 - tau)
+              if (!mover) Tp[slot0 + jb] = (R)-1 - Tp[slot0 + jb];
+              v.ctl->defer_over = 1;
             }
             ++pos;
           }
@@ -884,11 +885,42 @@ __device__ __noinline__ int push_deferred(const View &v, const int t, const int 
 // The second pass over the step's deferred list.
 __global__ void __launch_bounds__(256) k_push_deferred(View v) {
   const unsigned long long n0 = v.ctl->defer_n;
-  const int64_t n = n0 < (unsigned long long)v.defer_cap ? (int64_t)n0 : v.defer_cap;
+  const int64_t n = n0 < (unsigned long long)v.defer_use ? (int64_t)n0 : v.defer_use;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t ts = v.defer_ts[i];
     const int t = (int)(ts & 0x3FFFFFFFu), s = (int)((ts >> 30) & 1u);
     const int dead = push_deferred<float>(v, t, s, v.defer_slot[i], (ts >> 31) != 0);
+    if (dead) atomicAdd(&v.seg_alive[s][t], -dead);
+  }
+}
+
+// The leptons the first pass could not put on a full deferred list, found in
+// the store: nothing to do unless the list overflowed this step; then the
+// blocks take the (species, tile) segments in turn.  A lepton whose node lies
+// outside its tile moved on; one with a negative optical depth emits (its
+// depth is restored first).
+__global__ void __launch_bounds__(256) k_push_overflow(View v) {
+  if (!v.ctl->defer_over) return;
+  const int cur = v.ctl->lep_cur;
+  for (int st = blockIdx.x; st < 2 * v.n_tiles; st += gridDim.x) {
+    const int s = st / v.n_tiles, t = st % v.n_tiles;
+    const TileDev ti = v.tiles[t];
+    const int64_t start = v.seg_start[s][t];
+    const int used = v.seg_used[s][t];
+    int32_t *Kp = v.lk[cur][s];
+    float *Tp = as<float>(v.ltau[cur][s]);
+    int dead = 0;
+    for (int i = threadIdx.x; i < used; i += blockDim.x) {
+      const int64_t slot = start + i;
+      const int32_t k = Kp[slot];
+      if (k < 0) continue;
+      if (k < ti.k0 || k >= ti.k0 + ti.nk) {
+        dead += push_deferred<float>(v, t, s, slot, true);
+      } else if (Tp[slot] < 0.0f) {
+        Tp[slot] = -1.0f - Tp[slot];
+        dead += push_deferred<float>(v, t, s, slot, false);
+      }
+    }
     if (dead) atomicAdd(&v.seg_alive[s][t], -dead);
   }
 }
@@ -2100,6 +2132,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
   }
   if (threadIdx.x == 0) {
     v.ctl->defer_n = 0ull;
+    v.ctl->defer_over = 0;
     v.item_start[n] = carry;
     if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
     v.ctl->push_items = carry < v.item_cap ? carry : v.item_cap;
@@ -2197,7 +2230,10 @@ void launch_push(const View &v, int threads, cudaStream_t st) {
 // protons, the transverse fields (before E_h moves on) and Ampere of the
 // gaps that leave it to k_filter_apply.
 void launch_push_tail(const View &v, cudaStream_t st) {
-  if (two_pass_push(v)) k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
+  if (two_pass_push(v)) {
+    k_push_deferred<<<kPushGrid, 256, 0, st>>>(v);
+    k_push_overflow<<<kPushGrid, 256, 0, st>>>(v);  // returns at once unless the list overflowed
+  }
   if (v.pr_any) k_push_heavy<<<148 * 4, 256, 0, st>>>(v);  // protons
   launch_em(v, st);
   launch_filter(v, 0, st);
@@ -2216,7 +2252,7 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
 
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
-  return (lean ? 1 : 2) + (two_pass_push(v) ? 1 : 0) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
+  return (lean ? 1 : 2) + (two_pass_push(v) ? 2 : 0) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
          (v.qed_any ? 2 : 0) + (v.filter_any ? 2 : 0) + (v.defer_any && v.merge_any ? 2 : 0) + (v.pr_any ? 1 : 0) + (v.em_any ? 2 : 0);
 }
 
