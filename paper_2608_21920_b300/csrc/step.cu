@@ -4,6 +4,10 @@
 //   k_push_lean Ampere update of E fused per tile (gaps with a current filter
 //   k_push_tma  leave it to filter.cu); k_push takes work items from a
 //               persistent grid, the lean and bulk-copy pushes one tile per block
+//   k_push_items  the work items of k_push
+//   k_push_deferred, k_push_overflow  the second pass of the two-pass FP32
+//               QED push (emitters and leptons that moved into another tile)
+//   k_push_heavy  protons
 //   (photon propagation and pair creation: photons.cu)
 //   k_inject    surface injection of electrons, cold or at the atmosphere's
 //               temperature (Sect. 2.3 / 6.1)
