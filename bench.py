@@ -267,7 +267,7 @@ def run_ours(args):
             del g
             torch.cuda.empty_cache()
             Ehost = torch.empty(NX, dtype=torch.float64, pin_memory=True)
-            Ke = args.e2e_steps
+            Ke = args.e2e_steps or args.steps  # the timed steps of the headline, end to end
             barrier()
             t0 = time.perf_counter()
             g = Gap(cfg, precision=precision, tile=args.tile, threads=args.threads, variant=args.variant,
@@ -633,7 +633,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--steady-steps", type=int, default=192,
                     help="steps timed after the headline window, compactions included (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end run (0: --steps)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
