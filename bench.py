@@ -262,11 +262,12 @@ def run_ours(args):
         results[precision] = r
         if precision == "fp32" and not args.no_e2e:
             # end to end through the public API: init from host parameters,
-            # then every step the result (E and counters) read back to pinned
-            # host memory
+            # then every step the result (E) read back to pinned host memory,
+            # the transfer on a second stream overlapping the next step
             del g
             torch.cuda.empty_cache()
             Ehost = torch.empty(NX, dtype=torch.float64, pin_memory=True)
+            copy = torch.cuda.Stream()
             Ke = args.e2e_steps or args.steps  # the timed steps of the headline, end to end
             barrier()
             t0 = time.perf_counter()
@@ -274,11 +275,11 @@ def run_ours(args):
                     rebin_every=args.rebin_every)
             torch.cuda.synchronize()
             t_init = time.perf_counter() - t0
-            import ctypes as C
             for _ in range(Ke):
                 g.step(1)
-                A.check(A.lib().gap_get_field(g.handle, 0, C.c_void_p(Ehost.data_ptr()), NX, g.stream()),
-                        g.handle, "get_field")
+                g.field_async(Ehost, copy)
+            copy.synchronize()
+            torch.cuda.synchronize()
             barrier()
             t_e2e = rank_max(time.perf_counter() - t0)
             # host->device bytes of gap_init: gap and tile tables, tile-edge
@@ -290,7 +291,7 @@ def run_ours(args):
             h2d_init = 256 + 16 * nt + NX + 2 * 12 * nt + 1024 * 8 + 2 * 577 * 8
             r["e2e"] = dict(value=world * N_PARTICLES * Ke / t_e2e, steps=Ke, init_s=rank_max(t_init),
                             h2d_bytes_per_step=int(math.ceil(h2d_init / Ke)),
-                            d2h_bytes_per_step=int(NX * 8 + 64))
+                            d2h_bytes_per_step=int(NX * 8))
         del g
         torch.cuda.empty_cache()
     qr = None
@@ -346,7 +347,8 @@ def run_ours(args):
         e = r32["e2e"]
         line["e2e"] = {"value": e["value"], "unit": UNIT, "h2d_bytes_per_step": e["h2d_bytes_per_step"],
                        "d2h_bytes_per_step": e["d2h_bytes_per_step"], "steps": e["steps"], "init_s": e["init_s"],
-                       "includes": "gap_init from host parameters + per-step E readback to pinned host"}
+                       "includes": "gap_init from host parameters + per-step E readback to pinned host "
+                                   "(gap_get_field_async: the transfer overlaps the next step)"}
     if "fp64" in results:
         r64 = results["fp64"]
         v64 = job_throughput(N_PARTICLES, r64["K"], r64["ms"], world)

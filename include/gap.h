@@ -278,6 +278,19 @@ int gap_diag(gap_handle *h, int32_t gap, gap_diag_out *out, double *host_spectru
 int gap_get_field(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream);
 int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, void *stream);
 
+/* E of gap `gap` after the steps enqueued on `stream`, copied to host_E
+ * (pinned host memory, n >= the gap's node count) on `copy_stream` without a
+ * host synchronisation, so that the transfer overlaps the later steps: a
+ * kernel on copy_stream, after the work enqueued on `stream`, copies E to a
+ * staging buffer of the workspace; `stream` waits for that copy only, not
+ * for the transfer; the transfer to host_E then runs on copy_stream.  host_E
+ * is complete when copy_stream has passed the call (synchronise it, or an
+ * event recorded on it).  A later call reuses the staging buffer after the
+ * earlier transfer (both on copy_stream).  The two streams must differ.
+ * GAP_EINVAL for a bad gap, buffer or n; device errors surface at the next
+ * call that reads the control block (gap_diag, gap_get_field). */
+int gap_get_field_async(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream, void *copy_stream);
+
 /* Transverse fields of a gap with em = 1 (App. A): component GAP_EM_EY or
    GAP_EM_EZ (nx cell values, at step - 1/2 after `step` steps), GAP_EM_BY or
    GAP_EM_BZ (nnode node values, at the step).  `n` must be at least the

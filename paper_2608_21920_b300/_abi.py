@@ -102,6 +102,7 @@ def lib():
     L.gap_profile_phases.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
     L.gap_hold_copies.argtypes = [vp, i32]
     L.gap_defer_limit.argtypes = [vp, i64]
+    L.gap_get_field_async.argtypes = [vp, i32, vp, i64, vp, vp]
     L.gap_state_bytes.argtypes = [vp]
     L.gap_state_bytes.restype = sz
     L.gap_save.argtypes = [vp, vp, sz, vp]
@@ -122,7 +123,7 @@ def lib():
 
 EXPORTED = ["gap_workspace_bytes", "gap_init", "gap_step", "gap_step_graph", "gap_diag",
             "gap_get_field", "gap_set_field", "gap_get_em", "gap_set_em", "gap_get_particles", "gap_sample_particles", "gap_tile_particles", "gap_spectra", "gap_return_spectrum", "gap_add_particles",
-            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_defer_limit", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
+            "gap_solve_gauss", "gap_set_background", "gap_steps_done", "gap_profile", "gap_profile_phases", "gap_hold_copies", "gap_defer_limit", "gap_get_field_async", "gap_state_bytes", "gap_save", "gap_load", "gap_spectrum_inverse", "gap_qspectrum_inverse", "gap_pair_split", "gap_power_spectrum_noalloc", "gap_free",
             "gap_last_error", "gap_status_string", "ode_forward", "ode_adjoint", "ode_ext_forward", "ode_ext_adjoint"]
 
 

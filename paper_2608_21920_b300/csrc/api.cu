@@ -38,6 +38,8 @@ struct gap_handle {
   size_t ev_used = 0;
   double phase_ms[GAP_NPHASES] = {0, 0, 0, 0, 0};
   int64_t phase_steps = 0;
+  // gap_get_field_async: after the enqueued steps; after the staging copy
+  cudaEvent_t fa_after_steps = nullptr, fa_after_stage = nullptr;
 };
 
 static constexpr size_t kProfEvents = 6;
@@ -540,6 +542,7 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.max_nx = max_nx;
   v.max_P = max_P;
   v.dmom = C.take<double>(8 * (size_t)max_nx);
+  v.fstage = C.take<double>((size_t)max_nx);
   v.dcharge = C.take<unsigned long long>(dchg);
   v.dcharge_len = dchg;
   v.Dflt = C.take<double>(filter_any ? 2 * (size_t)dchg : 0);
@@ -854,6 +857,28 @@ int gap_get_field(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *s
                                   cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_check(h, e, "get field");
+}
+
+int gap_get_field_async(gap_handle *h, int32_t gap, double *host_E, int64_t n, void *stream, void *copy_stream) {
+  if (!h || gap < 0 || gap >= h->n_gaps || !host_E) return GAP_EINVAL;
+  if (h->status) return h->status;
+  const GapDev &g = h->gaps_h[gap];
+  if (n < g.nnode) return GAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+  cudaError_t e = cudaSuccess;
+  if (!h->fa_after_steps) e = cudaEventCreateWithFlags(&h->fa_after_steps, cudaEventDisableTiming);
+  if (e == cudaSuccess && !h->fa_after_stage) e = cudaEventCreateWithFlags(&h->fa_after_stage, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(h->fa_after_steps, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->fa_after_steps, 0);
+  if (e == cudaSuccess) {
+    launch_copy_field(h->v, gap, cs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->fa_after_stage, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->fa_after_stage, 0);  // later steps wait for the staging only
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host_E, h->v.fstage, sizeof(double) * g.nnode, cudaMemcpyDeviceToHost, cs);
+  return cuda_check(h, e, "get field async");
 }
 
 int gap_set_field(gap_handle *h, int32_t gap, const double *host_E, int64_t n, void *stream) {
@@ -1284,6 +1309,8 @@ void gap_free(gap_handle *h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->fa_after_steps) cudaEventDestroy(h->fa_after_steps);
+  if (h->fa_after_stage) cudaEventDestroy(h->fa_after_stage);
   delete h;
 }
 

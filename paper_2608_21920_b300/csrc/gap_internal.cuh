@@ -230,6 +230,7 @@ struct View {
   int32_t quad_n;
   double quad_h;
   // diagnostics scratch
+  double *fstage;         // [max_nx] staging of gap_get_field_async
   double *dmom;                 // [8][max_nx]
   unsigned long long *dcharge;  // [max_nx] exact charge (int64 or double bits)
   double *fft[2];               // complex scratch [2][2*max_P]

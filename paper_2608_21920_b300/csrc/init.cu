@@ -769,4 +769,15 @@ void launch_spectra(const View &v, int gap, int n_tiles_gap, int nbins, double l
   if (v.qed_any) k_spectra_photons<<<148, 256, 0, st>>>(v, gap, nbins, lo, hi);
 }
 
+// E of one gap (the buffer of the current step) into the staging buffer of
+// gap_get_field_async: the host does not read the control block to choose it.
+__global__ void k_copy_field(View v, int gap) {
+  const GapDev &g = v.gaps[gap];
+  const double *E = v.E[v.ctl->e_cur] + g.node_off;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nnode; i += (int64_t)gridDim.x * blockDim.x)
+    v.fstage[i] = E[i];
+}
+
+void launch_copy_field(const View &v, int gap, cudaStream_t st) { k_copy_field<<<2 * 148, 256, 0, st>>>(v, gap); }
+
 }  // namespace gapk

@@ -15,6 +15,7 @@ struct LoadSpec {  // initial load of one gap
 void launch_step(const View &v, int threads, cudaStream_t st);
 void launch_push(const View &v, int threads, cudaStream_t st);
 void launch_push_tail(const View &v, cudaStream_t st);
+void launch_copy_field(const View &v, int gap, cudaStream_t st);
 void launch_after_push(const View &v, cudaStream_t st);
 int launches_per_step(const View &v);
 void launch_rebin(const View &v, double slack, cudaStream_t st);

@@ -166,6 +166,16 @@ class Gap:
         A.check(A.lib().gap_get_field(self._h, gap, _ptr(out), out.size, self.stream()), self._h, "gap_get_field")
         return out
 
+    def field_async(self, out, copy_stream, gap: int = 0):
+        """E after the steps enqueued so far, copied into `out` (a pinned
+        host float64 tensor of at least nnode(gap) values) on `copy_stream`
+        (a torch.cuda.Stream other than the current one) without waiting:
+        later steps overlap the transfer; `out` is complete once copy_stream
+        has passed this call."""
+        assert out.dtype == torch.float64 and out.is_pinned() and out.numel() >= self.nnode(gap)
+        A.check(A.lib().gap_get_field_async(self._h, gap, C.c_void_p(out.data_ptr()), out.numel(), self.stream(),
+                                            C.c_void_p(copy_stream.cuda_stream)), self._h, "gap_get_field_async")
+
     def set_field(self, E, gap: int = 0):
         E = np.ascontiguousarray(E, dtype=np.float64)
         A.check(A.lib().gap_set_field(self._h, gap, _ptr(E), E.size, self.stream()), self._h, "gap_set_field")
