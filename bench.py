@@ -517,11 +517,16 @@ def _total_leptons(g):
     return n
 
 
-def batch_params(n_gaps):
+def batch_params(n_gaps, cap_per_cell=0):
     """The batch workload's gap parameters with the options of SETUP (the
-    absorbing layer only on surface gaps)."""
+    absorbing layer only on surface gaps); cap_per_cell > 0 sets each gap's
+    cap to that many macro-particles per initial one (16 in the workload), for
+    profiling the merge on a small slice."""
     from paper_2608_21920_b300 import workloads
     params = [dict(p, **SETUP) for p in workloads.batch(n_gaps)]
+    if cap_per_cell > 0:
+        for p in params:
+            p["cap"] = int(cap_per_cell * p["nx"] * p["ppc"])
     if SETUP["em"]:
         for p in params:
             if p.get("boundary", 0) == 0:  # surface gap
@@ -536,7 +541,7 @@ def batch_measure(args, world=1, local=0):
     import torch
     from paper_2608_21920_b300 import Gap, autotune
     rank = rank_info()[0]
-    params = batch_params(args.gaps)
+    params = batch_params(args.gaps, args.cap_per_cell)
     peaks, peak_kind = measured_peaks()
     tuned = None
     tile, threads, rebin = args.tile if args.tile != 256 else 128, args.threads, args.rebin_every or 64
@@ -589,7 +594,9 @@ def batch_measure(args, world=1, local=0):
     torch.cuda.empty_cache()
     res = {
         "value": world * nmean * K / (ms / 1e3), "steps": K, "warmup": args.warmup * chunk, "ms_per_step": ms / K,
-        "config": {"workload": BATCH_NAME.format(n=args.gaps, last=args.gaps - 1), "gaps": args.gaps,
+        "config": {"workload": BATCH_NAME.format(n=args.gaps, last=args.gaps - 1).replace(
+                       "cap 16x initial", f"cap {args.cap_per_cell:g}x initial" if args.cap_per_cell else "cap 16x initial"),
+                   "gaps": args.gaps,
                    "capacity_factor": args.capacity_factor or None, "graph_chunk": chunk, "tile": tile,
                    "threads": threads, "rebin_every": rebin, "advanced_before_timing": args.batch_advance,
                    "leptons_mean": nmean, "l2": "inputs larger than L2, no flush"},
@@ -647,6 +654,8 @@ def main():
                     help="roofline: the Nx=2^20 push+deposit microbenchmark (the headline); "
                          "batch: the 256-gap QED sweep")
     ap.add_argument("--gaps", type=int, default=256)
+    ap.add_argument("--cap-per-cell", type=float, default=0.0,
+                    help="batch: each gap's cap in macro-particles per initial one (0: the workload's 16)")
     ap.add_argument("--graph-chunk", type=int, default=50)
     ap.add_argument("--batch-advance", type=int, default=1500)
     ap.add_argument("--capacity-factor", type=float, default=0.0,
