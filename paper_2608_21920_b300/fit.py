@@ -17,7 +17,16 @@ Loss of a set (mean over the trace samples):
 The gate is the smoothed one (H_delta, delta = 1e-2) so that the loss is
 differentiable; the PIC itself is not differentiated.
 
+With model="ext" the fitted model is the extended one, G = m_pm <gamma^-3>
+a fifth state (ode.py): ln gamma_min (the pair-birth Lorentz factor, eq.
+gam_inj) and ln gamma_rad (the radiation-limited one, eq. gam_rad) replace
+ln g3, drawn over gamma_min in [1e2, 1e3] and gamma_rad in [1e6, 1e8], and the
+plasma present at the start carries gamma_min^-3 too: G(0) = m(0)
+gamma_min^-3.  The extended model is stiff near the Fig. 2 point (steps of a
+few 1e-6 t_esc), so `every` (ODE steps per trace sample) has to be large.
+
     python -m paper_2608_21920_b300.fit --traces batch.npz --starts 16 --iters 40
+    python -m paper_2608_21920_b300.fit --traces batch.npz --model ext --every 2000
 """
 from __future__ import annotations
 
@@ -33,6 +42,9 @@ from . import ode
 
 DELTA = 1e-2
 BOUNDS = ((1e-4, 1e-2), (1e-4, 1e-2), (1e-8, 1e-7), (1e-8, 1e-6))  # t_x, t_pm, t_acc, g3
+# t_x, t_pm, t_acc, gamma_min, gamma_rad
+BOUNDS_EXT = ((1e-4, 1e-2), (1e-4, 1e-2), (1e-8, 1e-7), (1e2, 1e3), (1e6, 1e8))
+NAMES = {"base": ("t_x", "t_pm", "t_acc", "g3"), "ext": ("t_x", "t_pm", "t_acc", "gamma_min", "gamma_rad")}
 
 
 def load_traces(path: str) -> dict:
@@ -48,10 +60,16 @@ def load_traces(path: str) -> dict:
 
 
 class Problem:
-    """The batched fit: B = gaps x starts parameter sets."""
+    """The batched fit: B = gaps x starts parameter sets; theta [B, K + 1]
+    holds the K log-parameters of the model (NAMES[model]) and ln E_s."""
 
     def __init__(self, tr: dict, starts: int = 16, every: int = 50, seed: int = 0,
-                 dtype=torch.float64, device="cuda"):
+                 dtype=torch.float64, device="cuda", model: str = "base", bounds=None):
+        if model not in NAMES:
+            raise ValueError(f"model {model!r}: 'base' or 'ext'")
+        bounds = bounds or (BOUNDS if model == "base" else BOUNDS_EXT)
+        assert len(bounds) == len(NAMES[model])
+        self.model, self.K = model, len(bounds)
         M = torch.as_tensor(tr["M"], dtype=dtype)
         E = torch.as_tensor(tr["E"], dtype=dtype)
         S1, G = M.shape
@@ -68,25 +86,29 @@ class Problem:
         self.dt = (torch.as_tensor(tr["sample_dt"], dtype=dtype)[gi] / t_esc / every).to(device)
         self.alpha = alpha.to(device)
         g = torch.Generator().manual_seed(seed)
-        lo = torch.tensor([math.log(b[0]) for b in BOUNDS], dtype=dtype)
-        hi = torch.tensor([math.log(b[1]) for b in BOUNDS], dtype=dtype)
-        th = lo + (hi - lo) * torch.rand(self.B, 4, generator=g, dtype=dtype)
+        lo = torch.tensor([math.log(b[0]) for b in bounds], dtype=dtype)
+        hi = torch.tensor([math.log(b[1]) for b in bounds], dtype=dtype)
+        th = lo + (hi - lo) * torch.rand(self.B, self.K, generator=g, dtype=dtype)
         Emax = self.E.max(dim=0).values.cpu().clamp_min(1e-12)
         lnEs = torch.log(Emax / 2.0) + 0.5 * torch.randn(self.B, generator=g, dtype=dtype)
         self.theta = torch.cat([th, lnEs[:, None]], dim=1).to(device).requires_grad_(True)
         self.dtype, self.device = dtype, device
 
     def params(self, theta):
-        p = torch.cat([self.alpha[:, None], torch.exp(theta[:, :4])], dim=1)
-        Es = torch.exp(theta[:, 4])
-        y0 = torch.stack([self.M[0].clamp_min(1e-6), torch.zeros_like(Es), self.E[0] / Es, torch.zeros_like(Es)], dim=1)
-        return p, y0, Es
+        K = self.K
+        p = torch.cat([self.alpha[:, None], torch.exp(theta[:, :K])], dim=1)
+        Es = torch.exp(theta[:, K])
+        m0 = self.M[0].clamp_min(1e-6)
+        y = [m0, torch.zeros_like(Es), self.E[0] / Es, torch.zeros_like(Es)]
+        if self.model == "ext":
+            y.append(m0 * torch.exp(-3.0 * theta[:, 3]))  # G(0) = m(0) gamma_min^-3
+        return p, torch.stack(y, dim=1), Es
 
     def loss_per_set(self, theta, out=None):
         p, y0, Es = self.params(theta)
         if out is None:
             out = ode.integrate(p.contiguous(), y0.contiguous(), self.dt, self.nsteps, self.every,
-                                ckpt_every=100, delta=DELTA)
+                                ckpt_every=100, delta=DELTA, model=self.model)
         m = out[:, :, 0].clamp_min(0.0)
         eps = out[:, :, 2]
         lm = (torch.log1p(m) - torch.log1p(self.M)) ** 2
@@ -99,7 +121,8 @@ class Problem:
     def finite(self, theta):
         with torch.no_grad():
             p, y0, Es = self.params(theta)
-            out, _ = ode.forward(p.contiguous(), y0.contiguous(), self.dt, self.nsteps, self.every, 0, DELTA)
+            out, _ = ode.forward(p.contiguous(), y0.contiguous(), self.dt, self.nsteps, self.every, 0, DELTA,
+                                 model=self.model)
             L = ((torch.log1p(out[:, :, 0].clamp_min(0.0)) - torch.log1p(self.M)) ** 2).mean(dim=0)
             # runaway sets (multiplicity far beyond any trace) count as overflowed
             return torch.isfinite(L) & (L < 1e4) & torch.isfinite(out).all(dim=2).all(dim=0)
@@ -111,12 +134,14 @@ class Problem:
             L = self.loss_per_set(self.theta)
             L = torch.where(ok, L, torch.full_like(L, float("inf"))).view(self.G, self.starts)
             best = L.argmin(dim=1)
-            th = self.theta.view(self.G, self.starts, 5)
-            src = th[torch.arange(self.G), best]                       # [G, 5]
+            th = self.theta.view(self.G, self.starts, self.K + 1)
+            src = th[torch.arange(self.G), best]                       # [G, K + 1]
             bad = (~ok).view(self.G, self.starts)
             noise = 0.3 * torch.randn_like(th)
             fresh = torch.isinf(L.min(dim=1).values)[:, None, None]
-            shift = torch.tensor([1.0, 1.0, 0.0, 0.0, 0.5], dtype=th.dtype, device=th.device)
+            # a gap with no finite start: slower pair production, smaller field scale
+            shift = torch.zeros(self.K + 1, dtype=th.dtype, device=th.device)
+            shift[0], shift[1], shift[self.K] = 1.0, 1.0, 0.5
             new = torch.where(fresh, th + shift, src[:, None, :] + noise)
             th.copy_(torch.where(bad[:, :, None], new, th))
             return int((~ok).sum())
@@ -127,8 +152,8 @@ class Problem:
 
 def fd_check(prob: Problem, ok, n: int = 8, h: float = 1e-6, seed: int = 1):
     """Largest and median relative difference between the adjoint gradient
-    and central differences (step h in the log-parameters) over the five
-    log-parameters of n finite sets."""
+    and central differences (step h in the log-parameters) over all the
+    log-parameters (the model's and ln E_s) of n finite sets."""
     g = torch.Generator().manual_seed(seed)
     cand = torch.nonzero(ok.cpu()).flatten()
     idx = cand[torch.randperm(cand.numel(), generator=g)[:n]].to(prob.device)
@@ -136,7 +161,7 @@ def fd_check(prob: Problem, ok, n: int = 8, h: float = 1e-6, seed: int = 1):
     L = prob.loss_per_set(th)
     (grad,) = torch.autograd.grad(L[idx].sum(), th)
     errs = []
-    for c in range(5):
+    for c in range(prob.K + 1):
         e = torch.zeros_like(th)
         e[:, c] = h
         with torch.no_grad():
@@ -150,8 +175,9 @@ def fd_check(prob: Problem, ok, n: int = 8, h: float = 1e-6, seed: int = 1):
     return float(errs.max()), float(errs.median())
 
 
-def run(tr: dict, starts=16, iters=40, lr=0.05, every=50, device="cuda", log=print) -> dict:
-    prob = Problem(tr, starts=starts, every=every, device=device)
+def run(tr: dict, starts=16, iters=40, lr=0.05, every=50, device="cuda", log=print, model="base",
+        bounds=None) -> dict:
+    prob = Problem(tr, starts=starts, every=every, device=device, model=model, bounds=bounds)
     opt = torch.optim.Adam([prob.theta], lr=lr)
     hist, times = [], []
     reseeded = 0
@@ -179,18 +205,18 @@ def run(tr: dict, starts=16, iters=40, lr=0.05, every=50, device="cuda", log=pri
         per_final = per[ok]
         per = torch.where(ok, per, torch.full_like(per, float("inf"))).view(prob.G, starts)
         best = per.argmin(dim=1)
-        th = prob.theta.view(prob.G, starts, 5)[torch.arange(prob.G), best]
+        th = prob.theta.view(prob.G, starts, prob.K + 1)[torch.arange(prob.G), best]
     fd, fd_med = fd_check(prob, ok)
     # FP32 forward at the fitted parameters against FP64
     p, y0, Es = prob.params(prob.theta.detach())
-    o64, _ = ode.forward(p, y0, prob.dt, prob.nsteps, every, 0, DELTA)
-    o32, _ = ode.forward(p.float(), y0.float(), prob.dt.float(), prob.nsteps, every, 0, DELTA)
+    o64, _ = ode.forward(p, y0, prob.dt, prob.nsteps, every, 0, DELTA, model=model)
+    o32, _ = ode.forward(p.float(), y0.float(), prob.dt.float(), prob.nsteps, every, 0, DELTA, model=model)
     m64, m32 = o64[:, ok, 0], o32[:, ok, 0].double()
     rel = ((m32 - m64).abs() / m64.abs().clamp_min(1.0)).max(dim=0).values
     fp32_err = float(rel.max())
     fp32_err_med = float(rel.median())
-    fitted = torch.exp(th[:, :4]).cpu().numpy()
-    return dict(gaps=prob.G, sets=prob.B, ode_steps=prob.nsteps, iters=iters, reseeded=reseeded,
+    fitted = torch.exp(th[:, :prob.K]).cpu().numpy()
+    return dict(model=model, gaps=prob.G, sets=prob.B, ode_steps=prob.nsteps, iters=iters, reseeded=reseeded,
                 finite_sets_final=int(ok.sum()),
                 loss_first=hist[0], loss_last=hist[-1], loss_median_first=med_first,
                 loss_median_last=float(per_final.median()),
@@ -198,8 +224,7 @@ def run(tr: dict, starts=16, iters=40, lr=0.05, every=50, device="cuda", log=pri
                 fd_rel_err_max=fd, fd_rel_err_median=fd_med, fp32_vs_fp64_m_rel_err_max=fp32_err,
                 fp32_vs_fp64_m_rel_err_median=fp32_err_med,
                 best_loss_median=float(per.min(dim=1).values[torch.isfinite(per.min(dim=1).values)].median()),
-                fitted_median=dict(t_x=float(np.median(fitted[:, 0])), t_pm=float(np.median(fitted[:, 1])),
-                                   t_acc=float(np.median(fitted[:, 2])), g3=float(np.median(fitted[:, 3]))))
+                fitted_median={k: float(np.median(fitted[:, i])) for i, k in enumerate(NAMES[model])})
 
 
 def main():
@@ -208,9 +233,11 @@ def main():
     ap.add_argument("--starts", type=int, default=16)
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--lr", type=float, default=0.05)
+    ap.add_argument("--every", type=int, default=50, help="ODE steps per trace sample")
+    ap.add_argument("--model", default="base", choices=sorted(NAMES))
     ap.add_argument("--out", default="")
     a = ap.parse_args()
-    res = run(load_traces(a.traces), starts=a.starts, iters=a.iters, lr=a.lr)
+    res = run(load_traces(a.traces), starts=a.starts, iters=a.iters, lr=a.lr, every=a.every, model=a.model)
     print(json.dumps(res), flush=True)
     if a.out:
         with open(a.out, "w") as f:

@@ -22,11 +22,12 @@ def fit(monkeypatch):
     from paper_2608_21920_b300 import fit as F
     from paper_2608_21920_b300 import ode as O
 
-    def forward(p, y0, dt, nsteps, every=1, ckpt_every=0, delta=0.0):
-        return oracle_ode.rk4(y0, p, dt[:, None], nsteps, delta=delta or None, record_every=every), None
+    def forward(p, y0, dt, nsteps, every=1, ckpt_every=0, delta=0.0, model="base"):
+        rk = oracle_ode.rk4 if model == "base" else oracle_ode.rk4_ext
+        return rk(y0, p, dt[:, None], nsteps, delta=delta or None, record_every=every), None
 
-    def integrate(p, y0, dt, nsteps, every=1, ckpt_every=None, delta=0.0):
-        return oracle_ode.rk4(y0, p, dt[:, None], nsteps, delta=delta or None, record_every=every)
+    def integrate(p, y0, dt, nsteps, every=1, ckpt_every=None, delta=0.0, model="base"):
+        return forward(p, y0, dt, nsteps, every, 0, delta, model)[0]
 
     monkeypatch.setattr(O, "forward", forward)
     monkeypatch.setattr(O, "integrate", integrate)
@@ -100,3 +101,77 @@ def test_load_traces_takes_t_esc_from_the_gap_length(tmp_path):
     tr = fit.load_traces(str(p))
     assert np.allclose(tr["t_esc"], [5.0, 16.0])
     assert np.allclose(tr["sample_dt"], 0.45)
+
+
+# ---------------------------------------------------------------- extended model
+# a point of the extended model whose stiffness a step of 1e-4 t_esc resolves
+TRUTH_EXT = dict(alpha=2.0, t_x=3e-2, t_pm=2e-2, t_acc=3e-3, gamma_min=4.0, gamma_rad=30.0)
+BOUNDS_EXT = ((1e-2, 1e-1), (1e-2, 1e-1), (1e-3, 1e-2), (2.0, 10.0), (10.0, 100.0))
+EVERY_EXT, S_EXT, SAMPLE_DT_EXT = 10, 81, 1e-3
+
+
+def _traces_ext(fit):
+    keys = ("alpha", "t_x", "t_pm", "t_acc", "gamma_min", "gamma_rad")
+    p = torch.tensor([[TRUTH_EXT[k] for k in keys], [3.0] + [TRUTH_EXT[k] for k in keys[1:]]], dtype=torch.float64)
+    m0 = 1.0
+    y0 = torch.tensor([[m0, 0.0, 1.2, 0.0, m0 * TRUTH_EXT["gamma_min"] ** -3]] * 2, dtype=torch.float64)
+    dt = torch.full((2, 1), SAMPLE_DT_EXT / EVERY_EXT, dtype=torch.float64)
+    out = oracle_ode.rk4_ext(y0, p, dt, (S_EXT - 1) * EVERY_EXT, delta=fit.DELTA, record_every=EVERY_EXT)
+    return dict(M=out[:, :, 0].numpy(), E=(out[:, :, 2].abs() * ES).numpy(), alpha=np.array([2.0, 3.0]),
+                t_esc=np.ones(2), sample_dt=np.full(2, SAMPLE_DT_EXT))
+
+
+def _truth_theta_ext(prob):
+    th = torch.tensor([math.log(TRUTH_EXT[k]) for k in ("t_x", "t_pm", "t_acc", "gamma_min", "gamma_rad")]
+                      + [math.log(ES)], dtype=torch.float64)
+    return th.repeat(prob.B, 1)
+
+
+def test_ext_problem_has_the_extended_parameters(fit):
+    prob = fit.Problem(_traces_ext(fit), starts=3, every=EVERY_EXT, device="cpu", model="ext", bounds=BOUNDS_EXT)
+    assert prob.theta.shape == (6, 6)
+    p, y0, Es = prob.params(_truth_theta_ext(prob))
+    assert p.shape == (6, 6) and y0.shape == (6, 5)
+    assert torch.allclose(p[0, 1:], torch.tensor([3e-2, 2e-2, 3e-3, 4.0, 30.0], dtype=torch.float64))
+    # the plasma present at the start carries gamma_min^-3
+    assert torch.allclose(y0[:, 4], y0[:, 0] / 64.0)
+    assert torch.allclose(Es, torch.full((6,), ES, dtype=torch.float64))
+    # draws inside the given bounds
+    lo = torch.tensor([math.log(b[0]) for b in BOUNDS_EXT], dtype=torch.float64)
+    hi = torch.tensor([math.log(b[1]) for b in BOUNDS_EXT], dtype=torch.float64)
+    th = prob.theta.detach()[:, :5]
+    assert bool(((th >= lo) & (th <= hi)).all())
+    with pytest.raises(ValueError):
+        fit.Problem(_traces_ext(fit), starts=1, every=EVERY_EXT, device="cpu", model="other")
+
+
+def test_ext_loss_vanishes_at_the_generating_parameters(fit):
+    tr = _traces_ext(fit)
+    assert tr["M"][-1].min() > 10 * tr["M"][0].max()  # the traces contain a discharge
+    prob = fit.Problem(tr, starts=3, every=EVERY_EXT, device="cpu", model="ext", bounds=BOUNDS_EXT)
+    assert prob.loss_per_set(_truth_theta_ext(prob)).max() < 1e-20
+    # the base model fitted to the same traces cannot reproduce them exactly
+    base = fit.Problem(tr, starts=3, every=EVERY_EXT, device="cpu")
+    th = torch.tensor([math.log(v) for v in (3e-2, 2e-2, 3e-3, 4.0 ** -3, ES)], dtype=torch.float64).repeat(6, 1)
+    assert base.loss_per_set(th).min() > 1e-8
+
+
+def test_ext_gradient_matches_central_differences(fit):
+    prob = fit.Problem(_traces_ext(fit), starts=2, every=EVERY_EXT, device="cpu", model="ext", bounds=BOUNDS_EXT)
+    with torch.no_grad():
+        prob.theta.copy_(_truth_theta_ext(prob) + 0.05 * torch.randn(prob.B, 6, dtype=torch.float64,
+                                                                       generator=torch.Generator().manual_seed(4)))
+    ok = prob.finite(prob.theta)
+    assert bool(ok.all())
+    mx, med = fit.fd_check(prob, ok, n=2, h=1e-6)
+    assert med < 1e-5 and mx < 1e-3
+
+
+def test_ext_reseed_keeps_the_width(fit):
+    prob = fit.Problem(_traces_ext(fit), starts=3, every=EVERY_EXT, device="cpu", model="ext", bounds=BOUNDS_EXT)
+    before = prob.theta.detach().clone()
+    ok = torch.tensor([True, True, False, True, True, True])
+    assert prob.reseed(ok) == 1
+    after = prob.theta.detach()
+    assert after.shape == before.shape
+    assert torch.equal(after[ok], before[ok]) and not torch.equal(after[2], before[2])
