@@ -569,7 +569,10 @@ def batch_measure(args, world=1, local=0):
     torch.cuda.synchronize()
     with torch.cuda.stream(s):
         e0.record(s)
+        # NVTX ranges mark the timed steps and the eager ones below for launch lists
+        torch.cuda.nvtx.range_push("batch_timed")
         g.step(K, graph_chunk=chunk)
+        torch.cuda.nvtx.range_pop()
         e1.record(s)
     e1.synchronize()
     import torch.distributed as dist
@@ -579,7 +582,9 @@ def batch_measure(args, world=1, local=0):
     # the push kernel alone, eagerly launched between CUDA events
     g.profile(True)
     Kp = 20
+    torch.cuda.nvtx.range_push("batch_eager")  # launch lists: ncu --nvtx --nvtx-include batch_eager/
     g.step(Kp)
+    torch.cuda.nvtx.range_pop()
     phases, nph = g.profile_phases()
     push_ms, push_n, lps = g.profile(False)
     n2 = _total_leptons(g)

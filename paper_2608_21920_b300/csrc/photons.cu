@@ -454,6 +454,7 @@ __global__ void k_photon_moments(View v, int gap) {
   const int64_t step = v.ctl->step;
   const GapDev &g = v.gaps[gap];
   double en = 0.0;
+  unsigned long long cnt = 0;  // summed per warp: one global atomic per warp, not per photon
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (v.pgap[b][i] != gap || v.pev[b][i] == kPhDead) continue;
@@ -463,14 +464,20 @@ __global__ void k_photon_moments(View v, int gap) {
     if (c >= g.nx) c = g.nx - 1;
     atomicAdd(&v.dmom[7 * g.nx + c], v.pw[b][i] / g.dx);
     en += v.pw[b][i] * v.px[b][i];
-    atomicAdd(reinterpret_cast<unsigned long long *>(&v.dred[20]), 1ull);
+    ++cnt;
   }
-  for (int o = 16; o > 0; o >>= 1) en += __shfl_down_sync(0xffffffffu, en, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&v.dred[17], en);
+  for (int o = 16; o > 0; o >>= 1) {
+    en += __shfl_down_sync(0xffffffffu, en, o);
+    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(&v.dred[17], en);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&v.dred[20]), cnt);
+  }
 }
 
 void launch_photon_moments(const View &v, int gap, cudaStream_t st) {
-  k_photon_moments<<<148, 256, 0, st>>>(v, gap);
+  k_photon_moments<<<4 * 148, 256, 0, st>>>(v, gap);
 }
 
 }  // namespace gapk
