@@ -860,7 +860,9 @@ __device__ __forceinline__ float tbw_f(float chi) {
   return 0.23f * expf(-8.0f / (3.0f * chi)) * exp2f(-log2f(1.0f + 0.22f * chi) * (1.0f / 3.0f));
 }
 __device__ __forceinline__ float bw_step_depth_f(const GapDev &g, float x, int32_t n0, int64_t m) {
-  const float lmid = ((float)(m - (int64_t)n0) + 0.5f) * g.f_dt;
+  // the step count since birth fits 32 bits: converted from int32 (64-bit
+  // type conversions run at the low FP64 rate here)
+  const float lmid = ((float)(int32_t)(m - (int64_t)n0) + 0.5f) * g.f_dt;
   const float sp = fabsf(sinf(lmid / g.f_rho));
   const float chi = x * g.f_b * sp;
   return g.f_dt * g.f_rate * (float)kAlphaEm / g.f_lam * g.f_b * sp * tbw_f(chi);

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
   unsigned long long *minid = reinterpret_cast<unsigned long long *>(wb + 4 * kMergeKeys);
   A *sw = reinterpret_cast<A *>(wb + 12 * kMergeKeys);                                // sum w
   A *sphi = reinterpret_cast<A *>(wb + 20 * kMergeKeys);                              // sum w phi
-  double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then eta
+  double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then E = exp(eta)
   double *sm = reinterpret_cast<double *>(wb + 36 * kMergeKeys);                      // sum w (g-u), then D
   short *touched = reinterpret_cast<short *>(wb + 44 * kMergeKeys);                   // [kMergeKeys]
   int *hist = reinterpret_cast<int *>(msm + (size_t)kMergeWarps * kMergeWarpBytes);  // [nk + 1]
@@ -189,20 +189,19 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
   // rounding of t <= 256 and of 1/width adds ~2e-5.
   const float winv_f = (float)(1.0 / width);
   auto key_of = [&](int64_t src) -> int {
-    const double u = (double)as<R>(v.lu[nxt][s])[src];
-    const float uf = (float)u;
+    const R ur = as<R>(v.lu[nxt][s])[src];
+    const float uf = (float)ur;  // FP32 state: the stored value, no 64-bit type conversion (FP64 rate)
     const float tf = logf(sqrtf(1.0f + uf * uf)) * winv_f;
     const float bf = floorf(tf);
-    int64_t b;
+    int b;
     if (tf - bf > 1e-3f && bf + 1.0f - tf > 1e-3f && tf < (float)(kMergeBins - 1)) {
-      b = (int64_t)bf;
+      b = (int)bf;
     } else {
-      const double gm = sqrt(1.0 + u * u);
-      b = (int64_t)floor(log(gm) / width);
-      if (b < 0) b = 0;
-      if (b > kMergeBins - 1) b = kMergeBins - 1;
+      const double u = (double)ur;
+      const double t = floor(log(sqrt(1.0 + u * u)) / width);
+      b = t < 0.0 ? 0 : (t > (double)(kMergeBins - 1) ? kMergeBins - 1 : (int)t);
     }
-    return (u >= 0.0 ? 1 : 0) * kMergeBins + (int)b;
+    return (ur >= (R)0 ? 1 : 0) * kMergeBins + b;
   };
   // a group merges when it has three or more members; in the FP32 state
   // its children carry 32-bit weights, so a group whose summed weight would
@@ -249,23 +248,33 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     }
     __syncwarp();
     const int nt = ntouched[wid];
-    // centre rapidity eta into sp[]; sm[] then accumulates
-    // D = sum w 2 sinh^2((asinh u - eta)/2), so that M = W + D and
-    // M^2 - W^2 = D (2W + D) carry no cancellation for nearly cold groups
+    // E = exp(eta) = sqrt(S+/S-), the centre's rapidity factor, into sp[];
+    // sm[] then accumulates D = sum w 2 sinh^2((asinh u - eta)/2), so that
+    // M = W + D and M^2 - W^2 = D (2W + D) carry no cancellation for nearly
+    // cold groups
     for (int j = lane; j < nt; j += 32) {
       const int key = touched[j];
       if (!merges(key)) continue;
-      sp[key] = 0.5 * log(sp[key] / sm[key]);
+      sp[key] = sqrt(sp[key] / sm[key]);
       sm[key] = 0.0;
     }
     __syncwarp();
+    // With e = exp(asinh u) = gamma + u and x = e/E = exp(asinh u - eta),
+    // 2 sinh^2((asinh u - eta)/2) = (x + 1/x - 2)/2 = (e - E)^2/(2 e E):
+    // for u >= 0, e = gamma + |u|; for u < 0, e = 1/(gamma + |u|) and the
+    // term is (1 - E (gamma + |u|))^2/(2 E (gamma + |u|)).  The difference
+    // carries the rounding of e and E alone (a few 1e-16 relative), as
+    // asinh u - eta does, with a square root and a division in place of the
+    // FP64 asinh and sinh (FP64 runs at a small fraction of the FP32 rate).
     for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
       if (!merges(key)) continue;
       const double u = (double)as<R>(v.lu[nxt][s])[src];
-      const double h = sinh(0.5 * (asinh(u) - sp[key]));
-      atomicAdd(&sm[key], weight_of(src) * 2.0 * h * h);
+      const double E = sp[key];
+      const double big = sqrt(1.0 + u * u) + fabs(u);
+      const double d = u >= 0.0 ? big - E : fma(-E, big, 1.0);
+      atomicAdd(&sm[key], weight_of(src) * (d * d) / (2.0 * E * big));
     }
     __syncwarp();
     // leptons of groups that do not merge are copied through
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       }
       const double wad = sizeof(R) == 4 ? (double)wa * g.w_unit : (double)wa;
       const double wbd = sizeof(R) == 4 ? (double)wb * g.w_unit : (double)wb;
-      const double eta = sp[key], D = sm[key], M = Wt + D;
+      const double eta = log(sp[key]), D = sm[key], M = Wt + D;
       const double q2 = D * (2.0 * Wt + D) * (M * M - (wad - wbd) * (wad - wbd));
       const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
       const double ua = sinh(eta + asinh(ps / wad)), ub = sinh(eta - asinh(ps / wbd));
