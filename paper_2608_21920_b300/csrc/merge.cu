@@ -22,7 +22,9 @@ namespace gapk {
 
 constexpr int kMergeBins = 256;
 constexpr int kMergeKeys = 2 * kMergeBins;  // direction x bin
-constexpr int kMergeWarpBytes = 46 * kMergeKeys;  // one warp's key table and touched list
+constexpr int kMergeCache = 256;  // leptons of a node whose gamma + |u| and its inverse a warp keeps
+// one warp's key table, touched list and the cache of its node's leptons
+constexpr int kMergeWarpBytes = 46 * kMergeKeys + 16 * kMergeCache;
 constexpr uint32_t CH_MERGE = 10;
 
 // One thread per gap: decide whether the gap merges this step.
@@ -102,6 +104,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
   double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then E = exp(eta)
   double *sm = reinterpret_cast<double *>(wb + 36 * kMergeKeys);                      // sum w (g-u), then D
   short *touched = reinterpret_cast<short *>(wb + 44 * kMergeKeys);                   // [kMergeKeys]
+  double *cbig = reinterpret_cast<double *>(wb + 46 * kMergeKeys);                    // [kMergeCache]
+  double *crb = cbig + kMergeCache;                                                   // [kMergeCache]
   int *hist = reinterpret_cast<int *>(msm + (size_t)kMergeWarps * kMergeWarpBytes);  // [nk + 1]
   __shared__ int wsum[kMergeWarps];
   __shared__ int ntouched[kMergeWarps];
@@ -211,10 +215,10 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     if (sizeof(R) == 4 && (unsigned long long)sw[key] > 2ull * 0xffffffffull) return false;
     return true;
   };
-  auto weight_of = [&](int64_t src) -> double {
-    const W wq = as<W>(v.lw[nxt][s])[src];
-    return sizeof(R) == 4 ? (double)wq * g.w_unit : (double)wq;
-  };
+  // weights in the state's units (FP32 state: integer multiples of w_unit);
+  // S+, S- and D are summed in these units and D converted per group
+  auto weight_of = [&](int64_t src) -> double { return (double)as<W>(v.lw[nxt][s])[src]; };
+  const double wscale = sizeof(R) == 4 ? g.w_unit : 1.0;
 
   // 2. one warp per node: group, merge, write back into the current buffer
   for (int node = wid; node < nk; node += kMergeWarps) {
@@ -228,9 +232,12 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       const int key = key_of(src);
       const double u = (double)as<R>(v.lu[nxt][s])[src];
       const double w = weight_of(src);
-      const double gm = sqrt(1.0 + u * u);
-      const double big = gm + fabs(u);
-      const double gp = u >= 0.0 ? big : 1.0 / big, gmn = u >= 0.0 ? 1.0 / big : big;
+      const double big = sqrt(1.0 + u * u) + fabs(u), rb = 1.0 / big;  // gamma + |u| and its inverse
+      if (i - r0 < kMergeCache) {  // kept for the D pass (a square root and a division in FP64)
+        cbig[i - r0] = big;
+        crb[i - r0] = rb;
+      }
+      const double gp = u >= 0.0 ? big : rb, gmn = u >= 0.0 ? rb : big;
       const R phi = as<R>(v.lphi[nxt][s])[src];
       if (atomicAdd(&cnt[key], 1) == 0) touched[atomicAdd(&ntouched[wid], 1)] = (short)key;
       atomicMin(&minid[key], (unsigned long long)v.lid[nxt][s][src]);
@@ -264,17 +271,26 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     // for u >= 0, e = gamma + |u|; for u < 0, e = 1/(gamma + |u|) and the
     // term is (1 - E (gamma + |u|))^2/(2 E (gamma + |u|)).  The difference
     // carries the rounding of e and E alone (a few 1e-16 relative), as
-    // asinh u - eta does, with a square root and a division in place of the
-    // FP64 asinh and sinh (FP64 runs at a small fraction of the FP32 rate).
+    // asinh u - eta does, without the FP64 asinh and sinh (FP64 runs at a
+    // small fraction of the FP32 rate); sm[] sums w d^2/(gamma + |u|) and
+    // the group's 1/(2E) is applied once.
     for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
       if (!merges(key)) continue;
-      const double u = (double)as<R>(v.lu[nxt][s])[src];
+      const R ur = as<R>(v.lu[nxt][s])[src];
+      double big, rb;
+      if (i - r0 < kMergeCache) {
+        big = cbig[i - r0];
+        rb = crb[i - r0];
+      } else {
+        const double u = (double)ur;
+        big = sqrt(1.0 + u * u) + fabs(u);
+        rb = 1.0 / big;
+      }
       const double E = sp[key];
-      const double big = sqrt(1.0 + u * u) + fabs(u);
-      const double d = u >= 0.0 ? big - E : fma(-E, big, 1.0);
-      atomicAdd(&sm[key], weight_of(src) * (d * d) / (2.0 * E * big));
+      const double d = ur >= (R)0 ? big - E : fma(-E, big, 1.0);
+      atomicAdd(&sm[key], weight_of(src) * (d * d) * rb);
     }
     __syncwarp();
     // leptons of groups that do not merge are copied through
@@ -313,7 +329,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       }
       const double wad = sizeof(R) == 4 ? (double)wa * g.w_unit : (double)wa;
       const double wbd = sizeof(R) == 4 ? (double)wb * g.w_unit : (double)wb;
-      const double eta = log(sp[key]), D = sm[key], M = Wt + D;
+      const double E = sp[key], eta = log(E), D = sm[key] * wscale / (2.0 * E), M = Wt + D;
       const double q2 = D * (2.0 * Wt + D) * (M * M - (wad - wbd) * (wad - wbd));
       const double ps = q2 > 0.0 ? sqrt(q2) / (2.0 * M) : 0.0;
       const double ua = sinh(eta + asinh(ps / wad)), ub = sinh(eta - asinh(ps / wbd));
