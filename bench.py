@@ -361,7 +361,7 @@ def run_ours(args):
         line["qed"] = {"metric": METRIC, "value": qr["value"], "unit": UNIT, "steps": qr["steps"],
                        "ms_per_step": qr["ms_per_step"], "roofline": qr["roofline"], "clocks": qr["clocks"],
                        "gpu_launches": qr["gpu_launches"], "config": qr["config"],
-                       "phases_ms_per_step": qr["phases_ms_per_step"],
+                       "phases_ms_per_step": qr["phases_ms_per_step"], "phases_window": qr["phases_window"],
                        "counts": {k: qr[k] for k in ("pairs", "merged", "photons_merged", "emit_events")}}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -579,9 +579,10 @@ def batch_measure(args, world=1, local=0):
     ms = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, "cuda")
     clk = clocks.stop()
     n1 = _total_leptons(g)
-    # the push kernel alone, eagerly launched between CUDA events
+    # the push kernel alone and the step's phases, over as many eagerly
+    # launched steps as were timed (the merge and the compactions are bursty)
     g.profile(True)
-    Kp = 20
+    Kp = K
     torch.cuda.nvtx.range_push("batch_eager")  # launch lists: ncu --nvtx --nvtx-include batch_eager/
     g.step(Kp)
     torch.cuda.nvtx.range_pop()
@@ -615,6 +616,7 @@ def batch_measure(args, world=1, local=0):
         "photons_merged": int(sum(x["photons_merged"] for x in c)),
         "emit_events": int(sum(x["emit_events"] for x in c)),
         "phases_ms_per_step": {k: v / max(nph, 1) for k, v in phases.items()},
+        "phases_window": f"the {Kp} steps after the timed ones, eagerly launched between CUDA events",
     }
     if tuned:
         res["config"]["autotune_ms_per_step"] = tuned
