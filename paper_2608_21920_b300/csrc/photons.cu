@@ -340,30 +340,68 @@ __global__ void k_photon_work_reset(View v) { v.ctl->ph_work_n = 0; }
 
 // Compaction of the photon store into the other buffer (once a quarter of
 // the store is dead, or it is half full): the survivors keep their records;
-// the order is not kept.
-__global__ void k_photon_compact(View v) {
+// the order is not kept.  A block takes kPhCompactPer photons per thread in a
+// round and reserves its survivors' slots with one atomic (one counter
+// serves the whole GPU: an atomic per warp had the copy wait on it).
+constexpr int kPhCompactPer = 4;
+__global__ void __launch_bounds__(256) k_photon_compact(View v) {
   if (!v.ctl->need_ph_compact) return;
+  __shared__ int wcnt[8];  // <= 8 warps
+  __shared__ long long sbase;
   const int b = v.ctl->ph_cur, o = b ^ 1;
   const int64_t n = photon_fill(v, b);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (v.pev[b][i] == kPhDead) continue;
-    const long long d = warp_reserve(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[o]));
-    v.pXr[o][d] = v.pXr[b][i];
-    v.px[o][d] = v.px[b][i];
-    v.pw[o][d] = v.pw[b][i];
-    v.pts[o][d] = v.pts[b][i];
-    v.pta[o][d] = v.pta[b][i];
-    v.pid[o][d] = v.pid[b][i];
-    v.pn0[o][d] = v.pn0[b][i];
-    v.pnr[o][d] = v.pnr[b][i];
-    v.pdir[o][d] = v.pdir[b][i];
-    v.pgap[o][d] = v.pgap[b][i];
-    v.pm[o][d] = v.pm[b][i];
-    v.pmn[o][d] = v.pmn[b][i];
-    v.ptan[o][d] = v.ptan[b][i];
-    v.pkind[o][d] = v.pkind[b][i];
-    v.pev[o][d] = v.pev[b][i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t per_round = (int64_t)blockDim.x * kPhCompactPer;
+  for (int64_t r0 = (int64_t)blockIdx.x * per_round; r0 < n; r0 += (int64_t)gridDim.x * per_round) {
+    // photon r0 + j blockDim + thread: the j-th vector of the warp's lanes;
+    // survivors of vector j go after those of vectors < j, in lane order
+    unsigned bal[kPhCompactPer];
+    int total = 0;
+#pragma unroll
+    for (int j = 0; j < kPhCompactPer; ++j) {
+      const int64_t i = r0 + (int64_t)j * blockDim.x + threadIdx.x;
+      bal[j] = __ballot_sync(0xffffffffu, i < n && v.pev[b][i] != kPhDead);
+      total += __popc(bal[j]);
+    }
+    if (lane == 0) wcnt[wid] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int c = wcnt[w];
+        wcnt[w] = acc;
+        acc += c;
+      }
+      sbase = acc > 0 ? (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&v.ctl->ph_count[o]),
+                                             (unsigned long long)acc)
+                      : 0ll;
+    }
+    __syncthreads();
+    long long d0 = sbase + wcnt[wid];
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kPhCompactPer; ++j) {
+      const long long d = d0 + __popc(bal[j] & below);
+      d0 += __popc(bal[j]);
+      if (!((bal[j] >> lane) & 1u)) continue;
+      const int64_t i = r0 + (int64_t)j * blockDim.x + threadIdx.x;
+      v.pXr[o][d] = v.pXr[b][i];
+      v.px[o][d] = v.px[b][i];
+      v.pw[o][d] = v.pw[b][i];
+      v.pts[o][d] = v.pts[b][i];
+      v.pta[o][d] = v.pta[b][i];
+      v.pid[o][d] = v.pid[b][i];
+      v.pn0[o][d] = v.pn0[b][i];
+      v.pnr[o][d] = v.pnr[b][i];
+      v.pdir[o][d] = v.pdir[b][i];
+      v.pgap[o][d] = v.pgap[b][i];
+      v.pm[o][d] = v.pm[b][i];
+      v.pmn[o][d] = v.pmn[b][i];
+      v.ptan[o][d] = v.ptan[b][i];
+      v.pkind[o][d] = v.pkind[b][i];
+      v.pev[o][d] = v.pev[b][i];
+    }
+    __syncthreads();  // wcnt and sbase are rewritten by the next round
   }
 }
 

@@ -1887,43 +1887,62 @@ __global__ void __launch_bounds__(1024) k_rebin_layout(View v, double slack) {
 // uniform weights the optical depth and the weight are not part of the state
 // and are not copied.
 template <class R>
-__global__ void k_rebin_compact(View v) {
+__global__ void __launch_bounds__(256) k_rebin_compact(View v) {
   using W = typename Prec<R>::W;
   if (!v.ctl->need_rebin || (v.ctl->error & 4)) return;
-  __shared__ int warp_cnt[32];
-  __shared__ int carry;
+  // a round takes kCompactPer vectors of blockDim slots; the survivors keep
+  // their order: position = survivors of the earlier vectors, then of the
+  // earlier warps in this vector, then of the lower lanes
+  constexpr int kCompactPer = 4;
+  __shared__ int wcnt[kCompactPer][8];  // <= 8 warps
+  __shared__ int carry, rtotal;
   const int s = blockIdx.x / v.n_tiles, t = blockIdx.x % v.n_tiles;
   const int cur = v.ctl->lep_cur, nxt = cur ^ 1;
   const int64_t src0 = v.seg_start[s][t];
   const int used = v.seg_used[s][t];
   const int64_t dst0 = v.new_start[s][t];
+  const int cap = v.new_cap[s][t];
   const bool full_state = v.qed_any || v.has_w;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < used; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    int32_t k = -1;
-    if (i < used) k = v.lk[cur][s][src0 + i];
-    const bool alive = k >= 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, alive);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_cnt[wid] = __popc(bal);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0;
-      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
-        int c = warp_cnt[wv];
-        warp_cnt[wv] = acc;
-        acc += c;
-      }
-      warp_cnt[31] = acc;  // block total (blockDim <= 992 threads keeps slot 31 free)
+  for (int base = 0; base < used; base += kCompactPer * blockDim.x) {
+    int32_t kk[kCompactPer];
+    unsigned bal[kCompactPer];
+#pragma unroll
+    for (int j = 0; j < kCompactPer; ++j) {
+      const int i = base + j * blockDim.x + threadIdx.x;
+      kk[j] = i < used ? v.lk[cur][s][src0 + i] : -1;
+      bal[j] = __ballot_sync(0xffffffffu, kk[j] >= 0);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < kCompactPer; ++j) wcnt[j][wid] = __popc(bal[j]);
     }
     __syncthreads();
-    const int pos = carry + warp_cnt[wid] + __popc(bal & ((1u << lane) - 1u));
-    if (alive && pos >= v.new_cap[s][t]) atomicOr(&v.ctl->error, 8);  // never: cap >= alive count
-    if (alive && pos < v.new_cap[s][t]) {
-      const int64_t d = dst0 + pos, sidx = src0 + i;
-      v.lk[nxt][s][d] = k;
+    if (wid == 0) {  // exclusive scan of the (vector, warp) counts, vector-major: one per lane
+      const int j = lane / nw, w = lane % nw;
+      const int c = lane < kCompactPer * nw ? wcnt[j][w] : 0;
+      int x = c;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+      }
+      if (lane < kCompactPer * nw) wcnt[j][w] = x - c;
+      if (lane == 31) rtotal = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kCompactPer; ++j) {
+      if (kk[j] < 0) continue;
+      const int pos = carry + wcnt[j][wid] + __popc(bal[j] & below);
+      if (pos >= cap) {  // never: cap >= alive count
+        atomicOr(&v.ctl->error, 8);
+        continue;
+      }
+      const int64_t d = dst0 + pos, sidx = src0 + base + j * blockDim.x + threadIdx.x;
+      v.lk[nxt][s][d] = kk[j];
       as<R>(v.lphi[nxt][s])[d] = as<R>(v.lphi[cur][s])[sidx];
       as<R>(v.lu[nxt][s])[d] = as<R>(v.lu[cur][s])[sidx];
       v.lid[nxt][s][d] = v.lid[cur][s][sidx];
@@ -1933,7 +1952,7 @@ __global__ void k_rebin_compact(View v) {
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) carry += warp_cnt[31];
+    if (threadIdx.x == 0) carry += rtotal;
     __syncthreads();
   }
   if (threadIdx.x == 0) v.new_fill[s][t] = carry;
