@@ -511,6 +511,12 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   v.q0 = C.take<unsigned long long>(n);
   v.merge_state = C.take<int32_t>(4 * (size_t)n);
   v.merge_width = C.take<double>(n);
+  {
+    const size_t nseg = merge_any ? 2 * (size_t)NT : 0;
+    v.mlist = C.take<int32_t>(nseg);
+    v.mout = C.take<int32_t>(nseg);
+    v.mrun = C.take<int32_t>(nseg * (size_t)(cfg.tile + 4));
+  }
   v.ph_gap = C.take<int32_t>(n);
   {  // photon merge table: twice the photon store (newborns are at most all of it), 2^10 .. 2^22 entries
     int64_t H = 0;

@@ -136,6 +136,7 @@ struct Ctl {
   int64_t new_total[2];
   int64_t ph_nb_start;  // photon store fill before this step's push (0 after a photon compaction)
   int64_t phm_end;      // photon store fill when the photon merge began
+  int32_t mlist_n, mlist_pad;  // (species, tile) segments of merging gaps listed this step
 };
 
 // Everything a kernel needs, passed by value.
@@ -166,6 +167,9 @@ struct View {
   float2 *bw_tab;  // pair energy split: per row of ln chi, (G, dG/d(1/2 - eta)) on kQsNodes nodes
   int32_t *merge_state;  // [gap][4]: merge flag, level
   double *merge_width;   // [gap]
+  // the merge's segments: [2 n_tiles] list of s n_tiles + t, output cursors;
+  // [2 n_tiles][tile + 4] end of each node's run after the sort by node
+  int32_t *mlist, *mout, *mrun;
   // photon merge at birth: open-addressing table of phm_size (a power of
   // two) keys with the sums of each group; zero between merges
   int64_t phm_size;

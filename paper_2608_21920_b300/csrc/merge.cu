@@ -30,6 +30,7 @@ constexpr uint32_t CH_MERGE = 10;
 // One thread per gap: decide whether the gap merges this step.
 __global__ void k_merge_check(View v) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi == 0) v.ctl->mlist_n = 0;  // the merging segments of this step are listed afresh
   if (gi >= v.n_gaps) return;
   const GapDev &g = v.gaps[gi];
   int32_t *st = v.merge_state + 4 * gi;  // [flag, level, -, -]
@@ -65,6 +66,9 @@ struct MergeAcc<float> {  // FP32 state: exact integer sums of m and m Phi (2^-2
 };
 
 constexpr int kMergeWarps = 4;  // warps per merge block, each with its own key table
+// nodes of a tile: tile, or up to 3 more for the last tile of a gap (a
+// remainder below 4 joins the previous tile); mrun rows have this length
+__device__ __forceinline__ int merge_row(const View &v) { return v.tile + 4; }
 
 // An output slot for each lane of a warp that asks for one.
 __device__ __forceinline__ int warp_slot(int *cursor) {
@@ -77,59 +81,27 @@ __device__ __forceinline__ int warp_slot(int *cursor) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Part 1, per (species, tile) segment of a merging gap: a counting sort of
+// the segment by node into the other buffer; the end of each node's run
+// (from the segment's start) goes to mrun, and the segment is listed.
 template <class R>
-__global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
+__global__ void __launch_bounds__(256) k_merge_sort(View v) {
   using W = typename Prec<R>::W;
-  using A = typename MergeAcc<R>::T;
   if (!(v.ctl->flags & 1)) return;
   const int s = blockIdx.x / v.n_tiles, t = blockIdx.x % v.n_tiles;
   const TileDev ti = v.tiles[t];
-  const GapDev &g = v.gaps[ti.gap];
   if (!v.merge_state[4 * ti.gap]) return;
-  const double width = v.merge_width[ti.gap];
+  const GapDev &g = v.gaps[ti.gap];
   const int nk = ti.nk, k0 = ti.k0;
   const int cur = v.ctl->lep_cur, nxt = cur ^ 1;
-  const int64_t step = v.ctl->step;  // the step just completed is step - 1
-  const int q = s == 0 ? -1 : 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  // per warp: a direct-mapped table over the 512 (direction, bin) keys and
-  // the list of keys the current node touched (only those are reset)
-  extern __shared__ __align__(16) unsigned char msm[];
-  unsigned char *wb = msm + (size_t)wid * kMergeWarpBytes;
-  int *cnt = reinterpret_cast<int *>(wb);
-  unsigned long long *minid = reinterpret_cast<unsigned long long *>(wb + 4 * kMergeKeys);
-  A *sw = reinterpret_cast<A *>(wb + 12 * kMergeKeys);                                // sum w
-  A *sphi = reinterpret_cast<A *>(wb + 20 * kMergeKeys);                              // sum w phi
-  double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then E = exp(eta)
-  double *sm = reinterpret_cast<double *>(wb + 36 * kMergeKeys);                      // sum w (g-u), then D
-  short *touched = reinterpret_cast<short *>(wb + 44 * kMergeKeys);                   // [kMergeKeys]
-  double *cbig = reinterpret_cast<double *>(wb + 46 * kMergeKeys);                    // [kMergeCache]
-  double *crb = cbig + kMergeCache;                                                   // [kMergeCache]
-  int *hist = reinterpret_cast<int *>(msm + (size_t)kMergeWarps * kMergeWarpBytes);  // [nk + 1]
-  __shared__ int wsum[kMergeWarps];
-  __shared__ int ntouched[kMergeWarps];
-  __shared__ int carry, out_cursor;
-  __shared__ unsigned long long merged_count;
-
+  extern __shared__ int hist[];  // [nk + 1]
+  __shared__ int wsum[8];        // <= 8 warps
+  __shared__ int carry;
   const int64_t seg0 = v.seg_start[s][t];
   const int used = v.seg_used[s][t];
-  for (int i = lane; i < kMergeKeys; i += 32) {
-    cnt[i] = 0;
-    minid[i] = ~0ull;
-    sw[i] = (A)0;
-    sphi[i] = (A)0;
-    sp[i] = 0.0;
-    sm[i] = 0.0;
-  }
-  if (lane == 0) ntouched[wid] = 0;
-  // 1. counting sort of the segment by node into the other buffer
   for (int i = threadIdx.x; i <= nk; i += blockDim.x) hist[i] = 0;
-  if (threadIdx.x == 0) {
-    carry = 0;
-    out_cursor = 0;
-    merged_count = 0;
-  }
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < used; i += blockDim.x) {
     const int32_t k = v.lk[cur][s][seg0 + i];
@@ -173,60 +145,119 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     v.lid[nxt][s][d] = v.lid[cur][s][src];
   }
   __syncthreads();
-  // after the scatter hist[i] holds the end of node i's run = start of node i+1
+  // after the scatter hist[i] holds the end of node i's run
+  const int seg = s * v.n_tiles + t;
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) v.mrun[(int64_t)seg * merge_row(v) + i] = hist[i];
+  if (threadIdx.x == 0) {
+    v.mout[seg] = 0;
+    v.mlist[atomicAdd(&v.ctl->mlist_n, 1)] = seg;
+  }
+}
 
-  auto copy_out = [&](int64_t src) {
-    const int64_t d = seg0 + warp_slot(&out_cursor);
-    v.lk[cur][s][d] = v.lk[nxt][s][src];
-    as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
-    as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
-    as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
-    as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
-    v.lid[cur][s][d] = v.lid[nxt][s][src];
-  };
-  // the bin floor(ln gamma / width) of the FP64 evaluation (FP64 runs at a
-  // small fraction of the FP32 rate here): taken from an FP32 evaluation t
-  // where that lies more than 1e-3 of a bin from a bin edge, else evaluated
-  // in FP64.  The FP32 t is within 1e-4 of a bin of the FP64 one: the
-  // rounding of u, 1 + u^2 and the square root moves ln gamma by ~2e-7,
-  // logf's ulp at ln gamma <= 21 is <= 2e-6, times 1/width <= 10, and the
-  // rounding of t <= 256 and of 1/width adds ~2e-5.
-  const float winv_f = (float)(1.0 / width);
-  auto key_of = [&](int64_t src) -> int {
-    const R ur = as<R>(v.lu[nxt][s])[src];
-    const float uf = (float)ur;  // FP32 state: the stored value, no 64-bit type conversion (FP64 rate)
-    const float tf = logf(sqrtf(1.0f + uf * uf)) * winv_f;
-    const float bf = floorf(tf);
-    int b;
-    if (tf - bf > 1e-3f && bf + 1.0f - tf > 1e-3f && tf < (float)(kMergeBins - 1)) {
-      b = (int)bf;
-    } else {
-      const double u = (double)ur;
-      const double t = floor(log(sqrt(1.0 + u * u)) / width);
-      b = t < 0.0 ? 0 : (t > (double)(kMergeBins - 1) ? kMergeBins - 1 : (int)t);
-    }
-    return (ur >= (R)0 ? 1 : 0) * kMergeBins + b;
-  };
-  // a group merges when it has three or more members; in the FP32 state
-  // its children carry 32-bit weights, so a group whose summed weight would
-  // not split into two of them is left unmerged
-  auto merges = [&](int key) -> bool {
-    if (cnt[key] < 3) return false;
-    if (sizeof(R) == 4 && (unsigned long long)sw[key] > 2ull * 0xffffffffull) return false;
-    return true;
-  };
-  // weights in the state's units (FP32 state: integer multiples of w_unit);
-  // S+, S- and D are summed in these units and D converted per group
-  auto weight_of = [&](int64_t src) -> double { return (double)as<W>(v.lw[nxt][s])[src]; };
-  const double wscale = sizeof(R) == 4 ? g.w_unit : 1.0;
+// Part 2: the nodes of the listed segments, one warp per node, spread over
+// every warp of the GPU (a tile's nodes in one block made the densest tiles
+// a long serial chain that the rest of the GPU waited on): group, merge,
+// write back into the current buffer at the segment's output cursor.
+template <class R>
+__global__ void __launch_bounds__(32 * kMergeWarps) k_merge_nodes(View v) {
+  using W = typename Prec<R>::W;
+  using A = typename MergeAcc<R>::T;
+  if (!(v.ctl->flags & 1)) return;
+  const int cur = v.ctl->lep_cur, nxt = cur ^ 1;
+  const int64_t step = v.ctl->step;  // the step just completed is step - 1
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-  // 2. one warp per node: group, merge, write back into the current buffer
-  for (int node = wid; node < nk; node += kMergeWarps) {
-    const int r0 = node == 0 ? 0 : hist[node - 1], r1 = hist[node];
+  // per warp: a direct-mapped table over the 512 (direction, bin) keys, the
+  // list of keys the current node touched (only those are reset), and the
+  // cache of the node's gamma + |u|
+  extern __shared__ __align__(16) unsigned char msm[];
+  unsigned char *wb = msm + (size_t)wid * kMergeWarpBytes;
+  int *cnt = reinterpret_cast<int *>(wb);
+  unsigned long long *minid = reinterpret_cast<unsigned long long *>(wb + 4 * kMergeKeys);
+  A *sw = reinterpret_cast<A *>(wb + 12 * kMergeKeys);                                // sum w
+  A *sphi = reinterpret_cast<A *>(wb + 20 * kMergeKeys);                              // sum w phi
+  double *sp = reinterpret_cast<double *>(wb + 28 * kMergeKeys);                      // sum w (g+u), then E = exp(eta)
+  double *sm = reinterpret_cast<double *>(wb + 36 * kMergeKeys);                      // sum w (g-u), then D
+  short *touched = reinterpret_cast<short *>(wb + 44 * kMergeKeys);                   // [kMergeKeys]
+  double *cbig = reinterpret_cast<double *>(wb + 46 * kMergeKeys);                    // [kMergeCache]
+  double *crb = cbig + kMergeCache;                                                   // [kMergeCache]
+  __shared__ int ntouched[kMergeWarps];
+  for (int i = lane; i < kMergeKeys; i += 32) {
+    cnt[i] = 0;
+    minid[i] = ~0ull;
+    sw[i] = (A)0;
+    sphi[i] = (A)0;
+    sp[i] = 0.0;
+    sm[i] = 0.0;
+  }
+  if (lane == 0) ntouched[wid] = 0;
+  __syncwarp();
+
+  const int row = merge_row(v);
+  const int64_t ntask = (int64_t)v.ctl->mlist_n * row;
+  const int64_t nwarps = (int64_t)gridDim.x * kMergeWarps;
+  for (int64_t task = (int64_t)blockIdx.x * kMergeWarps + wid; task < ntask; task += nwarps) {
+    const int seg = v.mlist[task / row], node = (int)(task % row);
+    const int s = seg / v.n_tiles, t = seg % v.n_tiles;
+    const TileDev ti = v.tiles[t];
+    if (node >= ti.nk) continue;
+    const GapDev &g = v.gaps[ti.gap];
+    const double width = v.merge_width[ti.gap];
+    const int q = s == 0 ? -1 : 1;
+    const int64_t seg0 = v.seg_start[s][t];
+    int *out_cursor = &v.mout[seg];
+    const int32_t *run = v.mrun + (int64_t)seg * row;
+    const int r0 = node == 0 ? 0 : run[node - 1], r1 = run[node];
+
+    auto copy_out = [&](int64_t src) {
+      const int64_t d = seg0 + warp_slot(out_cursor);
+      v.lk[cur][s][d] = v.lk[nxt][s][src];
+      as<R>(v.lphi[cur][s])[d] = as<R>(v.lphi[nxt][s])[src];
+      as<R>(v.lu[cur][s])[d] = as<R>(v.lu[nxt][s])[src];
+      as<W>(v.lw[cur][s])[d] = as<W>(v.lw[nxt][s])[src];
+      as<R>(v.ltau[cur][s])[d] = as<R>(v.ltau[nxt][s])[src];
+      v.lid[cur][s][d] = v.lid[nxt][s][src];
+    };
     if (r1 - r0 < 3) {  // nothing to merge: copy through
       for (int i = r0 + lane; i < r1; i += 32) copy_out(seg0 + i);
       continue;
     }
+    // the bin floor(ln gamma / width) of the FP64 evaluation (FP64 runs at a
+    // small fraction of the FP32 rate here): taken from an FP32 evaluation t
+    // where that lies more than 1e-3 of a bin from a bin edge, else evaluated
+    // in FP64.  The FP32 t is within 1e-4 of a bin of the FP64 one: the
+    // rounding of u, 1 + u^2 and the square root moves ln gamma by ~2e-7,
+    // logf's ulp at ln gamma <= 21 is <= 2e-6, times 1/width <= 10, and the
+    // rounding of t <= 256 and of 1/width adds ~2e-5.
+    const float winv_f = (float)(1.0 / width);
+    auto key_of = [&](int64_t src) -> int {
+      const R ur = as<R>(v.lu[nxt][s])[src];
+      const float uf = (float)ur;  // FP32 state: the stored value, no 64-bit type conversion (FP64 rate)
+      const float tf = logf(sqrtf(1.0f + uf * uf)) * winv_f;
+      const float bf = floorf(tf);
+      int b;
+      if (tf - bf > 1e-3f && bf + 1.0f - tf > 1e-3f && tf < (float)(kMergeBins - 1)) {
+        b = (int)bf;
+      } else {
+        const double u = (double)ur;
+        const double tt = floor(log(sqrt(1.0 + u * u)) / width);
+        b = tt < 0.0 ? 0 : (tt > (double)(kMergeBins - 1) ? kMergeBins - 1 : (int)tt);
+      }
+      return (ur >= (R)0 ? 1 : 0) * kMergeBins + b;
+    };
+    // a group merges when it has three or more members; in the FP32 state
+    // its children carry 32-bit weights, so a group whose summed weight would
+    // not split into two of them is left unmerged
+    auto merges = [&](int key) -> bool {
+      if (cnt[key] < 3) return false;
+      if (sizeof(R) == 4 && (unsigned long long)sw[key] > 2ull * 0xffffffffull) return false;
+      return true;
+    };
+    // weights in the state's units (FP32 state: integer multiples of w_unit);
+    // S+, S- and D are summed in these units and D converted per group
+    auto weight_of = [&](int64_t src) -> double { return (double)as<W>(v.lw[nxt][s])[src]; };
+    const double wscale = sizeof(R) == 4 ? g.w_unit : 1.0;
+
     for (int i = r0 + lane; i < r1; i += 32) {
       const int64_t src = seg0 + i;
       const int key = key_of(src);
@@ -299,7 +330,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       if (!merges(key_of(src))) copy_out(src);
     }
     // groups of three or more become two
-    const int32_t kn = k0 + node;
+    const int32_t kn = ti.k0 + node;
+    unsigned long long merged = 0;
     for (int j = lane; j < nt; j += 32) {
       const int key = touched[j];
       const int n = cnt[key];
@@ -343,7 +375,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
       } else if (flux != 0.0 && (g.periodic || node_g > 0)) {
         atomicAdd(&v.E[v.ctl->e_cur][g.node_off + node_g], -flux);
       }
-      const int o = atomicAdd(&out_cursor, 2);
+      const int o = atomicAdd(out_cursor, 2);
       for (int c = 0; c < 2; ++c) {
         const int64_t d = seg0 + o + c;
         const uint64_t id = child_id(minid[key], (uint32_t)(step - 1), CH_MERGE, (uint32_t)c) & ~kPhotonBit;
@@ -354,8 +386,10 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
         as<R>(v.ltau[cur][s])[d] = (R)(-log(uniform53(g.seed, id, (uint32_t)step, CH_TAU0, 0)));
         v.lid[cur][s][d] = id;
       }
-      atomicAdd(&merged_count, (unsigned long long)(n - 2));
+      merged += (unsigned long long)(n - 2);
     }
+    for (int o = 16; o > 0; o >>= 1) merged += __shfl_down_sync(0xffffffffu, merged, o);
+    if (lane == 0 && merged) atomicAdd(&v.counters[ti.gap * C_NCNT + C_MERGED], merged);
     __syncwarp();
     // reset the touched keys for the warp's next node
     for (int j = lane; j < nt; j += 32) {
@@ -371,12 +405,19 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge(View v) {
     if (lane == 0) ntouched[wid] = 0;
     __syncwarp();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    v.seg_used[s][t] = out_cursor;
-    v.seg_append[s][t] = out_cursor;
-    v.seg_alive[s][t] = out_cursor;
-    if (merged_count) atomicAdd(&v.counters[ti.gap * C_NCNT + C_MERGED], merged_count);
+}
+
+// Part 3: the listed segments take their output cursors as their fill.
+__global__ void k_merge_fin(View v) {
+  if (!(v.ctl->flags & 1)) return;
+  const int n = v.ctl->mlist_n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int seg = v.mlist[j];
+    const int s = seg / v.n_tiles, t = seg % v.n_tiles;
+    const int o = v.mout[seg];
+    v.seg_used[s][t] = o;
+    v.seg_append[s][t] = o;
+    v.seg_alive[s][t] = o;
   }
 }
 
@@ -505,17 +546,23 @@ __global__ void k_merge_done(View v) { v.ctl->flags &= ~1; }
 
 void launch_merge(const View &v, cudaStream_t st) {
   k_merge_check<<<(v.n_gaps + 127) / 128, 128, 0, st>>>(v);
-  const size_t smem = (size_t)kMergeWarps * kMergeWarpBytes + (size_t)(v.tile + 8) * sizeof(int) + 64;
-  // shared memory above 48 KB is opted into once, for the largest tile
+  const size_t hist = (size_t)(v.tile + 8) * sizeof(int);
+  const int smem = kMergeWarps * kMergeWarpBytes;  // above 48 KB: opted into once
   static bool attr_set = false;
   if (!attr_set) {
-    const int most = (int)((size_t)kMergeWarps * kMergeWarpBytes + (size_t)(4096 + 8) * sizeof(int) + 64);
-    cudaFuncSetAttribute(k_merge<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_merge<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_merge_nodes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_merge_nodes<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr_set = true;
   }
-  if (v.precision == GAP_FP32_STATE) k_merge<float><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
-  else k_merge<double><<<2 * v.n_tiles, 32 * kMergeWarps, smem, st>>>(v);
+  // the node kernel runs two blocks per SM (its tables), each warp taking nodes in turn
+  if (v.precision == GAP_FP32_STATE) {
+    k_merge_sort<float><<<2 * v.n_tiles, 256, hist, st>>>(v);
+    k_merge_nodes<float><<<2 * 148, 32 * kMergeWarps, smem, st>>>(v);
+  } else {
+    k_merge_sort<double><<<2 * v.n_tiles, 256, hist, st>>>(v);
+    k_merge_nodes<double><<<2 * 148, 32 * kMergeWarps, smem, st>>>(v);
+  }
+  k_merge_fin<<<(2 * v.n_tiles + 255) / 256, 256, 0, st>>>(v);
   if (v.phm_size > 0) {
     k_phm_insert<<<2 * 148, 256, 0, st>>>(v);
     k_phm_emit<<<2 * 148, 256, 0, st>>>(v);
