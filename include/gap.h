@@ -456,12 +456,13 @@ int gap_profile_phases(gap_handle *h, double *ms_out, int64_t *steps_out);
 int gap_hold_copies(gap_handle *h, int32_t on);
 
 /* Test hook for the overflow path of the two-pass FP32 QED push (variants 0
- * and 1): the push's list of deferred leptons (emitters and leptons that
- * moved into another tile; sized for an eighth of the lepton slots) is used
- * up to n entries in the later steps; the leptons that do not fit are found
- * in the store by a third kernel, with the same results.  n is clamped to
- * the list's size; GAP_EINVAL for n < 0.  The value is a launch parameter:
- * steps replayed from CUDA graphs captured earlier keep the old one. */
+ * and 1): the push's list of deferred leptons (leptons that moved into
+ * another tile in its first half, emitters in its second; sized for an
+ * eighth of the lepton slots) is used up to n entries (n/2 per half) in the
+ * later steps; the leptons that do not fit are found in the store by a third
+ * kernel, with the same results.  n is clamped to the list's size;
+ * GAP_EINVAL for n < 0.  The value is a launch parameter: steps replayed
+ * from CUDA graphs captured earlier keep the old one. */
 int gap_defer_limit(gap_handle *h, int64_t n);
 
 /* Checkpoint and resume.  A handle's whole state (particles, photons and

@@ -496,9 +496,10 @@ static int build_layout(const gap_params *p, int32_t n, const gap_config &cfg, c
   const int64_t item_cap = 2 * (lep_cap / kPushChunkMin) + 2 * (int64_t)NT + 2;
   v.item_tile = C.take<int32_t>((size_t)item_cap);
   {  // the two-pass FP32 QED push (variants 0 and 1): its deferred list, an
-     // eighth of the lepton slots (the emitters and tile movers of a step are
-     // a few per cent; the rest, if ever, are found in the store)
-    const int64_t dcap = two_pass ? std::max<int64_t>(1 << 20, lep_cap / 8) : 0;
+     // eighth of the lepton slots, half for the tile movers and half for the
+     // emitters (each a few per cent of a step's leptons; the rest, if ever,
+     // are found in the store)
+    const int64_t dcap = two_pass ? std::max<int64_t>(1 << 21, lep_cap / 8) : 0;
     v.defer_slot = C.take<int64_t>((size_t)dcap);
     v.defer_ts = C.take<uint32_t>((size_t)dcap);
     v.defer_cap = dcap;

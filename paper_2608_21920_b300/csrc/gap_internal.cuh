@@ -130,7 +130,8 @@ struct Ctl {
   int32_t hold_copies;  // test hook: bulk-copy pushes leave their first stage unissued
   int32_t push_items, push_next;  // the push work list of this step and its counter
   int32_t push_chunk, push_pad;   // leptons per item this step (kPushChunkMin .. kPushChunk)
-  unsigned long long defer_n;     // entries of the deferred list this step (may exceed its capacity)
+  unsigned long long defer_n;     // movers on the deferred list this step (may exceed its half)
+  unsigned long long defer_ne;    // emitters on the deferred list this step (may exceed its half)
   int32_t defer_over, defer_pad;  // some deferred lepton did not fit on the list this step
   int64_t spill_n[2];
   int64_t new_total[2];

@@ -525,33 +525,48 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
           }
         }
         // queue the deferred leptons in lane order (at most 32 VD more): a
-        // lane's entries go after those of the lanes below it
+        // lane's entries go after those of the lanes below it.  Movers fill
+        // the first half of the list and emitters the second, so that the
+        // second pass runs each kind in warps of its own (a mover's append
+        // is short, an emitter's events long)
+        if (!__any_sync(0xffffffffu, later != 0u)) continue;  // most groups: nothing deferred
         const unsigned below = (1u << lane) - 1u;
-        int before = 0, total = 0;
+        const unsigned emit = later & ~moved;
+        int before_m = 0, total_m = 0, before_e = 0, total_e = 0;
 #pragma unroll
         for (int jj = 0; jj < VD; ++jj) {
-          const unsigned bj = __ballot_sync(0xffffffffu, (later >> jj) & 1u);
-          before += __popc(bj & below);
-          total += __popc(bj);
+          const unsigned bm = __ballot_sync(0xffffffffu, (moved >> jj) & 1u);
+          const unsigned be = __ballot_sync(0xffffffffu, (emit >> jj) & 1u);
+          before_m += __popc(bm & below);
+          total_m += __popc(bm);
+          before_e += __popc(be & below);
+          total_e += __popc(be);
         }
-        if (total > 0) {  // warp-uniform: reserve the warp's entries of the list
-          unsigned long long first = 0ull;
-          if (lane == 0) first = atomicAdd(&v.ctl->defer_n, (unsigned long long)total);
-          first = __shfl_sync(0xffffffffu, first, 0);
-          unsigned long long pos = first + (unsigned long long)before;
+        if (total_m + total_e > 0) {  // warp-uniform: reserve the warp's entries of the two halves
+          unsigned long long first_m = 0ull, first_e = 0ull;
+          if (lane == 0) {
+            if (total_m) first_m = atomicAdd(&v.ctl->defer_n, (unsigned long long)total_m);
+            if (total_e) first_e = atomicAdd(&v.ctl->defer_ne, (unsigned long long)total_e);
+          }
+          first_m = __shfl_sync(0xffffffffu, first_m, 0);
+          first_e = __shfl_sync(0xffffffffu, first_e, 0);
+          const unsigned long long half = (unsigned long long)(v.defer_use / 2);
+          unsigned long long pos_m = first_m + (unsigned long long)before_m;
+          unsigned long long pos_e = first_e + (unsigned long long)before_e;
           for (unsigned b = later; b; b &= b - 1u) {
             const int jb = __ffs(b) - 1;
             const bool mover = (moved >> jb) & 1u;
-            if (pos < (unsigned long long)v.defer_use) {
-              v.defer_slot[pos] = slot0 + jb;
-              v.defer_ts[pos] = (uint32_t)t | ((uint32_t)s << 30) | (mover ? 0x80000000u : 0u);
-            } else {  // the list is full: k_push_overflow finds the lepton in the store
+            const unsigned long long pos = mover ? pos_m++ : pos_e++;
+            if (pos < half) {
+              const unsigned long long at = mover ? pos : half + pos;
+              v.defer_slot[at] = slot0 + jb;
+              v.defer_ts[at] = (uint32_t)t | ((uint32_t)s << 30) | (mover ? 0x80000000u : 0u);
+            } else {  // the half is full: k_push_overflow finds the lepton in the store
               // (a mover by its node outside the tile, an emitter by its
               // optical depth stored as -1 - tau)
               if (!mover) Tp[slot0 + jb] = (R)-1 - Tp[slot0 + jb];
               v.ctl->defer_over = 1;
             }
-            ++pos;
           }
         }
       }
@@ -886,11 +901,16 @@ __device__ __noinline__ int push_deferred(const View &v, const int t, const int 
   return 1;
 }
 
-// The second pass over the step's deferred list.
+// The second pass over the step's deferred list: the movers of its first
+// half, then the emitters of its second half.
 __global__ void __launch_bounds__(256) k_push_deferred(View v) {
-  const unsigned long long n0 = v.ctl->defer_n;
-  const int64_t n = n0 < (unsigned long long)v.defer_use ? (int64_t)n0 : v.defer_use;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t half = v.defer_use / 2;
+  const unsigned long long nm0 = v.ctl->defer_n, ne0 = v.ctl->defer_ne;
+  const int64_t nm = nm0 < (unsigned long long)half ? (int64_t)nm0 : half;
+  const int64_t ne = ne0 < (unsigned long long)half ? (int64_t)ne0 : half;
+  for (int64_t vi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; vi < nm + ne;
+       vi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = vi < nm ? vi : half + (vi - nm);
     const uint32_t ts = v.defer_ts[i];
     const int t = (int)(ts & 0x3FFFFFFFu), s = (int)((ts >> 30) & 1u);
     const int dead = push_deferred<float>(v, t, s, v.defer_slot[i], (ts >> 31) != 0);
@@ -1827,13 +1847,30 @@ __global__ void __launch_bounds__(1024) k_rebin_layout(View v, double slack) {
       b_loc += (double)(cnt + head + 64);
       e_loc += extra;
     }
-    atomicAdd(&s_base, b_loc);
-    atomicAdd(&s_extra, e_loc);
+    for (int o = 16; o > 0; o >>= 1) {  // one shared atomic per warp (the 1024 of the block contended)
+      b_loc += __shfl_down_sync(0xffffffffu, b_loc, o);
+      e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&s_base, b_loc);
+      atomicAdd(&s_extra, e_loc);
+    }
     __syncthreads();
     double f = 0.0;
     if (s_extra > 0.0) {
       f = ((double)v.lep_capacity - s_base) / s_extra;
       f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+    }
+    // the store's room beyond that, half of it shared out as up to 1024 more
+    // slots per segment: a burst of pairs in a tile that grew little before
+    // then fits without a spill (a spill re-lays out the whole store)
+    long long bonus = 0;
+    {
+      const double spare = (double)v.lep_capacity - s_base - f * s_extra;
+      if (spare > 0.0 && n > 0) {
+        const double b = 0.5 * spare / (double)n;
+        bonus = b >= 1024.0 ? 1024ll : ((long long)b & ~31ll);
+      }
     }
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -1844,7 +1881,7 @@ __global__ void __launch_bounds__(1024) k_rebin_layout(View v, double slack) {
         long long cnt, head;
         double extra;
         counts(t, cnt, head, extra);
-        cap = (cnt + head + (long long)(f * extra) + 31) & ~31ll;
+        cap = (cnt + head + (long long)(f * extra) + bonus + 31) & ~31ll;
         if (cap > 0x7fffffe0ll) cap = 0x7fffffe0ll;
         v.new_cap[s][t] = (int32_t)cap;
       }
@@ -2155,6 +2192,7 @@ __global__ void __launch_bounds__(1024) k_push_items(View v) {
   }
   if (threadIdx.x == 0) {
     v.ctl->defer_n = 0ull;
+    v.ctl->defer_ne = 0ull;
     v.ctl->defer_over = 0;
     v.item_start[n] = carry;
     if (carry > v.item_cap) atomicOr(&v.ctl->error, 256);  // never: item_cap bounds the items
