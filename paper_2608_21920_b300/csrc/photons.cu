@@ -317,14 +317,14 @@ __global__ void __launch_bounds__(256, 5) k_photon_scan(View v) {
   if (wn > 0) flush();
 }
 
-// Part 2 (five blocks of 256 threads per SM, at most 51 registers: the
-// kernel is latency-bound and needs the warps; the rare conversion with a
-// quantum pair split spills instead): the work list, one photon per thread:
-// a photon to be scheduled
-// (new, imported, or at its re-schedule step) is scheduled, and may have its
-// event in this very step; a photon at its event converts or escapes.
+// Part 2 (four blocks of 256 threads per SM, at most 64 registers: the
+// kernel is latency-bound and needs the warps, and at five blocks, 51
+// registers, it measured 2 % slower): the work list, one photon per thread:
+// a photon to be scheduled (new, imported, or at its re-schedule step) is
+// scheduled, and may have its event in this very step; a photon at its
+// event converts or escapes.
 template <class R>
-__global__ void __launch_bounds__(256, 5) k_photon_schedule(View v) {
+__global__ void __launch_bounds__(256, 4) k_photon_schedule(View v) {
   const int b = v.ctl->ph_cur;
   const int64_t n = v.ctl->ph_work_n;
   const int64_t step = v.ctl->step;

@@ -563,8 +563,9 @@ __global__ void __launch_bounds__(256, MINB) k_push(View v) {
               v.defer_ts[at] = (uint32_t)t | ((uint32_t)s << 30) | (mover ? 0x80000000u : 0u);
             } else {  // the half is full: k_push_overflow finds the lepton in the store
               // (a mover by its node outside the tile, an emitter by its
-              // optical depth stored as -1 - tau)
-              if (!mover) Tp[slot0 + jb] = (R)-1 - Tp[slot0 + jb];
+              // node stored as -2 - k: below the dead mark -1, and undone
+              // exactly, which -1 - tau in floating point was not)
+              if (!mover) Kp[slot0 + jb] = -2 - Kp[slot0 + jb];
               v.ctl->defer_over = 1;
             }
           }
@@ -920,9 +921,9 @@ __global__ void __launch_bounds__(256) k_push_deferred(View v) {
 
 // The leptons the first pass could not put on a full deferred list, found in
 // the store: nothing to do unless the list overflowed this step; then the
-// blocks take the (species, tile) segments in turn.  A lepton whose node lies
-// outside its tile moved on; one with a negative optical depth emits (its
-// depth is restored first).
+// blocks take the (species, tile) segments in turn.  A lepton whose node is
+// stored as -2 - k (below the dead mark -1) emits, its node restored first;
+// one whose node lies outside its tile moved on.
 __global__ void __launch_bounds__(256) k_push_overflow(View v) {
   if (!v.ctl->defer_over) return;
   const int cur = v.ctl->lep_cur;
@@ -932,17 +933,16 @@ __global__ void __launch_bounds__(256) k_push_overflow(View v) {
     const int64_t start = v.seg_start[s][t];
     const int used = v.seg_used[s][t];
     int32_t *Kp = v.lk[cur][s];
-    float *Tp = as<float>(v.ltau[cur][s]);
     int dead = 0;
     for (int i = threadIdx.x; i < used; i += blockDim.x) {
       const int64_t slot = start + i;
       const int32_t k = Kp[slot];
-      if (k < 0) continue;
-      if (k < ti.k0 || k >= ti.k0 + ti.nk) {
-        dead += push_deferred<float>(v, t, s, slot, true);
-      } else if (Tp[slot] < 0.0f) {
-        Tp[slot] = -1.0f - Tp[slot];
+      if (k == -1) continue;  // dead
+      if (k <= -2) {
+        Kp[slot] = -2 - k;
         dead += push_deferred<float>(v, t, s, slot, false);
+      } else if (k < ti.k0 || k >= ti.k0 + ti.nk) {
+        dead += push_deferred<float>(v, t, s, slot, true);
       }
     }
     if (dead) atomicAdd(&v.seg_alive[s][t], -dead);

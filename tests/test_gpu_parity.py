@@ -241,9 +241,10 @@ def test_empty_gap_and_graph_replay():
 
 
 def test_fp32_qed_two_pass_overflow_is_bit_identical():
-    """The two-pass QED push with its list of deferred leptons cut to 16
-    entries: the emitters and tile movers beyond them are found in the store
-    by the overflow pass, and leptons, photons, E and the counters agree bit
+    """The two-pass QED push with its list of deferred leptons cut to 4
+    entries (2 tile movers, 2 emitters): the emitters and tile movers beyond
+    them are found in the store by the overflow pass (an emitter by its node
+    stored as -2 - k), and leptons, photons, E and the counters agree bit
     for bit with the push in place over a discharge that emits, converts and
     merges."""
     from paper_2608_21920_b300 import Gap
@@ -251,7 +252,7 @@ def test_fp32_qed_two_pass_overflow_is_bit_identical():
     cfg = dict(P.SMALL_DISCHARGE, cap=450)
     ref = Gap(P.gpu_params(cfg), precision="fp32", tile=32, variant=2)
     alt = Gap(P.gpu_params(cfg), precision="fp32", tile=32, variant=0)
-    A.check(A.lib().gap_defer_limit(alt.handle, 16), alt.handle, "gap_defer_limit")
+    A.check(A.lib().gap_defer_limit(alt.handle, 4), alt.handle, "gap_defer_limit")
     for n in (300, 400, 300):
         ref.step(n)
         alt.step(n)
