@@ -2311,9 +2311,11 @@ void launch_step(const View &v, int threads, cudaStream_t st) {
   launch_after_push(v, st);
 }
 
+// Kernels one step launches (the merge: check, sort, nodes, finish, done,
+// and the photon merge's three when the table exists).
 int launches_per_step(const View &v) {
   const bool lean = v.precision == GAP_FP32_STATE && !v.qed_any && !v.has_w;
-  return (lean ? 1 : 2) + (two_pass_push(v) ? 2 : 0) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 6 : 3) : 0) + 5 +
+  return (lean ? 1 : 2) + (two_pass_push(v) ? 2 : 0) + (v.qed_any ? 3 : 0) + (v.surface_any ? 1 : 0) + 1 + (v.merge_any ? (v.phm_size > 0 ? 8 : 5) : 0) + 5 +
          (v.qed_any ? 2 : 0) + (v.filter_any ? 2 : 0) + (v.defer_any && v.merge_any ? 2 : 0) + (v.pr_any ? 1 : 0) + (v.em_any ? 2 : 0);
 }
 
