@@ -799,7 +799,7 @@ static int mkey_cmp(const void *a, const void *b) {
   if (x->id != y->id) return x->id < y->id ? -1 : 1;
   return 0;
 }
-/* Photons under the cap (the survey's N -> 1 conserving w and w x), merged
+/* Photons under the cap (N -> 1, conserving w and w x), merged
  * at birth: while the gap is over its cap, the photons born in this step's
  * push (n0 = n + 1) of each (cell floor(X), direction, bin of ln x of the
  * leptons' width) group with at least two members become one photon of

@@ -140,7 +140,7 @@ def test_quantum_pair_creation_matches_oracle():
 def test_config1_quantum_parity_first_200_steps():
     """Config 1 with the quantum photon spectrum and pair split (FP64): E and
     every lepton within 1e-10 of the oracle with identical event counters over
-    the first 200 steps (the survey's parity criterion), the emissions drawn
+    the first 200 steps (the state parity criterion), the emissions drawn
     on the exact spectrum."""
     cfg = dict(P.CONFIG1, qed_quantum=1)
     g, o = P.make_pair(cfg, "fp64", tile=64)
