@@ -334,14 +334,27 @@ void launch_gauss(const View &v, int set_background, cudaStream_t st) {
 // Diagnostics of one gap (Sect. 6.2 Fig. 5, Sect. 6.6 Fig. 8).
 // dmom layout: [0..3] density of (species, direction) per cell, [4] sum w
 // gamma^-3, [5] sum w, [6] charge (double copy), [7] photon density.
+// One block per tile.  With priv, the tile's cells k0-1 .. k0+nk-1 are summed
+// in shared memory and added to the gap's arrays once per cell (the leptons
+// of a tile crowd few cells, and their global atomics had contended).
 template <class R>
-__global__ void k_moments(View v, int gap) {
+__global__ void __launch_bounds__(256) k_moments(View v, int gap, int priv) {
   using W = typename Prec<R>::W;
   const GapDev &g = v.gaps[gap];
   const int t = g.tile_begin + blockIdx.x;
+  const TileDev ti = v.tiles[t];
   const int cur = v.ctl->lep_cur;
   const int64_t nx = g.nx;
   double *M = v.dmom;
+  const int ncell = ti.nk + 1;
+  extern __shared__ __align__(16) unsigned char msh[];
+  double *sM = reinterpret_cast<double *>(msh);                                  // [6][ncell]
+  unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sM + 6 * ncell);  // [ncell]
+  if (priv) {
+    for (int i = threadIdx.x; i < 6 * ncell; i += blockDim.x) sM[i] = 0.0;
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) sQ[i] = 0ull;
+    __syncthreads();
+  }
   double en = 0.0;
   for (int s = 0; s < 2; ++s) {
     const int q = s == 0 ? -1 : 1;
@@ -366,20 +379,43 @@ __global__ void k_moments(View v, int gap) {
         dr = (double)fr * kPhiUnit;
       }
       for (int side = 0; side < 2; ++side) {
-        int64_t c = side == 0 ? (int64_t)k - 1 : (int64_t)k;
-        if (g.periodic) c = (c + nx) % nx;
-        else if (c < 0 || c >= nx) continue;
         const double fr_ = side == 0 ? dl : dr;
         if (fr_ == 0.0) continue;
+        const int64_t cu = side == 0 ? (int64_t)k - 1 : (int64_t)k;  // before the wrap
+        const int64_t lc = cu - (ti.k0 - 1);
+        const long long qv = sizeof(R) == 4 ? (long long)q * (long long)wq * (side == 0 ? fl : fr) : 0ll;
+        if (priv && lc >= 0 && lc < ncell) {
+          atomicAdd(&sM[(s * 2 + dir) * ncell + lc], w * fr_ / g.dx);
+          atomicAdd(&sM[4 * ncell + lc], w * fr_ / (gm * gm * gm));
+          atomicAdd(&sM[5 * ncell + lc], w * fr_);
+          if (sizeof(R) == 4) atomicAdd(&sQ[lc], (unsigned long long)qv);
+          else atomicAdd(reinterpret_cast<double *>(&sQ[lc]), (double)q * w * fr_);
+          continue;
+        }
+        int64_t c = cu;
+        if (g.periodic) c = (c + nx) % nx;
+        else if (c < 0 || c >= nx) continue;
         atomicAdd(&M[(s * 2 + dir) * nx + c], w * fr_ / g.dx);
         atomicAdd(&M[4 * nx + c], w * fr_ / (gm * gm * gm));
         atomicAdd(&M[5 * nx + c], w * fr_);
-        if (sizeof(R) == 4) {
-          const long long val = (long long)q * (long long)wq * (side == 0 ? fl : fr);
-          atomicAdd(&v.dcharge[c], (unsigned long long)val);
-        } else {
-          atomicAdd(reinterpret_cast<double *>(&v.dcharge[c]), (double)q * w * fr_);
-        }
+        if (sizeof(R) == 4) atomicAdd(&v.dcharge[c], (unsigned long long)qv);
+        else atomicAdd(reinterpret_cast<double *>(&v.dcharge[c]), (double)q * w * fr_);
+      }
+    }
+  }
+  if (priv) {
+    __syncthreads();
+    for (int lc = threadIdx.x; lc < ncell; lc += blockDim.x) {
+      int64_t c = (int64_t)ti.k0 - 1 + lc;
+      if (g.periodic) c = (c + nx) % nx;
+      else if (c < 0 || c >= nx) continue;
+      for (int row = 0; row < 6; ++row) {
+        const double x = sM[row * ncell + lc];
+        if (x != 0.0) atomicAdd(&M[row * nx + c], x);
+      }
+      if (sQ[lc] != 0ull) {
+        if (sizeof(R) == 4) atomicAdd(&v.dcharge[c], sQ[lc]);
+        else atomicAdd(reinterpret_cast<double *>(&v.dcharge[c]), __longlong_as_double((long long)sQ[lc]));
       }
     }
   }
@@ -561,8 +597,12 @@ void launch_diag(const View &v, int gap, int64_t nx, int64_t P, cudaStream_t st)
   GapDev gh;
   cudaMemcpyAsync(&gh, &v.gaps[gap], sizeof(GapDev), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  if (v.precision == GAP_FP32_STATE) k_moments<float><<<gh.n_tiles, 256, 0, st>>>(v, gap);
-  else k_moments<double><<<gh.n_tiles, 256, 0, st>>>(v, gap);
+  // a tile's cells summed in shared memory while they fit without opting
+  // into more than 48 KB (7 sums of 8 bytes per cell)
+  const size_t msm = (size_t)(v.tile + 4) * 7 * sizeof(double);
+  const int priv = msm <= 48 * 1024 ? 1 : 0;
+  if (v.precision == GAP_FP32_STATE) k_moments<float><<<gh.n_tiles, 256, priv ? msm : 0, st>>>(v, gap, priv);
+  else k_moments<double><<<gh.n_tiles, 256, priv ? msm : 0, st>>>(v, gap, priv);
   launch_photon_moments(v, gap, st);
   if (v.pr_any) k_proton_charge<<<148 * 4, 256, 0, st>>>(v, gap, v.dcharge);  // for the Gauss residual
   k_reduce<<<1, 1024, 0, st>>>(v, gap);
